@@ -1,0 +1,193 @@
+/*
+ * lf.h -- C ABI of the GB300-native semantic light-field EM.
+ *
+ * Method: Kaveti, Katt & Singh, "Removing Dynamic Objects for Static Scene
+ * Reconstruction using Light Fields" (arXiv 2003.11076).  For every pixel of
+ * the reference view of a rectified linear camera array the library
+ *   1. rasterises the piecewise-planar disparity prior of the Delaunay
+ *      triangulation of sparse support points (Sec. III-C "Disparity Prior"),
+ *   2. runs the per-pixel hard EM (Sec. III-B schedule): an M-step that sweeps
+ *      D disparity candidates and keeps the arg-max of the photometric-variance
+ *      likelihood plus prior (Sec. III-C, M-step energy), and an E-step that
+ *      enumerates all 2^K static/dynamic label vectors of the pixel's K rays
+ *      (Sec. III-D "Segmentation update", Eq. e-step general),
+ *   3. reports per-ray posteriors of the final labels and synthesises the
+ *      refocused static image (Eq. 2, Sec. III-E "Refocused Image Synthesis").
+ *
+ * Conventions shared by every entry point:
+ *   - No C++ exception crosses this ABI.  Every call returns an lf_status;
+ *     lf_last_error() gives a one-line message for the calling thread.
+ *   - Layouts are dense, row-major, C order.  "K" is the number of cameras,
+ *     H x W the image size, C the number of image channels (1 or 3).
+ *   - Geometry: camera k sits at signed position b_k on the line, relative to
+ *     the reference camera (b_ref = 0).  A reference pixel (u, v) at disparity
+ *     d sees camera k at column u - d * b_k of row v (Eq. 1 for a rectified
+ *     linear array).  Out-of-image columns clamp to the border; fractional
+ *     columns interpolate linearly (Sec. III-F: non-integral disparities).
+ *   - Candidate disparities: d_j = d_min + j * (d_max - d_min) / (D - 1),
+ *     j = 0..D-1 (D == 1: d_min).
+ *   - Device pointers are read and written on the context's stream
+ *     (lf_set_stream); the caller keeps them alive until that stream has
+ *     passed the work.  Host pointers are copied within the call.
+ *   - All compute runs in the library's sm_103a CUDA kernels; there is no CPU
+ *     fallback.  Without a usable GPU every compute call returns LF_ECUDA.
+ */
+#ifndef LF_H
+#define LF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lf_ctx lf_ctx; /* opaque; created by lf_create, owned by the library */
+
+typedef enum lf_status {
+    LF_OK = 0,
+    LF_EINVAL = 1,   /* an argument is out of range or inconsistent */
+    LF_ENOMEM = 2,   /* a device or host allocation failed */
+    LF_ECUDA = 3,    /* a CUDA call failed (message in lf_last_error) */
+    LF_ESTATE = 4,   /* call order violated (e.g. run before inputs) */
+    LF_ETIMEOUT = 5  /* a bounded device wait expired; results are invalid */
+} lf_status;
+
+typedef enum lf_dtype {
+    LF_U8 = 0,       /* uint8, value / 255 is the intensity in [0, 1] */
+    LF_F32 = 1       /* float32 intensity in [0, 1] */
+} lf_dtype;
+
+typedef enum lf_precision {
+    LF_PREC_F32 = 0, /* staged descriptors and sampled rays in float32 */
+    LF_PREC_F16 = 1, /* ... stored in float16, accumulation in float32 */
+    LF_PREC_BF16 = 2 /* ... stored in bfloat16, accumulation in float32 */
+} lf_precision;
+
+/*
+ * Model and run parameters.  The paper names beta, gamma, sigma and the
+ * initial threshold (Sec. III-C energy, Sec. III-F) but prints a value only
+ * for the threshold (0.7); the defaults of lf_default_params are
+ * beta = 200, gamma = 0.1, sigma = 2, seg_threshold = 0.7, eps = 1e-4,
+ * mstep_seg_term = 1, median = 0, precision = LF_PREC_F32, early_exit = 1.
+ */
+typedef struct lf_params {
+    float beta;          /* weight of the static rays' descriptor variance */
+    float gamma;         /* uniform floor of the disparity prior */
+    float sigma;         /* width of the prior's sampled Gaussian (disparity units) */
+    float seg_threshold; /* first M-step: a ray is dynamic iff P(dynamic) >= this */
+    float eps;           /* floor inside log P and log(1 - P) */
+    int mstep_seg_term;  /* 1: the M-step maximises the complete-data objective
+                            (likelihood + disparity prior + segmentation prior);
+                            0: likelihood + disparity prior only (Eq. mstep) */
+    int median;          /* 1: 3x3 median on the refocused image (Sec. III-E) */
+    int precision;       /* lf_precision */
+    int early_exit;      /* 1: a warp stops iterating once all of its pixels
+                            reached an EM fixed point (results are identical) */
+} lf_params;
+
+/* Statistics of the last completed lf_run_em (valid after the stream synced). */
+typedef struct lf_stats {
+    uint64_t nominal_ray_samples;  /* H * W * K * D * iters */
+    uint64_t executed_ray_samples; /* pixel-sweeps actually run x K x D */
+    int halo_left, halo_right;     /* staged column halo, pixels */
+    int tile_rows, tile_cols;      /* sweep tile shape */
+    int kernels_launched;          /* kernels one lf_run_em enqueues */
+} lf_stats;
+
+/* Fill *p with the documented defaults. */
+void lf_default_params(lf_params *p);
+
+/*
+ * Create a context for one camera array and image size (Sec. III-A problem
+ * setup).  baselines: [n_cams] host floats, exactly one of them 0 (the
+ * reference camera; Sec. III-F takes the leftmost, any works).  p may be NULL
+ * for the defaults; it is copied.  Allocates the context's device buffers on
+ * the current CUDA device.
+ * Errors: LF_EINVAL if n_cams < 1 or > 12, no baseline is 0, H or W < 3,
+ * D < 1 or > 1024, d_max < d_min, a parameter is non-finite, or the
+ * disparity halo does not fit the kernel's staging limit; LF_ENOMEM; LF_ECUDA.
+ * On error *out is NULL.
+ */
+lf_status lf_create(lf_ctx **out, int n_cams, const float *baselines, int H, int W,
+                    float d_min, float d_max, int D, const lf_params *p);
+
+/* Use `stream` (a cudaStream_t; NULL = the legacy default stream) for every
+ * later call on this context. */
+lf_status lf_set_stream(lf_ctx *ctx, void *stream);
+
+/*
+ * Hand one frame to the context (Fig. 1 inputs: the K frames, the per-view
+ * segmentation probabilities and the sparse support points).
+ *   images       [K][H][W][C], dtype LF_U8 or LF_F32, C = 1 (gray) or 3 (RGB;
+ *                luminance Y = 0.299 R + 0.587 G + 0.114 B drives the
+ *                likelihood, the refocus is per channel).
+ *   seg_prior    [K][H][W] float32, P(pixel is dynamic) in [0, 1]
+ *                (Sec. III-B; the Bodypix convention of Sec. III-F).
+ *   sparse_points [M][3] float32 HOST memory, (u, v, d) in reference-view
+ *                pixel units; triangulated on the host (Delaunay), repeated
+ *                (u, v) keep their first occurrence; fewer than 3
+ *                non-collinear points give a uniform prior everywhere.
+ *   on_device    1: images and seg_prior are device pointers (borrowed until
+ *                the stream passes the next lf_run_em); 0: host pointers
+ *                (copied now, synchronously with respect to the caller).
+ * Errors: LF_EINVAL (NULL pointer, C not 1 or 3, bad dtype, M < 0,
+ * non-finite point), LF_ECUDA.
+ */
+lf_status lf_set_inputs(lf_ctx *ctx, const void *images, int C, int dtype,
+                        const float *seg_prior, const float *sparse_points, int M,
+                        int on_device);
+
+/*
+ * Run the whole hot path on the last inputs: prior raster, `iters` EM
+ * iterations (M-step first, Sec. III-B), posteriors, refocus (Eq. 2) and the
+ * optional median.  Outputs (any may be NULL except disparity_idx):
+ *   disparity_idx [H][W] int32   arg-max candidate index j of the last M-step
+ *   disparity     [H][W] float32 d_j
+ *   posteriors    [K][H][W] float32, marginal P(ray k static) under
+ *                 q(S) proportional to exp J(d_T, S) over all 2^K label vectors
+ *   labels        [H][W] uint16, bit k set = ray k static in the final E-step
+ *   refocused     [H][W][C] float32 in [0, 1]; pixels with no static ray keep
+ *                 the reference image
+ * outputs_on_device: 1 = device pointers (the call returns once the work is
+ * enqueued; lf_synchronize waits and reports device errors); 0 = host pointers
+ * (the call waits for the results).
+ * Errors: LF_ESTATE before lf_set_inputs, LF_EINVAL (iters < 1 or > 255, NULL
+ * disparity_idx), LF_ETIMEOUT (a bounded device wait expired), LF_ECUDA.
+ */
+lf_status lf_run_em(lf_ctx *ctx, int iters, int32_t *disparity_idx, float *disparity,
+                    float *posteriors, uint16_t *labels, float *refocused,
+                    int outputs_on_device);
+
+/* Wait for the context's stream and report device-side errors of the last
+ * run (LF_ETIMEOUT if a bounded wait expired). */
+lf_status lf_synchronize(lf_ctx *ctx);
+
+/* Copy the rasterised prior of the last run (Sec. III-C "Disparity Prior"):
+ * mu [H][W] float32, the interpolated disparity, NaN outside the
+ * triangulation.  on_device as for lf_run_em outputs. */
+lf_status lf_get_prior(lf_ctx *ctx, float *mu, int on_device);
+
+/* Statistics of the last run; synchronises the stream. */
+lf_status lf_get_stats(lf_ctx *ctx, lf_stats *out);
+
+/* One-line description of the calling thread's last error ("" if none).
+ * ctx may be NULL.  The string stays valid until the thread's next call. */
+const char *lf_last_error(const lf_ctx *ctx);
+
+/* Free the context and its device buffers (waits for its stream). */
+void lf_destroy(lf_ctx *ctx);
+
+/*
+ * Host utility (no GPU needed): Delaunay triangulation of the (u, v) of
+ * `points` ([M][3] float32, (u, v, d)) as used for the prior (Sec. III-C,
+ * triangulation of the support points, as in ELAS).  Writes up to max_tris
+ * counter-clockwise index triples into tris ([max_tris][3] int32, indices into
+ * `points`) and returns the number of triangles, or -1 on invalid arguments.
+ */
+int lf_triangulate(const float *points, int M, int32_t *tris, int max_tris);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LF_H */

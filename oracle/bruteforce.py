@@ -1,0 +1,145 @@
+"""Brute-force restatement of the per-pixel EM for tiny inputs.
+
+TEST INFRASTRUCTURE ONLY (imported by the CPU test-suite).  It pins the C
+oracle from outside: every quantity is computed by a different route than the
+C core uses --
+
+* descriptors: Sobel through ``scipy.ndimage.correlate`` (mode 'nearest');
+* ray sampling: ``numpy.interp``, whose end-point clamping is the
+  clamp-to-edge reading of out-of-image rays;
+* variance of the static rays: the pairwise form
+  ``Var = (1 / n^2) * sum_{i<j} |f_i - f_j|^2`` instead of mean-then-deviations;
+* disparity prior: ``logaddexp(log gamma, -(d - mu)^2 / (2 sigma^2))``;
+* the EM: the full table J[d, S] over every candidate and every label vector
+  is formed first; the M-step is an arg-max down a column, the E-step an
+  arg-max along a row (Sec. III-B schedule, Eqs. e-step / m-step).
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+from scipy import ndimage
+
+SOBEL_X = np.array([[-1.0, 0.0, 1.0], [-2.0, 0.0, 2.0], [-1.0, 0.0, 1.0]])
+
+
+def descriptors(images: np.ndarray) -> np.ndarray:
+    """[K,3,H,W] = [Y, Sobel-x/8, Sobel-y/8]."""
+    imgs = np.asarray(images)
+    x = imgs.astype(np.float64) / (255.0 if imgs.dtype == np.uint8 else 1.0)
+    if x.ndim == 4:
+        Y = x @ np.array([0.299, 0.587, 0.114])
+    else:
+        Y = x
+    out = np.zeros((Y.shape[0], 3) + Y.shape[1:])
+    for k in range(Y.shape[0]):
+        out[k, 0] = Y[k]
+        out[k, 1] = ndimage.correlate(Y[k], SOBEL_X, mode="nearest") / 8.0
+        out[k, 2] = ndimage.correlate(Y[k], SOBEL_X.T, mode="nearest") / 8.0
+    return out
+
+
+def _interp(row: np.ndarray, x: float) -> float:
+    return float(np.interp(x, np.arange(row.shape[0], dtype=np.float64), row))
+
+
+def pairwise_variance(f: np.ndarray) -> float:
+    n = f.shape[0]
+    if n <= 1:
+        return 0.0
+    acc = 0.0
+    for i in range(n):
+        for j in range(i + 1, n):
+            acc += float(np.sum((f[i] - f[j]) ** 2))
+    return acc / (n * n)
+
+
+def log_prior(d, mu, inside, gamma, sigma):
+    if not inside:
+        return 0.0
+    return float(np.logaddexp(np.log(gamma), -((d - mu) ** 2) / (2.0 * sigma * sigma)))
+
+
+def em_pixel_table(feat, ls, ld, images, baselines, u, v, dvals, mu, inside, p):
+    """J[d_j, S] for every candidate and every label vector, plus the
+    per-candidate initial label vector S(d_j) and the sampled images."""
+    K = feat.shape[0]
+    D = len(dvals)
+    nS = 1 << K
+    J = np.zeros((D, nS))
+    S_init = np.zeros(D, dtype=np.int64)
+    thr = p.seg_threshold
+    for j, d in enumerate(dvals):
+        xs = [u - d * float(baselines[k]) for k in range(K)]
+        f = np.array([[_interp(feat[k, c, v], xs[k]) for c in range(3)] for k in range(K)])
+        sls = np.array([_interp(ls[k, v], xs[k]) for k in range(K)])
+        sld = np.array([_interp(ld[k, v], xs[k]) for k in range(K)])
+        lp = log_prior(d, mu, inside, p.gamma, p.sigma)
+        # initial threshold: static iff the normalised dynamic probability of
+        # the two interpolated log-priors is below thr
+        pd = np.exp(sld) / (np.exp(sld) + np.exp(sls))
+        S_init[j] = sum(1 << k for k in range(K) if pd[k] < thr)
+        for S in range(nS):
+            members = [k for k in range(K) if S >> k & 1]
+            var = pairwise_variance(f[members]) if members else 0.0
+            seg = sum(sls[k] if S >> k & 1 else sld[k] for k in range(K))
+            J[j, S] = -p.beta * var + lp + seg
+    return J, S_init
+
+
+def run(images, seg_prior, baselines, mu, inside, d_min, d_max, D, iters, p):
+    """Full EM on every pixel of a tiny frame.  Returns dict like the oracle's
+    (d_idx, labels, post, refocus) plus ``joint_max`` = max over (d, S)."""
+    imgs = np.asarray(images)
+    K, H, W = imgs.shape[:3]
+    feat = descriptors(imgs)
+    P = np.asarray(seg_prior, np.float64)
+    ls = np.log(np.maximum(1.0 - P, p.eps))
+    ld = np.log(np.maximum(P, p.eps))
+    dvals = [float(d_min)] if D == 1 else [float(d_min) + j * ((float(d_max) - float(d_min)) / (D - 1))
+                                            for j in range(D)]
+    x = imgs.astype(np.float64) / (255.0 if imgs.dtype == np.uint8 else 1.0)
+    if x.ndim == 3:
+        x = x[..., None]
+    C = x.shape[3]
+    ref = int(np.flatnonzero(np.asarray(baselines) == 0)[0])
+    out = {k: None for k in ("d_idx", "labels", "post", "refocus", "J_final", "joint_max")}
+    d_idx = np.zeros((H, W), np.int64)
+    labels = np.zeros((H, W), np.int64)
+    post = np.zeros((K, H, W))
+    refocus = np.zeros((H, W, C))
+    J_final = np.zeros((H, W))
+    joint = np.zeros((H, W))
+    for v in range(H):
+        for u in range(W):
+            J, S_init = em_pixel_table(feat, ls, ld, imgs, baselines, u, v, dvals, mu[v, u], inside[v, u], p)
+            if not p.mstep_seg_term:
+                raise NotImplementedError
+            S = None
+            for t in range(iters):
+                col = J[np.arange(len(dvals)), S_init] if t == 0 else J[:, S]
+                j = int(np.argmax(col))          # first maximum = lowest index
+                S = int(np.argmax(J[j]))          # first maximum = smallest mask
+            d_idx[v, u], labels[v, u] = j, S
+            J_final[v, u] = J[j, S]
+            joint[v, u] = J.max()
+            row = J[j]
+            q = np.exp(row - row.max())
+            q /= q.sum()
+            for k in range(K):
+                post[k, v, u] = sum(q[s] for s in range(1 << K) if s >> k & 1)
+            members = [k for k in range(K) if S >> k & 1]
+            if not members:
+                refocus[v, u] = x[ref, v, u]
+            else:
+                for c in range(C):
+                    refocus[v, u, c] = np.mean([_interp(x[k, v, :, c], u - dvals[j] * float(baselines[k]))
+                                                for k in members])
+    out.update(d_idx=d_idx, labels=labels, post=post, refocus=refocus[..., 0] if C == 1 else refocus,
+               J_final=J_final, joint_max=joint)
+    return out
+
+
+def all_label_vectors(K):
+    return list(itertools.product((0, 1), repeat=K))
