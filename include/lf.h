@@ -92,6 +92,8 @@ typedef struct lf_stats {
     int halo_left, halo_right;     /* staged column halo, pixels */
     int tile_rows, tile_cols;      /* sweep tile shape */
     int kernels_launched;          /* kernels one lf_run_em enqueues */
+    float ms_prior, ms_sweep, ms_refocus, ms_median; /* device times of the last
+                                      run's kernels (lf_set_timing on), else 0 */
 } lf_stats;
 
 /* Fill *p with the documented defaults. */
@@ -166,6 +168,11 @@ lf_status lf_synchronize(lf_ctx *ctx);
  * mu [H][W] float32, the interpolated disparity, NaN outside the
  * triangulation.  on_device as for lf_run_em outputs. */
 lf_status lf_get_prior(lf_ctx *ctx, float *mu, int on_device);
+
+/* 1: record CUDA events on the context's stream around every kernel that
+ * lf_run_em enqueues, so that lf_get_stats reports their device times; 0 (the
+ * default): no events. */
+lf_status lf_set_timing(lf_ctx *ctx, int enable);
 
 /* Statistics of the last run; synchronises the stream. */
 lf_status lf_get_stats(lf_ctx *ctx, lf_stats *out);

@@ -1,0 +1,524 @@
+// Fused per-pixel EM sweep (Sec. III-B schedule; M-step Sec. III-C; E-step
+// Sec. III-D; posteriors of the final labels), one CTA per tile of
+// TR x TW reference pixels, one thread per pixel.
+//
+// Phases of one CTA:
+//   1. TMA (cp.async.bulk.tensor) stages, for all K cameras at once, the raw
+//      image rows v0-1 .. v0+TR (Sobel needs one row above and below) and the
+//      P(dynamic) rows v0 .. v0+TR-1, over the tile's columns plus the
+//      disparity halo, completing on one mbarrier (bounded wait).
+//   2. Luminance, Sobel-x/8, Sobel-y/8, log(1-P) and log(P) per staged texel
+//      are computed into shared memory with the image border replicated
+//      (Sec. III-C descriptors).  Nothing of this is written to HBM.
+//   3. Each thread runs the whole EM for its pixel.  The D x K cost volume is
+//      never materialised: the M-step keeps, per camera, the two texels that
+//      bracket the current sample in registers and reloads them only when the
+//      integer part of u - d_j * b_k changes (the change mask is the same for
+//      every pixel, so the reload branch is warp-uniform).  Each ray sample is
+//      a linear interpolation (Sec. III-F non-integral disparities) and an
+//      accumulation of the shifted sums of the static rays' descriptors.
+//   4. The E-step enumerates all 2^K label vectors in increasing mask order
+//      as a depth-first subset tree (each subset's sums built from its
+//      parent, no subtraction), keeping the first maximum.
+//   5. Posteriors: the same enumeration at the final disparity gives the
+//      per-ray marginals of q(S) ~ exp J(d_T, S).
+//
+// Numerics: descriptors are shifted by the reference ray's descriptor before
+// summation, so the variance sum(|g|^2) - |sum g|^2 / n is formed from small
+// numbers; all accumulation is float32.
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+
+#include "lf_internal.h"
+
+namespace lf {
+namespace dev {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// Spin on the mbarrier phase for at most limit_ns; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase,
+                                                  unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, phase)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, phase)) {
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__host__ __device__ inline size_t align_up(size_t x, size_t n) { return (x + n - 1) / n * n; }
+
+// Shared-memory carve-up, identical on host (size) and device (offsets).
+struct SmemLayout {
+  size_t raw_img, raw_p, luma, feat, wtab, otab, chg, dval, rcp, bar, total;
+};
+
+__host__ __device__ inline SmemLayout sweep_layout(int K, const SweepArgs& a) {
+  SmemLayout L{};
+  size_t o = 0;
+  L.raw_img = o;
+  o = align_up(o + static_cast<size_t>(K) * (a.TR + 2) * a.RW * a.bpp, 128);
+  L.raw_p = o;
+  o = align_up(o + static_cast<size_t>(K) * a.TR * a.RW * 4, 128);
+  L.luma = o;
+  o = align_up(o + static_cast<size_t>(K) * (a.TR + 2) * a.RW * 4, 16);
+  L.feat = o;
+  o = align_up(o + static_cast<size_t>(K) * a.TR * 5 * a.SWp * 4, 16);
+  L.wtab = o;
+  o = align_up(o + static_cast<size_t>(a.D) * a.KP * 4, 16);
+  L.otab = o;
+  o = align_up(o + static_cast<size_t>(a.D) * a.KP * 4, 16);
+  L.chg = o;
+  o = align_up(o + static_cast<size_t>(a.D) * 4, 16);
+  L.dval = o;
+  o = align_up(o + static_cast<size_t>(a.D) * 4, 16);
+  L.rcp = o;
+  o = align_up(o + 16 * 4, 16);
+  L.bar = o;
+  o = align_up(o + 8, 16);
+  L.total = o;
+  return L;
+}
+
+__device__ __forceinline__ int floor16(int x) { return x >= 0 ? (x & ~15) : -((-x + 15) & ~15); }
+
+// View of one CTA's staged descriptor maps for one thread's pixel.
+struct Staged {
+  const float* F;       // camera 0, this thread's tile row, map 0
+  int cam_stride;       // floats between cameras
+  int SWp;              // floats between maps
+  int cbase;            // staged column of this pixel (offset 0)
+};
+
+// ---------------------------------------------------------------- M-step
+// Arg-max over the D candidates of J(d_j, S) for one pixel (lowest j wins
+// ties).  INIT: first iteration, where each ray's label is thresholded at the
+// ray's own sample (ld - ls < log(thr / (1 - thr)) means static).
+template <int K, bool INIT>
+__device__ __forceinline__ int m_step(const SweepArgs& a, const Staged& st, const float* s_w,
+                                      const int* s_o, const unsigned* s_chg, const float* s_d,
+                                      const float* s_rcp, float cy, float cx, float cz, float mu,
+                                      bool inside, unsigned S) {
+  float y0[K], dy[K], x0[K], dx[K], z0[K], dz[K], l0[K], dl[K], m0[K], dm[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    y0[k] = dy[k] = x0[k] = dx[k] = z0[k] = dz[k] = l0[k] = dl[k] = m0[k] = dm[k] = 0.f;
+  }
+  const int SWp = st.SWp;
+  const float rn_fixed = s_rcp[__popc(S)];
+  float best = -INFINITY;
+  int jb = 0;
+  for (int j = 0; j < a.D; ++j) {
+    const unsigned ch = s_chg[j];
+    float w[K];
+    {
+      const float4* w4 = reinterpret_cast<const float4*>(s_w + j * a.KP);
+#pragma unroll
+      for (int q = 0; q < (K + 3) / 4; ++q) {
+        const float4 t = w4[q];
+        if (4 * q + 0 < K) w[(4 * q + 0) % K] = t.x;
+        if (4 * q + 1 < K) w[(4 * q + 1) % K] = t.y;
+        if (4 * q + 2 < K) w[(4 * q + 2) % K] = t.z;
+        if (4 * q + 3 < K) w[(4 * q + 3) % K] = t.w;
+      }
+    }
+    float sy = 0.f, sx = 0.f, sz = 0.f, q = 0.f, seg = 0.f;
+    int n = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (ch & (1u << k)) {  // same for every pixel: warp-uniform branch
+        const int c = st.cbase + s_o[j * a.KP + k];
+        const float* Fk = st.F + k * st.cam_stride;
+        const float Y0 = Fk[c], Y1 = Fk[c + 1];
+        const float X0 = Fk[SWp + c], X1 = Fk[SWp + c + 1];
+        const float Z0 = Fk[2 * SWp + c], Z1 = Fk[2 * SWp + c + 1];
+        if (INIT) {
+          y0[k] = Y0 - cy; dy[k] = Y1 - Y0;
+          x0[k] = X0 - cx; dx[k] = X1 - X0;
+          z0[k] = Z0 - cz; dz[k] = Z1 - Z0;
+          l0[k] = Fk[3 * SWp + c]; dl[k] = Fk[3 * SWp + c + 1] - l0[k];
+          m0[k] = Fk[4 * SWp + c]; dm[k] = Fk[4 * SWp + c + 1] - m0[k];
+        } else {
+          const bool stat = (S >> k) & 1u;
+          const float s = stat ? 1.f : 0.f;
+          y0[k] = s * (Y0 - cy); dy[k] = s * (Y1 - Y0);
+          x0[k] = s * (X0 - cx); dx[k] = s * (X1 - X0);
+          z0[k] = s * (Z0 - cz); dz[k] = s * (Z1 - Z0);
+          const float* Lk = Fk + (stat ? 3 : 4) * SWp;
+          l0[k] = Lk[c]; dl[k] = Lk[c + 1] - l0[k];
+        }
+      }
+      if (INIT) {
+        const float ls = fmaf(w[k], dl[k], l0[k]);
+        const float ld = fmaf(w[k], dm[k], m0[k]);
+        const bool stat = (ld - ls) < a.log_thr;
+        const float gy = stat ? fmaf(w[k], dy[k], y0[k]) : 0.f;
+        const float gx = stat ? fmaf(w[k], dx[k], x0[k]) : 0.f;
+        const float gz = stat ? fmaf(w[k], dz[k], z0[k]) : 0.f;
+        seg += stat ? ls : ld;
+        n += stat ? 1 : 0;
+        sy += gy; sx += gx; sz += gz;
+        q = fmaf(gy, gy, q); q = fmaf(gx, gx, q); q = fmaf(gz, gz, q);
+      } else {
+        const float gy = fmaf(w[k], dy[k], y0[k]);
+        const float gx = fmaf(w[k], dx[k], x0[k]);
+        const float gz = fmaf(w[k], dz[k], z0[k]);
+        seg += fmaf(w[k], dl[k], l0[k]);
+        sy += gy; sx += gx; sz += gz;
+        q = fmaf(gy, gy, q); q = fmaf(gx, gx, q); q = fmaf(gz, gz, q);
+      }
+    }
+    const float rn = INIT ? s_rcp[n] : rn_fixed;
+    const float ss = fmaf(sz, sz, fmaf(sx, sx, sy * sy));
+    const float var = fmaf(-ss, rn, q) * rn;
+    float J = a.mseg ? seg : 0.f;
+    if (inside) {
+      const float t = s_d[j] - mu;
+      J += __logf(a.gamma + __expf(-(t * t) * a.inv2s2));
+    }
+    J = fmaf(-a.beta, var, J);
+    if (J > best) { best = J; jb = j; }
+  }
+  return jb;
+}
+
+// ---------------------------------------------------------------- E-step
+struct Rays {
+  // per camera: shifted descriptors, |g|^2, log p(static) - log p(dynamic)
+  float gy[kMaxCams], gx[kMaxCams], gz[kMaxCams], qk[kMaxCams], ak[kMaxCams];
+  float base;  // sum_k log p(dynamic)
+};
+
+template <int K>
+__device__ __forceinline__ void sample_rays(const SweepArgs& a, const Staged& st, const float* s_w,
+                                            const int* s_o, int jt, float cy, float cx, float cz,
+                                            Rays& r) {
+  const int SWp = st.SWp;
+  r.base = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float w = s_w[jt * a.KP + k];
+    const int c = st.cbase + s_o[jt * a.KP + k];
+    const float* Fk = st.F + k * st.cam_stride;
+    const float Y0 = Fk[c], Y1 = Fk[c + 1];
+    const float X0 = Fk[SWp + c], X1 = Fk[SWp + c + 1];
+    const float Z0 = Fk[2 * SWp + c], Z1 = Fk[2 * SWp + c + 1];
+    const float S0 = Fk[3 * SWp + c], S1 = Fk[3 * SWp + c + 1];
+    const float D0 = Fk[4 * SWp + c], D1 = Fk[4 * SWp + c + 1];
+    const float gy = fmaf(w, Y1 - Y0, Y0 - cy);
+    const float gx = fmaf(w, X1 - X0, X0 - cx);
+    const float gz = fmaf(w, Z1 - Z0, Z0 - cz);
+    const float ls = fmaf(w, S1 - S0, S0);
+    const float ld = fmaf(w, D1 - D0, D0);
+    r.gy[k] = gy; r.gx[k] = gx; r.gz[k] = gz;
+    r.qk[k] = fmaf(gz, gz, fmaf(gx, gx, gy * gy));
+    r.ak[k] = ls - ld;
+    r.base += ld;
+  }
+}
+
+struct Acc {
+  float sy, sx, sz, q, sa;
+};
+
+// Leaf evaluation shared by the arg-max and the posterior passes so that both
+// see bit-identical objectives.
+__device__ __forceinline__ float leaf_objective(const Acc& acc, float rn, float base, float beta) {
+  const float ss = fmaf(acc.sz, acc.sz, fmaf(acc.sx, acc.sx, acc.sy * acc.sy));
+  const float var = fmaf(-ss, rn, acc.q) * rn;
+  return fmaf(-beta, var, base + acc.sa);
+}
+
+template <int L>
+struct EnumState {
+  float best;        // arg-max pass: best objective so far
+  unsigned bmask;    // arg-max pass: its mask
+  float emax;        // posterior pass: the maximum objective
+  float Z;           // posterior pass: partition sum of this high block
+  float pl[L > 0 ? L : 1];  // posterior pass: mass on each low camera
+};
+
+// Depth-first over cameras k, k-1, ..., 0 of the low block; the "without
+// camera k" subtree first so leaves come in increasing mask order.
+// MODE 0: arg-max (first maximum kept); MODE 1: accumulate exp(J - Jmax).
+template <int MODE, int L, int k, int N, unsigned MASK>
+__device__ __forceinline__ void enum_low(const Rays& r, const Acc& acc, const float (&rnv)[L + 1],
+                                         unsigned high, float beta, EnumState<L>& s) {
+  if constexpr (k < 0) {
+    const float E = leaf_objective(acc, rnv[N], r.base, beta);
+    if constexpr (MODE == 0) {
+      if (E > s.best) { s.best = E; s.bmask = high | MASK; }
+    } else {
+      const float e = expf(E - s.emax);
+      s.Z += e;
+#pragma unroll
+      for (int i = 0; i < L; ++i)
+        if (MASK >> i & 1u) s.pl[i] += e;
+    }
+  } else {
+    enum_low<MODE, L, k - 1, N, MASK>(r, acc, rnv, high, beta, s);
+    const Acc a2{acc.sy + r.gy[k], acc.sx + r.gx[k], acc.sz + r.gz[k], acc.q + r.qk[k], acc.sa + r.ak[k]};
+    enum_low<MODE, L, k - 1, N + 1, MASK | (1u << k)>(r, a2, rnv, high, beta, s);
+  }
+}
+
+// Full enumeration: cameras >= L form a runtime loop over "high" masks (sums
+// built from scratch), cameras < L the unrolled subset tree.
+template <int MODE, int K>
+__device__ __forceinline__ void enumerate(const Rays& r, const float* s_rcp, float beta, float emax,
+                                          unsigned& bmask, float& best, float* post) {
+  constexpr int L = K < 6 ? K : 6;
+  constexpr int NH = K - L;
+  float ph[NH > 0 ? NH : 1];
+#pragma unroll
+  for (int i = 0; i < (NH > 0 ? NH : 1); ++i) ph[i] = 0.f;
+  EnumState<L> s;
+  s.best = -INFINITY;
+  s.bmask = 0;
+  s.emax = emax;
+#pragma unroll
+  for (int i = 0; i < (L > 0 ? L : 1); ++i) s.pl[i] = 0.f;
+  float Ztot = 0.f;
+  for (unsigned h = 0; h < (1u << NH); ++h) {
+    Acc acc{0.f, 0.f, 0.f, 0.f, 0.f};
+    int nh = 0;
+#pragma unroll
+    for (int i = 0; i < NH; ++i) {
+      if (h >> i & 1u) {
+        acc.sy += r.gy[L + i]; acc.sx += r.gx[L + i]; acc.sz += r.gz[L + i];
+        acc.q += r.qk[L + i]; acc.sa += r.ak[L + i];
+        ++nh;
+      }
+    }
+    float rnv[L + 1];
+#pragma unroll
+    for (int i = 0; i <= L; ++i) rnv[i] = s_rcp[nh + i];
+    s.Z = 0.f;
+    enum_low<MODE, L, L - 1, 0, 0u>(r, acc, rnv, h << L, beta, s);
+    if constexpr (MODE == 1) {
+      Ztot += s.Z;
+#pragma unroll
+      for (int i = 0; i < NH; ++i)
+        if (h >> i & 1u) ph[i] += s.Z;
+    }
+  }
+  if constexpr (MODE == 0) {
+    bmask = s.bmask;
+    best = s.best;
+  } else {
+    const float inv = 1.f / Ztot;
+#pragma unroll
+    for (int i = 0; i < L; ++i) post[i] = s.pl[i] * inv;
+#pragma unroll
+    for (int i = 0; i < NH; ++i) post[L + i] = ph[i] * inv;
+  }
+}
+
+// ---------------------------------------------------------------- kernel
+template <int K>
+__global__ void __launch_bounds__(256) em_sweep_kernel(const __grid_constant__ CUtensorMap img_map,
+                                                       const __grid_constant__ CUtensorMap p_map,
+                                                       const SweepArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const SmemLayout Ly = sweep_layout(K, a);
+  uint8_t* s_img = smem + Ly.raw_img;
+  const float* s_p = reinterpret_cast<const float*>(smem + Ly.raw_p);
+  float* s_luma = reinterpret_cast<float*>(smem + Ly.luma);
+  float* s_feat = reinterpret_cast<float*>(smem + Ly.feat);
+  float* s_w = reinterpret_cast<float*>(smem + Ly.wtab);
+  int* s_o = reinterpret_cast<int*>(smem + Ly.otab);
+  unsigned* s_chg = reinterpret_cast<unsigned*>(smem + Ly.chg);
+  float* s_d = reinterpret_cast<float*>(smem + Ly.dval);
+  float* s_rcp = reinterpret_cast<float*>(smem + Ly.rcp);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Ly.bar);
+
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int u0 = blockIdx.x * a.TW, v0 = blockIdx.y * a.TR;
+  const int cs = floor16(u0 - a.L - 1);  // first staged raw column (16-px aligned)
+  const int W = a.W, H = a.H, RW = a.RW, LR = a.TR + 2;
+
+  // ---- 1. stage raw rows with TMA (destinations must be 128-byte aligned)
+  if ((smem_u32(smem) & 127u) != 0u) {
+    if (tid == 0) atomicOr(a.status, kStatusSmemMisaligned);
+    return;
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned bytes = static_cast<unsigned>(K * LR * RW * a.bpp + K * a.TR * RW * 4);
+    mbar_arrive_expect_tx(bar, bytes);
+    tma_load_3d(s_img, &img_map, cs * a.bpp / 8, v0 - 1, 0, bar);
+    tma_load_3d(smem + Ly.raw_p, &p_map, cs / 2, v0, 0, bar);
+  }
+  for (int i = tid; i < a.D * a.KP; i += nthr) {
+    s_w[i] = a.wtab[i];
+    s_o[i] = a.otab[i];
+  }
+  for (int i = tid; i < a.D; i += nthr) {
+    s_chg[i] = a.chg[i];
+    s_d[i] = a.dval[i];
+  }
+  if (tid < 16) s_rcp[tid] = tid >= 2 ? 1.f / static_cast<float>(tid) : 0.f;
+  const bool ok = mbar_wait_bounded(bar, 0, a.timeout_ns);
+  if (__syncthreads_or(!ok)) {
+    if (!ok) {
+      atomicOr(a.status, kStatusTmaTimeout);
+      mbar_wait_bounded(bar, 0, a.timeout_ns);  // let the copy land before the CTA exits
+    }
+    return;
+  }
+
+  // ---- 2. descriptors and log priors (border replicated)
+  for (int i = tid; i < K * LR * RW; i += nthr) {
+    const uint8_t* px = s_img + static_cast<size_t>(i) * a.bpp;
+    float y;
+    if (a.dtype == 0) {
+      y = a.C == 1 ? static_cast<float>(px[0])
+                   : fmaf(0.114f, static_cast<float>(px[2]),
+                          fmaf(0.587f, static_cast<float>(px[1]), 0.299f * static_cast<float>(px[0])));
+      y *= (1.f / 255.f);
+    } else {
+      const float* f = reinterpret_cast<const float*>(px);
+      y = a.C == 1 ? f[0] : fmaf(0.114f, f[2], fmaf(0.587f, f[1], 0.299f * f[0]));
+    }
+    s_luma[i] = y;
+  }
+  __syncthreads();
+  const int cam_stride = a.TR * 5 * a.SWp;
+  for (int i = tid; i < K * a.TR * a.SW; i += nthr) {
+    const int c = i % a.SW;
+    const int r = (i / a.SW) % a.TR;
+    const int k = i / (a.SW * a.TR);
+    const int Xc = min(max(u0 - a.L + c, 0), W - 1);
+    const int V = min(v0 + r, H - 1);
+    const int rm = max(V - 1, 0) - (v0 - 1), r0 = V - (v0 - 1), rp = min(V + 1, H - 1) - (v0 - 1);
+    const int cm = max(Xc - 1, 0) - cs, c0 = Xc - cs, cp = min(Xc + 1, W - 1) - cs;
+    const float* Lk = s_luma + static_cast<size_t>(k) * LR * RW;
+    const float a00 = Lk[rm * RW + cm], a01 = Lk[rm * RW + c0], a02 = Lk[rm * RW + cp];
+    const float a10 = Lk[r0 * RW + cm], a11 = Lk[r0 * RW + c0], a12 = Lk[r0 * RW + cp];
+    const float a20 = Lk[rp * RW + cm], a21 = Lk[rp * RW + c0], a22 = Lk[rp * RW + cp];
+    const float gx = ((a02 + 2.f * a12) + a22) - ((a00 + 2.f * a10) + a20);
+    const float gy = ((a20 + 2.f * a21) + a22) - ((a00 + 2.f * a01) + a02);
+    const float P = s_p[(static_cast<size_t>(k) * a.TR + (V - v0)) * RW + c0];
+    float* F = s_feat + static_cast<size_t>(k) * cam_stride + static_cast<size_t>(r) * 5 * a.SWp;
+    F[c] = a11;
+    F[a.SWp + c] = gx * 0.125f;
+    F[2 * a.SWp + c] = gy * 0.125f;
+    F[3 * a.SWp + c] = logf(fmaxf(1.f - P, a.eps));
+    F[4 * a.SWp + c] = logf(fmaxf(P, a.eps));
+  }
+  __syncthreads();
+
+  // ---- 3-5. per-pixel EM
+  const int r = tid / a.TW, tx = tid % a.TW;
+  const int u = u0 + tx, v = v0 + r;
+  const bool valid = (u < W) && (v < H);
+  const float mu = a.mu[static_cast<size_t>(min(v, H - 1)) * W + min(u, W - 1)];
+  const bool inside = !isnan(mu);
+  Staged st;
+  st.F = s_feat + static_cast<size_t>(r) * 5 * a.SWp;
+  st.cam_stride = cam_stride;
+  st.SWp = a.SWp;
+  st.cbase = tx + a.L;
+  const float* Fr = st.F + a.ref * cam_stride;
+  const float cy = Fr[st.cbase], cx = Fr[a.SWp + st.cbase], cz = Fr[2 * a.SWp + st.cbase];
+
+  Rays rays;
+  int jb = m_step<K, true>(a, st, s_w, s_o, s_chg, s_d, s_rcp, cy, cx, cz, mu, inside, 0u);
+  sample_rays<K>(a, st, s_w, s_o, jb, cy, cx, cz, rays);
+  unsigned S = 0;
+  float emax = 0.f;
+  enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
+  int t_done = 1;
+  for (int t = 2; t <= a.iters; ++t) {
+    const unsigned Sp = S;
+    jb = m_step<K, false>(a, st, s_w, s_o, s_chg, s_d, s_rcp, cy, cx, cz, mu, inside, S);
+    sample_rays<K>(a, st, s_w, s_o, jb, cy, cx, cz, rays);
+    enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
+    t_done = t;
+    const bool conv = (S == Sp) || !valid;
+    if (a.early_exit && __all_sync(0xffffffffu, conv)) break;
+  }
+  float post[K];
+  if (a.post) {
+    unsigned dummy;
+    float dummyf;
+    enumerate<1, K>(rays, s_rcp, a.beta, emax, dummy, dummyf, post);
+  }
+  if (valid) {
+    const size_t pix = static_cast<size_t>(v) * W + u;
+    a.d_idx[pix] = jb;
+    if (a.d_out) a.d_out[pix] = s_d[jb];
+    if (a.labels) a.labels[pix] = static_cast<uint16_t>(S);
+    if (a.post) {
+      const size_t HW = static_cast<size_t>(H) * W;
+#pragma unroll
+      for (int k = 0; k < K; ++k) a.post[k * HW + pix] = post[k];
+    }
+  }
+  const unsigned nvalid = __popc(__ballot_sync(0xffffffffu, valid));
+  if ((tid & 31) == 0 && nvalid) atomicAdd(a.counter, static_cast<unsigned long long>(t_done) * nvalid);
+}
+
+template <int K>
+cudaError_t launch_em_sweep_k(const CUtensorMap& img_map, const CUtensorMap& p_map, const SweepArgs& a,
+                              cudaStream_t s) {
+  const size_t smem = sweep_layout(K, a).total;
+  cudaError_t e = cudaFuncSetAttribute(em_sweep_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.W + a.TW - 1) / a.TW, (a.H + a.TR - 1) / a.TR);
+  em_sweep_kernel<K><<<grid, a.TR * a.TW, smem, s>>>(img_map, p_map, a);
+  return cudaGetLastError();
+}
+
+}  // namespace dev
+}  // namespace lf

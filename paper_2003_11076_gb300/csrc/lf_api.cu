@@ -1,0 +1,653 @@
+// Host side of the C ABI declared in include/lf.h: validation, the per-(d, k)
+// sampling tables, the host Delaunay and triangle bins of the prior, TMA
+// descriptors, buffer ownership and kernel launches.  No compute happens on
+// the host beyond the triangulation of the sparse support points.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "em_sweep.cuh"
+#include "lf.h"
+#include "lf_internal.h"
+
+namespace lf {
+#define LF_DECL_SWEEP(k) \
+  cudaError_t launch_em_sweep_k##k(const CUtensorMap&, const CUtensorMap&, const SweepArgs&, cudaStream_t);
+LF_DECL_SWEEP(1) LF_DECL_SWEEP(2) LF_DECL_SWEEP(3) LF_DECL_SWEEP(4) LF_DECL_SWEEP(5) LF_DECL_SWEEP(6)
+LF_DECL_SWEEP(7) LF_DECL_SWEEP(8) LF_DECL_SWEEP(9) LF_DECL_SWEEP(10) LF_DECL_SWEEP(11) LF_DECL_SWEEP(12)
+#undef LF_DECL_SWEEP
+
+size_t sweep_smem_bytes(int K, const SweepArgs& a) { return dev::sweep_layout(K, a).total; }
+
+cudaError_t launch_em_sweep(int K, const CUtensorMap& i, const CUtensorMap& p, const SweepArgs& a,
+                            cudaStream_t s) {
+  switch (K) {
+    case 1: return launch_em_sweep_k1(i, p, a, s);
+    case 2: return launch_em_sweep_k2(i, p, a, s);
+    case 3: return launch_em_sweep_k3(i, p, a, s);
+    case 4: return launch_em_sweep_k4(i, p, a, s);
+    case 5: return launch_em_sweep_k5(i, p, a, s);
+    case 6: return launch_em_sweep_k6(i, p, a, s);
+    case 7: return launch_em_sweep_k7(i, p, a, s);
+    case 8: return launch_em_sweep_k8(i, p, a, s);
+    case 9: return launch_em_sweep_k9(i, p, a, s);
+    case 10: return launch_em_sweep_k10(i, p, a, s);
+    case 11: return launch_em_sweep_k11(i, p, a, s);
+    case 12: return launch_em_sweep_k12(i, p, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+}  // namespace lf
+
+using namespace lf;
+
+namespace {
+
+thread_local std::string g_err;
+
+lf_status fail(lf_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+lf_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(LF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LF_CUDA(call, what)                         \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+template <class T>
+lf_status grow(T** ptr, size_t* cap, size_t need, const char* what) {
+  if (need <= *cap && *ptr) return LF_OK;
+  if (*ptr) cudaFree(*ptr);
+  *ptr = nullptr;
+  *cap = 0;
+  size_t n = std::max<size_t>(need, 1);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), n * sizeof(T));
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    return e == cudaErrorMemoryAllocation ? fail(LF_ENOMEM, std::string(what) + ": out of device memory")
+                                          : cuda_fail(e, what);
+  }
+  *cap = n;
+  return LF_OK;
+}
+
+constexpr unsigned long long kTimeoutNs = 2000000000ull;  // 2 s bounded device waits
+
+}  // namespace
+
+struct lf_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int K = 0, H = 0, W = 0, D = 0, ref = 0;
+  float d_min = 0.f, d_max = 0.f;
+  std::vector<float> b;
+  lf_params p{};
+  // sampling tables (pixel independent): o = floor(-d_j b_k), w = -d_j b_k - o
+  int KP = 4, L = 0, R = 0;
+  std::vector<float> wtab, dval;
+  std::vector<int> otab;
+  std::vector<unsigned> chg;
+  float* d_wtab = nullptr;
+  int* d_otab = nullptr;
+  unsigned* d_chg = nullptr;
+  float* d_dval = nullptr;
+  float* d_mu = nullptr;
+  unsigned long long* d_counter = nullptr;
+  unsigned* d_status = nullptr;
+  // current inputs
+  bool have_inputs = false;
+  int C = 0, dtype = 0, bpp = 0;
+  const uint8_t* img = nullptr;
+  size_t img_pitch = 0;
+  const float* P = nullptr;
+  size_t p_pitch = 0;
+  uint8_t* own_img = nullptr;
+  size_t own_img_cap = 0;
+  float* own_P = nullptr;
+  size_t own_P_cap = 0;
+  // prior
+  std::vector<PriorTri> h_tris;
+  std::vector<int> h_bins;  // [nbins + 1] starts, then items
+  PriorTri* d_tris = nullptr;
+  size_t tris_cap = 0;
+  int* d_bins = nullptr;
+  size_t bins_cap = 0;
+  int nbx = 0, nby = 0;
+  // staging for host outputs
+  int32_t* o_didx = nullptr;
+  float* o_d = nullptr;
+  uint16_t* o_labels = nullptr;
+  float* o_post = nullptr;
+  float* o_ref = nullptr;
+  float* o_tmp = nullptr;
+  size_t o_didx_cap = 0, o_d_cap = 0, o_labels_cap = 0, o_post_cap = 0, o_ref_cap = 0, o_tmp_cap = 0;
+  // TMA descriptors of the current inputs
+  CUtensorMap img_map{}, p_map{};
+  // tiles
+  int TR = 2, TW = 128, SW = 0, SWp = 0, RW = 0;
+  lf_stats stats{};
+  // optional per-kernel timing: events before prior, sweep, refocus, median, after
+  bool timing = false;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool ev_used[5] = {false, false, false, false, false};
+};
+
+namespace {
+
+bool finite(float x) { return std::isfinite(x); }
+
+// Pick the sweep tile: the widest tile whose staged rows fit one TMA box
+// (256 eight-byte words per row) and whose shared memory allows at least
+// two CTAs per SM, else at least one.
+lf_status choose_tiles(lf_ctx* c) {
+  static const int cand[][2] = {{2, 128}, {1, 128}, {4, 64}, {2, 64}, {1, 64}, {2, 32}, {1, 32}};
+  int dev_smem = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  if (e != cudaSuccess || dev_smem <= 0) dev_smem = 227 * 1024;
+  for (int pass = 0; pass < 2; ++pass) {
+    const size_t limit = pass == 0 ? std::min<size_t>(dev_smem, 110 * 1024) : static_cast<size_t>(dev_smem);
+    for (auto& t : cand) {
+      SweepArgs a{};
+      a.TR = t[0];
+      a.TW = t[1];
+      a.SW = a.TW + c->L + c->R;
+      a.SWp = (a.SW + 31) / 32 * 32;
+      a.RW = (a.SW + 17 + 15) / 16 * 16;
+      a.bpp = c->bpp;
+      a.D = c->D;
+      a.KP = c->KP;
+      if (a.RW * a.bpp / 8 > 256 || a.RW / 2 > 256) continue;
+      if (sweep_smem_bytes(c->K, a) > limit) continue;
+      c->TR = a.TR;
+      c->TW = a.TW;
+      c->SW = a.SW;
+      c->SWp = a.SWp;
+      c->RW = a.RW;
+      return LF_OK;
+    }
+  }
+  return fail(LF_EINVAL, "disparity halo too wide for the sweep kernel's shared-memory staging");
+}
+
+lf_status encode_maps(lf_ctx* c) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return fail(LF_ECUDA, "cuTensorMapEncodeTiled unavailable from the driver");
+  {
+    const cuuint64_t dims[3] = {static_cast<cuuint64_t>((static_cast<size_t>(c->W) * c->bpp + 7) / 8),
+                                static_cast<cuuint64_t>(c->H), static_cast<cuuint64_t>(c->K)};
+    const cuuint64_t strides[2] = {static_cast<cuuint64_t>(c->img_pitch),
+                                   static_cast<cuuint64_t>(c->img_pitch * c->H)};
+    const cuuint32_t box[3] = {static_cast<cuuint32_t>(c->RW * c->bpp / 8), static_cast<cuuint32_t>(c->TR + 2),
+                               static_cast<cuuint32_t>(c->K)};
+    const cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(&c->img_map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<uint8_t*>(c->img), dims, strides,
+                     box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(LF_ECUDA, "cuTensorMapEncodeTiled(images) failed: " + std::to_string(r));
+  }
+  {
+    const cuuint64_t dims[3] = {static_cast<cuuint64_t>((c->W + 1) / 2), static_cast<cuuint64_t>(c->H),
+                                static_cast<cuuint64_t>(c->K)};
+    const cuuint64_t strides[2] = {static_cast<cuuint64_t>(c->p_pitch), static_cast<cuuint64_t>(c->p_pitch * c->H)};
+    const cuuint32_t box[3] = {static_cast<cuuint32_t>(c->RW / 2), static_cast<cuuint32_t>(c->TR),
+                               static_cast<cuuint32_t>(c->K)};
+    const cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(&c->p_map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<float*>(c->P), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(LF_ECUDA, "cuTensorMapEncodeTiled(seg_prior) failed: " + std::to_string(r));
+  }
+  return LF_OK;
+}
+
+// Host triangulation + plane coefficients + 16x16 bins of the prior.
+void build_prior(lf_ctx* c, const float* pts, int M) {
+  c->h_tris.clear();
+  std::vector<double> xy(static_cast<size_t>(2) * M);
+  for (int i = 0; i < M; ++i) {
+    xy[2 * i] = pts[3 * i];
+    xy[2 * i + 1] = pts[3 * i + 1];
+  }
+  std::vector<int> tris(static_cast<size_t>(6) * std::max(M, 1) + 6);
+  int nt = M >= 3 ? lf::delaunay(xy.data(), M, tris.data(), static_cast<int>(tris.size() / 3)) : 0;
+  if (nt > static_cast<int>(tris.size() / 3)) {
+    tris.resize(static_cast<size_t>(3) * nt);
+    nt = lf::delaunay(xy.data(), M, tris.data(), nt);
+  }
+  for (int t = 0; t < nt; ++t) {
+    const int ia = tris[3 * t], ib = tris[3 * t + 1], ic = tris[3 * t + 2];
+    PriorTri T;
+    T.ua = pts[3 * ia]; T.va = pts[3 * ia + 1];
+    T.ub = pts[3 * ib]; T.vb = pts[3 * ib + 1];
+    T.uc = pts[3 * ic]; T.vc = pts[3 * ic + 1];
+    const double da = pts[3 * ia + 2], db = pts[3 * ib + 2], dc = pts[3 * ic + 2];
+    const double du1 = static_cast<double>(T.ub) - T.ua, dv1 = static_cast<double>(T.vb) - T.va;
+    const double du2 = static_cast<double>(T.uc) - T.ua, dv2 = static_cast<double>(T.vc) - T.va;
+    const double det = du1 * dv2 - du2 * dv1;
+    if (det == 0.0) continue;
+    T.da = da;
+    T.gu = ((db - da) * dv2 - (dc - da) * dv1) / det;
+    T.gv = (du1 * (dc - da) - du2 * (db - da)) / det;
+    c->h_tris.push_back(T);
+  }
+  c->nbx = (c->W + kBinSize - 1) / kBinSize;
+  c->nby = (c->H + kBinSize - 1) / kBinSize;
+  const int nb = c->nbx * c->nby;
+  std::vector<int> count(static_cast<size_t>(nb) + 1, 0);
+  auto bbox = [&](const PriorTri& T, int& bx0, int& bx1, int& by0, int& by1) {
+    const double u0 = std::ceil(std::min({T.ua, T.ub, T.uc})), u1 = std::floor(std::max({T.ua, T.ub, T.uc}));
+    const double v0 = std::ceil(std::min({T.va, T.vb, T.vc})), v1 = std::floor(std::max({T.va, T.vb, T.vc}));
+    const double uu0 = std::max(u0, 0.0), uu1 = std::min(u1, static_cast<double>(c->W - 1));
+    const double vv0 = std::max(v0, 0.0), vv1 = std::min(v1, static_cast<double>(c->H - 1));
+    if (uu1 < uu0 || vv1 < vv0) return false;
+    bx0 = static_cast<int>(uu0) / kBinSize; bx1 = static_cast<int>(uu1) / kBinSize;
+    by0 = static_cast<int>(vv0) / kBinSize; by1 = static_cast<int>(vv1) / kBinSize;
+    return true;
+  };
+  for (const PriorTri& T : c->h_tris) {
+    int bx0, bx1, by0, by1;
+    if (!bbox(T, bx0, bx1, by0, by1)) continue;
+    for (int by = by0; by <= by1; ++by)
+      for (int bx = bx0; bx <= bx1; ++bx) count[by * c->nbx + bx + 1]++;
+  }
+  for (int i = 0; i < nb; ++i) count[i + 1] += count[i];
+  c->h_bins.assign(static_cast<size_t>(nb) + 1 + count[nb], 0);
+  std::copy(count.begin(), count.end(), c->h_bins.begin());
+  std::vector<int> fill(count.begin(), count.end() - 1);
+  for (size_t t = 0; t < c->h_tris.size(); ++t) {
+    int bx0, bx1, by0, by1;
+    if (!bbox(c->h_tris[t], bx0, bx1, by0, by1)) continue;
+    for (int by = by0; by <= by1; ++by)
+      for (int bx = bx0; bx <= bx1; ++bx) c->h_bins[nb + 1 + fill[by * c->nbx + bx]++] = static_cast<int>(t);
+  }
+}
+
+lf_status copy_plane(lf_ctx* c, const void* src, size_t row_bytes, bool on_device, uint8_t** own,
+                     size_t* own_cap, const uint8_t** use, size_t* pitch) {
+  const size_t rows = static_cast<size_t>(c->K) * c->H;
+  const bool aligned = (reinterpret_cast<uintptr_t>(src) % 16 == 0) && (row_bytes % 16 == 0);
+  if (on_device && aligned) {  // borrow the caller's buffer
+    *use = static_cast<const uint8_t*>(src);
+    *pitch = row_bytes;
+    return LF_OK;
+  }
+  const size_t p = (row_bytes + 15) / 16 * 16;
+  lf_status s = grow(own, own_cap, rows * p, "input staging");
+  if (s != LF_OK) return s;
+  LF_CUDA(cudaMemcpy2DAsync(*own, p, src, row_bytes, row_bytes, rows,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
+          "input copy");
+  *use = *own;
+  *pitch = p;
+  return LF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lf_default_params(lf_params* p) {
+  if (!p) return;
+  p->beta = 200.f;
+  p->gamma = 0.1f;
+  p->sigma = 2.f;
+  p->seg_threshold = 0.7f;
+  p->eps = 1e-4f;
+  p->mstep_seg_term = 1;
+  p->median = 0;
+  p->precision = LF_PREC_F32;
+  p->early_exit = 1;
+}
+
+const char* lf_last_error(const lf_ctx*) { return g_err.c_str(); }
+
+int lf_triangulate(const float* points, int M, int32_t* tris, int max_tris) {
+  if (M < 0 || (M > 0 && !points) || max_tris < 0 || (max_tris > 0 && !tris)) return -1;
+  std::vector<double> xy(static_cast<size_t>(2) * M);
+  for (int i = 0; i < M; ++i) {
+    if (!std::isfinite(points[3 * i]) || !std::isfinite(points[3 * i + 1])) return -1;
+    xy[2 * i] = points[3 * i];
+    xy[2 * i + 1] = points[3 * i + 1];
+  }
+  return lf::delaunay(xy.data(), M, tris, max_tris);
+}
+
+lf_status lf_create(lf_ctx** out, int n_cams, const float* baselines, int H, int W, float d_min, float d_max,
+                    int D, const lf_params* p) {
+  g_err.clear();
+  if (!out) return fail(LF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_cams < 1 || n_cams > kMaxCams) return fail(LF_EINVAL, "n_cams must be in [1, 12]");
+  if (!baselines) return fail(LF_EINVAL, "baselines is NULL");
+  if (H < 3 || W < 3) return fail(LF_EINVAL, "H and W must be >= 3");
+  if (D < 1 || D > kMaxD) return fail(LF_EINVAL, "D must be in [1, 1024]");
+  if (!finite(d_min) || !finite(d_max) || d_max < d_min) return fail(LF_EINVAL, "need finite d_min <= d_max");
+  int ref = -1;
+  for (int k = 0; k < n_cams; ++k) {
+    if (!finite(baselines[k])) return fail(LF_EINVAL, "non-finite baseline");
+    if (baselines[k] == 0.f && ref < 0) ref = k;
+  }
+  if (ref < 0) return fail(LF_EINVAL, "no baseline equals 0 (reference camera)");
+  lf_params prm;
+  lf_default_params(&prm);
+  if (p) prm = *p;
+  if (!finite(prm.beta) || !finite(prm.gamma) || !finite(prm.sigma) || !finite(prm.seg_threshold) ||
+      !finite(prm.eps) || prm.sigma <= 0.f || prm.gamma < 0.f || prm.eps <= 0.f || prm.seg_threshold <= 0.f ||
+      prm.seg_threshold >= 1.f || prm.beta < 0.f)
+    return fail(LF_EINVAL, "invalid lf_params");
+  if (prm.precision != LF_PREC_F32) return fail(LF_EINVAL, "only LF_PREC_F32 is implemented by this build");
+
+  lf_ctx* c = new (std::nothrow) lf_ctx();
+  if (!c) return fail(LF_ENOMEM, "host allocation failed");
+  c->K = n_cams;
+  c->H = H;
+  c->W = W;
+  c->D = D;
+  c->ref = ref;
+  c->d_min = d_min;
+  c->d_max = d_max;
+  c->b.assign(baselines, baselines + n_cams);
+  c->p = prm;
+  cudaGetDevice(&c->device);
+  c->KP = (n_cams + 3) / 4 * 4;
+  c->wtab.assign(static_cast<size_t>(D) * c->KP, 0.f);
+  c->otab.assign(static_cast<size_t>(D) * c->KP, 0);
+  c->chg.assign(static_cast<size_t>(D), 0u);
+  c->dval.assign(static_cast<size_t>(D), 0.f);
+  int omin = 0, omax = 0;
+  for (int j = 0; j < D; ++j) {
+    const double dj = D == 1 ? static_cast<double>(d_min)
+                             : static_cast<double>(d_min) +
+                                   j * ((static_cast<double>(d_max) - static_cast<double>(d_min)) / (D - 1));
+    c->dval[j] = static_cast<float>(dj);
+    unsigned m = 0;
+    for (int k = 0; k < n_cams; ++k) {
+      const double x = -dj * static_cast<double>(baselines[k]);
+      const double o = std::floor(x);
+      const int oi = static_cast<int>(o);
+      c->otab[j * c->KP + k] = oi;
+      c->wtab[j * c->KP + k] = static_cast<float>(x - o);
+      if (j == 0 || c->otab[(j - 1) * c->KP + k] != oi) m |= 1u << k;
+      omin = std::min(omin, oi);
+      omax = std::max(omax, oi + 1);
+    }
+    c->chg[j] = m;
+  }
+  c->L = -omin;
+  c->R = omax;
+  lf_status s = LF_OK;
+  size_t cap = 0;
+  auto bail = [&](lf_status st) {
+    lf_destroy(c);
+    return st;
+  };
+  if ((s = grow(&c->d_wtab, &cap, c->wtab.size(), "tables")) != LF_OK) return bail(s);
+  cap = 0;
+  if ((s = grow(&c->d_otab, &cap, c->otab.size(), "tables")) != LF_OK) return bail(s);
+  cap = 0;
+  if ((s = grow(&c->d_chg, &cap, c->chg.size(), "tables")) != LF_OK) return bail(s);
+  cap = 0;
+  if ((s = grow(&c->d_dval, &cap, c->dval.size(), "tables")) != LF_OK) return bail(s);
+  cap = 0;
+  if ((s = grow(&c->d_mu, &cap, static_cast<size_t>(H) * W, "prior")) != LF_OK) return bail(s);
+  cap = 0;
+  if ((s = grow(&c->d_counter, &cap, 1, "counter")) != LF_OK) return bail(s);
+  cap = 0;
+  if ((s = grow(&c->d_status, &cap, 1, "status")) != LF_OK) return bail(s);
+  cudaError_t e;
+  if ((e = cudaMemcpy(c->d_wtab, c->wtab.data(), c->wtab.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(c->d_otab, c->otab.data(), c->otab.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(c->d_chg, c->chg.data(), c->chg.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(c->d_dval, c->dval.data(), c->dval.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(cuda_fail(e, "table upload"));
+  // the tile choice depends on the bytes per pixel of the inputs and is made
+  // again in lf_set_inputs; reject now a halo that no input type can stage
+  c->bpp = 1;
+  if ((s = choose_tiles(c)) != LF_OK) return bail(s);
+  c->bpp = 0;
+  *out = c;
+  return LF_OK;
+}
+
+lf_status lf_set_stream(lf_ctx* c, void* stream) {
+  g_err.clear();
+  if (!c) return fail(LF_EINVAL, "ctx is NULL");
+  c->stream = static_cast<cudaStream_t>(stream);
+  return LF_OK;
+}
+
+lf_status lf_set_inputs(lf_ctx* c, const void* images, int C, int dtype, const float* seg_prior,
+                        const float* sparse_points, int M, int on_device) {
+  g_err.clear();
+  if (!c) return fail(LF_EINVAL, "ctx is NULL");
+  if (!images || !seg_prior) return fail(LF_EINVAL, "images and seg_prior must not be NULL");
+  if (C != 1 && C != 3) return fail(LF_EINVAL, "C must be 1 or 3");
+  if (dtype != LF_U8 && dtype != LF_F32) return fail(LF_EINVAL, "dtype must be LF_U8 or LF_F32");
+  if (M < 0 || (M > 0 && !sparse_points)) return fail(LF_EINVAL, "bad sparse points");
+  for (int i = 0; i < 3 * M; ++i)
+    if (!std::isfinite(sparse_points[i])) return fail(LF_EINVAL, "non-finite sparse point");
+  c->have_inputs = false;
+  c->C = C;
+  c->dtype = dtype;
+  c->bpp = C * (dtype == LF_U8 ? 1 : 4);
+  lf_status s = choose_tiles(c);
+  if (s != LF_OK) return s;
+  s = copy_plane(c, images, static_cast<size_t>(c->W) * c->bpp, on_device != 0, &c->own_img, &c->own_img_cap,
+                 &c->img, &c->img_pitch);
+  if (s != LF_OK) return s;
+  const uint8_t* pp = nullptr;
+  uint8_t* ownP = reinterpret_cast<uint8_t*>(c->own_P);
+  s = copy_plane(c, seg_prior, static_cast<size_t>(c->W) * 4, on_device != 0, &ownP, &c->own_P_cap, &pp,
+                 &c->p_pitch);
+  c->own_P = reinterpret_cast<float*>(ownP);
+  if (s != LF_OK) return s;
+  c->P = reinterpret_cast<const float*>(pp);
+  build_prior(c, sparse_points, M);
+  if ((s = grow(&c->d_tris, &c->tris_cap, std::max<size_t>(c->h_tris.size(), 1), "prior")) != LF_OK) return s;
+  if ((s = grow(&c->d_bins, &c->bins_cap, c->h_bins.size(), "prior")) != LF_OK) return s;
+  if (!c->h_tris.empty())
+    LF_CUDA(cudaMemcpyAsync(c->d_tris, c->h_tris.data(), c->h_tris.size() * sizeof(PriorTri),
+                            cudaMemcpyHostToDevice, c->stream),
+            "prior upload");
+  LF_CUDA(cudaMemcpyAsync(c->d_bins, c->h_bins.data(), c->h_bins.size() * sizeof(int), cudaMemcpyHostToDevice,
+                          c->stream),
+          "prior upload");
+  if ((s = encode_maps(c)) != LF_OK) return s;
+  if (!on_device) LF_CUDA(cudaStreamSynchronize(c->stream), "input copy");
+  c->have_inputs = true;
+  return LF_OK;
+}
+
+lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* disparity, float* posteriors,
+                    uint16_t* labels, float* refocused, int outputs_on_device) {
+  g_err.clear();
+  if (!c) return fail(LF_EINVAL, "ctx is NULL");
+  if (!c->have_inputs) return fail(LF_ESTATE, "lf_run_em called before lf_set_inputs");
+  if (iters < 1 || iters > 255) return fail(LF_EINVAL, "iters must be in [1, 255]");
+  if (!disparity_idx) return fail(LF_EINVAL, "disparity_idx must not be NULL");
+  const size_t HW = static_cast<size_t>(c->H) * c->W;
+  const bool dev = outputs_on_device != 0;
+  int32_t* didx = disparity_idx;
+  float* dout = disparity;
+  uint16_t* lab = labels;
+  float* post = posteriors;
+  float* refo = refocused;
+  lf_status s;
+  if (!dev) {
+    if ((s = grow(&c->o_didx, &c->o_didx_cap, HW, "outputs")) != LF_OK) return s;
+    didx = c->o_didx;
+    if (disparity) {
+      if ((s = grow(&c->o_d, &c->o_d_cap, HW, "outputs")) != LF_OK) return s;
+      dout = c->o_d;
+    }
+    if (posteriors) {
+      if ((s = grow(&c->o_post, &c->o_post_cap, HW * c->K, "outputs")) != LF_OK) return s;
+      post = c->o_post;
+    }
+    if (refocused) {
+      if ((s = grow(&c->o_ref, &c->o_ref_cap, HW * c->C, "outputs")) != LF_OK) return s;
+      refo = c->o_ref;
+    }
+  }
+  // the refocus needs the labels even when the caller does not want them
+  if (!lab || !dev) {
+    if ((s = grow(&c->o_labels, &c->o_labels_cap, HW, "outputs")) != LF_OK) return s;
+    lab = c->o_labels;
+  }
+  float* refo_stage = refo;
+  if (refo && c->p.median) {
+    if ((s = grow(&c->o_tmp, &c->o_tmp_cap, HW * c->C, "outputs")) != LF_OK) return s;
+    refo_stage = c->o_tmp;
+  }
+  int launched = 0;
+  for (bool& u : c->ev_used) u = false;
+  auto mark = [&](int i) -> cudaError_t {
+    if (!c->timing) return cudaSuccess;
+    c->ev_used[i] = true;
+    return cudaEventRecord(c->ev[i], c->stream);
+  };
+  LF_CUDA(mark(0), "event");
+  PriorArgs pa{c->H, c->W, c->nbx, c->nby, c->d_tris, c->d_bins, c->d_bins + (c->nbx * c->nby + 1), c->d_mu};
+  LF_CUDA(launch_prior_raster(pa, c->stream), "prior_raster launch");
+  ++launched;
+  LF_CUDA(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream), "memset");
+  LF_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream), "memset");
+  LF_CUDA(mark(1), "event");
+  SweepArgs a{};
+  a.H = c->H; a.W = c->W; a.C = c->C; a.D = c->D; a.ref = c->ref; a.dtype = c->dtype; a.bpp = c->bpp;
+  a.TR = c->TR; a.TW = c->TW; a.L = c->L; a.R = c->R; a.SW = c->SW; a.SWp = c->SWp; a.RW = c->RW; a.KP = c->KP;
+  a.iters = iters;
+  a.early_exit = c->p.early_exit;
+  a.mseg = c->p.mstep_seg_term;
+  a.beta = c->p.beta;
+  a.gamma = c->p.gamma;
+  a.inv2s2 = static_cast<float>(1.0 / (2.0 * static_cast<double>(c->p.sigma) * c->p.sigma));
+  a.log_thr = static_cast<float>(std::log(static_cast<double>(c->p.seg_threshold) / (1.0 - c->p.seg_threshold)));
+  a.eps = c->p.eps;
+  a.wtab = c->d_wtab; a.otab = c->d_otab; a.chg = c->d_chg; a.dval = c->d_dval; a.mu = c->d_mu;
+  a.d_idx = didx; a.d_out = dout; a.labels = lab; a.post = post;
+  a.counter = c->d_counter; a.status = c->d_status; a.timeout_ns = kTimeoutNs;
+  LF_CUDA(launch_em_sweep(c->K, c->img_map, c->p_map, a, c->stream), "em_sweep launch");
+  ++launched;
+  LF_CUDA(mark(2), "event");
+  if (refo) {
+    RefocusArgs r{c->H, c->W, c->C, c->K, c->ref, c->dtype, c->KP, c->img_pitch, c->img, c->d_wtab, c->d_otab,
+                  didx, lab, refo_stage};
+    LF_CUDA(launch_refocus(r, c->stream), "refocus launch");
+    ++launched;
+    LF_CUDA(mark(3), "event");
+    if (c->p.median) {
+      LF_CUDA(launch_median3(refo_stage, refo, c->H, c->W, c->C, c->stream), "median launch");
+      ++launched;
+      LF_CUDA(mark(4), "event");
+    }
+  }
+  c->stats.nominal_ray_samples = static_cast<uint64_t>(HW) * c->K * c->D * iters;
+  c->stats.halo_left = c->L;
+  c->stats.halo_right = c->R;
+  c->stats.tile_rows = c->TR;
+  c->stats.tile_cols = c->TW;
+  c->stats.kernels_launched = launched;
+  if (dev) return LF_OK;
+  LF_CUDA(cudaMemcpyAsync(disparity_idx, didx, HW * 4, cudaMemcpyDeviceToHost, c->stream), "output copy");
+  if (disparity) LF_CUDA(cudaMemcpyAsync(disparity, dout, HW * 4, cudaMemcpyDeviceToHost, c->stream), "output copy");
+  if (labels) LF_CUDA(cudaMemcpyAsync(labels, lab, HW * 2, cudaMemcpyDeviceToHost, c->stream), "output copy");
+  if (posteriors)
+    LF_CUDA(cudaMemcpyAsync(posteriors, post, HW * 4 * c->K, cudaMemcpyDeviceToHost, c->stream), "output copy");
+  if (refocused)
+    LF_CUDA(cudaMemcpyAsync(refocused, refo, HW * 4 * c->C, cudaMemcpyDeviceToHost, c->stream), "output copy");
+  return lf_synchronize(c);
+}
+
+lf_status lf_synchronize(lf_ctx* c) {
+  g_err.clear();
+  if (!c) return fail(LF_EINVAL, "ctx is NULL");
+  LF_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+  unsigned st = 0;
+  LF_CUDA(cudaMemcpy(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost), "status read");
+  if (st & kStatusTmaTimeout) return fail(LF_ETIMEOUT, "a bounded TMA wait in the sweep kernel expired");
+  if (st & kStatusSmemMisaligned) return fail(LF_ECUDA, "sweep kernel: dynamic shared memory not 128-byte aligned");
+  return LF_OK;
+}
+
+lf_status lf_get_prior(lf_ctx* c, float* mu, int on_device) {
+  g_err.clear();
+  if (!c || !mu) return fail(LF_EINVAL, "NULL argument");
+  const size_t bytes = static_cast<size_t>(c->H) * c->W * 4;
+  LF_CUDA(cudaMemcpyAsync(mu, c->d_mu, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          c->stream),
+          "prior copy");
+  if (!on_device) LF_CUDA(cudaStreamSynchronize(c->stream), "prior copy");
+  return LF_OK;
+}
+
+lf_status lf_set_timing(lf_ctx* c, int enable) {
+  g_err.clear();
+  if (!c) return fail(LF_EINVAL, "ctx is NULL");
+  if (enable && !c->ev[0])
+    for (cudaEvent_t& e : c->ev) LF_CUDA(cudaEventCreate(&e), "event create");
+  c->timing = enable != 0;
+  return LF_OK;
+}
+
+lf_status lf_get_stats(lf_ctx* c, lf_stats* out) {
+  g_err.clear();
+  if (!c || !out) return fail(LF_EINVAL, "NULL argument");
+  LF_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+  unsigned long long n = 0;
+  LF_CUDA(cudaMemcpy(&n, c->d_counter, sizeof(n), cudaMemcpyDeviceToHost), "counter read");
+  c->stats.executed_ray_samples = static_cast<uint64_t>(n) * c->K * c->D;
+  float* ms[4] = {&c->stats.ms_prior, &c->stats.ms_sweep, &c->stats.ms_refocus, &c->stats.ms_median};
+  for (int i = 0; i < 4; ++i) {
+    *ms[i] = 0.f;
+    if (c->ev_used[i] && c->ev_used[i + 1]) LF_CUDA(cudaEventElapsedTime(ms[i], c->ev[i], c->ev[i + 1]), "event time");
+  }
+  *out = c->stats;
+  return LF_OK;
+}
+
+void lf_destroy(lf_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  void* bufs[] = {c->d_wtab, c->d_otab, c->d_chg, c->d_dval, c->d_mu, c->d_counter, c->d_status,
+                  c->own_img, c->own_P, c->d_tris, c->d_bins, c->o_didx, c->o_d, c->o_labels,
+                  c->o_post, c->o_ref, c->o_tmp};
+  for (void* p : bufs)
+    if (p) cudaFree(p);
+  for (cudaEvent_t e : c->ev)
+    if (e) cudaEventDestroy(e);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Internal declarations shared by the host library and its kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace lf {
+
+constexpr int kMaxCams = 12;       // 2^K label vectors per E-step
+constexpr int kMaxD = 1024;        // candidate disparities per sweep
+constexpr int kPrecF32 = 0, kPrecF16 = 1, kPrecBF16 = 2;
+
+// Device status word bits (written by kernels, read by the host after a sync).
+constexpr unsigned kStatusTmaTimeout = 1u;
+constexpr unsigned kStatusSmemMisaligned = 2u;
+
+// One support-point triangle of the piecewise-planar prior: vertices (float
+// input coordinates, counter-clockwise) and the plane through them,
+// mu(u, v) = d_a + gu * (u - u_a) + gv * (v - v_a), coefficients in double.
+struct PriorTri {
+  float ua, va, ub, vb, uc, vc;
+  double da, gu, gv;
+};
+
+constexpr int kBinSize = 16;       // prior raster: triangles binned per 16x16 pixels
+
+struct PriorArgs {
+  int H, W, nbx, nby;
+  const PriorTri* tris;
+  const int* bin_start;            // [nbx * nby + 1]
+  const int* bin_items;            // triangle indices, ascending per bin
+  float* mu;                       // [H][W], NaN outside the triangulation
+};
+
+// Everything the fused sweep kernel needs besides the two tensor maps.
+struct SweepArgs {
+  int H, W, C, D, ref, dtype, bpp; // dtype 0 = uint8, 1 = float32; bpp = bytes per pixel
+  int TR, TW;                      // tile rows / columns; threads = TR * TW
+  int L, R;                        // staged texel halo left / right of the tile
+  int SW, SWp;                     // staged texels per row, padded to a multiple of 32
+  int RW;                          // staged raw pixels per row (multiple of 16)
+  int KP;                          // cameras padded to a multiple of 4 (table stride)
+  int iters, early_exit, mseg;
+  float beta, gamma, inv2s2, log_thr, eps;
+  const float* wtab;               // [D][KP] interpolation weight of camera k at d_j
+  const int* otab;                 // [D][KP] floor(-d_j * b_k)
+  const unsigned* chg;             // [D] bit k: otab[j][k] != otab[j-1][k] (j = 0: all)
+  const float* dval;               // [D] d_j
+  const float* mu;                 // [H][W] prior centre, NaN outside
+  int32_t* d_idx;                  // [H][W]
+  float* d_out;                    // [H][W] or null
+  uint16_t* labels;                // [H][W] or null
+  float* post;                     // [K][H][W] or null
+  unsigned long long* counter;     // executed pixel-sweeps
+  unsigned* status;                // kStatus* bits
+  unsigned long long timeout_ns;   // bounded-wait limit
+};
+
+struct RefocusArgs {
+  int H, W, C, K, ref, dtype, KP;
+  size_t pitch;                    // bytes per image row
+  const uint8_t* img;              // [K][H][pitch]
+  const float* wtab;
+  const int* otab;
+  const int32_t* d_idx;
+  const uint16_t* labels;
+  float* out;                      // [H][W][C]
+};
+
+// Shared-memory bytes of the sweep kernel for a tile configuration.
+size_t sweep_smem_bytes(int K, const SweepArgs& a);
+
+cudaError_t launch_prior_raster(const PriorArgs& a, cudaStream_t s);
+cudaError_t launch_em_sweep(int K, const CUtensorMap& img_map, const CUtensorMap& p_map,
+                            const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_refocus(const RefocusArgs& a, cudaStream_t s);
+cudaError_t launch_median3(const float* in, float* out, int H, int W, int C, cudaStream_t s);
+
+// Host Delaunay triangulation (Bowyer-Watson with a symbolic point at infinity).
+// pts: n points (x, y); writes counter-clockwise triangles into out (3 ints each).
+int delaunay(const double* xy, int n, int* out_tris, int max_tris);
+
+}  // namespace lf

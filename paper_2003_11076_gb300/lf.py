@@ -1,0 +1,250 @@
+"""Python binding of the C ABI in ``include/lf.h`` (ctypes; marshalling only).
+
+Every step of the path runs in the library's CUDA kernels.  Loading fails
+loudly when the in-tree ``_lib/liblf.so`` is missing -- there is no CPU
+fallback.  Host inputs are numpy arrays; device inputs are torch CUDA tensors
+(torch is only imported when such a tensor is passed), whose data pointers are
+handed to the library together with the current torch stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "liblf.so")
+
+LF_OK, LF_EINVAL, LF_ENOMEM, LF_ECUDA, LF_ESTATE, LF_ETIMEOUT = range(6)
+LF_U8, LF_F32 = 0, 1
+LF_PREC_F32, LF_PREC_F16, LF_PREC_BF16 = 0, 1, 2
+
+EXPORTS = ("lf_default_params", "lf_create", "lf_set_stream", "lf_set_inputs", "lf_run_em",
+           "lf_synchronize", "lf_get_prior", "lf_get_stats", "lf_last_error", "lf_destroy",
+           "lf_triangulate", "lf_set_timing")
+
+
+class LfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lf status {status}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_float), ("gamma", ctypes.c_float), ("sigma", ctypes.c_float),
+                ("seg_threshold", ctypes.c_float), ("eps", ctypes.c_float),
+                ("mstep_seg_term", ctypes.c_int), ("median", ctypes.c_int), ("precision", ctypes.c_int),
+                ("early_exit", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("nominal_ray_samples", ctypes.c_uint64), ("executed_ray_samples", ctypes.c_uint64),
+                ("halo_left", ctypes.c_int), ("halo_right", ctypes.c_int),
+                ("tile_rows", ctypes.c_int), ("tile_cols", ctypes.c_int),
+                ("kernels_launched", ctypes.c_int),
+                ("ms_prior", ctypes.c_float), ("ms_sweep", ctypes.c_float), ("ms_refocus", ctypes.c_float),
+                ("ms_median", ctypes.c_float)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the in-tree library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    lib.lf_default_params.argtypes = [ctypes.POINTER(Params)]
+    lib.lf_default_params.restype = None
+    lib.lf_create.argtypes = [ctypes.POINTER(P), I, P, I, I, ctypes.c_float, ctypes.c_float, I,
+                              ctypes.POINTER(Params)]
+    lib.lf_set_stream.argtypes = [P, P]
+    lib.lf_set_inputs.argtypes = [P, P, I, I, P, P, I, I]
+    lib.lf_run_em.argtypes = [P, I, P, P, P, P, P, I]
+    lib.lf_synchronize.argtypes = [P]
+    lib.lf_get_prior.argtypes = [P, P, I]
+    lib.lf_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    lib.lf_set_timing.argtypes = [P, I]
+    lib.lf_last_error.argtypes = [P]
+    lib.lf_last_error.restype = ctypes.c_char_p
+    lib.lf_destroy.argtypes = [P]
+    lib.lf_destroy.restype = None
+    lib.lf_triangulate.argtypes = [P, I, P, I]
+    lib.lf_triangulate.restype = I
+    for name in ("lf_create", "lf_set_stream", "lf_set_inputs", "lf_run_em", "lf_synchronize",
+                 "lf_get_prior", "lf_get_stats", "lf_set_timing"):
+        getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def default_params(**overrides) -> Params:
+    p = Params()
+    load().lf_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def _check(status: int):
+    if status != LF_OK:
+        msg = load().lf_last_error(None)
+        raise LfError(status, msg.decode() if msg else "")
+
+
+def triangulate(points: np.ndarray) -> np.ndarray:
+    """Delaunay triangles of the (u, v) of [M,3] points (host utility)."""
+    pts = np.ascontiguousarray(points, np.float32).reshape(-1, 3)
+    M = pts.shape[0]
+    cap = max(2 * M + 8, 8)
+    out = np.zeros((cap, 3), np.int32)
+    n = load().lf_triangulate(pts.ctypes.data, M, out.ctypes.data, cap)
+    if n < 0:
+        raise LfError(LF_EINVAL, "invalid points")
+    return out[:n].copy()
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+class Context:
+    """One camera array / image size; owns the library's device buffers."""
+
+    def __init__(self, baselines, H: int, W: int, d_min: float, d_max: float, D: int,
+                 params: Optional[Params] = None, stream=None):
+        lib = load()
+        self.K = len(baselines)
+        self.H, self.W, self.D = int(H), int(W), int(D)
+        b = np.ascontiguousarray(baselines, np.float32)
+        h = ctypes.c_void_p()
+        _check(lib.lf_create(ctypes.byref(h), self.K, b.ctypes.data, self.H, self.W, float(d_min), float(d_max),
+                             self.D, ctypes.byref(params) if params is not None else None))
+        self._h = h
+        self.C = None
+        if stream is not None:
+            self.set_stream(stream)
+
+    # -- plumbing
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+        handle = getattr(stream, "cuda_stream", stream)
+        _check(load().lf_set_stream(self._h, ctypes.c_void_p(handle or 0)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- the path
+    def set_inputs(self, images, seg_prior, points):
+        """images [K,H,W] / [K,H,W,3] uint8 or float32; seg_prior [K,H,W]
+        float32 P(dynamic); points [M,3] float32 (host).  numpy arrays are
+        host inputs, torch CUDA tensors device inputs."""
+        pts = np.ascontiguousarray(points, np.float32).reshape(-1, 3)
+        if _is_torch(images):
+            import torch
+            assert images.is_cuda and seg_prior.is_cuda and images.is_contiguous() and seg_prior.is_contiguous()
+            C = 1 if images.dim() == 3 else int(images.shape[3])
+            dt = LF_U8 if images.dtype == torch.uint8 else LF_F32
+            assert seg_prior.dtype == torch.float32
+            self._keep = (images, seg_prior)
+            _check(load().lf_set_inputs(self._h, images.data_ptr(), C, dt, seg_prior.data_ptr(),
+                                        pts.ctypes.data, pts.shape[0], 1))
+        else:
+            imgs = np.ascontiguousarray(images)
+            if imgs.dtype not in (np.uint8, np.float32):
+                imgs = imgs.astype(np.float32)
+            C = 1 if imgs.ndim == 3 else int(imgs.shape[3])
+            dt = LF_U8 if imgs.dtype == np.uint8 else LF_F32
+            seg = np.ascontiguousarray(seg_prior, np.float32)
+            _check(load().lf_set_inputs(self._h, imgs.ctypes.data, C, dt, seg.ctypes.data,
+                                        pts.ctypes.data, pts.shape[0], 0))
+        self.C = C
+
+    def run(self, iters: int, *, posteriors: bool = True, refocus: bool = True, disparity: bool = True,
+            labels: bool = True, out: Optional[dict] = None, device: bool = False) -> dict:
+        """Run the hot path.  device=False: numpy outputs (the call waits).
+        device=True: torch CUDA outputs written on the context's stream (pass
+        preallocated tensors in ``out`` to avoid allocation)."""
+        lib = load()
+        K, H, W, C = self.K, self.H, self.W, self.C
+        if C is None:
+            raise LfError(LF_ESTATE, "set_inputs first")
+        if device:
+            import torch
+            if out is None:
+                dev = torch.device("cuda")
+                out = {"d_idx": torch.empty((H, W), dtype=torch.int32, device=dev)}
+                if disparity:
+                    out["d"] = torch.empty((H, W), dtype=torch.float32, device=dev)
+                if posteriors:
+                    out["post"] = torch.empty((K, H, W), dtype=torch.float32, device=dev)
+                if labels:
+                    out["labels"] = torch.empty((H, W), dtype=torch.int16, device=dev)
+                if refocus:
+                    out["refocus"] = torch.empty((H, W, C) if C > 1 else (H, W), dtype=torch.float32, device=dev)
+            ptr = lambda k: out[k].data_ptr() if k in out else None
+            _check(lib.lf_run_em(self._h, int(iters), ptr("d_idx"), ptr("d"), ptr("post"), ptr("labels"),
+                                 ptr("refocus"), 1))
+            return out
+        if out is not None:
+            res = out
+        else:
+            res = {"d_idx": np.zeros((H, W), np.int32)}
+            if disparity:
+                res["d"] = np.zeros((H, W), np.float32)
+            if posteriors:
+                res["post"] = np.zeros((K, H, W), np.float32)
+            if labels:
+                res["labels"] = np.zeros((H, W), np.uint16)
+            if refocus:
+                res["refocus"] = np.zeros((H, W, C) if C > 1 else (H, W), np.float32)
+        ptr = lambda k: res[k].ctypes.data if k in res else None
+        _check(lib.lf_run_em(self._h, int(iters), ptr("d_idx"), ptr("d"), ptr("post"), ptr("labels"),
+                             ptr("refocus"), 0))
+        return res
+
+    def set_timing(self, enable: bool = True):
+        _check(load().lf_set_timing(self._h, int(enable)))
+
+    def synchronize(self):
+        _check(load().lf_synchronize(self._h))
+
+    def prior(self) -> np.ndarray:
+        mu = np.zeros((self.H, self.W), np.float32)
+        _check(load().lf_get_prior(self._h, mu.ctypes.data, 0))
+        return mu
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(load().lf_get_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+
+def run_scene(scene, params: Optional[Params] = None, iters: Optional[int] = None, **kw) -> dict:
+    """Convenience: one frame of a ``scenes.Scene`` through host buffers."""
+    with Context(scene.baselines, scene.H, scene.W, scene.d_min, scene.d_max, scene.D, params) as ctx:
+        ctx.set_inputs(scene.images, scene.seg_prior, scene.points)
+        out = ctx.run(scene.iters if iters is None else iters, **kw)
+        out["stats"] = ctx.stats()
+        out["mu"] = ctx.prior()
+    return out

@@ -1,0 +1,120 @@
+"""The C-ABI library loads, exports every symbol its header declares, and its
+host-only logic behaves (CPU; no compute call touches a GPU here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2003_11076_gb300 import build, lf
+    build.build()
+    return lf.load()
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "lf.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lf_[a-z_]+)\s*\(", text)))
+
+
+def test_header_symbols_are_exported(lib):
+    names = _declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_2003_11076_gb300 import lf
+    assert set(lf.EXPORTS) == set(names)
+
+
+def test_library_is_built_for_sm_103a_only():
+    from paper_2003_11076_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_default_params(lib):
+    from paper_2003_11076_gb300 import lf
+    p = lf.default_params()
+    assert (p.beta, p.gamma, p.sigma, p.eps) == (200.0, pytest.approx(0.1), 2.0, pytest.approx(1e-4))
+    assert p.seg_threshold == pytest.approx(0.7) and p.mstep_seg_term == 1 and p.early_exit == 1
+    assert p.median == 0 and p.precision == lf.LF_PREC_F32
+
+
+@pytest.mark.parametrize("kw,expect", [
+    (dict(K=0), "n_cams"), (dict(K=13), "n_cams"), (dict(b0=0.3), "reference"),
+    (dict(H=2), "H and W"), (dict(D=0), "D must"), (dict(D=2000), "D must"),
+    (dict(dmin=5.0, dmax=1.0), "d_min"),
+])
+def test_create_rejects_invalid_arguments(lib, kw, expect):
+    from paper_2003_11076_gb300 import lf
+    K = kw.get("K", 3)
+    b = np.zeros(max(K, 1), np.float32)
+    b[1:] = np.linspace(0.1, 0.3, max(K, 1) - 1)
+    if "b0" in kw:
+        b[0] = kw["b0"]
+    h = ctypes.c_void_p()
+    s = lib.lf_create(ctypes.byref(h), K, b.ctypes.data, kw.get("H", 16), 16, kw.get("dmin", 0.0),
+                      kw.get("dmax", 7.0), kw.get("D", 8), None)
+    assert s == lf.LF_EINVAL
+    assert not h.value
+    assert expect in lib.lf_last_error(None).decode()
+
+
+def test_null_context_calls_fail_cleanly(lib):
+    from paper_2003_11076_gb300 import lf
+    assert lib.lf_run_em(None, 3, None, None, None, None, None, 0) == lf.LF_EINVAL
+    assert lib.lf_synchronize(None) == lf.LF_EINVAL
+    lib.lf_destroy(None)
+
+
+def _tri_set(tris):
+    return {tuple(sorted(t)) for t in np.asarray(tris).tolist()}
+
+
+@pytest.mark.parametrize("seed,M", [(0, 3), (1, 10), (2, 40), (3, 300), (4, 1000)])
+def test_host_delaunay_matches_qhull(lib, seed, M):
+    """The library's Bowyer-Watson triangulation equals scipy's Qhull
+    Delaunay triangulation (general position: the triangulation is unique)."""
+    from scipy.spatial import Delaunay
+    from paper_2003_11076_gb300 import lf
+    rng = np.random.default_rng(seed)
+    pts = np.stack([rng.uniform(0, 960, M), rng.uniform(0, 600, M), rng.uniform(0, 60, M)], 1).astype(np.float32)
+    got = lf.triangulate(pts)
+    ref = Delaunay(pts[:, :2].astype(np.float64)).simplices
+    assert _tri_set(got) == _tri_set(ref)
+    # counter-clockwise
+    a, b, c = pts[got[:, 0], :2], pts[got[:, 1], :2], pts[got[:, 2], :2]
+    area = (b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0])
+    assert np.all(area > 0)
+
+
+def test_host_delaunay_degenerate_inputs(lib):
+    from paper_2003_11076_gb300 import lf
+    assert len(lf.triangulate(np.zeros((0, 3), np.float32))) == 0
+    assert len(lf.triangulate(np.array([[0, 0, 1], [1, 1, 1]], np.float32))) == 0
+    collinear = np.array([[0, 0, 1], [1, 1, 1], [2, 2, 1], [5, 5, 2]], np.float32)
+    assert len(lf.triangulate(collinear)) == 0
+    # repeated points keep their first occurrence; result as without repeats
+    pts = np.array([[0, 0, 1], [10, 0, 2], [0, 10, 3], [10, 0, 9], [7, 8, 4]], np.float32)
+    t = lf.triangulate(pts)
+    assert 3 not in t
+    sub = lf.triangulate(pts[[0, 1, 2, 4]])
+    remap = np.array([0, 1, 2, 4])
+    assert _tri_set(t) == _tri_set(remap[sub])
+    assert lib.lf_triangulate(None, 3, None, 0) == -1
+
+
+def test_package_never_imports_the_oracle():
+    """The product path neither imports nor links the oracle."""
+    pkg = os.path.join(ROOT, "paper_2003_11076_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle", src, re.M), f
+                assert "lf_oracle" not in src and "orc_" not in src, f

@@ -1,0 +1,245 @@
+"""GPU parity: the sm_103a path (through the C ABI) against the FP64 oracle.
+
+Tolerances (stated by the workload contract): the disparity index equal on at
+least 99.9 % of the pixels and on every pixel the oracle does not excuse
+(an arg-max or initial-threshold margin below 1e-4 * (1 + |J|) resp. 1e-5),
+refocused intensities within 1e-3 absolute on [0, 1] and posteriors within
+1e-4, on the pixels where disparity and labels agree.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2003_11076_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+D_FRAC = 0.999
+POST_TOL = 1e-4
+REF_TOL = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2003_11076_gb300 import build
+    build.build()
+    O.build()
+
+
+def _lf():
+    from paper_2003_11076_gb300 import lf
+    return lf
+
+
+def params_pair(**kw):
+    """The same model constants for both sides (the oracle gets the float32
+    values the library uses, widened to double)."""
+    lf = _lf()
+    gp = lf.default_params(**kw)
+    op = O.Params(beta=float(np.float32(gp.beta)), gamma=float(np.float32(gp.gamma)),
+                  sigma=float(np.float32(gp.sigma)), seg_threshold=float(np.float32(gp.seg_threshold)),
+                  eps=float(np.float32(gp.eps)), mstep_seg_term=int(gp.mstep_seg_term))
+    return gp, op
+
+
+def check_parity(g, o, rows=None, what=""):
+    sl = slice(None) if rows is None else rows
+    gd, od = g["d_idx"][sl], o["d_idx"][sl]
+    exc = O.excused({k: (v[:, sl] if k in ("m_margin", "e_margin", "J_t") else v[sl])
+                     for k, v in o.items() if k in ("m_margin", "e_margin", "J_t", "init_margin")})
+    same = gd == od
+    frac = same.mean()
+    assert frac >= D_FRAC, f"{what}: disparity agreement {frac:.5f}"
+    bad = ~same & ~exc
+    assert not bad.any(), f"{what}: {bad.sum()} non-excused disparity mismatches at {np.argwhere(bad)[:5]}"
+    gl, ol = g["labels"][sl].astype(np.int64), o["labels"][sl].astype(np.int64)
+    agree = same & (gl == ol)
+    badl = ~agree & ~exc
+    assert not badl.any(), f"{what}: {badl.sum()} non-excused label mismatches"
+    assert agree.mean() >= D_FRAC - 0.002
+    if "post" in g:
+        err = np.abs(g["post"][:, sl] - o["post"][:, sl])[:, agree]
+        assert err.size == 0 or err.max() <= POST_TOL, f"{what}: posterior err {err.max()}"
+    if "refocus" in g:
+        err = np.abs(g["refocus"][sl] - o["refocus"][sl])[agree]
+        assert err.size == 0 or err.max() <= REF_TOL, f"{what}: refocus err {err.max()}"
+    if "d" in g:
+        assert np.array_equal(g["d"][sl][same], o["d"][sl][same].astype(np.float32))
+    return frac, exc.mean()
+
+
+def run_both(scene, iters=None, gp=None, op=None, **kw):
+    lf = _lf()
+    if gp is None:
+        gp, op = params_pair()
+    g = lf.run_scene(scene, params=gp, iters=iters, **kw)
+    o = O.run_scene(scene, params=op, iters=iters)
+    return g, o
+
+
+def test_small_gray_frame_matches_oracle():
+    s = scenes.small_gray(0)
+    g, o = run_both(s)
+    check_parity(g, o, what="small_gray")
+    st = g["stats"]
+    assert st["nominal_ray_samples"] == s.H * s.W * s.K * s.D * s.iters
+    assert 0 < st["executed_ray_samples"] <= st["nominal_ray_samples"]
+
+
+@pytest.mark.parametrize("frame", [1, 2, 3])
+def test_small_gray_more_frames(frame):
+    g, o = run_both(scenes.small_gray(frame))
+    check_parity(g, o, what=f"frame {frame}")
+
+
+def test_prior_raster_matches_oracle():
+    s = scenes.small_gray(0)
+    g, o = run_both(s, iters=1)
+    mu_g = g["mu"]
+    inside_g = ~np.isnan(mu_g)
+    assert np.array_equal(inside_g, o["inside"] == 1)
+    assert np.max(np.abs(mu_g[inside_g] - o["mu"][inside_g])) <= 1e-4
+
+
+@pytest.mark.parametrize("H,W", [(37, 75), (3, 3), (50, 130), (9, 257)])
+def test_ragged_sizes(H, W):
+    s = scenes.small_gray(4, H=H, W=W, M=12)
+    g, o = run_both(s)
+    check_parity(g, o, what=f"{H}x{W}")
+
+
+@pytest.mark.parametrize("baselines", [
+    [0.0], [0.0, 0.3], [-0.15, 0.0, 0.2], [-0.3, -0.2, -0.1, 0.0],
+    [-0.25, -0.15, -0.05, 0.0, 0.05, 0.15, 0.3],
+    [-0.4, -0.3, -0.2, -0.1, 0.0, 0.1, 0.2, 0.3, 0.4],
+    [-0.5, -0.4, -0.3, -0.2, -0.1, 0.0, 0.1, 0.2, 0.3, 0.4, 0.5, 0.6],
+])
+def test_camera_counts(baselines):
+    s = scenes.small_gray(5, H=24, W=48, baselines=baselines, D=16, iters=4, M=15)
+    g, o = run_both(s)
+    check_parity(g, o, what=f"K={len(baselines)}")
+
+
+@pytest.mark.parametrize("D", [1, 2, 7])
+def test_small_D(D):
+    s = scenes.small_gray(6, D=D)
+    g, o = run_both(s)
+    check_parity(g, o, what=f"D={D}")
+
+
+def test_fractional_disparity_range():
+    """Non-integral candidates d_j = d_min + j (d_max - d_min) / (D - 1)."""
+    s = scenes.small_gray(7)
+    s.d_min, s.d_max, s.D = 1.5, 23.25, 40
+    g, o = run_both(s)
+    check_parity(g, o, what="fractional d")
+
+
+def test_rgb_uint8_frame():
+    s = scenes.street_rgb(0, H=80, W=120, D=32, iters=6, M=40)
+    g, o = run_both(s)
+    check_parity(g, o, what="rgb")
+
+
+def test_median_filter():
+    gp, op = params_pair(median=1)
+    s = scenes.small_gray(8)
+    g, o = run_both(s, gp=gp, op=op)
+    ref = O.median3(O.run_scene(s, params=op)["refocus"])
+    gl, ol = g["labels"], o["labels"]
+    ok = (g["d_idx"] == o["d_idx"]) & (gl == ol)
+    # a median output depends on its 3x3 neighbourhood: compare where all agree
+    from scipy import ndimage
+    ok3 = ndimage.minimum_filter(ok.astype(np.uint8), size=3, mode="nearest") == 1
+    assert ok3.mean() > 0.95
+    assert np.max(np.abs(g["refocus"][ok3] - ref[ok3])) <= REF_TOL
+
+
+def test_literal_mstep_energy():
+    gp, op = params_pair(mstep_seg_term=0)
+    g, o = run_both(scenes.small_gray(9), gp=gp, op=op)
+    check_parity(g, o, what="mstep_seg_term=0")
+
+
+def test_early_exit_is_exact():
+    lf = _lf()
+    s = scenes.small_gray(10)
+    a = lf.run_scene(s, params=lf.default_params(early_exit=1), iters=8)
+    b = lf.run_scene(s, params=lf.default_params(early_exit=0), iters=8)
+    for k in ("d_idx", "labels", "post", "refocus"):
+        assert np.array_equal(a[k], b[k]), k
+    assert a["stats"]["executed_ray_samples"] < b["stats"]["executed_ray_samples"]
+    assert b["stats"]["executed_ray_samples"] == b["stats"]["nominal_ray_samples"]
+
+
+def test_device_io_equals_host_io():
+    import torch
+    lf = _lf()
+    s = scenes.small_gray(11)
+    host = lf.run_scene(s)
+    with lf.Context(s.baselines, s.H, s.W, s.d_min, s.d_max, s.D) as ctx:
+        ctx.set_stream(torch.cuda.current_stream())
+        ctx.set_inputs(torch.from_numpy(s.images).cuda(), torch.from_numpy(s.seg_prior).cuda(), s.points)
+        out = ctx.run(s.iters, device=True)
+        torch.cuda.synchronize()
+        ctx.synchronize()
+    assert np.array_equal(out["d_idx"].cpu().numpy(), host["d_idx"])
+    assert np.array_equal(out["post"].cpu().numpy(), host["post"])
+    assert np.array_equal(out["refocus"].cpu().numpy(), host["refocus"])
+    assert np.array_equal(out["labels"].cpu().numpy().astype(np.uint16), host["labels"])
+
+
+def test_unaligned_device_inputs_are_staged():
+    """W * bytes-per-pixel not a multiple of 16 forces the library to copy the
+    borrowed device buffers into its pitched staging; results are the same."""
+    import torch
+    lf = _lf()
+    s = scenes.small_gray(12, W=61, H=33, M=15)
+    host = lf.run_scene(s)
+    with lf.Context(s.baselines, s.H, s.W, s.d_min, s.d_max, s.D) as ctx:
+        ctx.set_stream(torch.cuda.current_stream())
+        ctx.set_inputs(torch.from_numpy(s.images).cuda(), torch.from_numpy(s.seg_prior).cuda(), s.points)
+        out = ctx.run(s.iters, device=True)
+        ctx.synchronize()
+    assert np.array_equal(out["d_idx"].cpu().numpy(), host["d_idx"])
+
+
+def test_context_reuse_across_frames():
+    lf = _lf()
+    s0, s1 = scenes.small_gray(13), scenes.small_gray(14)
+    with lf.Context(s0.baselines, s0.H, s0.W, s0.d_min, s0.d_max, s0.D) as ctx:
+        for s in (s0, s1, s0):
+            ctx.set_inputs(s.images, s.seg_prior, s.points)
+            out = ctx.run(s.iters)
+            ref = lf.run_scene(s)
+            assert np.array_equal(out["d_idx"], ref["d_idx"])
+
+
+def test_call_order_and_argument_errors():
+    lf = _lf()
+    s = scenes.small_gray(0)
+    with lf.Context(s.baselines, s.H, s.W, s.d_min, s.d_max, s.D) as ctx:
+        with pytest.raises(lf.LfError) as e:
+            ctx.C = 1
+            ctx.run(3)
+        assert e.value.status == lf.LF_ESTATE
+        ctx.set_inputs(s.images, s.seg_prior, s.points)
+        with pytest.raises(lf.LfError) as e:
+            ctx.run(0)
+        assert e.value.status == lf.LF_EINVAL
+
+
+def test_street_rgb_full_size_sampled_rows():
+    """The 960x600 RGB frame in the benchmark's launch configuration; the
+    oracle checks row bands at the top, middle and bottom."""
+    lf = _lf()
+    s = scenes.street_rgb(0)
+    gp, op = params_pair()
+    g = lf.run_scene(s, params=gp)
+    for r0, r1 in ((0, 3), (299, 302), (597, 600)):
+        o = O.run_scene(s, params=op, rows=(r0, r1))
+        check_parity(g, o, rows=slice(r0, r1), what=f"street rows {r0}-{r1}")
+    post = g["post"]
+    assert np.all((post >= 0) & (post <= 1))
