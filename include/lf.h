@@ -85,15 +85,17 @@ typedef struct lf_params {
                             reached an EM fixed point (results are identical) */
 } lf_params;
 
-/* Statistics of the last completed lf_run_em (valid after the stream synced). */
+/* Statistics accumulated over the lf_run_em calls since the previous
+ * lf_get_stats (which resets them). */
 typedef struct lf_stats {
-    uint64_t nominal_ray_samples;  /* H * W * K * D * iters */
-    uint64_t executed_ray_samples; /* pixel-sweeps actually run x K x D */
+    uint64_t runs;                 /* lf_run_em calls covered */
+    uint64_t nominal_ray_samples;  /* H * W * K * D * iters of the last run */
+    uint64_t executed_ray_samples; /* sum over the runs: pixel-sweeps run x K x D */
     int halo_left, halo_right;     /* staged column halo, pixels */
     int tile_rows, tile_cols;      /* sweep tile shape */
     int kernels_launched;          /* kernels one lf_run_em enqueues */
-    float ms_prior, ms_sweep, ms_refocus, ms_median; /* device times of the last
-                                      run's kernels (lf_set_timing on), else 0 */
+    float ms_prior, ms_sweep, ms_refocus, ms_median; /* mean device time per run
+                                      of each kernel (lf_set_timing on), else 0 */
 } lf_stats;
 
 /* Fill *p with the documented defaults. */
@@ -170,11 +172,12 @@ lf_status lf_synchronize(lf_ctx *ctx);
 lf_status lf_get_prior(lf_ctx *ctx, float *mu, int on_device);
 
 /* 1: record CUDA events on the context's stream around every kernel that
- * lf_run_em enqueues, so that lf_get_stats reports their device times; 0 (the
- * default): no events. */
+ * lf_run_em enqueues, so that lf_get_stats reports their mean device times
+ * over the runs it covers; 0 (the default): no events. */
 lf_status lf_set_timing(lf_ctx *ctx, int enable);
 
-/* Statistics of the last run; synchronises the stream. */
+/* Statistics of the runs since the previous call (then reset); synchronises
+ * the stream. */
 lf_status lf_get_stats(lf_ctx *ctx, lf_stats *out);
 
 /* One-line description of the calling thread's last error ("" if none).

@@ -3,20 +3,25 @@
 // in ELAS).  Host code, double precision, compiled without FP contraction so
 // that every machine rounds the predicates identically.
 //
-// Algorithm: Bowyer-Watson incremental insertion.  The unbounded outside of
-// the current hull is covered by "ghost" triangles that share a symbolic
-// vertex at infinity, so no finite super-triangle (and none of its precision
-// trouble near the hull) is needed:
+// Algorithm: Bowyer-Watson incremental insertion over a triangle mesh with
+// neighbour links.  The unbounded outside of the current hull is covered by
+// "ghost" triangles sharing a symbolic vertex at infinity, so no finite
+// super-triangle (and none of its precision trouble near the hull) is needed:
 //   * a finite triangle (a, b, c), counter-clockwise, conflicts with p when p
 //     lies strictly inside its circumcircle;
 //   * a ghost triangle (a, b, inf) -- hull edge a->b with the outside on its
 //     left -- conflicts with p when p is strictly left of a->b, or on the
 //     line a-b strictly between a and b.
-// Inserting p deletes every conflicting triangle and fans the boundary of the
-// deleted cavity to p.  Points are inserted in input order; repeated (x, y)
-// are skipped.  With points in general position the result is the unique
-// Delaunay triangulation.
+// Each point is located by a visibility walk from the last inserted
+// triangle (points are inserted in Morton order of their coordinates, so the
+// walks are short); the conflict cavity is grown from the located triangle
+// by breadth-first search over neighbours (it is connected), deleted, and its
+// boundary fanned to the new point.  Repeated (x, y) keep their first
+// occurrence.  With points in general position the result is the unique
+// Delaunay triangulation, independent of the insertion order.
+#include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <vector>
 
 #include "lf_internal.h"
@@ -27,7 +32,9 @@ namespace {
 constexpr int kInf = -1;
 
 struct Tri {
-  int v[3];
+  int v[3];   // counter-clockwise; a ghost has kInf in slot 2
+  int nb[3];  // nb[i]: the triangle across the edge opposite v[i]
+  bool dead;
 };
 
 inline double orient(const double* P, int a, int b, int c) {
@@ -58,7 +65,6 @@ bool conflicts(const double* P, const Tri& t, int p) {
   const double o = orient(P, a, b, p);
   if (o > 0.0) return true;
   if (o < 0.0) return false;
-  // collinear with the hull edge: conflict when strictly inside the segment
   const double ax = P[2 * a], ay = P[2 * a + 1], bx = P[2 * b], by = P[2 * b + 1];
   const double px = P[2 * p], py = P[2 * p + 1];
   const double t0 = (px - ax) * (bx - ax) + (py - ay) * (by - ay);
@@ -66,89 +72,258 @@ bool conflicts(const double* P, const Tri& t, int p) {
   return t0 > 0.0 && t0 < len;
 }
 
-// Rotate so that a symbolic vertex, if any, sits in slot 2 (cyclic order kept).
-Tri make_tri(int a, int b, int c) {
-  if (a == kInf) return Tri{{b, c, a}};
-  if (b == kInf) return Tri{{c, a, b}};
-  return Tri{{a, b, c}};
+uint32_t spread16(uint32_t x) {
+  x &= 0xffffu;
+  x = (x | (x << 8)) & 0x00ff00ffu;
+  x = (x | (x << 4)) & 0x0f0f0f0fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  return x;
 }
+
+class Mesh {
+ public:
+  explicit Mesh(const double* P) : P_(P) {}
+
+  void seed(int a, int b, int c) {
+    // finite (a, b, c) ccw plus three ghosts on its outside
+    tris_.clear();
+    tris_.push_back(Tri{{a, b, c}, {-1, -1, -1}, false});      // 0
+    tris_.push_back(Tri{{b, a, kInf}, {-1, -1, -1}, false});   // 1: across edge a-b
+    tris_.push_back(Tri{{c, b, kInf}, {-1, -1, -1}, false});   // 2: across edge b-c
+    tris_.push_back(Tri{{a, c, kInf}, {-1, -1, -1}, false});   // 3: across edge c-a
+    link_all();
+    last_ = 0;
+  }
+
+  // Insert point p; returns false when p could not be placed (not expected).
+  bool insert(int p) {
+    const int t = locate(p);
+    if (t < 0) return false;
+    // grow the conflict cavity by breadth-first search from t
+    cavity_.clear();
+    next_stamp();
+    mark(t);
+    cavity_.push_back(t);
+    for (size_t q = 0; q < cavity_.size(); ++q) {
+      const int u = cavity_[q];
+      for (int i = 0; i < 3; ++i) {
+        const int n = tris_[u].nb[i];
+        if (n < 0 || marked(n)) continue;
+        mark(n);
+        if (conflicts(P_, tris_[n], p)) cavity_.push_back(n);
+      }
+    }
+    for (int u : cavity_) tris_[u].dead = true;
+    // boundary of the cavity: edge (a -> b) of a dead triangle whose
+    // neighbour across it survives
+    bedges_.clear();
+    for (int u : cavity_)
+      for (int i = 0; i < 3; ++i) {
+        const int n = tris_[u].nb[i];
+        if (n >= 0 && tris_[n].dead) continue;
+        bedges_.push_back(Edge{tris_[u].v[(i + 1) % 3], tris_[u].v[(i + 2) % 3], n});
+      }
+    // fan the boundary to p: triangle (a, b, p), rotated so that a symbolic
+    // vertex sits in slot 2; dead slots are reused
+    made_.clear();
+    size_t reuse = 0;
+    for (const Edge& e : bedges_) {
+      int slot;
+      if (reuse < cavity_.size()) {
+        slot = cavity_[reuse++];
+      } else {
+        slot = static_cast<int>(tris_.size());
+        tris_.push_back(Tri{});
+      }
+      Tri& T = tris_[slot];
+      if (e.a == kInf) { T.v[0] = e.b; T.v[1] = p; T.v[2] = kInf; }
+      else if (e.b == kInf) { T.v[0] = p; T.v[1] = e.a; T.v[2] = kInf; }
+      else { T.v[0] = e.a; T.v[1] = e.b; T.v[2] = p; }
+      T.nb[0] = T.nb[1] = T.nb[2] = -1;
+      T.dead = false;
+      set_nb_across(slot, e.a, e.b, e.out);
+      if (e.out >= 0) set_nb_across(e.out, e.a, e.b, slot);
+      made_.push_back(slot);
+    }
+    link_fan(p);
+    last_ = made_.empty() ? last_ : made_.back();
+    return true;
+  }
+
+  int write(int* out, int max_tris) const {
+    int m = 0;
+    for (const Tri& t : tris_) {
+      if (t.dead || t.v[2] == kInf) continue;
+      if (out && m < max_tris) {
+        out[3 * m] = t.v[0];
+        out[3 * m + 1] = t.v[1];
+        out[3 * m + 2] = t.v[2];
+      }
+      ++m;
+    }
+    return m;
+  }
+
+ private:
+  struct Edge {
+    int a, b, out;
+  };
+
+  const double* P_;
+  std::vector<Tri> tris_;
+  std::vector<int> cavity_, made_;
+  std::vector<Edge> bedges_;
+  std::vector<uint32_t> mark_;
+  uint32_t stamp_ = 0;
+  int last_ = 0;
+
+  void next_stamp() {
+    if (mark_.size() < tris_.size()) mark_.resize(tris_.size() + 64, 0u);
+    if (++stamp_ == 0) {
+      std::fill(mark_.begin(), mark_.end(), 0u);
+      stamp_ = 1;
+    }
+  }
+  void mark(int t) {
+    if (static_cast<size_t>(t) >= mark_.size()) mark_.resize(tris_.size() + 64, 0u);
+    mark_[t] = stamp_;
+  }
+  bool marked(int t) const { return static_cast<size_t>(t) < mark_.size() && mark_[t] == stamp_; }
+
+  // edge (a -> b) of triangle t: slot i with v[i+1] == a, v[i+2] == b
+  static int edge_slot(const Tri& T, int a, int b) {
+    for (int i = 0; i < 3; ++i)
+      if (T.v[(i + 1) % 3] == a && T.v[(i + 2) % 3] == b) return i;
+    return -1;
+  }
+
+  // in triangle t, the neighbour across its edge with endpoints {a, b}
+  void set_nb_across(int t, int a, int b, int n) {
+    Tri& T = tris_[t];
+    int i = edge_slot(T, a, b);
+    if (i < 0) i = edge_slot(T, b, a);
+    if (i >= 0) T.nb[i] = n;
+  }
+
+  void link_all() {
+    for (size_t t = 0; t < tris_.size(); ++t)
+      for (int i = 0; i < 3; ++i) {
+        const int a = tris_[t].v[(i + 1) % 3], b = tris_[t].v[(i + 2) % 3];
+        for (size_t s = 0; s < tris_.size(); ++s) {
+          if (s == t) continue;
+          if (edge_slot(tris_[s], b, a) >= 0) { tris_[t].nb[i] = static_cast<int>(s); break; }
+        }
+      }
+  }
+
+  // The new triangle made from boundary edge (a_i -> b_i) meets, across its
+  // edge (b_i, p), the new triangle whose boundary edge starts at b_i.
+  void link_fan(int p) {
+    const size_t m = made_.size();
+    for (size_t i = 0; i < m; ++i) {
+      const int bi = bedges_[i].b;
+      for (size_t j = 0; j < m; ++j) {
+        if (j == i || bedges_[j].a != bi) continue;
+        set_nb_across(made_[i], bi, p, made_[j]);
+        set_nb_across(made_[j], bi, p, made_[i]);
+        break;
+      }
+    }
+  }
+
+  int find_alive_from(size_t hint) const {
+    for (size_t t = std::min(hint, tris_.size() - 1) + 1; t-- > 0;)
+      if (!tris_[t].dead) return static_cast<int>(t);
+    return 0;
+  }
+
+  // Visibility walk to a triangle in conflict with p (a finite triangle
+  // containing p, or a ghost whose hull edge sees p); linear scan fallback.
+  int locate(int p) {
+    int t = (last_ >= 0 && static_cast<size_t>(last_) < tris_.size() && !tris_[last_].dead) ? last_
+                                                                                            : find_alive_from(tris_.size());
+    const int limit = 4 * static_cast<int>(tris_.size()) + 16;
+    for (int step = 0; step < limit; ++step) {
+      const Tri& T = tris_[t];
+      if (T.v[2] == kInf) {
+        if (conflicts(P_, T, p)) return t;
+        // step into the finite triangle across the hull edge
+        t = T.nb[2];
+        if (t < 0) break;
+        continue;
+      }
+      int next = -1;
+      const int start = step % 3;
+      for (int r = 0; r < 3; ++r) {
+        const int i = (start + r) % 3;
+        const int a = T.v[(i + 1) % 3], b = T.v[(i + 2) % 3];
+        if (orient(P_, a, b, p) < 0.0) { next = T.nb[i]; break; }
+      }
+      if (next < 0) return conflicts(P_, T, p) ? t : scan(p);
+      t = next;
+    }
+    return scan(p);
+  }
+
+  int scan(int p) const {
+    for (size_t t = 0; t < tris_.size(); ++t)
+      if (!tris_[t].dead && conflicts(P_, tris_[t], p)) return static_cast<int>(t);
+    return -1;
+  }
+};
 
 }  // namespace
 
 int delaunay(const double* P, int n, int* out, int max_tris) {
   if (n < 3) return 0;
-  // seed: first point, first point distinct from it, first point off their line
-  int i0 = 0, i1 = -1, i2 = -1;
-  for (int i = 1; i < n; ++i)
-    if (P[2 * i] != P[0] || P[2 * i + 1] != P[1]) { i1 = i; break; }
-  if (i1 < 0) return 0;
-  for (int i = i1 + 1; i < n; ++i)
-    if (orient(P, i0, i1, i) != 0.0) { i2 = i; break; }
-  if (i2 < 0) return 0;  // all points collinear: no triangle
-  if (orient(P, i0, i1, i2) < 0.0) { int t = i1; i1 = i2; i2 = t; }
-
-  std::vector<Tri> tris;
-  tris.reserve(static_cast<size_t>(2 * n + 8));
-  tris.push_back(Tri{{i0, i1, i2}});
-  tris.push_back(Tri{{i1, i0, kInf}});
-  tris.push_back(Tri{{i2, i1, kInf}});
-  tris.push_back(Tri{{i0, i2, kInf}});
-
-  std::vector<char> inserted(static_cast<size_t>(n), 0);
-  inserted[i0] = inserted[i1] = inserted[i2] = 1;
-  std::vector<char> bad;
-  std::vector<int> badlist;
-  std::vector<int> edges;  // boundary edges of the cavity, as (from, to) pairs
-  for (int p = 0; p < n; ++p) {
-    if (inserted[p]) continue;
-    inserted[p] = 1;
-    bool dup = false;
-    for (int q = 0; q < p && !dup; ++q)
-      if (q != p && P[2 * q] == P[2 * p] && P[2 * q + 1] == P[2 * p + 1] && inserted[q]) dup = true;
-    if (dup) continue;
-    bad.assign(tris.size(), 0);
-    badlist.clear();
-    for (size_t t = 0; t < tris.size(); ++t)
-      if (conflicts(P, tris[t], p)) { bad[t] = 1; badlist.push_back(static_cast<int>(t)); }
-    if (badlist.empty()) continue;  // cannot happen for a new distinct point; be safe
-    // cavity boundary: directed edges of bad triangles whose reverse edge is
-    // not also in a bad triangle
-    edges.clear();
-    for (int t : badlist) {
-      for (int e = 0; e < 3; ++e) {
-        const int a = tris[t].v[e], b = tris[t].v[(e + 1) % 3];
-        bool shared = false;
-        for (int s2 : badlist) {
-          if (s2 == t) continue;
-          for (int f = 0; f < 3; ++f)
-            if (tris[s2].v[f] == b && tris[s2].v[(f + 1) % 3] == a) { shared = true; break; }
-          if (shared) break;
-        }
-        if (!shared) { edges.push_back(a); edges.push_back(b); }
-      }
-    }
-    std::vector<Tri> keep;
-    keep.reserve(tris.size() + edges.size() / 2);
-    for (size_t t = 0; t < tris.size(); ++t)
-      if (!bad[t]) keep.push_back(tris[t]);
-    for (size_t e = 0; e < edges.size(); e += 2) {
-      const int a = edges[e], b = edges[e + 1];
-      if (a == kInf && b == kInf) continue;
-      keep.push_back(make_tri(a, b, p));
-    }
-    tris.swap(keep);
+  // keep the first occurrence of every (x, y)
+  std::vector<int> idx(static_cast<size_t>(n));
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+    if (P[2 * a] != P[2 * b]) return P[2 * a] < P[2 * b];
+    return P[2 * a + 1] < P[2 * b + 1];
+  });
+  std::vector<int> keep;
+  keep.reserve(idx.size());
+  for (size_t i = 0; i < idx.size(); ++i) {
+    if (i > 0 && P[2 * idx[i]] == P[2 * idx[i - 1]] && P[2 * idx[i] + 1] == P[2 * idx[i - 1] + 1]) continue;
+    keep.push_back(idx[i]);  // stable sort: the first of equal keys is the first occurrence
   }
-  int m = 0;
-  for (const Tri& t : tris) {
-    if (t.v[2] == kInf) continue;
-    if (m < max_tris && out) {
-      out[3 * m] = t.v[0];
-      out[3 * m + 1] = t.v[1];
-      out[3 * m + 2] = t.v[2];
-    }
-    ++m;
+  if (keep.size() < 3) return 0;
+  // Morton order for short walks
+  double x0 = P[2 * keep[0]], x1 = x0, y0 = P[2 * keep[0] + 1], y1 = y0;
+  for (int i : keep) {
+    x0 = std::min(x0, P[2 * i]); x1 = std::max(x1, P[2 * i]);
+    y0 = std::min(y0, P[2 * i + 1]); y1 = std::max(y1, P[2 * i + 1]);
   }
-  return m;
+  const double sx = x1 > x0 ? 65535.0 / (x1 - x0) : 0.0, sy = y1 > y0 ? 65535.0 / (y1 - y0) : 0.0;
+  std::vector<std::pair<uint32_t, int>> order;
+  order.reserve(keep.size());
+  for (int i : keep) {
+    const uint32_t qx = static_cast<uint32_t>((P[2 * i] - x0) * sx);
+    const uint32_t qy = static_cast<uint32_t>((P[2 * i + 1] - y0) * sy);
+    order.emplace_back(spread16(qx) | (spread16(qy) << 1), i);
+  }
+  std::sort(order.begin(), order.end());
+  std::vector<int> pts;
+  pts.reserve(order.size());
+  for (auto& o : order) pts.push_back(o.second);
+  // seed: first point, next point, first point off their line
+  const int a = pts[0], b = pts[1];
+  int c = -1;
+  size_t ci = 0;
+  for (size_t i = 2; i < pts.size(); ++i)
+    if (orient(P, a, b, pts[i]) != 0.0) { c = pts[i]; ci = i; break; }
+  if (c < 0) return 0;  // all points collinear
+  Mesh mesh(P);
+  if (orient(P, a, b, c) > 0.0) mesh.seed(a, b, c);
+  else mesh.seed(a, c, b);
+  for (size_t i = 2; i < pts.size(); ++i) {
+    if (i == ci) continue;
+    mesh.insert(pts[i]);
+  }
+  return mesh.write(out, max_tris);
 }
 
 }  // namespace lf

@@ -512,9 +512,13 @@ template <int K>
 cudaError_t launch_em_sweep_k(const CUtensorMap& img_map, const CUtensorMap& p_map, const SweepArgs& a,
                               cudaStream_t s) {
   const size_t smem = sweep_layout(K, a).total;
-  cudaError_t e = cudaFuncSetAttribute(em_sweep_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
-  if (e != cudaSuccess) return e;
+  static int configured = -1;  // largest dynamic shared size set so far (per process)
+  if (static_cast<int>(smem) > configured) {
+    cudaError_t e = cudaFuncSetAttribute(em_sweep_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    configured = static_cast<int>(smem);
+  }
   dim3 grid((a.W + a.TW - 1) / a.TW, (a.H + a.TR - 1) / a.TR);
   em_sweep_kernel<K><<<grid, a.TR * a.TW, smem, s>>>(img_map, p_map, a);
   return cudaGetLastError();

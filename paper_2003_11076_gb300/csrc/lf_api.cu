@@ -157,10 +157,16 @@ struct lf_ctx {
   // tiles
   int TR = 2, TW = 128, SW = 0, SWp = 0, RW = 0;
   lf_stats stats{};
-  // optional per-kernel timing: events before prior, sweep, refocus, median, after
+  // optional per-kernel timing: per run, events before prior, sweep, refocus,
+  // median and after; summed by lf_get_stats
   bool timing = false;
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  bool ev_used[5] = {false, false, false, false, false};
+  struct RunEvents {
+    cudaEvent_t ev[5];
+    bool used[5];
+  };
+  std::vector<RunEvents> events;
+  size_t events_used = 0;
+  uint64_t runs = 0;
 };
 
 namespace {
@@ -426,6 +432,9 @@ lf_status lf_create(lf_ctx** out, int n_cams, const float* baselines, int H, int
   cap = 0;
   if ((s = grow(&c->d_status, &cap, 1, "status")) != LF_OK) return bail(s);
   cudaError_t e;
+  if ((e = cudaMemset(c->d_counter, 0, sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMemset(c->d_status, 0, sizeof(unsigned))) != cudaSuccess)
+    return bail(cuda_fail(e, "counter init"));
   if ((e = cudaMemcpy(c->d_wtab, c->wtab.data(), c->wtab.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(c->d_otab, c->otab.data(), c->otab.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(c->d_chg, c->chg.data(), c->chg.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -531,18 +540,25 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
     refo_stage = c->o_tmp;
   }
   int launched = 0;
-  for (bool& u : c->ev_used) u = false;
+  lf_ctx::RunEvents* re = nullptr;
+  if (c->timing) {
+    if (c->events_used == c->events.size()) {
+      lf_ctx::RunEvents fresh{};
+      for (cudaEvent_t& e : fresh.ev) LF_CUDA(cudaEventCreate(&e), "event create");
+      c->events.push_back(fresh);
+    }
+    re = &c->events[c->events_used++];
+    for (bool& u : re->used) u = false;
+  }
   auto mark = [&](int i) -> cudaError_t {
-    if (!c->timing) return cudaSuccess;
-    c->ev_used[i] = true;
-    return cudaEventRecord(c->ev[i], c->stream);
+    if (!re) return cudaSuccess;
+    re->used[i] = true;
+    return cudaEventRecord(re->ev[i], c->stream);
   };
   LF_CUDA(mark(0), "event");
   PriorArgs pa{c->H, c->W, c->nbx, c->nby, c->d_tris, c->d_bins, c->d_bins + (c->nbx * c->nby + 1), c->d_mu};
   LF_CUDA(launch_prior_raster(pa, c->stream), "prior_raster launch");
   ++launched;
-  LF_CUDA(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream), "memset");
-  LF_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream), "memset");
   LF_CUDA(mark(1), "event");
   SweepArgs a{};
   a.H = c->H; a.W = c->W; a.C = c->C; a.D = c->D; a.ref = c->ref; a.dtype = c->dtype; a.bpp = c->bpp;
@@ -573,6 +589,7 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
       LF_CUDA(mark(4), "event");
     }
   }
+  ++c->runs;
   c->stats.nominal_ray_samples = static_cast<uint64_t>(HW) * c->K * c->D * iters;
   c->stats.halo_left = c->L;
   c->stats.halo_right = c->R;
@@ -596,6 +613,7 @@ lf_status lf_synchronize(lf_ctx* c) {
   LF_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
   unsigned st = 0;
   LF_CUDA(cudaMemcpy(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost), "status read");
+  if (st) LF_CUDA(cudaMemset(c->d_status, 0, sizeof(st)), "status reset");
   if (st & kStatusTmaTimeout) return fail(LF_ETIMEOUT, "a bounded TMA wait in the sweep kernel expired");
   if (st & kStatusSmemMisaligned) return fail(LF_ECUDA, "sweep kernel: dynamic shared memory not 128-byte aligned");
   return LF_OK;
@@ -615,8 +633,6 @@ lf_status lf_get_prior(lf_ctx* c, float* mu, int on_device) {
 lf_status lf_set_timing(lf_ctx* c, int enable) {
   g_err.clear();
   if (!c) return fail(LF_EINVAL, "ctx is NULL");
-  if (enable && !c->ev[0])
-    for (cudaEvent_t& e : c->ev) LF_CUDA(cudaEventCreate(&e), "event create");
   c->timing = enable != 0;
   return LF_OK;
 }
@@ -627,13 +643,24 @@ lf_status lf_get_stats(lf_ctx* c, lf_stats* out) {
   LF_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
   unsigned long long n = 0;
   LF_CUDA(cudaMemcpy(&n, c->d_counter, sizeof(n), cudaMemcpyDeviceToHost), "counter read");
+  LF_CUDA(cudaMemset(c->d_counter, 0, sizeof(n)), "counter reset");
+  c->stats.runs = c->runs;
   c->stats.executed_ray_samples = static_cast<uint64_t>(n) * c->K * c->D;
   float* ms[4] = {&c->stats.ms_prior, &c->stats.ms_sweep, &c->stats.ms_refocus, &c->stats.ms_median};
   for (int i = 0; i < 4; ++i) {
-    *ms[i] = 0.f;
-    if (c->ev_used[i] && c->ev_used[i + 1]) LF_CUDA(cudaEventElapsedTime(ms[i], c->ev[i], c->ev[i + 1]), "event time");
+    double acc = 0.0;
+    for (size_t r = 0; r < c->events_used; ++r) {
+      const lf_ctx::RunEvents& e = c->events[r];
+      if (!e.used[i] || !e.used[i + 1]) continue;
+      float t = 0.f;
+      LF_CUDA(cudaEventElapsedTime(&t, e.ev[i], e.ev[i + 1]), "event time");
+      acc += t;
+    }
+    *ms[i] = c->events_used ? static_cast<float>(acc / c->events_used) : 0.f;
   }
   *out = c->stats;
+  c->events_used = 0;
+  c->runs = 0;
   return LF_OK;
 }
 
@@ -645,8 +672,9 @@ void lf_destroy(lf_ctx* c) {
                   c->o_post, c->o_ref, c->o_tmp};
   for (void* p : bufs)
     if (p) cudaFree(p);
-  for (cudaEvent_t e : c->ev)
-    if (e) cudaEventDestroy(e);
+  for (auto& re : c->events)
+    for (cudaEvent_t e : re.ev)
+      if (e) cudaEventDestroy(e);
   delete c;
 }
 

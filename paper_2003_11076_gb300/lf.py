@@ -39,7 +39,8 @@ class Params(ctypes.Structure):
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [("nominal_ray_samples", ctypes.c_uint64), ("executed_ray_samples", ctypes.c_uint64),
+    _fields_ = [("runs", ctypes.c_uint64), ("nominal_ray_samples", ctypes.c_uint64),
+                ("executed_ray_samples", ctypes.c_uint64),
                 ("halo_left", ctypes.c_int), ("halo_right", ctypes.c_int),
                 ("tile_rows", ctypes.c_int), ("tile_cols", ctypes.c_int),
                 ("kernels_launched", ctypes.c_int),

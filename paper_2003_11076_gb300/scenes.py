@@ -348,7 +348,9 @@ def street_rgb(frame: int = 0, *, H: int = 600, W: int = 960, baselines=None, D:
 
     # three fronto-parallel depth planes: far wall, a mid-depth side wall and a
     # near low structure (bench / railing), all static.
-    d_far, d_mid, d_near = 6.0 + 4.0 * rng.random(), 14.0 + 6.0 * rng.random(), 24.0 + 6.0 * rng.random()
+    sc = dmax / 63.0
+    d_far, d_mid, d_near = sc * (6.0 + 4.0 * rng.random()), sc * (14.0 + 6.0 * rng.random()), \
+        sc * (24.0 + 6.0 * rng.random())
     surfaces = [
         Surface(d_far, None, rgb_tex((24.0, 9.0, 3.0))),
         Surface(d_mid, (-1e9, -1e9, 0.3 * W, 1e9), rgb_tex((16.0, 6.0, 2.0))),
@@ -364,7 +366,7 @@ def street_rgb(frame: int = 0, *, H: int = 600, W: int = 960, baselines=None, D:
             bw = int(bh * rng.uniform(0.28, 0.42))
             u0 = int(rng.uniform(0.02 * W, W - bw - 0.02 * W))
             v0 = int(rng.uniform(0.05 * H, H - bh))
-            d = float(rng.uniform(34.0, 0.92 * dmax))
+            d = float(rng.uniform(0.54 * dmax, 0.92 * dmax))
             boxes.append((u0, v0, u0 + bw, v0 + bh, d))
             cover[v0:v0 + bh, u0:u0 + bw] = True
         frac = cover.mean()
