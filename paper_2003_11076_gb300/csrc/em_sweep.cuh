@@ -91,11 +91,35 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// Staged maps per camera and tile row: luminance, Sobel-x/8, Sobel-y/8,
+// log p(static) = log max(1-P, eps), log p(dynamic) = log max(P, eps), and
+// their difference Z = log p(dynamic) - log p(static) (first-iteration test).
+constexpr int kMapY = 0, kMapSx = 1, kMapSy = 2, kMapLs = 3, kMapLd = 4, kMapZ = 5, kMaps = 6;
+
+// First-iteration labels are decided on lerp(Z) < log(thr / (1 - thr)).  A
+// camera whose Z texels over the pixel's whole sample range stay at least
+// this far on one side of the threshold has the same label for every
+// candidate (the interpolated value cannot leave [min, max] by more than a
+// few units of float32 rounding, far below this margin).
+constexpr float kThresholdMargin = 1e-4f;
+
 __host__ __device__ inline size_t align_up(size_t x, size_t n) { return (x + n - 1) / n * n; }
 
 // Shared-memory carve-up, identical on host (size) and device (offsets).
 struct SmemLayout {
-  size_t raw_img, raw_p, luma, feat, wtab, otab, chg, dval, rcp, bar, total;
+  size_t raw_img, raw_p, luma, feat, wtab, otab, chg, dval, rcp, pix, wcnt, bar, total;
+};
+
+// Per-pixel EM state of one tile, kept in shared memory between iterations
+// so that the unconverged pixels can be regrouped into dense warps.
+struct PixelState {
+  int16_t* list;    // pixel indices (tile order) to process in the current pass
+  uint16_t* S;      // current labels
+  uint16_t* S0;     // first-iteration labels when they do not depend on d
+  int16_t* jb;      // current arg-max candidate
+  float* emax;      // objective of the current labels at jb
+  uint8_t* fixed0;  // S0 valid
+  uint8_t* conv;    // reached its fixed point
 };
 
 __host__ __device__ inline SmemLayout sweep_layout(int K, const SweepArgs& a) {
@@ -108,7 +132,7 @@ __host__ __device__ inline SmemLayout sweep_layout(int K, const SweepArgs& a) {
   L.luma = o;
   o = align_up(o + static_cast<size_t>(K) * (a.TR + 2) * a.RW * 4, 16);
   L.feat = o;
-  o = align_up(o + static_cast<size_t>(K) * a.TR * 5 * a.SWp * 4, 16);
+  o = align_up(o + static_cast<size_t>(K) * a.TR * kMaps * a.SWp * 4, 16);
   L.wtab = o;
   o = align_up(o + static_cast<size_t>(a.D) * a.KP * 4, 16);
   L.otab = o;
@@ -119,6 +143,10 @@ __host__ __device__ inline SmemLayout sweep_layout(int K, const SweepArgs& a) {
   o = align_up(o + static_cast<size_t>(a.D) * 4, 16);
   L.rcp = o;
   o = align_up(o + 16 * 4, 16);
+  L.pix = o;
+  o = align_up(o + static_cast<size_t>(a.TR) * a.TW * 14, 16);
+  L.wcnt = o;
+  o = align_up(o + 32 * 4, 16);
   L.bar = o;
   o = align_up(o + 8, 16);
   L.total = o;
@@ -127,9 +155,11 @@ __host__ __device__ inline SmemLayout sweep_layout(int K, const SweepArgs& a) {
 
 __device__ __forceinline__ int floor16(int x) { return x >= 0 ? (x & ~15) : -((-x + 15) & ~15); }
 
+
+
 // View of one CTA's staged descriptor maps for one thread's pixel.
 struct Staged {
-  const float* F;       // camera 0, this thread's tile row, map 0
+  const float* F;       // camera 0, this thread's tile row, map kMapY
   int cam_stride;       // floats between cameras
   int SWp;              // floats between maps
   int cbase;            // staged column of this pixel (offset 0)
@@ -144,10 +174,13 @@ __device__ __forceinline__ int m_step(const SweepArgs& a, const Staged& st, cons
                                       const int* s_o, const unsigned* s_chg, const float* s_d,
                                       const float* s_rcp, float cy, float cx, float cz, float mu,
                                       bool inside, unsigned S) {
-  float y0[K], dy[K], x0[K], dx[K], z0[K], dz[K], l0[K], dl[K], m0[K], dm[K];
+  // per camera: shifted descriptor taps (value at i0, slope to i1), the
+  // selected (or, INIT, both) log-prior taps and, INIT, the Z taps
+  float y0[K], dy[K], x0[K], dx[K], z0[K], dz[K], l0[K], dl[K], m0[K], dm[K], q0[K], dq[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    y0[k] = dy[k] = x0[k] = dx[k] = z0[k] = dz[k] = l0[k] = dl[k] = m0[k] = dm[k] = 0.f;
+    y0[k] = dy[k] = x0[k] = dx[k] = z0[k] = dz[k] = 0.f;
+    l0[k] = dl[k] = m0[k] = dm[k] = q0[k] = dq[k] = 0.f;
   }
   const int SWp = st.SWp;
   const float rn_fixed = s_rcp[__popc(S)];
@@ -181,26 +214,25 @@ __device__ __forceinline__ int m_step(const SweepArgs& a, const Staged& st, cons
           y0[k] = Y0 - cy; dy[k] = Y1 - Y0;
           x0[k] = X0 - cx; dx[k] = X1 - X0;
           z0[k] = Z0 - cz; dz[k] = Z1 - Z0;
-          l0[k] = Fk[3 * SWp + c]; dl[k] = Fk[3 * SWp + c + 1] - l0[k];
-          m0[k] = Fk[4 * SWp + c]; dm[k] = Fk[4 * SWp + c + 1] - m0[k];
+          l0[k] = Fk[kMapLs * SWp + c]; dl[k] = Fk[kMapLs * SWp + c + 1] - l0[k];
+          m0[k] = Fk[kMapLd * SWp + c]; dm[k] = Fk[kMapLd * SWp + c + 1] - m0[k];
+          q0[k] = Fk[kMapZ * SWp + c]; dq[k] = Fk[kMapZ * SWp + c + 1] - q0[k];
         } else {
           const bool stat = (S >> k) & 1u;
           const float s = stat ? 1.f : 0.f;
           y0[k] = s * (Y0 - cy); dy[k] = s * (Y1 - Y0);
           x0[k] = s * (X0 - cx); dx[k] = s * (X1 - X0);
           z0[k] = s * (Z0 - cz); dz[k] = s * (Z1 - Z0);
-          const float* Lk = Fk + (stat ? 3 : 4) * SWp;
+          const float* Lk = Fk + (stat ? kMapLs : kMapLd) * SWp;
           l0[k] = Lk[c]; dl[k] = Lk[c + 1] - l0[k];
         }
       }
       if (INIT) {
-        const float ls = fmaf(w[k], dl[k], l0[k]);
-        const float ld = fmaf(w[k], dm[k], m0[k]);
-        const bool stat = (ld - ls) < a.log_thr;
+        const bool stat = fmaf(w[k], dq[k], q0[k]) < a.log_thr;
         const float gy = stat ? fmaf(w[k], dy[k], y0[k]) : 0.f;
         const float gx = stat ? fmaf(w[k], dx[k], x0[k]) : 0.f;
         const float gz = stat ? fmaf(w[k], dz[k], z0[k]) : 0.f;
-        seg += stat ? ls : ld;
+        seg += fmaf(w[k], stat ? dl[k] : dm[k], stat ? l0[k] : m0[k]);
         n += stat ? 1 : 0;
         sy += gy; sx += gx; sz += gz;
         q = fmaf(gy, gy, q); q = fmaf(gx, gx, q); q = fmaf(gz, gz, q);
@@ -227,6 +259,30 @@ __device__ __forceinline__ int m_step(const SweepArgs& a, const Staged& st, cons
   return jb;
 }
 
+// First-iteration labels of one pixel when they are the same for every
+// candidate: bit k of *mask is camera k's label (static) and the return value
+// says whether every camera's Z texels stay clear of the threshold.
+template <int K>
+__device__ __forceinline__ bool constant_initial_labels(const SweepArgs& a, const Staged& st,
+                                                        unsigned* mask) {
+  bool all = true;
+  unsigned m = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float* Zk = st.F + k * st.cam_stride + kMapZ * st.SWp;
+    float lo = INFINITY, hi = -INFINITY;
+    for (int c = st.cbase + a.omin[k]; c <= st.cbase + a.omax[k] + 1; ++c) {
+      const float z = Zk[c];
+      lo = fminf(lo, z);
+      hi = fmaxf(hi, z);
+    }
+    if (hi < a.log_thr - kThresholdMargin) m |= 1u << k;
+    else if (!(lo >= a.log_thr + kThresholdMargin)) all = false;
+  }
+  *mask = m;
+  return all;
+}
+
 // ---------------------------------------------------------------- E-step
 struct Rays {
   // per camera: shifted descriptors, |g|^2, log p(static) - log p(dynamic)
@@ -248,8 +304,8 @@ __device__ __forceinline__ void sample_rays(const SweepArgs& a, const Staged& st
     const float Y0 = Fk[c], Y1 = Fk[c + 1];
     const float X0 = Fk[SWp + c], X1 = Fk[SWp + c + 1];
     const float Z0 = Fk[2 * SWp + c], Z1 = Fk[2 * SWp + c + 1];
-    const float S0 = Fk[3 * SWp + c], S1 = Fk[3 * SWp + c + 1];
-    const float D0 = Fk[4 * SWp + c], D1 = Fk[4 * SWp + c + 1];
+    const float S0 = Fk[kMapLs * SWp + c], S1 = Fk[kMapLs * SWp + c + 1];
+    const float D0 = Fk[kMapLd * SWp + c], D1 = Fk[kMapLd * SWp + c + 1];
     const float gy = fmaf(w, Y1 - Y0, Y0 - cy);
     const float gx = fmaf(w, X1 - X0, X0 - cx);
     const float gz = fmaf(w, Z1 - Z0, Z0 - cz);
@@ -359,9 +415,62 @@ __device__ __forceinline__ void enumerate(const Rays& r, const float* s_rcp, flo
   }
 }
 
+// ------------------------------------------------------- tile bookkeeping
+// Everything one thread needs to run the EM of pixel p of the tile.
+struct PixelCtx {
+  int u, v;
+  bool valid, inside;
+  float mu, cy, cx, cz;
+  Staged st;
+};
+
+__device__ __forceinline__ PixelCtx load_pixel(const SweepArgs& a, const float* s_feat, int u0, int v0,
+                                               int cam_stride, int p) {
+  PixelCtx c;
+  const int r = p / a.TW, tx = p - r * a.TW;
+  c.u = u0 + tx;
+  c.v = v0 + r;
+  c.valid = (c.u < a.W) && (c.v < a.H);
+  c.mu = a.mu[static_cast<size_t>(min(c.v, a.H - 1)) * a.W + min(c.u, a.W - 1)];
+  c.inside = !isnan(c.mu);
+  c.st.F = s_feat + static_cast<size_t>(r) * kMaps * a.SWp;
+  c.st.cam_stride = cam_stride;
+  c.st.SWp = a.SWp;
+  c.st.cbase = tx + a.L;
+  const float* Fr = c.st.F + a.ref * cam_stride;
+  c.cy = Fr[kMapY * a.SWp + c.st.cbase];
+  c.cx = Fr[kMapSx * a.SWp + c.st.cbase];
+  c.cz = Fr[kMapSy * a.SWp + c.st.cbase];
+  return c;
+}
+
+// Stable CTA-wide compaction: the threads (tile pixel p = threadIdx.x) with
+// pred set write p to list[base + rank]; returns how many did (every thread
+// gets the same count).  Contains two __syncthreads.
+__device__ __forceinline__ int compact(bool pred, int16_t* list, int base, int* s_wcnt) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const unsigned b = __ballot_sync(0xffffffffu, pred);
+  if (lane == 0) s_wcnt[warp] = __popc(b);
+  __syncthreads();
+  int off = 0, total = 0;
+  for (int w = 0; w < nw; ++w) {
+    const int c = s_wcnt[w];
+    off += w < warp ? c : 0;
+    total += c;
+  }
+  if (pred) list[base + off + __popc(b & ((1u << lane) - 1u))] = static_cast<int16_t>(tid);
+  __syncthreads();
+  return total;
+}
+
 // ---------------------------------------------------------------- kernel
+// Minimum resident CTAs per SM requested from the register allocator.
+#ifndef LF_SWEEP_MIN_BLOCKS
+#define LF_SWEEP_MIN_BLOCKS 1
+#endif
+
 template <int K>
-__global__ void __launch_bounds__(256) em_sweep_kernel(const __grid_constant__ CUtensorMap img_map,
+__global__ void __launch_bounds__(256, LF_SWEEP_MIN_BLOCKS) em_sweep_kernel(const __grid_constant__ CUtensorMap img_map,
                                                        const __grid_constant__ CUtensorMap p_map,
                                                        const SweepArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
@@ -432,7 +541,7 @@ __global__ void __launch_bounds__(256) em_sweep_kernel(const __grid_constant__ C
     s_luma[i] = y;
   }
   __syncthreads();
-  const int cam_stride = a.TR * 5 * a.SWp;
+  const int cam_stride = a.TR * kMaps * a.SWp;
   for (int i = tid; i < K * a.TR * a.SW; i += nthr) {
     const int c = i % a.SW;
     const int r = (i / a.SW) % a.TR;
@@ -448,64 +557,121 @@ __global__ void __launch_bounds__(256) em_sweep_kernel(const __grid_constant__ C
     const float gx = ((a02 + 2.f * a12) + a22) - ((a00 + 2.f * a10) + a20);
     const float gy = ((a20 + 2.f * a21) + a22) - ((a00 + 2.f * a01) + a02);
     const float P = s_p[(static_cast<size_t>(k) * a.TR + (V - v0)) * RW + c0];
-    float* F = s_feat + static_cast<size_t>(k) * cam_stride + static_cast<size_t>(r) * 5 * a.SWp;
-    F[c] = a11;
-    F[a.SWp + c] = gx * 0.125f;
-    F[2 * a.SWp + c] = gy * 0.125f;
-    F[3 * a.SWp + c] = logf(fmaxf(1.f - P, a.eps));
-    F[4 * a.SWp + c] = logf(fmaxf(P, a.eps));
+    float* F = s_feat + static_cast<size_t>(k) * cam_stride + static_cast<size_t>(r) * kMaps * a.SWp;
+    const float ls = logf(fmaxf(1.f - P, a.eps)), ld = logf(fmaxf(P, a.eps));
+    F[kMapY * a.SWp + c] = a11;
+    F[kMapSx * a.SWp + c] = gx * 0.125f;
+    F[kMapSy * a.SWp + c] = gy * 0.125f;
+    F[kMapLs * a.SWp + c] = ls;
+    F[kMapLd * a.SWp + c] = ld;
+    F[kMapZ * a.SWp + c] = ld - ls;
   }
   __syncthreads();
 
-  // ---- 3-5. per-pixel EM
-  const int r = tid / a.TW, tx = tid % a.TW;
-  const int u = u0 + tx, v = v0 + r;
-  const bool valid = (u < W) && (v < H);
-  const float mu = a.mu[static_cast<size_t>(min(v, H - 1)) * W + min(u, W - 1)];
-  const bool inside = !isnan(mu);
-  Staged st;
-  st.F = s_feat + static_cast<size_t>(r) * 5 * a.SWp;
-  st.cam_stride = cam_stride;
-  st.SWp = a.SWp;
-  st.cbase = tx + a.L;
-  const float* Fr = st.F + a.ref * cam_stride;
-  const float cy = Fr[st.cbase], cx = Fr[a.SWp + st.cbase], cz = Fr[2 * a.SWp + st.cbase];
+  // ---- 3-5. per-pixel EM.  The pixels still iterating are regrouped into
+  // dense warps before every pass (exact per-pixel early exit), and in the
+  // first pass the pixels whose first-iteration labels do not depend on the
+  // candidate come first, so that their warps run the ordinary M-step.
+  PixelState ps;
+  {
+    uint8_t* b = smem + Ly.pix;
+    const int P = a.TR * a.TW;
+    ps.emax = reinterpret_cast<float*>(b);
+    ps.S = reinterpret_cast<uint16_t*>(b + 4 * P);
+    ps.S0 = ps.S + P;
+    ps.jb = reinterpret_cast<int16_t*>(ps.S0 + P);
+    ps.list = ps.jb + P;
+    ps.fixed0 = reinterpret_cast<uint8_t*>(ps.list + P);
+    ps.conv = ps.fixed0 + P;
+  }
+  int* s_wcnt = reinterpret_cast<int*>(smem + Ly.wcnt);
+  const int warp = tid >> 5;
 
-  Rays rays;
-  int jb = m_step<K, true>(a, st, s_w, s_o, s_chg, s_d, s_rcp, cy, cx, cz, mu, inside, 0u);
-  sample_rays<K>(a, st, s_w, s_o, jb, cy, cx, cz, rays);
-  unsigned S = 0;
-  float emax = 0.f;
-  enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
-  int t_done = 1;
-  for (int t = 2; t <= a.iters; ++t) {
-    const unsigned Sp = S;
-    jb = m_step<K, false>(a, st, s_w, s_o, s_chg, s_d, s_rcp, cy, cx, cz, mu, inside, S);
-    sample_rays<K>(a, st, s_w, s_o, jb, cy, cx, cz, rays);
+  const bool my_valid = (u0 + tid % a.TW < W) && (v0 + tid / a.TW < H);
+  {
+    const PixelCtx me = load_pixel(a, s_feat, u0, v0, cam_stride, tid);
+    unsigned S0 = 0;
+    const bool f0 = me.valid && constant_initial_labels<K>(a, me.st, &S0);
+    ps.fixed0[tid] = f0;
+    ps.S0[tid] = static_cast<uint16_t>(S0);
+    ps.conv[tid] = 0;
+  }
+  const int nfast = compact(my_valid && ps.fixed0[tid], ps.list, 0, s_wcnt);
+  const int nact = nfast + compact(my_valid && !ps.fixed0[tid], ps.list, nfast, s_wcnt);
+  unsigned long long executed = static_cast<unsigned long long>(nact);
+
+  // t = 1
+  if (warp * 32 < nact) {
+    const bool active = tid < nact;
+    const int p = ps.list[active ? tid : nact - 1];
+    const PixelCtx c = load_pixel(a, s_feat, u0, v0, cam_stride, p);
+    const bool f0 = ps.fixed0[p];
+    const unsigned S0 = ps.S0[p];
+    const bool fast = __all_sync(0xffffffffu, f0);
+    const int jb = fast ? m_step<K, false>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, S0)
+                        : m_step<K, true>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, 0u);
+    Rays rays;
+    sample_rays<K>(a, c.st, s_w, s_o, jb, c.cy, c.cx, c.cz, rays);
+    unsigned S = 0;
+    float emax = 0.f;
     enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
-    t_done = t;
-    const bool conv = (S == Sp) || !valid;
-    if (a.early_exit && __all_sync(0xffffffffu, conv)) break;
+    if (active) {
+      ps.jb[p] = static_cast<int16_t>(jb);
+      ps.S[p] = static_cast<uint16_t>(S);
+      ps.emax[p] = emax;
+      // the second M-step would repeat the first one exactly
+      ps.conv[p] = a.early_exit && fast && S == S0;
+    }
   }
-  float post[K];
-  if (a.post) {
-    unsigned dummy;
-    float dummyf;
-    enumerate<1, K>(rays, s_rcp, a.beta, emax, dummy, dummyf, post);
+  __syncthreads();
+  // t >= 2: only the pixels not yet at their fixed point
+  for (int t = 2; t <= a.iters; ++t) {
+    const int n = compact(my_valid && !ps.conv[tid], ps.list, 0, s_wcnt);
+    if (n == 0) break;
+    executed += static_cast<unsigned long long>(n);
+    if (warp * 32 < n) {
+      const bool active = tid < n;
+      const int p = ps.list[active ? tid : n - 1];
+      const PixelCtx c = load_pixel(a, s_feat, u0, v0, cam_stride, p);
+      const unsigned Sp = ps.S[p];
+      const int jb = m_step<K, false>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, Sp);
+      Rays rays;
+      sample_rays<K>(a, c.st, s_w, s_o, jb, c.cy, c.cx, c.cz, rays);
+      unsigned S = 0;
+      float emax = 0.f;
+      enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
+      if (active) {
+        ps.jb[p] = static_cast<int16_t>(jb);
+        ps.S[p] = static_cast<uint16_t>(S);
+        ps.emax[p] = emax;
+        ps.conv[p] = a.early_exit && S == Sp;
+      }
+    }
+    __syncthreads();
   }
-  if (valid) {
-    const size_t pix = static_cast<size_t>(v) * W + u;
+
+  // posteriors and outputs, one thread per pixel
+  if (my_valid) {
+    const PixelCtx me = load_pixel(a, s_feat, u0, v0, cam_stride, tid);
+    const int jb = ps.jb[tid];
+    const unsigned S = ps.S[tid];
+    const size_t pix = static_cast<size_t>(me.v) * W + me.u;
     a.d_idx[pix] = jb;
     if (a.d_out) a.d_out[pix] = s_d[jb];
     if (a.labels) a.labels[pix] = static_cast<uint16_t>(S);
     if (a.post) {
+      Rays rays;
+      sample_rays<K>(a, me.st, s_w, s_o, jb, me.cy, me.cx, me.cz, rays);
+      float post[K];
+      unsigned dummy;
+      float dummyf;
+      enumerate<1, K>(rays, s_rcp, a.beta, ps.emax[tid], dummy, dummyf, post);
       const size_t HW = static_cast<size_t>(H) * W;
 #pragma unroll
       for (int k = 0; k < K; ++k) a.post[k * HW + pix] = post[k];
     }
   }
-  const unsigned nvalid = __popc(__ballot_sync(0xffffffffu, valid));
-  if ((tid & 31) == 0 && nvalid) atomicAdd(a.counter, static_cast<unsigned long long>(t_done) * nvalid);
+  if (tid == 0) atomicAdd(a.counter, executed);
 }
 
 template <int K>

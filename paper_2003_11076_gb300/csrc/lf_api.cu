@@ -572,6 +572,19 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
   a.log_thr = static_cast<float>(std::log(static_cast<double>(c->p.seg_threshold) / (1.0 - c->p.seg_threshold)));
   a.eps = c->p.eps;
   a.wtab = c->d_wtab; a.otab = c->d_otab; a.chg = c->d_chg; a.dval = c->d_dval; a.mu = c->d_mu;
+  for (int k = 0; k < kMaxCams; ++k) {
+    a.omin[k] = 0;
+    a.omax[k] = 0;
+  }
+  for (int k = 0; k < c->K; ++k) {
+    int lo = c->otab[k], hi = c->otab[k];
+    for (int j = 0; j < c->D; ++j) {
+      lo = std::min(lo, c->otab[j * c->KP + k]);
+      hi = std::max(hi, c->otab[j * c->KP + k]);
+    }
+    a.omin[k] = lo;
+    a.omax[k] = hi;
+  }
   a.d_idx = didx; a.d_out = dout; a.labels = lab; a.post = post;
   a.counter = c->d_counter; a.status = c->d_status; a.timeout_ns = kTimeoutNs;
   LF_CUDA(launch_em_sweep(c->K, c->img_map, c->p_map, a, c->stream), "em_sweep launch");

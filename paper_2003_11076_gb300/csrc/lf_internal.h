@@ -48,6 +48,7 @@ struct SweepArgs {
   const unsigned* chg;             // [D] bit k: otab[j][k] != otab[j-1][k] (j = 0: all)
   const float* dval;               // [D] d_j
   const float* mu;                 // [H][W] prior centre, NaN outside
+  int omin[kMaxCams], omax[kMaxCams];  // per camera: min / max over j of otab[j][k]
   int32_t* d_idx;                  // [H][W]
   float* d_out;                    // [H][W] or null
   uint16_t* labels;                // [H][W] or null
