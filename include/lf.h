@@ -188,6 +188,39 @@ const char *lf_last_error(const lf_ctx *ctx);
 void lf_destroy(lf_ctx *ctx);
 
 /*
+ * Allocation-free EM sweep.  The paper has no counterpart of this entry
+ * point; it exists for callers that cannot allocate device memory -- for
+ * example a host framework whose own memory pool owns the GPU and forbids raw
+ * cudaMalloc, or a latency-critical loop that must not trigger the
+ * device-wide synchronisation a cudaMalloc or cudaFree can cause.
+ *
+ * It runs the same fused EM sweep kernel as lf_run_em (same results for the
+ * same inputs), without the prior raster and the refocus.  Every input and
+ * output is a caller-owned DEVICE pointer with the layouts of lf_set_inputs /
+ * lf_run_em; mu is the caller's [H][W] float32 prior-centre map (NaN outside
+ * the triangulation), e.g. the one lf_get_prior returns.  The kernel's other
+ * scratch -- the per-(candidate, camera) sampling tables, the work counter and
+ * the status word -- lives in one fixed 64 KiB device array inside the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  The call allocates nothing: no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   Limits: D <= 256 (the tables the array holds); images and seg_prior rows
+ *   must start on 16-byte boundaries (W * bytes per pixel a multiple of 16),
+ *   because they are read in place; otherwise LF_EINVAL.
+ *   The first call on a device looks up the array's device address with that
+ *   device current; make that first call before any stream capture.
+ *   All calls share the one array and leave their contents in it (each call
+ *   clears the counter and status it needs); calls whose GPU work overlaps
+ *   would race on it, so the call serialises its callers and waits for
+ *   `stream` (a cudaStream_t, NULL = legacy default stream) before returning.
+ * Errors as lf_run_em (message in lf_last_error).
+ */
+lf_status lf_run_em_static(int n_cams, const float *baselines, int H, int W, float d_min, float d_max,
+                           int D, const lf_params *p, int iters, const void *images, int C, int dtype,
+                           const float *seg_prior, const float *mu, int32_t *disparity_idx,
+                           float *disparity, float *posteriors, uint16_t *labels, void *stream);
+
+/*
  * Host utility (no GPU needed): Delaunay triangulation of the (u, v) of
  * `points` ([M][3] float32, (u, v, d)) as used for the prior (Sec. III-C,
  * triangulation of the support points, as in ELAS).  Writes up to max_tris

@@ -106,6 +106,8 @@ constexpr unsigned long long kTimeoutNs = 2000000000ull;  // 2 s bounded device 
 
 }  // namespace
 
+void lf::set_error_message(const std::string& msg) { g_err = msg; }
+
 struct lf_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;

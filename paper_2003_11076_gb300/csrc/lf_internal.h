@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -77,6 +78,9 @@ cudaError_t launch_em_sweep(int K, const CUtensorMap& img_map, const CUtensorMap
                             const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_refocus(const RefocusArgs& a, cudaStream_t s);
 cudaError_t launch_median3(const float* in, float* out, int H, int W, int C, cudaStream_t s);
+
+// Sets the calling thread's message returned by lf_last_error.
+void set_error_message(const std::string& msg);
 
 // Host Delaunay triangulation (Bowyer-Watson with a symbolic point at infinity).
 // pts: n points (x, y); writes counter-clockwise triangles into out (3 ints each).

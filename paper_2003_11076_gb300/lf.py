@@ -22,7 +22,7 @@ LF_PREC_F32, LF_PREC_F16, LF_PREC_BF16 = 0, 1, 2
 
 EXPORTS = ("lf_default_params", "lf_create", "lf_set_stream", "lf_set_inputs", "lf_run_em",
            "lf_synchronize", "lf_get_prior", "lf_get_stats", "lf_last_error", "lf_destroy",
-           "lf_triangulate", "lf_set_timing")
+           "lf_triangulate", "lf_set_timing", "lf_run_em_static")
 
 
 class LfError(RuntimeError):
@@ -76,6 +76,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lf_last_error.restype = ctypes.c_char_p
     lib.lf_destroy.argtypes = [P]
     lib.lf_destroy.restype = None
+    lib.lf_run_em_static.argtypes = [I, P, I, I, ctypes.c_float, ctypes.c_float, I, ctypes.POINTER(Params), I,
+                                     P, I, I, P, P, P, P, P, P, P]
+    lib.lf_run_em_static.restype = I
     lib.lf_triangulate.argtypes = [P, I, P, I]
     lib.lf_triangulate.restype = I
     for name in ("lf_create", "lf_set_stream", "lf_set_inputs", "lf_run_em", "lf_synchronize",
@@ -109,6 +112,29 @@ def triangulate(points: np.ndarray) -> np.ndarray:
     if n < 0:
         raise LfError(LF_EINVAL, "invalid points")
     return out[:n].copy()
+
+
+def run_em_static(baselines, d_min: float, d_max: float, D: int, iters: int, images, seg_prior, mu,
+                  out: dict, params: Optional[Params] = None, stream=None) -> dict:
+    """The allocation-free sweep on caller-owned torch CUDA tensors.
+
+    images [K,H,W] / [K,H,W,3] uint8 or float32, seg_prior [K,H,W] float32,
+    mu [H,W] float32 (NaN outside the triangulation); out holds preallocated
+    tensors "d_idx" (int32, required) and optionally "d", "post", "labels".
+    The library allocates nothing; the call waits for ``stream``."""
+    import torch
+    b = np.ascontiguousarray(baselines, np.float32)
+    K, H, W = images.shape[:3]
+    C = 1 if images.dim() == 3 else int(images.shape[3])
+    dt = LF_U8 if images.dtype == torch.uint8 else LF_F32
+    ptr = lambda k: out[k].data_ptr() if k in out else None
+    handle = getattr(stream, "cuda_stream", stream)
+    _check(load().lf_run_em_static(int(K), b.ctypes.data, int(H), int(W), float(d_min), float(d_max), int(D),
+                                   ctypes.byref(params) if params is not None else None, int(iters),
+                                   images.data_ptr(), C, dt, seg_prior.data_ptr(), mu.data_ptr(),
+                                   ptr("d_idx"), ptr("d"), ptr("post"), ptr("labels"),
+                                   ctypes.c_void_p(handle or 0)))
+    return out
 
 
 def _is_torch(x) -> bool:
