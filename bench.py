@@ -38,7 +38,7 @@ METRIC = "EM ray-samples/s (nominal H*W*K*D*iters) at 5x960x600 RGB, D=64, 10 it
 UNIT = "ray-samples/s"
 WORKLOAD = "street_rgb: 5 cameras (0, +-0.1, +-0.2), 960x600 RGB uint8, D=64 (0..63), 10 EM iterations, " \
            "one frame per launch"
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "em_sweep_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "em_sweep_street_rgb_traffic.txt")
 SWEEP_SRC = os.path.join(ROOT, "paper_2003_11076_gb300", "csrc", "em_sweep.cuh")
 
 
@@ -302,12 +302,13 @@ def main():
         peak = n_sm * 128 * f_mhz * 1e6 / 1e9
         traffic = None
         if os.path.exists(TRAFFIC_FILE):
-            try:
-                tf = json.load(open(TRAFFIC_FILE))
-                if tf.get("kernel_sha") == sweep_source_hash():
-                    traffic = tf.get("dram_bytes_per_launch")
-            except (ValueError, OSError):
-                traffic = None
+            kv = {}
+            for line in open(TRAFFIC_FILE):
+                if "=" in line and not line.lstrip().startswith("#"):
+                    k, v = line.split("=", 1)
+                    kv[k.strip()] = v.strip()
+            if kv.get("kernel_sha") == sweep_source_hash():
+                traffic = float(kv["dram_bytes_per_launch"])
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
