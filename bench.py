@@ -192,6 +192,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="f32", choices=["f32", "f16", "bf16"],
+                    help="storage of the staged descriptor maps (arithmetic stays float32)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -207,7 +209,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     s = scenes.street_rgb(rank)
-    params = lf.default_params()
+    params = lf.default_params(precision={"f32": 0, "f16": 1, "bf16": 2}[args.precision])
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     img_d = torch.from_numpy(s.images).to(dev)
@@ -314,6 +316,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "staged_maps": args.precision,
                        "frames_per_s": args.steps * world / total_s,
                        "executed_ray_samples_per_frame": exec_mean,
                        "nominal_ray_samples_per_frame": nominal,

@@ -54,13 +54,20 @@ typedef enum lf_status {
 
 typedef enum lf_dtype {
     LF_U8 = 0,       /* uint8, value / 255 is the intensity in [0, 1] */
-    LF_F32 = 1       /* float32 intensity in [0, 1] */
+    LF_F32 = 1,      /* float32 intensity in [0, 1] */
+    LF_F16 = 2,      /* float16 intensity in [0, 1] */
+    LF_BF16 = 3      /* bfloat16 intensity in [0, 1] */
 } lf_dtype;
 
+/* Storage precision of the staged descriptor maps the rays are sampled from
+ * (luminance, Sobel responses, log segmentation priors) and of float32 input
+ * images, which the reduced modes convert to 16 bits on the device.  Every
+ * interpolation, likelihood, prior and posterior accumulation, the disparity
+ * arg-max and the refocus normalisation stay in float32. */
 typedef enum lf_precision {
-    LF_PREC_F32 = 0, /* staged descriptors and sampled rays in float32 */
-    LF_PREC_F16 = 1, /* ... stored in float16, accumulation in float32 */
-    LF_PREC_BF16 = 2 /* ... stored in bfloat16, accumulation in float32 */
+    LF_PREC_F32 = 0, /* staged maps in float32 */
+    LF_PREC_F16 = 1, /* staged maps and float32 images stored in float16 */
+    LF_PREC_BF16 = 2 /* staged maps and float32 images stored in bfloat16 */
 } lf_precision;
 
 /*
@@ -122,7 +129,7 @@ lf_status lf_set_stream(lf_ctx *ctx, void *stream);
 /*
  * Hand one frame to the context (Fig. 1 inputs: the K frames, the per-view
  * segmentation probabilities and the sparse support points).
- *   images       [K][H][W][C], dtype LF_U8 or LF_F32, C = 1 (gray) or 3 (RGB;
+ *   images       [K][H][W][C], dtype LF_U8, LF_F32, LF_F16 or LF_BF16, C = 1 (gray) or 3 (RGB;
  *                luminance Y = 0.299 R + 0.587 G + 0.114 B drives the
  *                likelihood, the refocus is per channel).
  *   seg_prior    [K][H][W] float32, P(pixel is dynamic) in [0, 1]

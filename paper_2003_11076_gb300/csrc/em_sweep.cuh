@@ -28,6 +28,9 @@
 // numbers; all accumulation is float32.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <cmath>
 #include <cstdint>
 
@@ -132,7 +135,7 @@ __host__ __device__ inline SmemLayout sweep_layout(int K, const SweepArgs& a) {
   L.luma = o;
   o = align_up(o + static_cast<size_t>(K) * (a.TR + 2) * a.RW * 4, 16);
   L.feat = o;
-  o = align_up(o + static_cast<size_t>(K) * a.TR * kMaps * a.SWp * 4, 16);
+  o = align_up(o + static_cast<size_t>(K) * a.TR * kMaps * a.SWp * (a.prec == 0 ? 4 : 2), 16);
   L.wtab = o;
   o = align_up(o + static_cast<size_t>(a.D) * a.KP * 4, 16);
   L.otab = o;
@@ -153,13 +156,23 @@ __host__ __device__ inline SmemLayout sweep_layout(int K, const SweepArgs& a) {
   return L;
 }
 
+// Staged descriptor maps are float32, or float16 / bfloat16 in the reduced-
+// precision modes; all arithmetic is float32.
+__device__ __forceinline__ float ldf(const float* p) { return *p; }
+__device__ __forceinline__ float ldf(const __half* p) { return __half2float(*p); }
+__device__ __forceinline__ float ldf(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void stf(float* p, float v) { *p = v; }
+__device__ __forceinline__ void stf(__half* p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ void stf(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
 __device__ __forceinline__ int floor16(int x) { return x >= 0 ? (x & ~15) : -((-x + 15) & ~15); }
 
 
 
 // View of one CTA's staged descriptor maps for one thread's pixel.
+template <typename TS>
 struct Staged {
-  const float* F;       // camera 0, this thread's tile row, map kMapY
+  const TS* F;          // camera 0, this thread's tile row, map kMapY
   int cam_stride;       // floats between cameras
   int SWp;              // floats between maps
   int cbase;            // staged column of this pixel (offset 0)
@@ -169,8 +182,8 @@ struct Staged {
 // Arg-max over the D candidates of J(d_j, S) for one pixel (lowest j wins
 // ties).  INIT: first iteration, where each ray's label is thresholded at the
 // ray's own sample (ld - ls < log(thr / (1 - thr)) means static).
-template <int K, bool INIT>
-__device__ __forceinline__ int m_step(const SweepArgs& a, const Staged& st, const float* s_w,
+template <int K, bool INIT, typename TS>
+__device__ __forceinline__ int m_step(const SweepArgs& a, const Staged<TS>& st, const float* s_w,
                                       const int* s_o, const unsigned* s_chg, const float* s_d,
                                       const float* s_rcp, float cy, float cx, float cz, float mu,
                                       bool inside, unsigned S) {
@@ -206,25 +219,25 @@ __device__ __forceinline__ int m_step(const SweepArgs& a, const Staged& st, cons
     for (int k = 0; k < K; ++k) {
       if (ch & (1u << k)) {  // same for every pixel: warp-uniform branch
         const int c = st.cbase + s_o[j * a.KP + k];
-        const float* Fk = st.F + k * st.cam_stride;
-        const float Y0 = Fk[c], Y1 = Fk[c + 1];
-        const float X0 = Fk[SWp + c], X1 = Fk[SWp + c + 1];
-        const float Z0 = Fk[2 * SWp + c], Z1 = Fk[2 * SWp + c + 1];
+        const TS* Fk = st.F + k * st.cam_stride;
+        const float Y0 = ldf(Fk + (c)), Y1 = ldf(Fk + (c + 1));
+        const float X0 = ldf(Fk + (SWp + c)), X1 = ldf(Fk + (SWp + c + 1));
+        const float Z0 = ldf(Fk + (2 * SWp + c)), Z1 = ldf(Fk + (2 * SWp + c + 1));
         if (INIT) {
           y0[k] = Y0 - cy; dy[k] = Y1 - Y0;
           x0[k] = X0 - cx; dx[k] = X1 - X0;
           z0[k] = Z0 - cz; dz[k] = Z1 - Z0;
-          l0[k] = Fk[kMapLs * SWp + c]; dl[k] = Fk[kMapLs * SWp + c + 1] - l0[k];
-          m0[k] = Fk[kMapLd * SWp + c]; dm[k] = Fk[kMapLd * SWp + c + 1] - m0[k];
-          q0[k] = Fk[kMapZ * SWp + c]; dq[k] = Fk[kMapZ * SWp + c + 1] - q0[k];
+          l0[k] = ldf(Fk + (kMapLs * SWp + c)); dl[k] = ldf(Fk + (kMapLs * SWp + c + 1)) - l0[k];
+          m0[k] = ldf(Fk + (kMapLd * SWp + c)); dm[k] = ldf(Fk + (kMapLd * SWp + c + 1)) - m0[k];
+          q0[k] = ldf(Fk + (kMapZ * SWp + c)); dq[k] = ldf(Fk + (kMapZ * SWp + c + 1)) - q0[k];
         } else {
           const bool stat = (S >> k) & 1u;
           const float s = stat ? 1.f : 0.f;
           y0[k] = s * (Y0 - cy); dy[k] = s * (Y1 - Y0);
           x0[k] = s * (X0 - cx); dx[k] = s * (X1 - X0);
           z0[k] = s * (Z0 - cz); dz[k] = s * (Z1 - Z0);
-          const float* Lk = Fk + (stat ? kMapLs : kMapLd) * SWp;
-          l0[k] = Lk[c]; dl[k] = Lk[c + 1] - l0[k];
+          const TS* Lk = Fk + (stat ? kMapLs : kMapLd) * SWp;
+          l0[k] = ldf(Lk + c); dl[k] = ldf(Lk + c + 1) - l0[k];
         }
       }
       if (INIT) {
@@ -262,17 +275,17 @@ __device__ __forceinline__ int m_step(const SweepArgs& a, const Staged& st, cons
 // First-iteration labels of one pixel when they are the same for every
 // candidate: bit k of *mask is camera k's label (static) and the return value
 // says whether every camera's Z texels stay clear of the threshold.
-template <int K>
-__device__ __forceinline__ bool constant_initial_labels(const SweepArgs& a, const Staged& st,
+template <int K, typename TS>
+__device__ __forceinline__ bool constant_initial_labels(const SweepArgs& a, const Staged<TS>& st,
                                                         unsigned* mask) {
   bool all = true;
   unsigned m = 0;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const float* Zk = st.F + k * st.cam_stride + kMapZ * st.SWp;
+    const TS* Zk = st.F + k * st.cam_stride + kMapZ * st.SWp;
     float lo = INFINITY, hi = -INFINITY;
     for (int c = st.cbase + a.omin[k]; c <= st.cbase + a.omax[k] + 1; ++c) {
-      const float z = Zk[c];
+      const float z = ldf(Zk + (c));
       lo = fminf(lo, z);
       hi = fmaxf(hi, z);
     }
@@ -290,8 +303,8 @@ struct Rays {
   float base;  // sum_k log p(dynamic)
 };
 
-template <int K>
-__device__ __forceinline__ void sample_rays(const SweepArgs& a, const Staged& st, const float* s_w,
+template <int K, typename TS>
+__device__ __forceinline__ void sample_rays(const SweepArgs& a, const Staged<TS>& st, const float* s_w,
                                             const int* s_o, int jt, float cy, float cx, float cz,
                                             Rays& r) {
   const int SWp = st.SWp;
@@ -300,12 +313,12 @@ __device__ __forceinline__ void sample_rays(const SweepArgs& a, const Staged& st
   for (int k = 0; k < K; ++k) {
     const float w = s_w[jt * a.KP + k];
     const int c = st.cbase + s_o[jt * a.KP + k];
-    const float* Fk = st.F + k * st.cam_stride;
-    const float Y0 = Fk[c], Y1 = Fk[c + 1];
-    const float X0 = Fk[SWp + c], X1 = Fk[SWp + c + 1];
-    const float Z0 = Fk[2 * SWp + c], Z1 = Fk[2 * SWp + c + 1];
-    const float S0 = Fk[kMapLs * SWp + c], S1 = Fk[kMapLs * SWp + c + 1];
-    const float D0 = Fk[kMapLd * SWp + c], D1 = Fk[kMapLd * SWp + c + 1];
+    const TS* Fk = st.F + k * st.cam_stride;
+    const float Y0 = ldf(Fk + (c)), Y1 = ldf(Fk + (c + 1));
+    const float X0 = ldf(Fk + (SWp + c)), X1 = ldf(Fk + (SWp + c + 1));
+    const float Z0 = ldf(Fk + (2 * SWp + c)), Z1 = ldf(Fk + (2 * SWp + c + 1));
+    const float S0 = ldf(Fk + (kMapLs * SWp + c)), S1 = ldf(Fk + (kMapLs * SWp + c + 1));
+    const float D0 = ldf(Fk + (kMapLd * SWp + c)), D1 = ldf(Fk + (kMapLd * SWp + c + 1));
     const float gy = fmaf(w, Y1 - Y0, Y0 - cy);
     const float gx = fmaf(w, X1 - X0, X0 - cx);
     const float gz = fmaf(w, Z1 - Z0, Z0 - cz);
@@ -417,16 +430,18 @@ __device__ __forceinline__ void enumerate(const Rays& r, const float* s_rcp, flo
 
 // ------------------------------------------------------- tile bookkeeping
 // Everything one thread needs to run the EM of pixel p of the tile.
+template <typename TS>
 struct PixelCtx {
   int u, v;
   bool valid, inside;
   float mu, cy, cx, cz;
-  Staged st;
+  Staged<TS> st;
 };
 
-__device__ __forceinline__ PixelCtx load_pixel(const SweepArgs& a, const float* s_feat, int u0, int v0,
-                                               int cam_stride, int p) {
-  PixelCtx c;
+template <typename TS>
+__device__ __forceinline__ PixelCtx<TS> load_pixel(const SweepArgs& a, const TS* s_feat, int u0, int v0,
+                                                   int cam_stride, int p) {
+  PixelCtx<TS> c;
   const int r = p / a.TW, tx = p - r * a.TW;
   c.u = u0 + tx;
   c.v = v0 + r;
@@ -437,10 +452,10 @@ __device__ __forceinline__ PixelCtx load_pixel(const SweepArgs& a, const float* 
   c.st.cam_stride = cam_stride;
   c.st.SWp = a.SWp;
   c.st.cbase = tx + a.L;
-  const float* Fr = c.st.F + a.ref * cam_stride;
-  c.cy = Fr[kMapY * a.SWp + c.st.cbase];
-  c.cx = Fr[kMapSx * a.SWp + c.st.cbase];
-  c.cz = Fr[kMapSy * a.SWp + c.st.cbase];
+  const TS* Fr = c.st.F + a.ref * cam_stride;
+  c.cy = ldf(Fr + kMapY * a.SWp + c.st.cbase);
+  c.cx = ldf(Fr + kMapSx * a.SWp + c.st.cbase);
+  c.cz = ldf(Fr + kMapSy * a.SWp + c.st.cbase);
   return c;
 }
 
@@ -469,7 +484,7 @@ __device__ __forceinline__ int compact(bool pred, int16_t* list, int base, int* 
 #define LF_SWEEP_MIN_BLOCKS 1
 #endif
 
-template <int K>
+template <int K, typename TS>
 __global__ void __launch_bounds__(256, LF_SWEEP_MIN_BLOCKS) em_sweep_kernel(const __grid_constant__ CUtensorMap img_map,
                                                        const __grid_constant__ CUtensorMap p_map,
                                                        const SweepArgs a) {
@@ -478,7 +493,7 @@ __global__ void __launch_bounds__(256, LF_SWEEP_MIN_BLOCKS) em_sweep_kernel(cons
   uint8_t* s_img = smem + Ly.raw_img;
   const float* s_p = reinterpret_cast<const float*>(smem + Ly.raw_p);
   float* s_luma = reinterpret_cast<float*>(smem + Ly.luma);
-  float* s_feat = reinterpret_cast<float*>(smem + Ly.feat);
+  TS* s_feat = reinterpret_cast<TS*>(smem + Ly.feat);
   float* s_w = reinterpret_cast<float*>(smem + Ly.wtab);
   int* s_o = reinterpret_cast<int*>(smem + Ly.otab);
   unsigned* s_chg = reinterpret_cast<unsigned*>(smem + Ly.chg);
@@ -534,8 +549,14 @@ __global__ void __launch_bounds__(256, LF_SWEEP_MIN_BLOCKS) em_sweep_kernel(cons
                    : fmaf(0.114f, static_cast<float>(px[2]),
                           fmaf(0.587f, static_cast<float>(px[1]), 0.299f * static_cast<float>(px[0])));
       y *= (1.f / 255.f);
-    } else {
+    } else if (a.dtype == 1) {
       const float* f = reinterpret_cast<const float*>(px);
+      y = a.C == 1 ? f[0] : fmaf(0.114f, f[2], fmaf(0.587f, f[1], 0.299f * f[0]));
+    } else {
+      float f[3];
+      for (int ch = 0; ch < a.C; ++ch)
+        f[ch] = a.dtype == 2 ? __half2float(reinterpret_cast<const __half*>(px)[ch])
+                             : __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(px)[ch]);
       y = a.C == 1 ? f[0] : fmaf(0.114f, f[2], fmaf(0.587f, f[1], 0.299f * f[0]));
     }
     s_luma[i] = y;
@@ -557,14 +578,14 @@ __global__ void __launch_bounds__(256, LF_SWEEP_MIN_BLOCKS) em_sweep_kernel(cons
     const float gx = ((a02 + 2.f * a12) + a22) - ((a00 + 2.f * a10) + a20);
     const float gy = ((a20 + 2.f * a21) + a22) - ((a00 + 2.f * a01) + a02);
     const float P = s_p[(static_cast<size_t>(k) * a.TR + (V - v0)) * RW + c0];
-    float* F = s_feat + static_cast<size_t>(k) * cam_stride + static_cast<size_t>(r) * kMaps * a.SWp;
+    TS* F = s_feat + static_cast<size_t>(k) * cam_stride + static_cast<size_t>(r) * kMaps * a.SWp;
     const float ls = logf(fmaxf(1.f - P, a.eps)), ld = logf(fmaxf(P, a.eps));
-    F[kMapY * a.SWp + c] = a11;
-    F[kMapSx * a.SWp + c] = gx * 0.125f;
-    F[kMapSy * a.SWp + c] = gy * 0.125f;
-    F[kMapLs * a.SWp + c] = ls;
-    F[kMapLd * a.SWp + c] = ld;
-    F[kMapZ * a.SWp + c] = ld - ls;
+    stf(F + kMapY * a.SWp + c, a11);
+    stf(F + kMapSx * a.SWp + c, gx * 0.125f);
+    stf(F + kMapSy * a.SWp + c, gy * 0.125f);
+    stf(F + kMapLs * a.SWp + c, ls);
+    stf(F + kMapLd * a.SWp + c, ld);
+    stf(F + kMapZ * a.SWp + c, ld - ls);
   }
   __syncthreads();
 
@@ -589,9 +610,9 @@ __global__ void __launch_bounds__(256, LF_SWEEP_MIN_BLOCKS) em_sweep_kernel(cons
 
   const bool my_valid = (u0 + tid % a.TW < W) && (v0 + tid / a.TW < H);
   {
-    const PixelCtx me = load_pixel(a, s_feat, u0, v0, cam_stride, tid);
+    const PixelCtx<TS> me = load_pixel(a, s_feat, u0, v0, cam_stride, tid);
     unsigned S0 = 0;
-    const bool f0 = me.valid && constant_initial_labels<K>(a, me.st, &S0);
+    const bool f0 = me.valid && constant_initial_labels<K, TS>(a, me.st, &S0);
     ps.fixed0[tid] = f0;
     ps.S0[tid] = static_cast<uint16_t>(S0);
     ps.conv[tid] = 0;
@@ -604,14 +625,14 @@ __global__ void __launch_bounds__(256, LF_SWEEP_MIN_BLOCKS) em_sweep_kernel(cons
   if (warp * 32 < nact) {
     const bool active = tid < nact;
     const int p = ps.list[active ? tid : nact - 1];
-    const PixelCtx c = load_pixel(a, s_feat, u0, v0, cam_stride, p);
+    const PixelCtx<TS> c = load_pixel(a, s_feat, u0, v0, cam_stride, p);
     const bool f0 = ps.fixed0[p];
     const unsigned S0 = ps.S0[p];
     const bool fast = __all_sync(0xffffffffu, f0);
-    const int jb = fast ? m_step<K, false>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, S0)
-                        : m_step<K, true>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, 0u);
+    const int jb = fast ? m_step<K, false, TS>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, S0)
+                        : m_step<K, true, TS>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, 0u);
     Rays rays;
-    sample_rays<K>(a, c.st, s_w, s_o, jb, c.cy, c.cx, c.cz, rays);
+    sample_rays<K, TS>(a, c.st, s_w, s_o, jb, c.cy, c.cx, c.cz, rays);
     unsigned S = 0;
     float emax = 0.f;
     enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
@@ -632,11 +653,11 @@ __global__ void __launch_bounds__(256, LF_SWEEP_MIN_BLOCKS) em_sweep_kernel(cons
     if (warp * 32 < n) {
       const bool active = tid < n;
       const int p = ps.list[active ? tid : n - 1];
-      const PixelCtx c = load_pixel(a, s_feat, u0, v0, cam_stride, p);
+      const PixelCtx<TS> c = load_pixel(a, s_feat, u0, v0, cam_stride, p);
       const unsigned Sp = ps.S[p];
-      const int jb = m_step<K, false>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, Sp);
+      const int jb = m_step<K, false, TS>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, Sp);
       Rays rays;
-      sample_rays<K>(a, c.st, s_w, s_o, jb, c.cy, c.cx, c.cz, rays);
+      sample_rays<K, TS>(a, c.st, s_w, s_o, jb, c.cy, c.cx, c.cz, rays);
       unsigned S = 0;
       float emax = 0.f;
       enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
@@ -652,7 +673,7 @@ __global__ void __launch_bounds__(256, LF_SWEEP_MIN_BLOCKS) em_sweep_kernel(cons
 
   // posteriors and outputs, one thread per pixel
   if (my_valid) {
-    const PixelCtx me = load_pixel(a, s_feat, u0, v0, cam_stride, tid);
+    const PixelCtx<TS> me = load_pixel(a, s_feat, u0, v0, cam_stride, tid);
     const int jb = ps.jb[tid];
     const unsigned S = ps.S[tid];
     const size_t pix = static_cast<size_t>(me.v) * W + me.u;
@@ -661,7 +682,7 @@ __global__ void __launch_bounds__(256, LF_SWEEP_MIN_BLOCKS) em_sweep_kernel(cons
     if (a.labels) a.labels[pix] = static_cast<uint16_t>(S);
     if (a.post) {
       Rays rays;
-      sample_rays<K>(a, me.st, s_w, s_o, jb, me.cy, me.cx, me.cz, rays);
+      sample_rays<K, TS>(a, me.st, s_w, s_o, jb, me.cy, me.cx, me.cz, rays);
       float post[K];
       unsigned dummy;
       float dummyf;
@@ -674,19 +695,19 @@ __global__ void __launch_bounds__(256, LF_SWEEP_MIN_BLOCKS) em_sweep_kernel(cons
   if (tid == 0) atomicAdd(a.counter, executed);
 }
 
-template <int K>
+template <int K, typename TS>
 cudaError_t launch_em_sweep_k(const CUtensorMap& img_map, const CUtensorMap& p_map, const SweepArgs& a,
                               cudaStream_t s) {
   const size_t smem = sweep_layout(K, a).total;
   static int configured = -1;  // largest dynamic shared size set so far (per process)
   if (static_cast<int>(smem) > configured) {
-    cudaError_t e = cudaFuncSetAttribute(em_sweep_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(em_sweep_kernel<K, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     configured = static_cast<int>(smem);
   }
   dim3 grid((a.W + a.TW - 1) / a.TW, (a.H + a.TR - 1) / a.TR);
-  em_sweep_kernel<K><<<grid, a.TR * a.TW, smem, s>>>(img_map, p_map, a);
+  em_sweep_kernel<K, TS><<<grid, a.TR * a.TW, smem, s>>>(img_map, p_map, a);
   return cudaGetLastError();
 }
 

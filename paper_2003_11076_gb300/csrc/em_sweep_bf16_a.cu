@@ -1,0 +1,17 @@
+// Instantiations of the fused EM sweep, bf16 staged maps, camera counts: 1 2 3 4.
+#include "em_sweep.cuh"
+
+namespace lf {
+cudaError_t launch_em_sweep_bf16_k1(const CUtensorMap& i, const CUtensorMap& p, const SweepArgs& a, cudaStream_t s) {
+  return dev::launch_em_sweep_k<1, __nv_bfloat16>(i, p, a, s);
+}
+cudaError_t launch_em_sweep_bf16_k2(const CUtensorMap& i, const CUtensorMap& p, const SweepArgs& a, cudaStream_t s) {
+  return dev::launch_em_sweep_k<2, __nv_bfloat16>(i, p, a, s);
+}
+cudaError_t launch_em_sweep_bf16_k3(const CUtensorMap& i, const CUtensorMap& p, const SweepArgs& a, cudaStream_t s) {
+  return dev::launch_em_sweep_k<3, __nv_bfloat16>(i, p, a, s);
+}
+cudaError_t launch_em_sweep_bf16_k4(const CUtensorMap& i, const CUtensorMap& p, const SweepArgs& a, cudaStream_t s) {
+  return dev::launch_em_sweep_k<4, __nv_bfloat16>(i, p, a, s);
+}
+}  // namespace lf

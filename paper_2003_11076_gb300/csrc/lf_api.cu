@@ -18,31 +18,32 @@
 #include "lf_internal.h"
 
 namespace lf {
-#define LF_DECL_SWEEP(k) \
-  cudaError_t launch_em_sweep_k##k(const CUtensorMap&, const CUtensorMap&, const SweepArgs&, cudaStream_t);
-LF_DECL_SWEEP(1) LF_DECL_SWEEP(2) LF_DECL_SWEEP(3) LF_DECL_SWEEP(4) LF_DECL_SWEEP(5) LF_DECL_SWEEP(6)
-LF_DECL_SWEEP(7) LF_DECL_SWEEP(8) LF_DECL_SWEEP(9) LF_DECL_SWEEP(10) LF_DECL_SWEEP(11) LF_DECL_SWEEP(12)
+#define LF_DECL_SWEEP(t, k) \
+  cudaError_t launch_em_sweep_##t##_k##k(const CUtensorMap&, const CUtensorMap&, const SweepArgs&, cudaStream_t);
+#define LF_DECL_SWEEPS(t)                                                                                     \
+  LF_DECL_SWEEP(t, 1) LF_DECL_SWEEP(t, 2) LF_DECL_SWEEP(t, 3) LF_DECL_SWEEP(t, 4) LF_DECL_SWEEP(t, 5)           \
+  LF_DECL_SWEEP(t, 6) LF_DECL_SWEEP(t, 7) LF_DECL_SWEEP(t, 8) LF_DECL_SWEEP(t, 9) LF_DECL_SWEEP(t, 10)          \
+  LF_DECL_SWEEP(t, 11) LF_DECL_SWEEP(t, 12)
+LF_DECL_SWEEPS(f32)
+LF_DECL_SWEEPS(f16)
+LF_DECL_SWEEPS(bf16)
+#undef LF_DECL_SWEEPS
 #undef LF_DECL_SWEEP
 
 size_t sweep_smem_bytes(int K, const SweepArgs& a) { return dev::sweep_layout(K, a).total; }
 
+typedef cudaError_t (*SweepLaunch)(const CUtensorMap&, const CUtensorMap&, const SweepArgs&, cudaStream_t);
+
 cudaError_t launch_em_sweep(int K, const CUtensorMap& i, const CUtensorMap& p, const SweepArgs& a,
                             cudaStream_t s) {
-  switch (K) {
-    case 1: return launch_em_sweep_k1(i, p, a, s);
-    case 2: return launch_em_sweep_k2(i, p, a, s);
-    case 3: return launch_em_sweep_k3(i, p, a, s);
-    case 4: return launch_em_sweep_k4(i, p, a, s);
-    case 5: return launch_em_sweep_k5(i, p, a, s);
-    case 6: return launch_em_sweep_k6(i, p, a, s);
-    case 7: return launch_em_sweep_k7(i, p, a, s);
-    case 8: return launch_em_sweep_k8(i, p, a, s);
-    case 9: return launch_em_sweep_k9(i, p, a, s);
-    case 10: return launch_em_sweep_k10(i, p, a, s);
-    case 11: return launch_em_sweep_k11(i, p, a, s);
-    case 12: return launch_em_sweep_k12(i, p, a, s);
-    default: return cudaErrorInvalidValue;
-  }
+#define LF_ROW(t)                                                                                           \
+  {launch_em_sweep_##t##_k1, launch_em_sweep_##t##_k2,  launch_em_sweep_##t##_k3,  launch_em_sweep_##t##_k4, \
+   launch_em_sweep_##t##_k5, launch_em_sweep_##t##_k6,  launch_em_sweep_##t##_k7,  launch_em_sweep_##t##_k8, \
+   launch_em_sweep_##t##_k9, launch_em_sweep_##t##_k10, launch_em_sweep_##t##_k11, launch_em_sweep_##t##_k12}
+  static const SweepLaunch table[3][kMaxCams] = {LF_ROW(f32), LF_ROW(f16), LF_ROW(bf16)};
+#undef LF_ROW
+  if (K < 1 || K > kMaxCams || a.prec < 0 || a.prec > 2) return cudaErrorInvalidValue;
+  return table[a.prec][K - 1](i, p, a, s);
 }
 }  // namespace lf
 
@@ -138,6 +139,8 @@ struct lf_ctx {
   size_t own_img_cap = 0;
   float* own_P = nullptr;
   size_t own_P_cap = 0;
+  uint8_t* own_img16 = nullptr;  // 16-bit copy of float32 images in the reduced-precision modes
+  size_t own_img16_cap = 0;
   // prior
   std::vector<PriorTri> h_tris;
   std::vector<int> h_bins;  // [nbins + 1] starts, then items
@@ -195,6 +198,7 @@ lf_status choose_tiles(lf_ctx* c) {
       a.bpp = c->bpp;
       a.D = c->D;
       a.KP = c->KP;
+      a.prec = c->p.precision;
       if (a.RW * a.bpp / 8 > 256 || a.RW / 2 > 256) continue;
       if (sweep_smem_bytes(c->K, a) > limit) continue;
       c->TR = a.TR;
@@ -374,7 +378,8 @@ lf_status lf_create(lf_ctx** out, int n_cams, const float* baselines, int H, int
       !finite(prm.eps) || prm.sigma <= 0.f || prm.gamma < 0.f || prm.eps <= 0.f || prm.seg_threshold <= 0.f ||
       prm.seg_threshold >= 1.f || prm.beta < 0.f)
     return fail(LF_EINVAL, "invalid lf_params");
-  if (prm.precision != LF_PREC_F32) return fail(LF_EINVAL, "only LF_PREC_F32 is implemented by this build");
+  if (prm.precision != LF_PREC_F32 && prm.precision != LF_PREC_F16 && prm.precision != LF_PREC_BF16)
+    return fail(LF_EINVAL, "precision must be LF_PREC_F32, LF_PREC_F16 or LF_PREC_BF16");
 
   lf_ctx* c = new (std::nothrow) lf_ctx();
   if (!c) return fail(LF_ENOMEM, "host allocation failed");
@@ -464,18 +469,33 @@ lf_status lf_set_inputs(lf_ctx* c, const void* images, int C, int dtype, const f
   if (!c) return fail(LF_EINVAL, "ctx is NULL");
   if (!images || !seg_prior) return fail(LF_EINVAL, "images and seg_prior must not be NULL");
   if (C != 1 && C != 3) return fail(LF_EINVAL, "C must be 1 or 3");
-  if (dtype != LF_U8 && dtype != LF_F32) return fail(LF_EINVAL, "dtype must be LF_U8 or LF_F32");
+  if (dtype != LF_U8 && dtype != LF_F32 && dtype != LF_F16 && dtype != LF_BF16)
+    return fail(LF_EINVAL, "dtype must be LF_U8, LF_F32, LF_F16 or LF_BF16");
   if (M < 0 || (M > 0 && !sparse_points)) return fail(LF_EINVAL, "bad sparse points");
   for (int i = 0; i < 3 * M; ++i)
     if (!std::isfinite(sparse_points[i])) return fail(LF_EINVAL, "non-finite sparse point");
   c->have_inputs = false;
   c->C = C;
   c->dtype = dtype;
-  c->bpp = C * (dtype == LF_U8 ? 1 : 4);
-  lf_status s = choose_tiles(c);
+  c->bpp = C * (dtype == LF_U8 ? 1 : dtype == LF_F32 ? 4 : 2);
+  lf_status s = copy_plane(c, images, static_cast<size_t>(c->W) * c->bpp, on_device != 0, &c->own_img,
+                           &c->own_img_cap, &c->img, &c->img_pitch);
   if (s != LF_OK) return s;
-  s = copy_plane(c, images, static_cast<size_t>(c->W) * c->bpp, on_device != 0, &c->own_img, &c->own_img_cap,
-                 &c->img, &c->img_pitch);
+  if (dtype == LF_F32 && c->p.precision != LF_PREC_F32) {
+    // reduced precision: the images are stored on the device in 16 bits
+    const int to_bf16 = c->p.precision == LF_PREC_BF16;
+    const size_t row16 = static_cast<size_t>(c->W) * C * 2, pitch16 = (row16 + 15) / 16 * 16;
+    s = grow(&c->own_img16, &c->own_img16_cap, pitch16 * c->H * c->K, "input staging");
+    if (s != LF_OK) return s;
+    LF_CUDA(launch_convert_f32(c->img, c->img_pitch, c->own_img16, pitch16, c->K * c->H, c->W * C, to_bf16,
+                               c->stream),
+            "image conversion");
+    c->img = c->own_img16;
+    c->img_pitch = pitch16;
+    c->dtype = to_bf16 ? LF_BF16 : LF_F16;
+    c->bpp = C * 2;
+  }
+  s = choose_tiles(c);
   if (s != LF_OK) return s;
   const uint8_t* pp = nullptr;
   uint8_t* ownP = reinterpret_cast<uint8_t*>(c->own_P);
@@ -568,6 +588,7 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
   a.iters = iters;
   a.early_exit = c->p.early_exit;
   a.mseg = c->p.mstep_seg_term;
+  a.prec = c->p.precision;
   a.beta = c->p.beta;
   a.gamma = c->p.gamma;
   a.inv2s2 = static_cast<float>(1.0 / (2.0 * static_cast<double>(c->p.sigma) * c->p.sigma));
@@ -683,7 +704,7 @@ void lf_destroy(lf_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   void* bufs[] = {c->d_wtab, c->d_otab, c->d_chg, c->d_dval, c->d_mu, c->d_counter, c->d_status,
-                  c->own_img, c->own_P, c->d_tris, c->d_bins, c->o_didx, c->o_d, c->o_labels,
+                  c->own_img, c->own_P, c->own_img16, c->d_tris, c->d_bins, c->o_didx, c->o_d, c->o_labels,
                   c->o_post, c->o_ref, c->o_tmp};
   for (void* p : bufs)
     if (p) cudaFree(p);

@@ -36,13 +36,14 @@ struct PriorArgs {
 
 // Everything the fused sweep kernel needs besides the two tensor maps.
 struct SweepArgs {
-  int H, W, C, D, ref, dtype, bpp; // dtype 0 = uint8, 1 = float32; bpp = bytes per pixel
+  int H, W, C, D, ref, dtype, bpp; // dtype 0 = uint8, 1 = float32, 2 = float16, 3 = bfloat16; bpp = bytes per pixel
   int TR, TW;                      // tile rows / columns; threads = TR * TW
   int L, R;                        // staged texel halo left / right of the tile
   int SW, SWp;                     // staged texels per row, padded to a multiple of 32
   int RW;                          // staged raw pixels per row (multiple of 16)
   int KP;                          // cameras padded to a multiple of 4 (table stride)
   int iters, early_exit, mseg;
+  int prec;                        // staged maps: kPrecF32, kPrecF16 or kPrecBF16
   float beta, gamma, inv2s2, log_thr, eps;
   const float* wtab;               // [D][KP] interpolation weight of camera k at d_j
   const int* otab;                 // [D][KP] floor(-d_j * b_k)
@@ -78,6 +79,9 @@ cudaError_t launch_em_sweep(int K, const CUtensorMap& img_map, const CUtensorMap
                             const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_refocus(const RefocusArgs& a, cudaStream_t s);
 cudaError_t launch_median3(const float* in, float* out, int H, int W, int C, cudaStream_t s);
+// float32 [rows][W*C] (pitch_in bytes) -> float16 (to_bf16 = 0) or bfloat16 rows (pitch_out bytes)
+cudaError_t launch_convert_f32(const uint8_t* in, size_t pitch_in, uint8_t* out, size_t pitch_out, int rows,
+                               int cols, int to_bf16, cudaStream_t s);
 
 // Sets the calling thread's message returned by lf_last_error.
 void set_error_message(const std::string& msg);

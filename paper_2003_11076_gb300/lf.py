@@ -17,7 +17,7 @@ import numpy as np
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "liblf.so")
 
 LF_OK, LF_EINVAL, LF_ENOMEM, LF_ECUDA, LF_ESTATE, LF_ETIMEOUT = range(6)
-LF_U8, LF_F32 = 0, 1
+LF_U8, LF_F32, LF_F16, LF_BF16 = 0, 1, 2, 3
 LF_PREC_F32, LF_PREC_F16, LF_PREC_BF16 = 0, 1, 2
 
 EXPORTS = ("lf_default_params", "lf_create", "lf_set_stream", "lf_set_inputs", "lf_run_em",
@@ -191,7 +191,8 @@ class Context:
             import torch
             assert images.is_cuda and seg_prior.is_cuda and images.is_contiguous() and seg_prior.is_contiguous()
             C = 1 if images.dim() == 3 else int(images.shape[3])
-            dt = LF_U8 if images.dtype == torch.uint8 else LF_F32
+            dt = {torch.uint8: LF_U8, torch.float32: LF_F32, torch.float16: LF_F16,
+                  torch.bfloat16: LF_BF16}[images.dtype]
             assert seg_prior.dtype == torch.float32
             self._keep = (images, seg_prior)
             _check(load().lf_set_inputs(self._h, images.data_ptr(), C, dt, seg_prior.data_ptr(),
