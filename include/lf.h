@@ -103,6 +103,7 @@ typedef struct lf_stats {
     int kernels_launched;          /* kernels one lf_run_em enqueues */
     float ms_prior, ms_sweep, ms_refocus, ms_median; /* mean device time per run
                                       of each kernel (lf_set_timing on), else 0 */
+    int graph_captures;            /* batches: CUDA graphs captured so far */
 } lf_stats;
 
 /* Fill *p with the documented defaults. */
@@ -193,6 +194,47 @@ const char *lf_last_error(const lf_ctx *ctx);
 
 /* Free the context and its device buffers (waits for its stream). */
 void lf_destroy(lf_ctx *ctx);
+
+/*
+ * Uneven batches (workload: many frames of different sizes, camera counts,
+ * candidate and iteration counts in one go).  Same method and results per
+ * frame as lf_run_em; the batch runs as one CUDA graph: a batched prior
+ * raster, one persistent sweep launch per camera count present (its CTAs take
+ * (frame, tile) items from a device-side queue, so small and large frames
+ * share the GPU without tail effects) and a batched refocus / median.  The
+ * graph reads its work lists from device memory and is captured again only
+ * when the batch's shape changes (camera counts present, shared-memory size,
+ * or a work list outgrowing its buffer); otherwise it is replayed.
+ *
+ * lf_batch_create: p as for lf_create (copied); autotune reserved (0).
+ * lf_batch_add: queue one frame.  images, seg_prior and every output are
+ *   DEVICE pointers with the layouts of lf_set_inputs / lf_run_em, owned by
+ *   the caller and kept alive until lf_batch_synchronize returns; outputs may
+ *   be NULL except disparity_idx.  sparse_points is HOST memory (copied).
+ *   iters is per frame.  *index (may be NULL) receives the frame's position.
+ *   Rows need not be aligned: unaligned inputs are staged by the batch.
+ * lf_batch_run: enqueue all queued frames on the batch's stream (async).
+ * lf_batch_synchronize: wait; LF_ETIMEOUT if a bounded wait expired.
+ * lf_batch_clear: forget the queued frames (device buffers are kept).
+ * lf_batch_get_stats: runs since the last call, nominal and executed ray
+ *   samples and kernel times (prior, all sweeps, refocus, median) of the last
+ *   run, graph captures so far; synchronises.
+ * Errors: LF_EINVAL (bad frame, halo too wide), LF_ESTATE (empty run),
+ * LF_ENOMEM, LF_ECUDA, LF_ETIMEOUT.
+ */
+typedef struct lf_batch lf_batch;
+lf_status lf_batch_create(lf_batch **out, const lf_params *p, int autotune);
+lf_status lf_batch_set_stream(lf_batch *b, void *stream);
+lf_status lf_batch_add(lf_batch *b, int n_cams, const float *baselines, int H, int W, float d_min,
+                       float d_max, int D, int iters, const void *images, int C, int dtype,
+                       const float *seg_prior, const float *sparse_points, int M,
+                       int32_t *disparity_idx, float *disparity, float *posteriors, uint16_t *labels,
+                       float *refocused, int *index);
+lf_status lf_batch_run(lf_batch *b);
+lf_status lf_batch_synchronize(lf_batch *b);
+lf_status lf_batch_clear(lf_batch *b);
+lf_status lf_batch_get_stats(lf_batch *b, lf_stats *out);
+void lf_batch_destroy(lf_batch *b);
 
 /*
  * Allocation-free EM sweep.  The paper has no counterpart of this entry

@@ -125,9 +125,17 @@ struct PixelState {
   uint8_t* conv;    // reached its fixed point
 };
 
+// Fixed head of the shared memory: the CTA's mbarrier, then (persistent
+// kernel) the current frame's arguments, then the item index.  Everything
+// after it depends on the frame.
+constexpr size_t kSmemBar = 0;
+constexpr size_t kSmemArgs = 16;
+constexpr size_t kSmemItem = kSmemArgs + ((sizeof(SweepArgs) + 15) / 16) * 16;
+constexpr size_t kSmemHead = ((kSmemItem + 16 + 127) / 128) * 128;
+
 __host__ __device__ inline SmemLayout sweep_layout(int K, const SweepArgs& a) {
   SmemLayout L{};
-  size_t o = 0;
+  size_t o = kSmemHead;
   L.raw_img = o;
   o = align_up(o + static_cast<size_t>(K) * (a.TR + 2) * a.RW * a.bpp, 128);
   L.raw_p = o;
@@ -150,8 +158,7 @@ __host__ __device__ inline SmemLayout sweep_layout(int K, const SweepArgs& a) {
   o = align_up(o + static_cast<size_t>(a.TR) * a.TW * 14, 16);
   L.wcnt = o;
   o = align_up(o + 32 * 4, 16);
-  L.bar = o;
-  o = align_up(o + 8, 16);
+  L.bar = kSmemBar;
   L.total = o;
   return L;
 }
@@ -484,11 +491,16 @@ __device__ __forceinline__ int compact(bool pred, int16_t* list, int base, int* 
 #define LF_SWEEP_MIN_BLOCKS 1
 #endif
 
+// One tile (tile_x, tile_y) of one frame: stage, run the EM, write the
+// outputs.  The CTA's mbarrier (initialised by the caller) completes phase
+// `phase` for this tile's copies.  load_tables: the frame differs from the
+// previous tile's (tables and constants must be staged again).  Ends with a
+// __syncthreads so that the next tile may reuse the shared memory.  Returns
+// false (same in every thread) when the staging wait timed out.
 template <int K, typename TS>
-__global__ void __launch_bounds__(256, LF_SWEEP_MIN_BLOCKS) em_sweep_kernel(const __grid_constant__ CUtensorMap img_map,
-                                                       const __grid_constant__ CUtensorMap p_map,
-                                                       const SweepArgs a) {
-  extern __shared__ __align__(128) uint8_t smem[];
+__device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap* img_map,
+                                           const CUtensorMap* p_map, int tile_x, int tile_y, uint8_t* smem,
+                                           unsigned phase, bool load_tables, bool maps_in_global) {
   const SmemLayout Ly = sweep_layout(K, a);
   uint8_t* s_img = smem + Ly.raw_img;
   const float* s_p = reinterpret_cast<const float*>(smem + Ly.raw_p);
@@ -502,42 +514,40 @@ __global__ void __launch_bounds__(256, LF_SWEEP_MIN_BLOCKS) em_sweep_kernel(cons
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Ly.bar);
 
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int u0 = blockIdx.x * a.TW, v0 = blockIdx.y * a.TR;
+  const int u0 = tile_x * a.TW, v0 = tile_y * a.TR;
   const int cs = floor16(u0 - a.L - 1);  // first staged raw column (16-px aligned)
   const int W = a.W, H = a.H, RW = a.RW, LR = a.TR + 2;
 
-  // ---- 1. stage raw rows with TMA (destinations must be 128-byte aligned)
-  if ((smem_u32(smem) & 127u) != 0u) {
-    if (tid == 0) atomicOr(a.status, kStatusSmemMisaligned);
-    return;
-  }
+  // ---- 1. stage raw rows with TMA
   if (tid == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  if (tid == 0) {
+    if (maps_in_global) {  // descriptors written by copies since their last use
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(img_map) : "memory");
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(p_map) : "memory");
+    }
     const unsigned bytes = static_cast<unsigned>(K * LR * RW * a.bpp + K * a.TR * RW * 4);
     mbar_arrive_expect_tx(bar, bytes);
-    tma_load_3d(s_img, &img_map, cs * a.bpp / 8, v0 - 1, 0, bar);
-    tma_load_3d(smem + Ly.raw_p, &p_map, cs / 2, v0, 0, bar);
+    tma_load_3d(s_img, img_map, cs * a.bpp / 8, v0 - 1, 0, bar);
+    tma_load_3d(smem + Ly.raw_p, p_map, cs / 2, v0, 0, bar);
   }
-  for (int i = tid; i < a.D * a.KP; i += nthr) {
-    s_w[i] = a.wtab[i];
-    s_o[i] = a.otab[i];
+  if (load_tables) {
+    for (int i = tid; i < a.D * a.KP; i += nthr) {
+      s_w[i] = a.wtab[i];
+      s_o[i] = a.otab[i];
+    }
+    for (int i = tid; i < a.D; i += nthr) {
+      s_chg[i] = a.chg[i];
+      s_d[i] = a.dval[i];
+    }
+    if (tid < 16) s_rcp[tid] = tid >= 2 ? 1.f / static_cast<float>(tid) : 0.f;
   }
-  for (int i = tid; i < a.D; i += nthr) {
-    s_chg[i] = a.chg[i];
-    s_d[i] = a.dval[i];
-  }
-  if (tid < 16) s_rcp[tid] = tid >= 2 ? 1.f / static_cast<float>(tid) : 0.f;
-  const bool ok = mbar_wait_bounded(bar, 0, a.timeout_ns);
+  const bool ok = mbar_wait_bounded(bar, phase, a.timeout_ns);
   if (__syncthreads_or(!ok)) {
     if (!ok) {
       atomicOr(a.status, kStatusTmaTimeout);
-      mbar_wait_bounded(bar, 0, a.timeout_ns);  // let the copy land before the CTA exits
+      mbar_wait_bounded(bar, phase, a.timeout_ns);  // let the copy land before the CTA moves on
     }
-    return;
+    __syncthreads();
+    return false;
   }
 
   // ---- 2. descriptors and log priors (border replicated)
@@ -693,6 +703,75 @@ __global__ void __launch_bounds__(256, LF_SWEEP_MIN_BLOCKS) em_sweep_kernel(cons
     }
   }
   if (tid == 0) atomicAdd(a.counter, executed);
+  __syncthreads();
+  return true;
+}
+
+// One CTA per tile of one frame.
+template <int K, typename TS>
+__global__ void __launch_bounds__(256, LF_SWEEP_MIN_BLOCKS) em_sweep_kernel(const __grid_constant__ CUtensorMap img_map,
+                                                       const __grid_constant__ CUtensorMap p_map,
+                                                       const SweepArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  if ((smem_u32(smem) & 127u) != 0u) {  // TMA destinations must be 128-byte aligned
+    if (threadIdx.x == 0) atomicOr(a.status, kStatusSmemMisaligned);
+    return;
+  }
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kSmemBar);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  sweep_tile<K, TS>(a, &img_map, &p_map, blockIdx.x, blockIdx.y, smem, 0u, true, false);
+}
+
+// Persistent form for uneven batches: every CTA takes items from one queue
+// (head counter in global memory) until it is empty; items of one frame are
+// adjacent, so a CTA restages the frame's tables only when the frame changes.
+// frames[] holds per-frame arguments and TMA descriptors in global memory.
+template <int K, typename TS>
+__global__ void __launch_bounds__(256, LF_SWEEP_MIN_BLOCKS) em_sweep_persistent(const FrameDesc* frames,
+                                                                                const TileItem* items,
+                                                                                const int* first_item,
+                                                                                const int* n_items,
+                                                                                unsigned* head) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  SweepArgs* s_args = reinterpret_cast<SweepArgs*>(smem + kSmemArgs);
+  int* s_item = reinterpret_cast<int*>(smem + kSmemItem);
+  if ((smem_u32(smem) & 127u) != 0u) {
+    if (threadIdx.x == 0) atomicOr(frames[0].args.status, kStatusSmemMisaligned);
+    return;
+  }
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kSmemBar);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int n = *n_items;
+  items += *first_item;  // this camera count's items start here
+  int cur = -1;
+  unsigned phase = 0;
+  for (;;) {
+    if (threadIdx.x == 0) *s_item = static_cast<int>(atomicAdd(head, 1u));
+    __syncthreads();
+    const int it = *s_item;
+    if (it >= n) break;
+    const TileItem item = items[it];
+    const bool fresh = item.frame != cur;
+    if (fresh) {
+      const int* src = reinterpret_cast<const int*>(&frames[item.frame].args);
+      int* dst = reinterpret_cast<int*>(s_args);
+      for (int i = threadIdx.x; i < static_cast<int>(sizeof(SweepArgs) / 4); i += blockDim.x) dst[i] = src[i];
+      cur = item.frame;
+      __syncthreads();
+    }
+    if (!sweep_tile<K, TS>(*s_args, &frames[item.frame].img_map, &frames[item.frame].p_map, item.x, item.y,
+                           smem, phase, fresh, true))
+      break;  // a bounded wait expired: stop taking work (the status word says why)
+    phase ^= 1u;
+  }
 }
 
 template <int K, typename TS>
@@ -708,6 +787,29 @@ cudaError_t launch_em_sweep_k(const CUtensorMap& img_map, const CUtensorMap& p_m
   }
   dim3 grid((a.W + a.TW - 1) / a.TW, (a.H + a.TR - 1) / a.TR);
   em_sweep_kernel<K, TS><<<grid, a.TR * a.TW, smem, s>>>(img_map, p_map, a);
+  return cudaGetLastError();
+}
+
+template <int K, typename TS>
+int em_sweep_persistent_occupancy_k(size_t smem) {
+  cudaFuncSetAttribute(em_sweep_persistent<K, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, em_sweep_persistent<K, TS>, 256, smem) != cudaSuccess)
+    return 0;
+  return blocks;
+}
+
+template <int K, typename TS>
+cudaError_t launch_em_sweep_persistent_k(const FrameDesc* frames, const TileItem* items, const int* first_item,
+                                         const int* n_items, unsigned* head, size_t smem, int grid, cudaStream_t s) {
+  static int configured = -1;
+  if (static_cast<int>(smem) > configured) {
+    cudaError_t e = cudaFuncSetAttribute(em_sweep_persistent<K, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    configured = static_cast<int>(smem);
+  }
+  em_sweep_persistent<K, TS><<<grid, 256, smem, s>>>(frames, items, first_item, n_items, head);
   return cudaGetLastError();
 }
 

@@ -18,8 +18,11 @@
 #include "lf_internal.h"
 
 namespace lf {
-#define LF_DECL_SWEEP(t, k) \
-  cudaError_t launch_em_sweep_##t##_k##k(const CUtensorMap&, const CUtensorMap&, const SweepArgs&, cudaStream_t);
+#define LF_DECL_SWEEP(t, k)                                                                                   \
+  cudaError_t launch_em_sweep_##t##_k##k(const CUtensorMap&, const CUtensorMap&, const SweepArgs&, cudaStream_t); \
+  cudaError_t launch_em_sweep_persistent_##t##_k##k(const FrameDesc*, const TileItem*, const int*, const int*, \
+                                                    unsigned*, size_t, int, cudaStream_t);                      \
+  int em_sweep_persistent_occupancy_##t##_k##k(size_t);
 #define LF_DECL_SWEEPS(t)                                                                                     \
   LF_DECL_SWEEP(t, 1) LF_DECL_SWEEP(t, 2) LF_DECL_SWEEP(t, 3) LF_DECL_SWEEP(t, 4) LF_DECL_SWEEP(t, 5)           \
   LF_DECL_SWEEP(t, 6) LF_DECL_SWEEP(t, 7) LF_DECL_SWEEP(t, 8) LF_DECL_SWEEP(t, 9) LF_DECL_SWEEP(t, 10)          \
@@ -44,6 +47,40 @@ cudaError_t launch_em_sweep(int K, const CUtensorMap& i, const CUtensorMap& p, c
 #undef LF_ROW
   if (K < 1 || K > kMaxCams || a.prec < 0 || a.prec > 2) return cudaErrorInvalidValue;
   return table[a.prec][K - 1](i, p, a, s);
+}
+
+typedef cudaError_t (*PersistentLaunch)(const FrameDesc*, const TileItem*, const int*, const int*, unsigned*,
+                                        size_t, int, cudaStream_t);
+typedef int (*PersistentOcc)(size_t);
+
+cudaError_t launch_em_sweep_persistent(int K, int prec, const FrameDesc* frames, const TileItem* items,
+                                       const int* first_item, const int* n_items, unsigned* head, size_t smem,
+                                       int grid, cudaStream_t s) {
+#define LF_ROW(t)                                                                                   \
+  {launch_em_sweep_persistent_##t##_k1, launch_em_sweep_persistent_##t##_k2,                         \
+   launch_em_sweep_persistent_##t##_k3, launch_em_sweep_persistent_##t##_k4,                         \
+   launch_em_sweep_persistent_##t##_k5, launch_em_sweep_persistent_##t##_k6,                         \
+   launch_em_sweep_persistent_##t##_k7, launch_em_sweep_persistent_##t##_k8,                         \
+   launch_em_sweep_persistent_##t##_k9, launch_em_sweep_persistent_##t##_k10,                        \
+   launch_em_sweep_persistent_##t##_k11, launch_em_sweep_persistent_##t##_k12}
+  static const PersistentLaunch table[3][kMaxCams] = {LF_ROW(f32), LF_ROW(f16), LF_ROW(bf16)};
+#undef LF_ROW
+  if (K < 1 || K > kMaxCams || prec < 0 || prec > 2) return cudaErrorInvalidValue;
+  return table[prec][K - 1](frames, items, first_item, n_items, head, smem, grid, s);
+}
+
+int em_sweep_persistent_occupancy(int K, int prec, size_t smem) {
+#define LF_ROW(t)                                                                                       \
+  {em_sweep_persistent_occupancy_##t##_k1, em_sweep_persistent_occupancy_##t##_k2,                       \
+   em_sweep_persistent_occupancy_##t##_k3, em_sweep_persistent_occupancy_##t##_k4,                       \
+   em_sweep_persistent_occupancy_##t##_k5, em_sweep_persistent_occupancy_##t##_k6,                       \
+   em_sweep_persistent_occupancy_##t##_k7, em_sweep_persistent_occupancy_##t##_k8,                       \
+   em_sweep_persistent_occupancy_##t##_k9, em_sweep_persistent_occupancy_##t##_k10,                      \
+   em_sweep_persistent_occupancy_##t##_k11, em_sweep_persistent_occupancy_##t##_k12}
+  static const PersistentOcc table[3][kMaxCams] = {LF_ROW(f32), LF_ROW(f16), LF_ROW(bf16)};
+#undef LF_ROW
+  if (K < 1 || K > kMaxCams || prec < 0 || prec > 2) return 0;
+  return table[prec][K - 1](smem);
 }
 }  // namespace lf
 

@@ -60,6 +60,14 @@ struct SweepArgs {
   unsigned long long timeout_ns;   // bounded-wait limit
 };
 
+// Per-frame arguments of the persistent sweep, in global memory (TMA
+// descriptors must be 64-byte aligned).
+struct alignas(64) FrameDesc {
+  CUtensorMap img_map;
+  CUtensorMap p_map;
+  SweepArgs args;
+};
+
 struct RefocusArgs {
   int H, W, C, K, ref, dtype, KP;
   size_t pitch;                    // bytes per image row
@@ -71,6 +79,22 @@ struct RefocusArgs {
   float* out;                      // [H][W][C]
 };
 
+struct MedianArgs {
+  int H, W, C;
+  const float* in;
+  float* out;                      // null: frame has no refocus output
+};
+
+// Work item of the batched raster-order kernels: one row of one frame.
+struct RowItem {
+  int frame, row;
+};
+
+// Work item of the persistent sweep: tile (x, y) of frame `frame`.
+struct TileItem {
+  int frame, x, y, pad;
+};
+
 // Shared-memory bytes of the sweep kernel for a tile configuration.
 size_t sweep_smem_bytes(int K, const SweepArgs& a);
 
@@ -79,6 +103,18 @@ cudaError_t launch_em_sweep(int K, const CUtensorMap& img_map, const CUtensorMap
                             const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_refocus(const RefocusArgs& a, cudaStream_t s);
 cudaError_t launch_median3(const float* in, float* out, int H, int W, int C, cudaStream_t s);
+cudaError_t launch_prior_raster_batched(const PriorArgs* frames, const RowItem* items, const int* n_items,
+                                        int grid, cudaStream_t s);
+cudaError_t launch_refocus_batched(const RefocusArgs* frames, const RowItem* items, const int* n_items, int grid,
+                                   cudaStream_t s);
+cudaError_t launch_median3_batched(const MedianArgs* frames, const RowItem* items, const int* n_items, int grid,
+                                   cudaStream_t s);
+// Persistent sweep over the items of one camera count.
+cudaError_t launch_em_sweep_persistent(int K, int prec, const FrameDesc* frames, const TileItem* items,
+                                       const int* first_item, const int* n_items, unsigned* head, size_t smem,
+                                       int grid, cudaStream_t s);
+// Resident CTAs per SM of the persistent sweep for this shared-memory size.
+int em_sweep_persistent_occupancy(int K, int prec, size_t smem);
 // float32 [rows][W*C] (pitch_in bytes) -> float16 (to_bf16 = 0) or bfloat16 rows (pitch_out bytes)
 cudaError_t launch_convert_f32(const uint8_t* in, size_t pitch_in, uint8_t* out, size_t pitch_out, int rows,
                                int cols, int to_bf16, cudaStream_t s);

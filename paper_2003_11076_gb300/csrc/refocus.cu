@@ -29,10 +29,7 @@ __global__ void convert_f32_kernel(const uint8_t* in, size_t pitch_in, uint8_t* 
   else reinterpret_cast<__half*>(o)[x] = __float2half_rn(v);
 }
 
-__global__ void refocus_kernel(const RefocusArgs a) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  const int v = blockIdx.y * blockDim.y + threadIdx.y;
-  if (u >= a.W || v >= a.H) return;
+__device__ __forceinline__ void refocus_pixel(const RefocusArgs& a, int u, int v) {
   const size_t pix = static_cast<size_t>(v) * a.W + u;
   const int j = a.d_idx[pix];
   const unsigned S = a.labels[pix];
@@ -63,16 +60,30 @@ __global__ void refocus_kernel(const RefocusArgs a) {
   }
 }
 
+__global__ void refocus_kernel(const RefocusArgs a) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y * blockDim.y + threadIdx.y;
+  if (u >= a.W || v >= a.H) return;
+  refocus_pixel(a, u, v);
+}
+
+__global__ void refocus_batched(const RefocusArgs* frames, const RowItem* items, const int* n_items) {
+  const int n = *n_items;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const RowItem r = items[it];
+    const RefocusArgs& f = frames[r.frame];
+    if (!f.out) continue;
+    for (int u = threadIdx.x; u < f.W; u += blockDim.x) refocus_pixel(f, u, r.row);
+  }
+}
+
 __device__ __forceinline__ void sort2(float& x, float& y) {
   const float lo = fminf(x, y), hi = fmaxf(x, y);
   x = lo;
   y = hi;
 }
 
-__global__ void median3_kernel(const float* in, float* out, int H, int W, int C) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  const int v = blockIdx.y * blockDim.y + threadIdx.y;
-  if (u >= W || v >= H) return;
+__device__ __forceinline__ void median_pixel(const float* in, float* out, int H, int W, int C, int u, int v) {
   for (int c = 0; c < C; ++c) {
     float p[9];
     int n = 0;
@@ -93,6 +104,23 @@ __global__ void median3_kernel(const float* in, float* out, int H, int W, int C)
   }
 }
 
+__global__ void median3_kernel(const float* in, float* out, int H, int W, int C) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y * blockDim.y + threadIdx.y;
+  if (u >= W || v >= H) return;
+  median_pixel(in, out, H, W, C, u, v);
+}
+
+__global__ void median3_batched(const MedianArgs* frames, const RowItem* items, const int* n_items) {
+  const int n = *n_items;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const RowItem r = items[it];
+    const MedianArgs& f = frames[r.frame];
+    if (!f.out) continue;
+    for (int u = threadIdx.x; u < f.W; u += blockDim.x) median_pixel(f.in, f.out, f.H, f.W, f.C, u, r.row);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_refocus(const RefocusArgs& a, cudaStream_t s) {
@@ -106,6 +134,18 @@ cudaError_t launch_convert_f32(const uint8_t* in, size_t pitch_in, uint8_t* out,
                                int cols, int to_bf16, cudaStream_t s) {
   dim3 grid((cols + 255) / 256, rows);
   convert_f32_kernel<<<grid, 256, 0, s>>>(in, pitch_in, out, pitch_out, rows, cols, to_bf16);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refocus_batched(const RefocusArgs* frames, const RowItem* items, const int* n_items, int grid,
+                                   cudaStream_t s) {
+  refocus_batched<<<grid, 256, 0, s>>>(frames, items, n_items);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_median3_batched(const MedianArgs* frames, const RowItem* items, const int* n_items, int grid,
+                                   cudaStream_t s) {
+  median3_batched<<<grid, 256, 0, s>>>(frames, items, n_items);
   return cudaGetLastError();
 }
 

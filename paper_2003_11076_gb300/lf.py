@@ -22,7 +22,9 @@ LF_PREC_F32, LF_PREC_F16, LF_PREC_BF16 = 0, 1, 2
 
 EXPORTS = ("lf_default_params", "lf_create", "lf_set_stream", "lf_set_inputs", "lf_run_em",
            "lf_synchronize", "lf_get_prior", "lf_get_stats", "lf_last_error", "lf_destroy",
-           "lf_triangulate", "lf_set_timing", "lf_run_em_static")
+           "lf_triangulate", "lf_set_timing", "lf_run_em_static", "lf_batch_create", "lf_batch_set_stream",
+           "lf_batch_add", "lf_batch_run", "lf_batch_synchronize", "lf_batch_clear", "lf_batch_get_stats",
+           "lf_batch_destroy")
 
 
 class LfError(RuntimeError):
@@ -45,7 +47,7 @@ class Stats(ctypes.Structure):
                 ("tile_rows", ctypes.c_int), ("tile_cols", ctypes.c_int),
                 ("kernels_launched", ctypes.c_int),
                 ("ms_prior", ctypes.c_float), ("ms_sweep", ctypes.c_float), ("ms_refocus", ctypes.c_float),
-                ("ms_median", ctypes.c_float)]
+                ("ms_median", ctypes.c_float), ("graph_captures", ctypes.c_int)]
 
 
 _lib = None
@@ -79,6 +81,19 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lf_run_em_static.argtypes = [I, P, I, I, ctypes.c_float, ctypes.c_float, I, ctypes.POINTER(Params), I,
                                      P, I, I, P, P, P, P, P, P, P]
     lib.lf_run_em_static.restype = I
+    lib.lf_batch_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(Params), I]
+    lib.lf_batch_set_stream.argtypes = [P, P]
+    lib.lf_batch_add.argtypes = [P, I, P, I, I, ctypes.c_float, ctypes.c_float, I, I, P, I, I, P, P, I,
+                                 P, P, P, P, P, ctypes.POINTER(I)]
+    lib.lf_batch_run.argtypes = [P]
+    lib.lf_batch_synchronize.argtypes = [P]
+    lib.lf_batch_clear.argtypes = [P]
+    lib.lf_batch_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    lib.lf_batch_destroy.argtypes = [P]
+    lib.lf_batch_destroy.restype = None
+    for name in ("lf_batch_create", "lf_batch_set_stream", "lf_batch_add", "lf_batch_run",
+                 "lf_batch_synchronize", "lf_batch_clear", "lf_batch_get_stats"):
+        getattr(lib, name).restype = I
     lib.lf_triangulate.argtypes = [P, I, P, I]
     lib.lf_triangulate.restype = I
     for name in ("lf_create", "lf_set_stream", "lf_set_inputs", "lf_run_em", "lf_synchronize",
@@ -266,6 +281,84 @@ class Context:
         s = Stats()
         _check(load().lf_get_stats(self._h, ctypes.byref(s)))
         return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+
+class Batch:
+    """Uneven batch of frames on device buffers (torch CUDA tensors), run as
+    one CUDA graph (see lf_batch_* in include/lf.h)."""
+
+    def __init__(self, params: Optional[Params] = None, stream=None):
+        h = ctypes.c_void_p()
+        _check(load().lf_batch_create(ctypes.byref(h), ctypes.byref(params) if params is not None else None, 0))
+        self._h = h
+        self._keep = []
+        if stream is not None:
+            self.set_stream(stream)
+
+    def set_stream(self, stream):
+        handle = getattr(stream, "cuda_stream", stream)
+        _check(load().lf_batch_set_stream(self._h, ctypes.c_void_p(handle or 0)))
+
+    def add(self, baselines, d_min, d_max, D, iters, images, seg_prior, points, out: dict) -> int:
+        """images / seg_prior: torch CUDA tensors; out: preallocated torch
+        CUDA tensors ("d_idx" required; "d", "post", "labels", "refocus")."""
+        import torch
+        b = np.ascontiguousarray(baselines, np.float32)
+        pts = np.ascontiguousarray(points, np.float32).reshape(-1, 3)
+        K, H, W = images.shape[:3]
+        C = 1 if images.dim() == 3 else int(images.shape[3])
+        dt = {torch.uint8: LF_U8, torch.float32: LF_F32, torch.float16: LF_F16, torch.bfloat16: LF_BF16}[images.dtype]
+        ptr = lambda k: out[k].data_ptr() if k in out else None
+        idx = ctypes.c_int(-1)
+        _check(load().lf_batch_add(self._h, int(K), b.ctypes.data, int(H), int(W), float(d_min), float(d_max),
+                                   int(D), int(iters), images.data_ptr(), C, dt, seg_prior.data_ptr(),
+                                   pts.ctypes.data, pts.shape[0], ptr("d_idx"), ptr("d"), ptr("post"),
+                                   ptr("labels"), ptr("refocus"), ctypes.byref(idx)))
+        self._keep.append((images, seg_prior, out))
+        return idx.value
+
+    def run(self):
+        _check(load().lf_batch_run(self._h))
+
+    def synchronize(self):
+        _check(load().lf_batch_synchronize(self._h))
+
+    def clear(self):
+        _check(load().lf_batch_clear(self._h))
+        self._keep = []
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(load().lf_batch_get_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def device_outputs(K: int, H: int, W: int, C: int, device=None) -> dict:
+    """Preallocated torch CUDA output tensors for one frame."""
+    import torch
+    dev = device or torch.device("cuda")
+    return {"d_idx": torch.empty((H, W), dtype=torch.int32, device=dev),
+            "d": torch.empty((H, W), dtype=torch.float32, device=dev),
+            "post": torch.empty((K, H, W), dtype=torch.float32, device=dev),
+            "labels": torch.empty((H, W), dtype=torch.int16, device=dev),
+            "refocus": torch.empty((H, W, C) if C > 1 else (H, W), dtype=torch.float32, device=dev)}
 
 
 def run_scene(scene, params: Optional[Params] = None, iters: Optional[int] = None, **kw) -> dict:
