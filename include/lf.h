@@ -75,7 +75,8 @@ typedef enum lf_precision {
  * initial threshold (Sec. III-C energy, Sec. III-F) but prints a value only
  * for the threshold (0.7); the defaults of lf_default_params are
  * beta = 200, gamma = 0.1, sigma = 2, seg_threshold = 0.7, eps = 1e-4,
- * mstep_seg_term = 1, median = 0, precision = LF_PREC_F32, early_exit = 1.
+ * mstep_seg_term = 1, median = 0, precision = LF_PREC_F32, early_exit = 1,
+ * dynamic_only = 0.
  */
 typedef struct lf_params {
     float beta;          /* weight of the static rays' descriptor variance */
@@ -88,8 +89,12 @@ typedef struct lf_params {
                             0: likelihood + disparity prior only (Eq. mstep) */
     int median;          /* 1: 3x3 median on the refocused image (Sec. III-E) */
     int precision;       /* lf_precision */
-    int early_exit;      /* 1: a warp stops iterating once all of its pixels
-                            reached an EM fixed point (results are identical) */
+    int early_exit;      /* 1: a pixel stops iterating once it reached an EM
+                            fixed point (results are identical) */
+    int dynamic_only;    /* 1: reconstruct only the reference pixels whose
+                            P(dynamic) >= seg_threshold (Sec. III-F: the other
+                            pixels already show the static background); see
+                            lf_run_em for what the other pixels receive */
 } lf_params;
 
 /* Statistics accumulated over the lf_run_em calls since the previous
@@ -104,6 +109,7 @@ typedef struct lf_stats {
     float ms_prior, ms_sweep, ms_refocus, ms_median; /* mean device time per run
                                       of each kernel (lf_set_timing on), else 0 */
     int graph_captures;            /* batches: CUDA graphs captured so far */
+    int tuned_signatures;          /* batches: tile shapes chosen by timing so far */
 } lf_stats;
 
 /* Fill *p with the documented defaults. */
@@ -160,6 +166,13 @@ lf_status lf_set_inputs(lf_ctx *ctx, const void *images, int C, int dtype,
  *   labels        [H][W] uint16, bit k set = ray k static in the final E-step
  *   refocused     [H][W][C] float32 in [0, 1]; pixels with no static ray keep
  *                 the reference image
+ * With dynamic_only, a reference pixel whose own P(dynamic) is below
+ * seg_threshold is not reconstructed: disparity_idx = the candidate nearest
+ * the prior centre mu (lower index on a tie; -1 outside the triangulation),
+ * disparity = that d_j (NaN outside), labels = 0, posteriors = NaN, refocused
+ * = the reference image; every other pixel gets exactly the full-mode result.
+ * Tiles without such a pixel are filled by a classification kernel and never
+ * staged.
  * outputs_on_device: 1 = device pointers (the call returns once the work is
  * enqueued; lf_synchronize waits and reports device errors); 0 = host pointers
  * (the call waits for the results).
@@ -178,6 +191,13 @@ lf_status lf_synchronize(lf_ctx *ctx);
  * mu [H][W] float32, the interpolated disparity, NaN outside the
  * triangulation.  on_device as for lf_run_em outputs. */
 lf_status lf_get_prior(lf_ctx *ctx, float *mu, int on_device);
+
+/* Sweep tile shape: tile_rows x tile_cols reference pixels per CTA (one
+ * thread each; tile_cols a multiple of 32, rows * cols <= 256).  0, 0 restores
+ * the library's choice.  LF_EINVAL if the shape does not fit the staging
+ * limits of the current inputs.  The batch autotuner uses this to time
+ * candidate shapes. */
+lf_status lf_set_tile(lf_ctx *ctx, int tile_rows, int tile_cols);
 
 /* 1: record CUDA events on the context's stream around every kernel that
  * lf_run_em enqueues, so that lf_get_stats reports their mean device times
@@ -206,7 +226,12 @@ void lf_destroy(lf_ctx *ctx);
  * when the batch's shape changes (camera counts present, shared-memory size,
  * or a work list outgrowing its buffer); otherwise it is replayed.
  *
- * lf_batch_create: p as for lf_create (copied); autotune reserved (0).
+ * lf_batch_create: p as for lf_create (copied).  autotune = 1: before a
+ *   frame whose signature (camera count, D, bytes per pixel, precision,
+ *   halo width and width class) has not been seen in this process runs, its
+ *   candidate 256-thread tile shapes are timed on that frame through the
+ *   single-frame path and the fastest is kept for the signature (a one-off
+ *   cost, synchronous); 0: the first shape that fits.
  * lf_batch_add: queue one frame.  images, seg_prior and every output are
  *   DEVICE pointers with the layouts of lf_set_inputs / lf_run_em, owned by
  *   the caller and kept alive until lf_batch_synchronize returns; outputs may

@@ -279,6 +279,91 @@ __device__ __forceinline__ int m_step(const SweepArgs& a, const Staged<TS>& st, 
   return jb;
 }
 
+// M-step with fixed labels S: every iteration after the first, and the first
+// when its labels do not depend on the candidate.  With g_k = m_k + w_jk s_k
+// (m_k: camera k's tap at floor(x) shifted by the reference descriptor, s_k:
+// the slope to the next tap; both zero for a dynamic ray) the static rays'
+// sums are
+//   sum_k g_k     = sum_k m_k     + sum_k w_jk s_k
+//   sum_k |g_k|^2 = sum_k |m_k|^2 + sum_k w_jk (2 m_k.s_k + w_jk |s_k|^2)
+// and likewise for the log priors, so one candidate costs six fused
+// multiply-adds per ray.  The base sums over k change only at candidates
+// where some camera's tap moves; they are then summed afresh (no drift).
+template <int K, typename TS>
+__device__ __forceinline__ int m_step_fixed(const SweepArgs& a, const Staged<TS>& st, const float* s_w,
+                                            const int* s_o, const unsigned* s_chg, const float* s_d,
+                                            const float* s_rcp, float cy, float cx, float cz, float mu,
+                                            bool inside, unsigned S) {
+  float my[K], mx[K], mz[K], sy[K], sx[K], sz[K], ml[K], sl[K], A[K], C[K], q0[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    my[k] = mx[k] = mz[k] = sy[k] = sx[k] = sz[k] = ml[k] = sl[k] = A[k] = C[k] = q0[k] = 0.f;
+  }
+  float BY = 0.f, BX = 0.f, BZ = 0.f, BQ = 0.f, BL = 0.f;
+  const int SWp = st.SWp;
+  const float rn = s_rcp[__popc(S)];
+  float best = -INFINITY;
+  int jb = 0;
+  for (int j = 0; j < a.D; ++j) {
+    const unsigned ch = s_chg[j];
+    float w[K];
+    {
+      const float4* w4 = reinterpret_cast<const float4*>(s_w + j * a.KP);
+#pragma unroll
+      for (int q = 0; q < (K + 3) / 4; ++q) {
+        const float4 t = w4[q];
+        if (4 * q + 0 < K) w[(4 * q + 0) % K] = t.x;
+        if (4 * q + 1 < K) w[(4 * q + 1) % K] = t.y;
+        if (4 * q + 2 < K) w[(4 * q + 2) % K] = t.z;
+        if (4 * q + 3 < K) w[(4 * q + 3) % K] = t.w;
+      }
+    }
+    if (ch) {  // same for every pixel: warp-uniform branch
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (!(ch & (1u << k))) continue;
+        const int c = st.cbase + s_o[j * a.KP + k];
+        const TS* Fk = st.F + k * st.cam_stride;
+        const bool stat = (S >> k) & 1u;
+        const float s = stat ? 1.f : 0.f;
+        const float Y0 = ldf(Fk + c), X0 = ldf(Fk + SWp + c), Z0 = ldf(Fk + 2 * SWp + c);
+        my[k] = s * (Y0 - cy); sy[k] = s * (ldf(Fk + c + 1) - Y0);
+        mx[k] = s * (X0 - cx); sx[k] = s * (ldf(Fk + SWp + c + 1) - X0);
+        mz[k] = s * (Z0 - cz); sz[k] = s * (ldf(Fk + 2 * SWp + c + 1) - Z0);
+        const TS* Lk = Fk + (stat ? kMapLs : kMapLd) * SWp;
+        ml[k] = ldf(Lk + c); sl[k] = ldf(Lk + c + 1) - ml[k];
+        A[k] = 2.f * fmaf(mz[k], sz[k], fmaf(mx[k], sx[k], my[k] * sy[k]));
+        C[k] = fmaf(sz[k], sz[k], fmaf(sx[k], sx[k], sy[k] * sy[k]));
+        q0[k] = fmaf(mz[k], mz[k], fmaf(mx[k], mx[k], my[k] * my[k]));
+      }
+      BY = my[0]; BX = mx[0]; BZ = mz[0]; BQ = q0[0]; BL = ml[0];
+#pragma unroll
+      for (int k = 1; k < K; ++k) {
+        BY += my[k]; BX += mx[k]; BZ += mz[k]; BQ += q0[k]; BL += ml[k];
+      }
+    }
+    float SY = BY, SX = BX, SZ = BZ, Q = BQ, SL = BL;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      SY = fmaf(w[k], sy[k], SY);
+      SX = fmaf(w[k], sx[k], SX);
+      SZ = fmaf(w[k], sz[k], SZ);
+      SL = fmaf(w[k], sl[k], SL);
+      Q = fmaf(w[k], fmaf(w[k], C[k], A[k]), Q);
+    }
+    const float ss = fmaf(SZ, SZ, fmaf(SX, SX, SY * SY));
+    const float var = fmaf(-ss, rn, Q) * rn;
+    float J = a.mseg ? SL : 0.f;
+    if (inside) {
+      const float t = s_d[j] - mu;
+      J += __logf(a.gamma + __expf(-(t * t) * a.inv2s2));
+    }
+    J = fmaf(-a.beta, var, J);
+    if (J > best) { best = J; jb = j; }
+  }
+  return jb;
+}
+
 // First-iteration labels of one pixel when they are the same for every
 // candidate: bit k of *mask is camera k's label (static) and the return value
 // says whether every camera's Z texels stay clear of the threshold.
@@ -435,6 +520,64 @@ __device__ __forceinline__ void enumerate(const Rays& r, const float* s_rcp, flo
   }
 }
 
+// Outputs of a reference pixel that the dynamic-only mode does not
+// reconstruct: disparity from the prior (nearest candidate, lower on a tie;
+// -1 / NaN outside the triangulation), no static ray, no posteriors (NaN).
+template <int K>
+__device__ __forceinline__ void write_static_pixel(const SweepArgs& a, int u, int v) {
+  const size_t pix = static_cast<size_t>(v) * a.W + u;
+  const float mu = a.mu[pix];
+  int j = -1;
+  if (!isnan(mu)) {
+    j = 0;
+    float bd = fabsf(a.dval[0] - mu);
+    for (int i = 1; i < a.D; ++i) {
+      const float dd = fabsf(a.dval[i] - mu);
+      if (dd < bd) { bd = dd; j = i; }
+    }
+  }
+  const float nan = __int_as_float(0x7fc00000);
+  a.d_idx[pix] = j;
+  if (a.d_out) a.d_out[pix] = j >= 0 ? a.dval[j] : nan;
+  if (a.labels) a.labels[pix] = 0;
+  if (a.post) {
+    const size_t HW = static_cast<size_t>(a.H) * a.W;
+#pragma unroll
+    for (int k = 0; k < K; ++k) a.post[k * HW + pix] = nan;
+  }
+}
+
+// Dynamic-only mode, before the sweep: one CTA per tile.  A tile with a
+// reference pixel whose P(dynamic) reaches the threshold is appended to the
+// list the sweep walks; the pixels of every other tile get their outputs here.
+template <int K>
+__global__ void tile_classify_kernel(const SweepArgs a, const float* seg_prior, size_t p_pitch, int* tile_list,
+                                     int* n_tiles) {
+  const int tiles_x = (a.W + a.TW - 1) / a.TW;
+  const int tile = blockIdx.x, u0 = (tile % tiles_x) * a.TW, v0 = (tile / tiles_x) * a.TR;
+  const int u = u0 + threadIdx.x % a.TW, v = v0 + threadIdx.x / a.TW;
+  const bool valid = u < a.W && v < a.H;
+  bool dyn = false;
+  if (valid) {
+    const float* row = reinterpret_cast<const float*>(reinterpret_cast<const uint8_t*>(seg_prior) +
+                                                      (static_cast<size_t>(a.ref) * a.H + v) * p_pitch);
+    dyn = row[u] >= a.seg_threshold;
+  }
+  if (__syncthreads_or(dyn)) {
+    if (threadIdx.x == 0) tile_list[atomicAdd(n_tiles, 1)] = tile;
+  } else if (valid) {
+    write_static_pixel<K>(a, u, v);
+  }
+}
+
+template <int K>
+cudaError_t launch_tile_classify_k(const SweepArgs& a, const float* seg_prior, size_t p_pitch, int* tile_list,
+                                   int* n_tiles, cudaStream_t s) {
+  const int tiles = ((a.W + a.TW - 1) / a.TW) * ((a.H + a.TR - 1) / a.TR);
+  tile_classify_kernel<K><<<tiles, a.TR * a.TW, 0, s>>>(a, seg_prior, p_pitch, tile_list, n_tiles);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------- tile bookkeeping
 // Everything one thread needs to run the EM of pixel p of the tile.
 template <typename TS>
@@ -486,10 +629,14 @@ __device__ __forceinline__ int compact(bool pred, int16_t* list, int base, int* 
 }
 
 // ---------------------------------------------------------------- kernel
-// Minimum resident CTAs per SM requested from the register allocator.
-#ifndef LF_SWEEP_MIN_BLOCKS
-#define LF_SWEEP_MIN_BLOCKS 1
-#endif
+// Minimum resident 256-thread CTAs per SM requested from the register
+// allocator: two (at most 128 registers) up to eight cameras; above that the
+// register taps and the wider E-step need more than 128 registers without
+// spilling, so one.
+template <int K>
+constexpr int sweep_min_blocks() {
+  return K <= 8 ? 2 : 1;
+}
 
 // One tile (tile_x, tile_y) of one frame: stage, run the EM, write the
 // outputs.  The CTA's mbarrier (initialised by the caller) completes phase
@@ -589,7 +736,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     const float gy = ((a20 + 2.f * a21) + a22) - ((a00 + 2.f * a01) + a02);
     const float P = s_p[(static_cast<size_t>(k) * a.TR + (V - v0)) * RW + c0];
     TS* F = s_feat + static_cast<size_t>(k) * cam_stride + static_cast<size_t>(r) * kMaps * a.SWp;
-    const float ls = logf(fmaxf(1.f - P, a.eps)), ld = logf(fmaxf(P, a.eps));
+    const float ls = __logf(fmaxf(1.f - P, a.eps)), ld = __logf(fmaxf(P, a.eps));
     stf(F + kMapY * a.SWp + c, a11);
     stf(F + kMapSx * a.SWp + c, gx * 0.125f);
     stf(F + kMapSy * a.SWp + c, gy * 0.125f);
@@ -618,7 +765,15 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
   int* s_wcnt = reinterpret_cast<int*>(smem + Ly.wcnt);
   const int warp = tid >> 5;
 
-  const bool my_valid = (u0 + tid % a.TW < W) && (v0 + tid / a.TW < H);
+  bool my_valid = (u0 + tid % a.TW < W) && (v0 + tid / a.TW < H);
+  if (a.dyn_only && my_valid) {  // Sec. III-F: only the reference pixels flagged dynamic
+    const int r = tid / a.TW, u = u0 + tid % a.TW;
+    const float Pref = s_p[(static_cast<size_t>(a.ref) * a.TR + r) * RW + (u - cs)];
+    if (!(Pref >= a.seg_threshold)) {
+      write_static_pixel<K>(a, u, v0 + r);
+      my_valid = false;
+    }
+  }
   {
     const PixelCtx<TS> me = load_pixel(a, s_feat, u0, v0, cam_stride, tid);
     unsigned S0 = 0;
@@ -639,7 +794,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     const bool f0 = ps.fixed0[p];
     const unsigned S0 = ps.S0[p];
     const bool fast = __all_sync(0xffffffffu, f0);
-    const int jb = fast ? m_step<K, false, TS>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, S0)
+    const int jb = fast ? m_step_fixed<K, TS>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, S0)
                         : m_step<K, true, TS>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, 0u);
     Rays rays;
     sample_rays<K, TS>(a, c.st, s_w, s_o, jb, c.cy, c.cx, c.cz, rays);
@@ -665,7 +820,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
       const int p = ps.list[active ? tid : n - 1];
       const PixelCtx<TS> c = load_pixel(a, s_feat, u0, v0, cam_stride, p);
       const unsigned Sp = ps.S[p];
-      const int jb = m_step<K, false, TS>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, Sp);
+      const int jb = m_step_fixed<K, TS>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, Sp);
       Rays rays;
       sample_rays<K, TS>(a, c.st, s_w, s_o, jb, c.cy, c.cx, c.cz, rays);
       unsigned S = 0;
@@ -709,7 +864,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
 
 // One CTA per tile of one frame.
 template <int K, typename TS>
-__global__ void __launch_bounds__(256, LF_SWEEP_MIN_BLOCKS) em_sweep_kernel(const __grid_constant__ CUtensorMap img_map,
+__global__ void __launch_bounds__(256, sweep_min_blocks<K>()) em_sweep_kernel(const __grid_constant__ CUtensorMap img_map,
                                                        const __grid_constant__ CUtensorMap p_map,
                                                        const SweepArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
@@ -723,7 +878,14 @@ __global__ void __launch_bounds__(256, LF_SWEEP_MIN_BLOCKS) em_sweep_kernel(cons
     fence_mbar_init();
   }
   __syncthreads();
-  sweep_tile<K, TS>(a, &img_map, &p_map, blockIdx.x, blockIdx.y, smem, 0u, true, false);
+  int tx = blockIdx.x, ty = blockIdx.y;
+  if (a.tile_list) {  // dynamic-only: this CTA's tile comes from the classified list
+    if (static_cast<int>(blockIdx.x) >= *a.n_tiles) return;
+    const int id = a.tile_list[blockIdx.x], tiles_x = (a.W + a.TW - 1) / a.TW;
+    tx = id % tiles_x;
+    ty = id / tiles_x;
+  }
+  sweep_tile<K, TS>(a, &img_map, &p_map, tx, ty, smem, 0u, true, false);
 }
 
 // Persistent form for uneven batches: every CTA takes items from one queue
@@ -731,7 +893,7 @@ __global__ void __launch_bounds__(256, LF_SWEEP_MIN_BLOCKS) em_sweep_kernel(cons
 // adjacent, so a CTA restages the frame's tables only when the frame changes.
 // frames[] holds per-frame arguments and TMA descriptors in global memory.
 template <int K, typename TS>
-__global__ void __launch_bounds__(256, LF_SWEEP_MIN_BLOCKS) em_sweep_persistent(const FrameDesc* frames,
+__global__ void __launch_bounds__(256, sweep_min_blocks<K>()) em_sweep_persistent(const FrameDesc* frames,
                                                                                 const TileItem* items,
                                                                                 const int* first_item,
                                                                                 const int* n_items,
@@ -786,22 +948,24 @@ cudaError_t launch_em_sweep_k(const CUtensorMap& img_map, const CUtensorMap& p_m
     configured = static_cast<int>(smem);
   }
   dim3 grid((a.W + a.TW - 1) / a.TW, (a.H + a.TR - 1) / a.TR);
+  if (a.tile_list) grid = dim3(grid.x * grid.y, 1);  // one CTA per listed tile (at most all)
   em_sweep_kernel<K, TS><<<grid, a.TR * a.TW, smem, s>>>(img_map, p_map, a);
   return cudaGetLastError();
 }
 
 template <int K, typename TS>
-int em_sweep_persistent_occupancy_k(size_t smem) {
+int em_sweep_persistent_occupancy_k(size_t smem, int threads) {
   cudaFuncSetAttribute(em_sweep_persistent<K, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, em_sweep_persistent<K, TS>, 256, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, em_sweep_persistent<K, TS>, threads, smem) != cudaSuccess)
     return 0;
   return blocks;
 }
 
 template <int K, typename TS>
 cudaError_t launch_em_sweep_persistent_k(const FrameDesc* frames, const TileItem* items, const int* first_item,
-                                         const int* n_items, unsigned* head, size_t smem, int grid, cudaStream_t s) {
+                                         const int* n_items, unsigned* head, size_t smem, int grid, int threads,
+                                         cudaStream_t s) {
   static int configured = -1;
   if (static_cast<int>(smem) > configured) {
     cudaError_t e = cudaFuncSetAttribute(em_sweep_persistent<K, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -809,7 +973,7 @@ cudaError_t launch_em_sweep_persistent_k(const FrameDesc* frames, const TileItem
     if (e != cudaSuccess) return e;
     configured = static_cast<int>(smem);
   }
-  em_sweep_persistent<K, TS><<<grid, 256, smem, s>>>(frames, items, first_item, n_items, head);
+  em_sweep_persistent<K, TS><<<grid, threads, smem, s>>>(frames, items, first_item, n_items, head);
   return cudaGetLastError();
 }
 

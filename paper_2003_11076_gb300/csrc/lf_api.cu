@@ -21,8 +21,8 @@ namespace lf {
 #define LF_DECL_SWEEP(t, k)                                                                                   \
   cudaError_t launch_em_sweep_##t##_k##k(const CUtensorMap&, const CUtensorMap&, const SweepArgs&, cudaStream_t); \
   cudaError_t launch_em_sweep_persistent_##t##_k##k(const FrameDesc*, const TileItem*, const int*, const int*, \
-                                                    unsigned*, size_t, int, cudaStream_t);                      \
-  int em_sweep_persistent_occupancy_##t##_k##k(size_t);
+                                                    unsigned*, size_t, int, int, cudaStream_t);                 \
+  int em_sweep_persistent_occupancy_##t##_k##k(size_t, int);
 #define LF_DECL_SWEEPS(t)                                                                                     \
   LF_DECL_SWEEP(t, 1) LF_DECL_SWEEP(t, 2) LF_DECL_SWEEP(t, 3) LF_DECL_SWEEP(t, 4) LF_DECL_SWEEP(t, 5)           \
   LF_DECL_SWEEP(t, 6) LF_DECL_SWEEP(t, 7) LF_DECL_SWEEP(t, 8) LF_DECL_SWEEP(t, 9) LF_DECL_SWEEP(t, 10)          \
@@ -30,6 +30,12 @@ namespace lf {
 LF_DECL_SWEEPS(f32)
 LF_DECL_SWEEPS(f16)
 LF_DECL_SWEEPS(bf16)
+#define LF_DECL_CLASSIFY(k) \
+  cudaError_t launch_tile_classify_k##k(const SweepArgs&, const float*, size_t, int*, int*, cudaStream_t);
+LF_DECL_CLASSIFY(1) LF_DECL_CLASSIFY(2) LF_DECL_CLASSIFY(3) LF_DECL_CLASSIFY(4) LF_DECL_CLASSIFY(5)
+LF_DECL_CLASSIFY(6) LF_DECL_CLASSIFY(7) LF_DECL_CLASSIFY(8) LF_DECL_CLASSIFY(9) LF_DECL_CLASSIFY(10)
+LF_DECL_CLASSIFY(11) LF_DECL_CLASSIFY(12)
+#undef LF_DECL_CLASSIFY
 #undef LF_DECL_SWEEPS
 #undef LF_DECL_SWEEP
 
@@ -50,12 +56,12 @@ cudaError_t launch_em_sweep(int K, const CUtensorMap& i, const CUtensorMap& p, c
 }
 
 typedef cudaError_t (*PersistentLaunch)(const FrameDesc*, const TileItem*, const int*, const int*, unsigned*,
-                                        size_t, int, cudaStream_t);
-typedef int (*PersistentOcc)(size_t);
+                                        size_t, int, int, cudaStream_t);
+typedef int (*PersistentOcc)(size_t, int);
 
 cudaError_t launch_em_sweep_persistent(int K, int prec, const FrameDesc* frames, const TileItem* items,
                                        const int* first_item, const int* n_items, unsigned* head, size_t smem,
-                                       int grid, cudaStream_t s) {
+                                       int grid, int threads, cudaStream_t s) {
 #define LF_ROW(t)                                                                                   \
   {launch_em_sweep_persistent_##t##_k1, launch_em_sweep_persistent_##t##_k2,                         \
    launch_em_sweep_persistent_##t##_k3, launch_em_sweep_persistent_##t##_k4,                         \
@@ -66,10 +72,21 @@ cudaError_t launch_em_sweep_persistent(int K, int prec, const FrameDesc* frames,
   static const PersistentLaunch table[3][kMaxCams] = {LF_ROW(f32), LF_ROW(f16), LF_ROW(bf16)};
 #undef LF_ROW
   if (K < 1 || K > kMaxCams || prec < 0 || prec > 2) return cudaErrorInvalidValue;
-  return table[prec][K - 1](frames, items, first_item, n_items, head, smem, grid, s);
+  return table[prec][K - 1](frames, items, first_item, n_items, head, smem, grid, threads, s);
 }
 
-int em_sweep_persistent_occupancy(int K, int prec, size_t smem) {
+cudaError_t launch_tile_classify(int K, const SweepArgs& a, const float* seg_prior, size_t p_pitch,
+                                 int* tile_list, int* n_tiles, cudaStream_t s) {
+  typedef cudaError_t (*Fn)(const SweepArgs&, const float*, size_t, int*, int*, cudaStream_t);
+  static const Fn table[kMaxCams] = {launch_tile_classify_k1,  launch_tile_classify_k2,  launch_tile_classify_k3,
+                                     launch_tile_classify_k4,  launch_tile_classify_k5,  launch_tile_classify_k6,
+                                     launch_tile_classify_k7,  launch_tile_classify_k8,  launch_tile_classify_k9,
+                                     launch_tile_classify_k10, launch_tile_classify_k11, launch_tile_classify_k12};
+  if (K < 1 || K > kMaxCams) return cudaErrorInvalidValue;
+  return table[K - 1](a, seg_prior, p_pitch, tile_list, n_tiles, s);
+}
+
+int em_sweep_persistent_occupancy(int K, int prec, size_t smem, int threads) {
 #define LF_ROW(t)                                                                                       \
   {em_sweep_persistent_occupancy_##t##_k1, em_sweep_persistent_occupancy_##t##_k2,                       \
    em_sweep_persistent_occupancy_##t##_k3, em_sweep_persistent_occupancy_##t##_k4,                       \
@@ -80,7 +97,7 @@ int em_sweep_persistent_occupancy(int K, int prec, size_t smem) {
   static const PersistentOcc table[3][kMaxCams] = {LF_ROW(f32), LF_ROW(f16), LF_ROW(bf16)};
 #undef LF_ROW
   if (K < 1 || K > kMaxCams || prec < 0 || prec > 2) return 0;
-  return table[prec][K - 1](smem);
+  return table[prec][K - 1](smem, threads);
 }
 }  // namespace lf
 
@@ -178,6 +195,8 @@ struct lf_ctx {
   size_t own_P_cap = 0;
   uint8_t* own_img16 = nullptr;  // 16-bit copy of float32 images in the reduced-precision modes
   size_t own_img16_cap = 0;
+  int* d_tiles = nullptr;        // dynamic-only: list of tiles to sweep, then its length
+  size_t tiles_cap = 0;
   // prior
   std::vector<PriorTri> h_tris;
   std::vector<int> h_bins;  // [nbins + 1] starts, then items
@@ -196,8 +215,9 @@ struct lf_ctx {
   size_t o_didx_cap = 0, o_d_cap = 0, o_labels_cap = 0, o_post_cap = 0, o_ref_cap = 0, o_tmp_cap = 0;
   // TMA descriptors of the current inputs
   CUtensorMap img_map{}, p_map{};
-  // tiles
+  // tiles (force_TR > 0: shape set by lf_set_tile)
   int TR = 2, TW = 128, SW = 0, SWp = 0, RW = 0;
+  int force_TR = 0, force_TW = 0;
   lf_stats stats{};
   // optional per-kernel timing: per run, events before prior, sweep, refocus,
   // median and after; summed by lf_get_stats
@@ -220,12 +240,15 @@ bool finite(float x) { return std::isfinite(x); }
 // two CTAs per SM, else at least one.
 lf_status choose_tiles(lf_ctx* c) {
   static const int cand[][2] = {{2, 128}, {1, 128}, {4, 64}, {2, 64}, {1, 64}, {2, 32}, {1, 32}};
+  const int forced[1][2] = {{c->force_TR, c->force_TW}};
   int dev_smem = 0;
   cudaError_t e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
   if (e != cudaSuccess || dev_smem <= 0) dev_smem = 227 * 1024;
   for (int pass = 0; pass < 2; ++pass) {
     const size_t limit = pass == 0 ? std::min<size_t>(dev_smem, 110 * 1024) : static_cast<size_t>(dev_smem);
-    for (auto& t : cand) {
+    const int ncand = c->force_TR > 0 ? 1 : static_cast<int>(sizeof(cand) / sizeof(cand[0]));
+    for (int ci = 0; ci < ncand; ++ci) {
+      const int* t = c->force_TR > 0 ? forced[0] : cand[ci];
       SweepArgs a{};
       a.TR = t[0];
       a.TW = t[1];
@@ -246,7 +269,8 @@ lf_status choose_tiles(lf_ctx* c) {
       return LF_OK;
     }
   }
-  return fail(LF_EINVAL, "disparity halo too wide for the sweep kernel's shared-memory staging");
+  return fail(LF_EINVAL, c->force_TR > 0 ? "the tile set by lf_set_tile does not fit the staging limits"
+                                         : "disparity halo too wide for the sweep kernel's shared-memory staging");
 }
 
 lf_status encode_maps(lf_ctx* c) {
@@ -377,6 +401,7 @@ void lf_default_params(lf_params* p) {
   p->median = 0;
   p->precision = LF_PREC_F32;
   p->early_exit = 1;
+  p->dynamic_only = 0;
 }
 
 const char* lf_last_error(const lf_ctx*) { return g_err.c_str(); }
@@ -626,6 +651,8 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
   a.early_exit = c->p.early_exit;
   a.mseg = c->p.mstep_seg_term;
   a.prec = c->p.precision;
+  a.dyn_only = c->p.dynamic_only != 0;
+  a.seg_threshold = c->p.seg_threshold;
   a.beta = c->p.beta;
   a.gamma = c->p.gamma;
   a.inv2s2 = static_cast<float>(1.0 / (2.0 * static_cast<double>(c->p.sigma) * c->p.sigma));
@@ -647,6 +674,16 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
   }
   a.d_idx = didx; a.d_out = dout; a.labels = lab; a.post = post;
   a.counter = c->d_counter; a.status = c->d_status; a.timeout_ns = kTimeoutNs;
+  if (a.dyn_only) {  // Sec. III-F: sweep only the tiles with dynamic reference pixels
+    const int tiles = ((c->W + c->TW - 1) / c->TW) * ((c->H + c->TR - 1) / c->TR);
+    if ((s = grow(&c->d_tiles, &c->tiles_cap, static_cast<size_t>(tiles) + 1, "tile list")) != LF_OK) return s;
+    LF_CUDA(cudaMemsetAsync(c->d_tiles + tiles, 0, sizeof(int), c->stream), "memset");
+    LF_CUDA(launch_tile_classify(c->K, a, c->P, c->p_pitch, c->d_tiles, c->d_tiles + tiles, c->stream),
+            "tile_classify launch");
+    ++launched;
+    a.tile_list = c->d_tiles;
+    a.n_tiles = c->d_tiles + tiles;
+  }
   LF_CUDA(launch_em_sweep(c->K, c->img_map, c->p_map, a, c->stream), "em_sweep launch");
   ++launched;
   LF_CUDA(mark(2), "event");
@@ -703,6 +740,26 @@ lf_status lf_get_prior(lf_ctx* c, float* mu, int on_device) {
   return LF_OK;
 }
 
+lf_status lf_set_tile(lf_ctx* c, int tile_rows, int tile_cols) {
+  g_err.clear();
+  if (!c) return fail(LF_EINVAL, "ctx is NULL");
+  if (tile_rows == 0 && tile_cols == 0) {
+    c->force_TR = c->force_TW = 0;
+  } else {
+    if (tile_rows < 1 || tile_cols < 32 || tile_cols % 32 != 0 || tile_rows * tile_cols > 256)
+      return fail(LF_EINVAL, "tile: columns a multiple of 32, rows * columns <= 256");
+    c->force_TR = tile_rows;
+    c->force_TW = tile_cols;
+  }
+  if (!c->have_inputs) return LF_OK;
+  lf_status s = choose_tiles(c);
+  if (s != LF_OK) {
+    c->have_inputs = false;
+    return s;
+  }
+  return encode_maps(c);
+}
+
 lf_status lf_set_timing(lf_ctx* c, int enable) {
   g_err.clear();
   if (!c) return fail(LF_EINVAL, "ctx is NULL");
@@ -741,7 +798,7 @@ void lf_destroy(lf_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   void* bufs[] = {c->d_wtab, c->d_otab, c->d_chg, c->d_dval, c->d_mu, c->d_counter, c->d_status,
-                  c->own_img, c->own_P, c->own_img16, c->d_tris, c->d_bins, c->o_didx, c->o_d, c->o_labels,
+                  c->own_img, c->own_P, c->own_img16, c->d_tiles, c->d_tris, c->d_bins, c->o_didx, c->o_d, c->o_labels,
                   c->o_post, c->o_ref, c->o_tmp};
   for (void* p : bufs)
     if (p) cudaFree(p);

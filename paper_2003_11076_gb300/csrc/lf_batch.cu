@@ -82,12 +82,22 @@ bool encode(CUtensorMap* m, const void* base, size_t pitch, int W, int H, int K,
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Tile shapes of the persistent sweep (256 threads per CTA).
-const int kTiles[][2] = {{2, 128}, {4, 64}, {1, 256}, {8, 32}};
-constexpr int kNumTiles = 4;
+// Tile shapes of the persistent sweep: 256-thread shapes first (the ones the
+// autotuner times), then 128- and 64-thread shapes for halos too wide for the
+// larger tiles' shared memory.  One launch per (camera count, threads).
+const int kTiles[][2] = {{2, 128}, {4, 64}, {1, 256}, {8, 32}, {1, 128}, {2, 64}, {4, 32}, {1, 64}, {2, 32}};
+constexpr int kNumTiles = 9;
+constexpr int kNumTuned = 4;  // shapes the autotuner times
+constexpr int kThreadClasses = 3;
+int thread_class(int tile) { return kTiles[tile][0] * kTiles[tile][1] == 256 ? 0 : kTiles[tile][0] * kTiles[tile][1] == 128 ? 1 : 2; }
+constexpr int kThreadsOf[kThreadClasses] = {256, 128, 64};
+constexpr int kGroups = kMaxCams * kThreadClasses;  // launch groups
+int group_of(int K, int tile) { return (K - 1) * kThreadClasses + thread_class(tile); }
 
 // Autotuner cache: frame signature -> index into kTiles (process wide).
-typedef std::tuple<int, int, int, int, int, int> TileKey;  // K, D, bpp, prec, halo, W/64
+// Signature: K, D, bytes per pixel, precision, halo in 8-px classes, width
+// in 256-px classes.
+typedef std::tuple<int, int, int, int, int, int> TileKey;
 std::mutex g_tune_mutex;
 std::map<TileKey, int> g_tune_cache;
 
@@ -118,6 +128,8 @@ struct Frame {
   size_t img_pitch = 0, p_pitch = 0;
   // tile
   int tile = 0;
+  bool untuned = false;
+  TileKey key{};
   SweepArgs args{};
   size_t smem = 0;
   // arena offsets
@@ -146,7 +158,7 @@ struct lf_batch {
   size_t items_cap = 0;
   RowItem* d_rows = nullptr;
   size_t rows_cap = 0;
-  int* d_counts = nullptr;  // [kMaxCams] items per camera count, [1] rows, [kMaxCams] first item
+  int* d_counts = nullptr;  // [kGroups] items per launch group, [1] rows, [kGroups] first item
   unsigned long long* d_fcount = nullptr;  // per frame: pixel-sweeps executed
   unsigned* d_heads = nullptr;
   unsigned long long* d_counter = nullptr;
@@ -158,6 +170,8 @@ struct lf_batch {
   bool ran = false;
   uint64_t runs = 0, nominal = 0;
   int graph_captures = 0;
+  int tuned = 0;
+  size_t grp_smem[kGroups] = {0};  // shared memory of every group launched so far (only grows)
 };
 
 namespace {
@@ -178,6 +192,8 @@ lf_status dev_grow(void** p, size_t* cap, size_t need, bool* moved = nullptr) {
   if (moved) *moved = true;
   return LF_OK;
 }
+
+void choose_tile(Frame& f, const lf_params& p, int smem_optin);
 
 // Host part of one frame: tables, prior triangles and bins, tile shape.
 void prepare_frame(Frame& f, const lf_params& p, int smem_optin) {
@@ -278,24 +294,30 @@ void prepare_frame(Frame& f, const lf_params& p, int smem_optin) {
   f.img_pitch = f.stage_img ? align_up(static_cast<size_t>(f.W) * f.bpp, 16) : in_row;
   f.stage_p = (static_cast<size_t>(f.W) * 4) % 16 != 0 || reinterpret_cast<uintptr_t>(f.src_p) % 16 != 0;
   f.p_pitch = f.stage_p ? align_up(static_cast<size_t>(f.W) * 4, 16) : static_cast<size_t>(f.W) * 4;
-  // tile: tuned if this signature was tuned, else the first shape that fits
-  // one TMA box per staged row and allows two CTAs per SM
+  choose_tile(f, p, smem_optin);
+}
+
+// Tile: the tuned shape of the frame's signature if there is one, else the
+// first shape that fits one TMA box per staged row and allows two CTAs per SM.
+void choose_tile(Frame& f, const lf_params& p, int smem_optin) {
   SweepArgs a{};
   a.D = f.D;
   a.KP = f.KP;
   a.bpp = f.bpp;
   a.prec = p.precision;
-  const TileKey key{f.K, f.D, f.bpp, p.precision, f.L + f.R, f.W / 64};
+  f.key = TileKey{f.K, f.D, f.bpp, p.precision, (f.L + f.R + 7) / 8, (f.W + 255) / 256};
   int tuned = -1;
   {
     std::lock_guard<std::mutex> lk(g_tune_mutex);
-    auto it = g_tune_cache.find(key);
+    auto it = g_tune_cache.find(f.key);
     if (it != g_tune_cache.end()) tuned = it->second;
   }
+  f.untuned = tuned < 0;
   f.tile = -1;
   for (int pass = 0; pass < 3 && f.tile < 0; ++pass) {
     for (int t = 0; t < kNumTiles; ++t) {
       if (pass == 0 && t != tuned) continue;
+      if (pass == 1 && t >= kNumTuned) continue;  // prefer 256-thread shapes with two CTAs per SM
       a.TR = kTiles[t][0];
       a.TW = kTiles[t][1];
       a.L = f.L;
@@ -312,6 +334,36 @@ void prepare_frame(Frame& f, const lf_params& p, int smem_optin) {
     }
   }
   f.args = a;
+}
+
+// Time every candidate tile shape of frame f through the single-frame path
+// (same kernel arithmetic, one CTA per tile) and return the fastest, or -1.
+int tune_frame(const Frame& f, const lf_params& p, cudaStream_t stream) {
+  lf_ctx* c = nullptr;
+  if (lf_create(&c, f.K, f.b.data(), f.H, f.W, f.d_min, f.d_max, f.D, &p) != LF_OK) return -1;
+  lf_set_stream(c, stream);
+  lf_set_timing(c, 1);
+  int best = -1;
+  float best_ms = 0.f;
+  const int M = static_cast<int>(f.pts.size() / 3);
+  if (lf_set_inputs(c, f.src_img, f.C, f.dtype, f.src_p, f.pts.data(), M, 1) == LF_OK) {
+    for (int t = 0; t < kNumTuned; ++t) {
+      if (lf_set_tile(c, kTiles[t][0], kTiles[t][1]) != LF_OK) continue;
+      lf_stats st{};
+      if (lf_run_em(c, f.iters, f.d_idx, nullptr, nullptr, nullptr, nullptr, 1) != LF_OK) break;
+      lf_get_stats(c, &st);  // warm-up run; resets the counters
+      bool ok = true;
+      for (int r = 0; r < 2 && ok; ++r)
+        ok = lf_run_em(c, f.iters, f.d_idx, nullptr, nullptr, nullptr, nullptr, 1) == LF_OK;
+      if (!ok || lf_get_stats(c, &st) != LF_OK) break;
+      if (best < 0 || st.ms_sweep < best_ms) {
+        best = t;
+        best_ms = st.ms_sweep;
+      }
+    }
+  }
+  lf_destroy(c);
+  return best;
 }
 
 std::string sig_string(const Frame& f) {
@@ -346,8 +398,8 @@ lf_status lf_batch_create(lf_batch** out, const lf_params* p, int autotune) {
   for (cudaEvent_t& ev : b->ev)
     if (e == cudaSuccess) e = cudaEventCreate(&ev);
   size_t cap = 0;
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_counts), sizeof(int) * (2 * kMaxCams + 1));
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_heads), sizeof(unsigned) * kMaxCams);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_counts), sizeof(int) * (2 * kGroups + 1));
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_heads), sizeof(unsigned) * kGroups);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_counter), sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_status), sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(unsigned));
@@ -437,6 +489,24 @@ lf_status lf_batch_run(lf_batch* b) {
       });
     for (auto& th : pool) th.join();
   }
+  if (b->autotune) {  // time the candidate tiles of signatures not seen before
+    std::map<TileKey, int> done;
+    for (Frame& f : b->frames) {
+      if (!f.untuned) continue;
+      auto it = done.find(f.key);
+      if (it == done.end()) {
+        const int t = tune_frame(f, b->p, b->stream);
+        it = done.emplace(f.key, t).first;
+        if (t >= 0) {
+          std::lock_guard<std::mutex> lk(g_tune_mutex);
+          g_tune_cache[f.key] = t;
+          ++b->tuned;
+        }
+      }
+      choose_tile(f, b->p, b->smem_optin);
+    }
+    set_error_message("");
+  }
   for (const Frame& f : b->frames)
     if (f.tile < 0) return fail(LF_EINVAL, "frame " + sig_string(f) + ": disparity halo too wide for staging");
   // 2. arena layout
@@ -513,18 +583,18 @@ lf_status lf_batch_run(lf_batch* b) {
   items.reserve(total_items);
   std::vector<RowItem> rows;
   rows.reserve(total_rows);
-  int counts[2 * kMaxCams + 1] = {0};
+  int counts[2 * kGroups + 1] = {0};
   uint8_t* A = b->arena;
   cudaStream_t st = b->stream;
   uint64_t nominal = 0;
-  for (int K = 1; K <= kMaxCams; ++K) {
+  for (int g = 0; g < kGroups; ++g) {
     for (int i = 0; i < nf; ++i) {
       Frame& f = b->frames[i];
-      if (f.K != K) continue;
+      if (group_of(f.K, f.tile) != g) continue;
       const int TR = kTiles[f.tile][0], TW = kTiles[f.tile][1];
       for (int y = 0; y < (f.H + TR - 1) / TR; ++y)
         for (int x = 0; x < (f.W + TW - 1) / TW; ++x) items.push_back(TileItem{i, x, y, 0});
-      counts[K - 1] += ((f.H + TR - 1) / TR) * ((f.W + TW - 1) / TW);
+      counts[g] += ((f.H + TR - 1) / TR) * ((f.W + TW - 1) / TW);
     }
   }
   for (int i = 0; i < nf; ++i) {
@@ -570,6 +640,8 @@ lf_status lf_batch_run(lf_batch* b) {
     a.early_exit = b->p.early_exit;
     a.mseg = b->p.mstep_seg_term;
     a.prec = b->p.precision;
+    a.dyn_only = b->p.dynamic_only != 0;
+    a.seg_threshold = b->p.seg_threshold;
     a.beta = b->p.beta;
     a.gamma = b->p.gamma;
     a.inv2s2 = static_cast<float>(1.0 / (2.0 * static_cast<double>(b->p.sigma) * b->p.sigma));
@@ -605,8 +677,8 @@ lf_status lf_batch_run(lf_batch* b) {
                         f.d_idx, lab, ref_out};
     ma[i] = MedianArgs{f.H, f.W, f.C, ref_out, b->p.median ? f.refocus : nullptr};
   }
-  counts[kMaxCams] = static_cast<int>(rows.size());
-  for (int K = 2; K <= kMaxCams; ++K) counts[kMaxCams + K] = counts[kMaxCams + K - 1] + counts[K - 2];
+  counts[kGroups] = static_cast<int>(rows.size());
+  for (int g = 1; g < kGroups; ++g) counts[kGroups + 1 + g] = counts[kGroups + g] + counts[g - 1];
   LF_CUDA(cudaMemcpyAsync(A, host.data(), host_bytes, cudaMemcpyHostToDevice, st), "batch upload");
   LF_CUDA(cudaMemcpyAsync(b->d_frames, fd.data(), nf * sizeof(FrameDesc), cudaMemcpyHostToDevice, st),
           "batch upload");
@@ -621,19 +693,27 @@ lf_status lf_batch_run(lf_batch* b) {
   LF_CUDA(cudaMemcpyAsync(b->d_rows, rows.data(), rows.size() * sizeof(RowItem), cudaMemcpyHostToDevice, st),
           "batch upload");
   LF_CUDA(cudaMemcpyAsync(b->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, st), "batch upload");
-  // 4. graph shape: per camera count present, the largest shared memory
-  size_t smem[kMaxCams] = {0};
-  for (const Frame& f : b->frames) smem[f.K - 1] = std::max(smem[f.K - 1], f.smem);
+  // 4. graph shape: every launch group seen so far, each with the largest
+  // shared memory it has needed (groups stay and sizes only grow, so that
+  // batches of other contents replay the same graph; a group without items
+  // in this batch finds an empty queue)
+  for (const Frame& f : b->frames) {
+    const int g = group_of(f.K, f.tile);
+    b->grp_smem[g] = std::max(b->grp_smem[g], f.smem);
+  }
+  const size_t* smem = b->grp_smem;
   std::vector<long long> key = {b->p.precision, b->p.median, reinterpret_cast<long long>(b->d_frames),
                                 reinterpret_cast<long long>(b->d_items), reinterpret_cast<long long>(b->d_rows)};
-  for (int K = 1; K <= kMaxCams; ++K) key.push_back(static_cast<long long>(smem[K - 1]));
+  for (int g = 0; g < kGroups; ++g) key.push_back(static_cast<long long>(smem[g]));
   if (!b->exec || key != b->key) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
     const int rgrid = b->num_sms * 8;
-    int grid[kMaxCams] = {0};  // resident CTAs of each persistent launch (queried before capturing)
-    for (int K = 1; K <= kMaxCams; ++K)
-      if (smem[K - 1]) grid[K - 1] = b->num_sms * std::max(1, em_sweep_persistent_occupancy(K, b->p.precision, smem[K - 1]));
+    int grid[kGroups] = {0};  // resident CTAs of each persistent launch (queried before capturing)
+    for (int g = 0; g < kGroups; ++g)
+      if (smem[g])
+        grid[g] = b->num_sms * std::max(1, em_sweep_persistent_occupancy(g / kThreadClasses + 1, b->p.precision,
+                                                                         smem[g], kThreadsOf[g % kThreadClasses]));
     cudaStream_t c = b->capture;
     LF_CUDA(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal), "graph capture");
     cudaError_t e = cudaSuccess;
@@ -641,19 +721,20 @@ lf_status lf_batch_run(lf_batch* b) {
       if (e == cudaSuccess) e = x;
     };
     chk(cudaEventRecordWithFlags(b->ev[0], c, cudaEventRecordExternal));
-    chk(launch_prior_raster_batched(b->d_prior, b->d_rows, b->d_counts + kMaxCams, rgrid, c));
-    chk(cudaMemsetAsync(b->d_heads, 0, sizeof(unsigned) * kMaxCams, c));
+    chk(launch_prior_raster_batched(b->d_prior, b->d_rows, b->d_counts + kGroups, rgrid, c));
+    chk(cudaMemsetAsync(b->d_heads, 0, sizeof(unsigned) * kGroups, c));
     chk(cudaMemsetAsync(b->d_fcount, 0, sizeof(unsigned long long) * b->frames_cap, c));
     chk(cudaEventRecordWithFlags(b->ev[1], c, cudaEventRecordExternal));
-    for (int K = 1; K <= kMaxCams; ++K) {
-      if (!smem[K - 1]) continue;
-      chk(launch_em_sweep_persistent(K, b->p.precision, b->d_frames, b->d_items, b->d_counts + kMaxCams + K,
-                                     b->d_counts + (K - 1), b->d_heads + (K - 1), smem[K - 1], grid[K - 1], c));
+    for (int g = 0; g < kGroups; ++g) {
+      if (!smem[g]) continue;
+      chk(launch_em_sweep_persistent(g / kThreadClasses + 1, b->p.precision, b->d_frames, b->d_items,
+                                     b->d_counts + kGroups + 1 + g, b->d_counts + g, b->d_heads + g, smem[g],
+                                     grid[g], kThreadsOf[g % kThreadClasses], c));
     }
     chk(cudaEventRecordWithFlags(b->ev[2], c, cudaEventRecordExternal));
-    chk(launch_refocus_batched(b->d_refocus, b->d_rows, b->d_counts + kMaxCams, rgrid, c));
+    chk(launch_refocus_batched(b->d_refocus, b->d_rows, b->d_counts + kGroups, rgrid, c));
     chk(cudaEventRecordWithFlags(b->ev[3], c, cudaEventRecordExternal));
-    if (b->p.median) chk(launch_median3_batched(b->d_median, b->d_rows, b->d_counts + kMaxCams, rgrid, c));
+    if (b->p.median) chk(launch_median3_batched(b->d_median, b->d_rows, b->d_counts + kGroups, rgrid, c));
     chk(cudaEventRecordWithFlags(b->ev[4], c, cudaEventRecordExternal));
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(c, &g);
@@ -702,12 +783,10 @@ lf_status lf_batch_get_stats(lf_batch* b, lf_stats* out) {
       r.executed_ray_samples += n[i] * static_cast<uint64_t>(b->frames[i].K) * b->frames[i].D;
     float* ms[4] = {&r.ms_prior, &r.ms_sweep, &r.ms_refocus, &r.ms_median};
     for (int i = 0; i < 4; ++i) LF_CUDA(cudaEventElapsedTime(ms[i], b->ev[i], b->ev[i + 1]), "event time");
-    r.kernels_launched = 0;
-    bool seen[kMaxCams] = {false};
-    for (const Frame& f : b->frames) seen[f.K - 1] = true;
-    for (bool x : seen) r.kernels_launched += x;
-    r.kernels_launched += 2 + b->p.median;
+    r.kernels_launched = 2 + b->p.median;
+    for (size_t x : b->grp_smem) r.kernels_launched += x != 0;
     r.graph_captures = b->graph_captures;
+    r.tuned_signatures = b->tuned;
   }
   b->runs = 0;
   *out = r;

@@ -44,6 +44,10 @@ struct SweepArgs {
   int KP;                          // cameras padded to a multiple of 4 (table stride)
   int iters, early_exit, mseg;
   int prec;                        // staged maps: kPrecF32, kPrecF16 or kPrecBF16
+  int dyn_only;                    // reconstruct only pixels with P_ref(dynamic) >= threshold
+  float seg_threshold;             // that threshold (probability)
+  const int* tile_list;            // non-null: blockIdx.x indexes this list of tile ids
+  const int* n_tiles;              // its length (CTAs beyond it exit)
   float beta, gamma, inv2s2, log_thr, eps;
   const float* wtab;               // [D][KP] interpolation weight of camera k at d_j
   const int* otab;                 // [D][KP] floor(-d_j * b_k)
@@ -99,6 +103,11 @@ struct TileItem {
 size_t sweep_smem_bytes(int K, const SweepArgs& a);
 
 cudaError_t launch_prior_raster(const PriorArgs& a, cudaStream_t s);
+// Dynamic-only mode: list the tiles holding a pixel with P_ref >= threshold
+// (tile_list / *n_tiles, n_tiles zeroed by the caller) and write the outputs
+// of the pixels of every other tile.
+cudaError_t launch_tile_classify(int K, const SweepArgs& a, const float* seg_prior, size_t p_pitch,
+                                 int* tile_list, int* n_tiles, cudaStream_t s);
 cudaError_t launch_em_sweep(int K, const CUtensorMap& img_map, const CUtensorMap& p_map,
                             const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_refocus(const RefocusArgs& a, cudaStream_t s);
@@ -112,9 +121,9 @@ cudaError_t launch_median3_batched(const MedianArgs* frames, const RowItem* item
 // Persistent sweep over the items of one camera count.
 cudaError_t launch_em_sweep_persistent(int K, int prec, const FrameDesc* frames, const TileItem* items,
                                        const int* first_item, const int* n_items, unsigned* head, size_t smem,
-                                       int grid, cudaStream_t s);
+                                       int grid, int threads, cudaStream_t s);
 // Resident CTAs per SM of the persistent sweep for this shared-memory size.
-int em_sweep_persistent_occupancy(int K, int prec, size_t smem);
+int em_sweep_persistent_occupancy(int K, int prec, size_t smem, int threads);
 // float32 [rows][W*C] (pitch_in bytes) -> float16 (to_bf16 = 0) or bfloat16 rows (pitch_out bytes)
 cudaError_t launch_convert_f32(const uint8_t* in, size_t pitch_in, uint8_t* out, size_t pitch_out, int rows,
                                int cols, int to_bf16, cudaStream_t s);

@@ -24,7 +24,7 @@ EXPORTS = ("lf_default_params", "lf_create", "lf_set_stream", "lf_set_inputs", "
            "lf_synchronize", "lf_get_prior", "lf_get_stats", "lf_last_error", "lf_destroy",
            "lf_triangulate", "lf_set_timing", "lf_run_em_static", "lf_batch_create", "lf_batch_set_stream",
            "lf_batch_add", "lf_batch_run", "lf_batch_synchronize", "lf_batch_clear", "lf_batch_get_stats",
-           "lf_batch_destroy")
+           "lf_batch_destroy", "lf_set_tile")
 
 
 class LfError(RuntimeError):
@@ -37,7 +37,7 @@ class Params(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_float), ("gamma", ctypes.c_float), ("sigma", ctypes.c_float),
                 ("seg_threshold", ctypes.c_float), ("eps", ctypes.c_float),
                 ("mstep_seg_term", ctypes.c_int), ("median", ctypes.c_int), ("precision", ctypes.c_int),
-                ("early_exit", ctypes.c_int)]
+                ("early_exit", ctypes.c_int), ("dynamic_only", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -47,7 +47,8 @@ class Stats(ctypes.Structure):
                 ("tile_rows", ctypes.c_int), ("tile_cols", ctypes.c_int),
                 ("kernels_launched", ctypes.c_int),
                 ("ms_prior", ctypes.c_float), ("ms_sweep", ctypes.c_float), ("ms_refocus", ctypes.c_float),
-                ("ms_median", ctypes.c_float), ("graph_captures", ctypes.c_int)]
+                ("ms_median", ctypes.c_float), ("graph_captures", ctypes.c_int),
+                ("tuned_signatures", ctypes.c_int)]
 
 
 _lib = None
@@ -74,6 +75,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lf_get_prior.argtypes = [P, P, I]
     lib.lf_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
     lib.lf_set_timing.argtypes = [P, I]
+    lib.lf_set_tile.argtypes = [P, I, I]
+    lib.lf_set_tile.restype = I
     lib.lf_last_error.argtypes = [P]
     lib.lf_last_error.restype = ctypes.c_char_p
     lib.lf_destroy.argtypes = [P]
@@ -266,6 +269,9 @@ class Context:
                              ptr("refocus"), 0))
         return res
 
+    def set_tile(self, tile_rows: int, tile_cols: int):
+        _check(load().lf_set_tile(self._h, int(tile_rows), int(tile_cols)))
+
     def set_timing(self, enable: bool = True):
         _check(load().lf_set_timing(self._h, int(enable)))
 
@@ -287,9 +293,10 @@ class Batch:
     """Uneven batch of frames on device buffers (torch CUDA tensors), run as
     one CUDA graph (see lf_batch_* in include/lf.h)."""
 
-    def __init__(self, params: Optional[Params] = None, stream=None):
+    def __init__(self, params: Optional[Params] = None, stream=None, autotune: bool = False):
         h = ctypes.c_void_p()
-        _check(load().lf_batch_create(ctypes.byref(h), ctypes.byref(params) if params is not None else None, 0))
+        _check(load().lf_batch_create(ctypes.byref(h), ctypes.byref(params) if params is not None else None,
+                                      int(autotune)))
         self._h = h
         self._keep = []
         if stream is not None:

@@ -1,0 +1,141 @@
+"""Dynamic-only mode (Sec. III-F): only the reference pixels whose own
+P(dynamic) reaches the threshold are reconstructed.
+
+Those pixels must get exactly what the full mode gives them (and so match the
+oracle within the parity tolerances); every other pixel gets the documented
+stand-in: the candidate nearest the prior centre (-1 outside the
+triangulation), no static ray, NaN posteriors and the reference image.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2003_11076_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2003_11076_gb300 import build
+    build.build()
+    O.build()
+
+
+def _frames():
+    return [scenes.small_gray(0), scenes.small_gray(2, H=37, W=75, M=12, D=16, iters=3),
+            scenes.street_rgb(3, H=72, W=96, D=32, iters=6, M=40),
+            scenes.small_gray(1, baselines=[-0.3, -0.15, 0.0, 0.1, 0.25, 0.4, 0.55], D=24, iters=4)]
+
+
+def _ref(s):
+    return int(np.argmin(np.abs(s.baselines)))
+
+
+def _dynamic_mask(s, thr):
+    return s.seg_prior[_ref(s)] >= np.float32(thr)
+
+
+def _check_stand_in(s, g, mu, mask):
+    st = ~mask
+    cand = (s.d_min + np.arange(s.D) * ((s.d_max - s.d_min) / max(s.D - 1, 1))).astype(np.float64)
+    outside = st & np.isnan(mu)
+    inside = st & ~np.isnan(mu)
+    assert np.all(g["d_idx"][outside] == -1)
+    assert np.all(np.isnan(g["d"][outside]))
+    j = g["d_idx"][inside]
+    assert np.all((j >= 0) & (j < s.D))
+    dist = np.abs(cand[None, :] - mu[inside].astype(np.float64)[:, None])
+    assert np.all(dist[np.arange(j.size), j] <= dist.min(axis=1) + 1e-4), "not the nearest candidate"
+    assert np.allclose(g["d"][inside], cand[j], atol=1e-5)
+    assert np.all(g["labels"][st] == 0)
+    assert np.all(np.isnan(g["post"][:, st]))
+    img = s.images[_ref(s)].astype(np.float32)
+    if s.images.dtype == np.uint8:
+        img = img / np.float32(255)
+    assert np.max(np.abs(g["refocus"][st] - img[st]), initial=0.0) <= 1e-6
+
+
+@pytest.mark.parametrize("i", range(4))
+def test_dynamic_pixels_equal_full_mode(i):
+    from paper_2003_11076_gb300 import lf
+    s = _frames()[i]
+    full = lf.run_scene(s, params=lf.default_params())
+    dyn = lf.run_scene(s, params=lf.default_params(dynamic_only=1))
+    mask = _dynamic_mask(s, 0.7)
+    assert 0 < mask.sum() < mask.size
+    assert np.array_equal(dyn["d_idx"][mask], full["d_idx"][mask])
+    assert np.array_equal(dyn["labels"][mask], full["labels"][mask])
+    assert np.array_equal(dyn["d"][mask], full["d"][mask])
+    assert np.array_equal(dyn["post"][:, mask], full["post"][:, mask])
+    assert np.array_equal(dyn["refocus"][mask], full["refocus"][mask])
+    _check_stand_in(s, dyn, full["mu"], mask)
+    # fewer pixel-sweeps, and one more kernel (the tile classifier)
+    assert dyn["stats"]["executed_ray_samples"] < full["stats"]["executed_ray_samples"]
+    assert dyn["stats"]["kernels_launched"] == full["stats"]["kernels_launched"] + 1
+
+
+def test_dynamic_pixels_match_oracle():
+    from paper_2003_11076_gb300 import lf
+    s = scenes.street_rgb(5, H=96, W=160, D=48, iters=8, M=60)
+    gp = lf.default_params(dynamic_only=1)
+    op = O.Params(beta=float(np.float32(gp.beta)), gamma=float(np.float32(gp.gamma)),
+                  sigma=float(np.float32(gp.sigma)), seg_threshold=float(np.float32(gp.seg_threshold)),
+                  eps=float(np.float32(gp.eps)), mstep_seg_term=int(gp.mstep_seg_term))
+    g = lf.run_scene(s, params=gp)
+    o = O.run_scene(s, params=op)
+    mask = _dynamic_mask(s, gp.seg_threshold)
+    same = g["d_idx"][mask] == o["d_idx"][mask]
+    exc = O.excused({k: (v[:, mask] if k in ("m_margin", "e_margin", "J_t") else v[mask])
+                     for k, v in o.items() if k in ("m_margin", "e_margin", "J_t", "init_margin")})
+    assert same.mean() >= 0.999
+    assert not (~same & ~exc).any()
+    agree = same & (g["labels"][mask].astype(np.int64) == o["labels"][mask].astype(np.int64))
+    assert np.max(np.abs(g["post"][:, mask] - o["post"][:, mask])[:, agree]) <= 1e-4
+    assert np.max(np.abs(g["refocus"][mask] - o["refocus"][mask])[agree]) <= 1e-3
+    _check_stand_in(s, g, g["mu"], mask)
+
+
+def test_no_dynamic_pixel_and_all_dynamic():
+    """A frame without a dynamic reference pixel launches the classifier and
+    an empty sweep; one where every pixel is dynamic equals the full mode."""
+    from paper_2003_11076_gb300 import lf
+    s = scenes.small_gray(0)
+    s.seg_prior = np.zeros_like(s.seg_prior)
+    dyn = lf.run_scene(s, params=lf.default_params(dynamic_only=1))
+    mask = np.zeros((s.H, s.W), bool)
+    _check_stand_in(s, dyn, dyn["mu"], mask)
+    assert dyn["stats"]["executed_ray_samples"] == 0
+    s.seg_prior = np.ones_like(s.seg_prior)
+    full = lf.run_scene(s, params=lf.default_params())
+    dyn = lf.run_scene(s, params=lf.default_params(dynamic_only=1))
+    for k in ("d_idx", "labels", "d", "post", "refocus"):
+        assert np.array_equal(dyn[k], full[k]), k
+
+
+def test_batch_dynamic_only_equals_single_frame():
+    import torch
+    from paper_2003_11076_gb300 import lf
+    frames = _frames()
+    p = lf.default_params(dynamic_only=1)
+    b = lf.Batch(p)
+    b.set_stream(torch.cuda.current_stream())
+    outs = []
+    for s in frames:
+        o = lf.device_outputs(s.K, s.H, s.W, s.C)
+        b.add(s.baselines, s.d_min, s.d_max, s.D, s.iters, torch.from_numpy(s.images).cuda(),
+              torch.from_numpy(s.seg_prior).cuda(), s.points, o)
+        outs.append(o)
+    b.run()
+    b.synchronize()
+    for s, o in zip(frames, outs):
+        got = {k: v.cpu().numpy() for k, v in o.items()}
+        alone = lf.run_scene(s, params=p)
+        assert np.array_equal(got["d_idx"], alone["d_idx"])
+        assert np.array_equal(got["labels"].view(np.uint16), alone["labels"])
+        assert np.array_equal(got["d"], alone["d"], equal_nan=True)
+        assert np.allclose(got["post"], alone["post"], rtol=0, atol=1e-6, equal_nan=True)
+        assert np.allclose(got["refocus"], alone["refocus"], rtol=0, atol=1e-6)
+    b.close()
