@@ -88,9 +88,21 @@ def em_pixel_table(feat, ls, ld, images, baselines, u, v, dvals, mu, inside, p):
     return J, S_init
 
 
-def run(images, seg_prior, baselines, mu, inside, d_min, d_max, D, iters, p):
-    """Full EM on every pixel of a tiny frame.  Returns dict like the oracle's
-    (d_idx, labels, post, refocus) plus ``joint_max`` = max over (d, S)."""
+def _softmax(row: np.ndarray) -> np.ndarray:
+    q = np.exp(row - row.max())
+    return q / q.sum()
+
+
+def run(images, seg_prior, baselines, mu, inside, d_min, d_max, D, iters, p, mode: str = "hard"):
+    """EM on every pixel of a tiny frame from the full J[d, S] table.
+
+    mode "hard": the paper's EM (M-step down the column of the current S,
+    E-step along the row of the current d).  "soft": after the first
+    iteration the M-step maximises the table's rows averaged under the
+    previous row's softmax, ``J @ q``.  "joint": the arg-max of the whole
+    table.  Returns dict like the oracle's (d_idx, labels, post, refocus)
+    plus ``joint_max`` = max over (d, S) and, per iteration, ``L_t`` = the
+    log-sum-exp of the row of d_t."""
     imgs = np.asarray(images)
     K, H, W = imgs.shape[:3]
     feat = descriptors(imgs)
@@ -111,16 +123,28 @@ def run(images, seg_prior, baselines, mu, inside, d_min, d_max, D, iters, p):
     refocus = np.zeros((H, W, C))
     J_final = np.zeros((H, W))
     joint = np.zeros((H, W))
+    L_t = np.zeros((iters, H, W))
     for v in range(H):
         for u in range(W):
             J, S_init = em_pixel_table(feat, ls, ld, imgs, baselines, u, v, dvals, mu[v, u], inside[v, u], p)
             if not p.mstep_seg_term:
                 raise NotImplementedError
             S = None
-            for t in range(iters):
-                col = J[np.arange(len(dvals)), S_init] if t == 0 else J[:, S]
-                j = int(np.argmax(col))          # first maximum = lowest index
-                S = int(np.argmax(J[j]))          # first maximum = smallest mask
+            q = None
+            if mode == "joint":
+                j, S = (int(i) for i in np.unravel_index(int(np.argmax(J)), J.shape))  # row-major first maximum
+            else:
+                for t in range(iters):
+                    if t == 0:
+                        col = J[np.arange(len(dvals)), S_init]
+                    elif mode == "soft":
+                        col = J @ q
+                    else:
+                        col = J[:, S]
+                    j = int(np.argmax(col))          # first maximum = lowest index
+                    S = int(np.argmax(J[j]))          # first maximum = smallest mask
+                    q = _softmax(J[j])
+                    L_t[t, v, u] = np.log(np.sum(np.exp(J[j] - J[j].max()))) + J[j].max()
             d_idx[v, u], labels[v, u] = j, S
             J_final[v, u] = J[j, S]
             joint[v, u] = J.max()
@@ -137,7 +161,7 @@ def run(images, seg_prior, baselines, mu, inside, d_min, d_max, D, iters, p):
                     refocus[v, u, c] = np.mean([_interp(x[k, v, :, c], u - dvals[j] * float(baselines[k]))
                                                 for k in members])
     out.update(d_idx=d_idx, labels=labels, post=post, refocus=refocus[..., 0] if C == 1 else refocus,
-               J_final=J_final, joint_max=joint)
+               J_final=J_final, joint_max=joint, L_t=L_t)
     return out
 
 

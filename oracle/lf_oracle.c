@@ -27,6 +27,10 @@
  *   EM schedule   M-step first, with S thresholded at P >= 0.7 at each
  *                 candidate's own sample, then E-step, repeat (Sec. III-B
  *                 schedule, Sec. III-F threshold)
+ *   variants      soft EM: after the first iteration the M-step maximises
+ *                 sum_S q(S) J(d, S) with q the previous E-step's posterior
+ *                 over all 2^K label vectors; joint MAP: the arg-max of
+ *                 J(d, S) over every (d, S) pair (Sec. III-B, Sec. III-C)
  *   outputs       d, hard S, per-ray marginals of q(S) ~ exp J(d_T, S), and
  *                 the refocused image of Eq. 2 (Sec. III-E)
  *   median        3x3 per channel, border replicated (Sec. III-E)
@@ -49,6 +53,7 @@ typedef struct {
     double seg_threshold; /* initial segmentation threshold on P(dynamic) (0.7) */
     double eps;           /* floor inside the log of the segmentation prior */
     int mstep_seg_term;   /* 1: M-step maximises the complete-data J */
+    int em_mode;          /* 0: hard EM (the paper's), 1: soft EM, 2: joint MAP */
 } orc_params;
 
 /* ---------------------------------------------------------------- inputs */
@@ -211,6 +216,28 @@ static void sample_rays(const orc_frame *F, int u, int v, double d,
 
 #define ORC_MAXK 16
 
+/* Posterior over the label vectors at one disparity (Sec. III-B: the E-step
+ * of EM computes p(S | x, d)): q[S] = exp J(d, S) / sum_S' exp J(d, S') over
+ * all 2^K vectors, with the rays already sampled at d.  Returns
+ * log sum_S exp J(d, S) (the log marginal of the observations at d, up to a
+ * constant) with the prior lp included. */
+static double label_posterior(int K, const double f[][3], const double *ls, const double *ld,
+                              double lp, const orc_params *p, double *q)
+{
+    double Jmax = -INFINITY;
+    for (unsigned s = 0; s < (1u << K); ++s) {
+        q[s] = objective(K, f, ls, ld, s, lp, 1, p);
+        if (q[s] > Jmax) Jmax = q[s];
+    }
+    double Z = 0.0;
+    for (unsigned s = 0; s < (1u << K); ++s) {
+        q[s] = exp(q[s] - Jmax);
+        Z += q[s];
+    }
+    for (unsigned s = 0; s < (1u << K); ++s) q[s] /= Z;
+    return Jmax + log(Z);
+}
+
 /* One reference pixel through the whole EM (Sec. III-B schedule, M-step
  * first).  Writes outputs and per-iteration diagnostics. */
 static void em_pixel(const orc_frame *F, int u, int v, double mu, int inside, int iters,
@@ -226,6 +253,44 @@ static void em_pixel(const orc_frame *F, int u, int v, double mu, int inside, in
     unsigned S = 0;
     int jbest = 0;
     double imargin = INFINITY;
+    /* soft EM: posterior over the label vectors from the previous E-step */
+    double *q = p->em_mode == 1 ? (double *)malloc(sizeof(double) * ((size_t)1 << K)) : NULL;
+
+    if (p->em_mode == 2) {
+        /* ---- joint MAP: (d, S) = argmax over every candidate and every
+         * label vector of J(d, S) (Sec. III-C considers all 2^K
+         * configurations); lowest d index first, then smallest mask.  There
+         * is nothing to iterate: every diagnostic slot holds the one result. */
+        double Mbest = -INFINITY, Msecond = -INFINITY;
+        unsigned Sbest = 0;
+        for (int j = 0; j < D; ++j) {
+            double d = F->dval[j];
+            sample_rays(F, u, v, d, f, ls, ld);
+            double lp = log_prior(d, mu, inside, p);
+            double Mj = -INFINITY;
+            unsigned Sj = 0;
+            for (unsigned s = 0; s < (1u << K); ++s) {
+                double J = objective(K, (const double(*)[3])f, ls, ld, s, lp, 1, p);
+                if (J > Mj) { Mj = J; Sj = s; }
+            }
+            if (Mj > Mbest) { Msecond = Mbest; Mbest = Mj; jbest = j; Sbest = Sj; }
+            else if (Mj > Msecond) Msecond = Mj;
+        }
+        S = Sbest;
+        sample_rays(F, u, v, F->dval[jbest], f, ls, ld);
+        double eb = -INFINITY, es = -INFINITY;
+        for (unsigned s = 0; s < (1u << K); ++s) {
+            double J = objective(K, (const double(*)[3])f, ls, ld, s, 0.0, 1, p);
+            if (J > eb) { es = eb; eb = J; }
+            else if (J > es) es = J;
+        }
+        for (int t = 1; t <= iters; ++t) {
+            m_margin[(size_t)(t - 1) * HW + pix] = Mbest - Msecond;
+            e_margin[(size_t)(t - 1) * HW + pix] = eb - es;
+            J_t[(size_t)(t - 1) * HW + pix] = Mbest;
+        }
+        iters = 0;  /* skip the EM loop below */
+    }
 
     for (int t = 1; t <= iters; ++t) {
         /* ---- M-step: d = argmax_d J(d, S), lowest index on ties */
@@ -246,8 +311,19 @@ static void em_pixel(const orc_frame *F, int u, int v, double mu, int inside, in
                     if (z < 0.0) Sj |= 1u << k;
                 }
             }
-            double J = objective(K, (const double(*)[3])f, ls, ld, Sj,
-                                 log_prior(d, mu, inside, p), p->mstep_seg_term, p);
+            double J;
+            if (p->em_mode == 1 && t > 1) {
+                /* soft EM (Sec. III-B, Eq. m-step 1 as an expectation): the
+                 * expected complete-data objective under the previous
+                 * posterior, Q(d) = sum_S q(S) J(d, S) */
+                J = 0.0;
+                for (unsigned s = 0; s < (1u << K); ++s)
+                    J += q[s] * objective(K, (const double(*)[3])f, ls, ld, s,
+                                          log_prior(d, mu, inside, p), p->mstep_seg_term, p);
+            } else {
+                J = objective(K, (const double(*)[3])f, ls, ld, Sj,
+                              log_prior(d, mu, inside, p), p->mstep_seg_term, p);
+            }
             if (J > best) { second = best; best = J; jb = j; }
             else if (J > second) second = J;
         }
@@ -267,9 +343,15 @@ static void em_pixel(const orc_frame *F, int u, int v, double mu, int inside, in
         }
         S = Sb;
         e_margin[(size_t)(t - 1) * HW + pix] = eb - es;
-        J_t[(size_t)(t - 1) * HW + pix] = eb + log_prior(d, mu, inside, p);
+        if (p->em_mode == 1)  /* soft EM: the posterior for the next M-step and
+                               * the log marginal, which EM never decreases */
+            J_t[(size_t)(t - 1) * HW + pix] =
+                label_posterior(K, (const double(*)[3])f, ls, ld, log_prior(d, mu, inside, p), p, q);
+        else
+            J_t[(size_t)(t - 1) * HW + pix] = eb + log_prior(d, mu, inside, p);
     }
     init_margin[pix] = imargin;
+    free(q);
 
     /* ---- outputs at (d_T, S_T) */
     double d = F->dval[jbest];
@@ -339,6 +421,7 @@ int orc_run(int K, const float *baselines, int H, int W, int C, int dtype,
             double *init_margin)
 {
     if (K < 1 || K > ORC_MAXK || H < 1 || W < 1 || D < 1 || iters < 1) return -1;
+    if (p->em_mode < 0 || p->em_mode > 2) return -1;
     if (C != 1 && C != 3) return -1;
     size_t HW = (size_t)H * W;
     double *feat = (double *)malloc(sizeof(double) * 3 * K * HW);

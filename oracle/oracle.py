@@ -45,12 +45,13 @@ class Params:
     seg_threshold: float = 0.7
     eps: float = 1e-4
     mstep_seg_term: int = 1
+    em_mode: int = 0          # 0 hard EM (the paper's), 1 soft EM, 2 joint MAP
 
 
 class _CParams(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("gamma", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("seg_threshold", ctypes.c_double), ("eps", ctypes.c_double),
-                ("mstep_seg_term", ctypes.c_int)]
+                ("mstep_seg_term", ctypes.c_int), ("em_mode", ctypes.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -101,7 +102,7 @@ def _ptr(a: np.ndarray):
 
 def _cparams(p: Optional[Params]) -> _CParams:
     p = p or Params()
-    return _CParams(p.beta, p.gamma, p.sigma, p.seg_threshold, p.eps, p.mstep_seg_term)
+    return _CParams(p.beta, p.gamma, p.sigma, p.seg_threshold, p.eps, p.mstep_seg_term, p.em_mode)
 
 
 def max_threads() -> int:

@@ -176,6 +176,64 @@ def test_em_matches_exhaustive_enumeration(seed, K, H, W, D):
     assert np.all(out["J_t"][-1] <= bf["joint_max"] + 1e-10)
 
 
+@pytest.mark.parametrize("seed,K,H,W,D", [(1, 3, 4, 6, 5), (2, 4, 3, 5, 6), (3, 2, 4, 6, 6), (6, 1, 4, 6, 5)])
+def test_soft_em_matches_exhaustive_table(seed, K, H, W, D):
+    """Soft EM: after the first iteration the M-step maximises the table's
+    rows averaged under the previous E-step's softmax (J @ q); the oracle's
+    arg-maxes, posteriors and log marginals agree with the table's."""
+    imgs, seg, b = _tiny_frame(K, H, W, seed)
+    rng = np.random.default_rng(seed + 100)
+    pts = np.stack([rng.uniform(-1, W, 6), rng.uniform(-1, H, 6), rng.uniform(0, 4, 6)], 1).astype(np.float32)
+    p = O.Params(beta=30.0, em_mode=1)
+    iters = 4
+    out = O.run(imgs, seg, b, pts, 0.0, 4.0, D, iters, params=p)
+    bf = BF.run(imgs, seg, b, out["mu"], out["inside"], 0.0, 4.0, D, iters, p, mode="soft")
+    ok = ~O.excused(out, tau_rel=1e-9, tau_init=1e-9)
+    assert ok.sum() >= 6
+    assert np.array_equal(out["d_idx"][ok], bf["d_idx"][ok])
+    assert np.array_equal(out["labels"][ok].astype(np.int64), bf["labels"][ok])
+    assert np.allclose(out["post"][:, ok], bf["post"][:, ok], atol=1e-11)
+    assert np.allclose(out["J_t"][:, ok], bf["L_t"][:, ok], atol=1e-10)
+    hard = O.run(imgs, seg, b, pts, 0.0, 4.0, D, iters, params=O.Params(beta=30.0))
+    if K > 1:  # the two EMs are different algorithms: some pixel must differ
+        assert not np.array_equal(out["J_t"], hard["J_t"])
+
+
+@pytest.mark.parametrize("seed,K,H,W,D", [(1, 3, 4, 6, 5), (2, 4, 3, 5, 6), (5, 3, 3, 7, 1), (6, 1, 4, 6, 5)])
+def test_joint_map_matches_exhaustive_table(seed, K, H, W, D):
+    """Joint MAP is the arg-max of the whole table (lowest d, then smallest
+    mask); its objective is the table maximum at every pixel, tie or not."""
+    imgs, seg, b = _tiny_frame(K, H, W, seed)
+    rng = np.random.default_rng(seed + 100)
+    pts = np.stack([rng.uniform(-1, W, 6), rng.uniform(-1, H, 6), rng.uniform(0, 4, 6)], 1).astype(np.float32)
+    p = O.Params(beta=30.0, em_mode=2)
+    out = O.run(imgs, seg, b, pts, 0.0, 4.0, D, 2, params=p)
+    bf = BF.run(imgs, seg, b, out["mu"], out["inside"], 0.0, 4.0, D, 2, p, mode="joint")
+    assert np.allclose(out["J_t"][0], bf["joint_max"], atol=1e-10)
+    assert np.array_equal(out["J_t"][0], out["J_t"][1])
+    ok = ~O.excused(out, tau_rel=1e-9, tau_init=1e-9)
+    assert ok.sum() >= 6
+    assert np.array_equal(out["d_idx"][ok], bf["d_idx"][ok])
+    assert np.array_equal(out["labels"][ok].astype(np.int64), bf["labels"][ok])
+    assert np.allclose(out["post"][:, ok], bf["post"][:, ok], atol=1e-11)
+    assert np.allclose(out["refocus"][ok], bf["refocus"][ok], atol=1e-12)
+    hard = O.run(imgs, seg, b, pts, 0.0, 4.0, D, 4, params=O.Params(beta=30.0))
+    assert np.all(hard["J_t"][-1] <= out["J_t"][0] + 1e-10)
+
+
+def test_soft_em_pin_catches_planted_uniform_posterior(monkeypatch):
+    """The soft-EM pin is sensitive: averaging the rows under a uniform
+    instead of the E-step's posterior changes the result somewhere."""
+    imgs, seg, b = _tiny_frame(3, 4, 6, 1)
+    p = O.Params(beta=30.0, em_mode=1)
+    out = O.run(imgs, seg, b, np.zeros((0, 3), np.float32), 0.0, 4.0, 5, 4, params=p)
+    good = BF.run(imgs, seg, b, out["mu"], out["inside"], 0.0, 4.0, 5, 4, p, mode="soft")
+    assert np.allclose(good["L_t"], out["J_t"], atol=1e-10)
+    monkeypatch.setattr(BF, "_softmax", lambda row: np.full(row.shape, 1.0 / row.size))
+    bad = BF.run(imgs, seg, b, out["mu"], out["inside"], 0.0, 4.0, 5, 4, p, mode="soft")
+    assert not np.allclose(bad["L_t"], out["J_t"], atol=1e-10)
+
+
 def test_brute_force_catches_planted_sign_error(monkeypatch):
     """The brute force is sensitive enough: flipping the sign of the variance
     term in the exhaustive table changes the arg-max somewhere."""
@@ -200,6 +258,27 @@ def test_objective_never_decreases():
     assert np.all(J[1:] >= J[:-1] - 1e-12)
     post = out["post"]
     assert np.all((post >= 0) & (post <= 1))
+
+
+def test_soft_em_log_marginal_never_decreases():
+    """Soft EM never decreases log sum_S exp J(d_t, S) (Jensen's bound: the
+    M-step raises the expected objective under the exact posterior at
+    d_{t-1}, which lower-bounds the log marginal and touches it at d_{t-1})."""
+    s = scenes.small_gray(0)
+    out = O.run_scene(s, params=O.Params(em_mode=1), iters=6)
+    L = out["J_t"]
+    assert np.all(L[1:] >= L[:-1] - 1e-9 * (1 + np.abs(L[:-1])))
+    hard = O.run_scene(s, iters=6)
+    assert not np.array_equal(out["d_idx"], hard["d_idx"]) or not np.array_equal(L[-1], hard["J_t"][-1])
+
+
+def test_joint_map_bounds_both_ems():
+    """The joint maximum over (d, S) is at least the final objective of the
+    hard EM at every pixel."""
+    s = scenes.small_gray(1)
+    joint = O.run_scene(s, params=O.Params(em_mode=2), iters=1)
+    hard = O.run_scene(s, iters=5)
+    assert np.all(hard["J_t"][-1] <= joint["J_t"][0] + 1e-9)
 
 
 def test_occluder_free_integer_shift_scene_is_exact():
