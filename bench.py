@@ -51,6 +51,24 @@ def sweep_ops_per_pixel_iter(K: int, D: int) -> int:
     return D * (11 * K + 12) + (1 << K) * 13
 
 
+def soft_ops_per_pixel_iter(K: int, D: int) -> int:
+    """Soft-EM iteration after the first: M-step per (candidate, camera) 5
+    interpolations + 1 expected segmentation term, per camera pair 7 (3
+    differences, 3 squares, 1 weighted add), per candidate 8 (prior, objective,
+    compare); E-step: the arg-max pass (13 per label vector) and the posterior
+    pass (13 objective + 3 exp/normalise per vector, one add per member ray
+    and per member pair: 2^(K-1) K + 2^(K-2) K(K-1)/2)."""
+    P = K * (K - 1) // 2
+    return D * (6 * K + 7 * P + 8) + (1 << K) * 29 + (1 << K) * K // 2 + (1 << K) * P // 4
+
+
+def joint_ops_per_pixel(K: int, D: int) -> int:
+    """Joint MAP per pixel: per (candidate, camera) 10 (5 interpolations, 3
+    squares, 2 segmentation terms), per candidate the E-step enumeration (13
+    per label vector) + 6 (prior, compare)."""
+    return D * (10 * K + (1 << K) * 13 + 6)
+
+
 def sweep_source_hash() -> str:
     return hashlib.sha256(open(SWEEP_SRC, "rb").read()).hexdigest()[:16]
 
@@ -151,9 +169,9 @@ def cpu_oracle_sample(scene, params, seconds: float = 12.0):
     t0 = time.perf_counter()
     O.run_scene(scene, params=params, rows=(mid, mid + rows))
     dt = time.perf_counter() - t0
-    samples = rows * scene.W * scene.K * scene.D * scene.iters
+    samples = rows * scene.W * scene.K * scene.D * (1 if params.em_mode == 2 else scene.iters)
     desc = f"rows {mid}..{mid + rows - 1} of the 960x600 frame ({rows} x 960 px x K*D*iters = {samples} " \
-           f"nominal ray samples, FP64 C oracle with OpenMP over rows)"
+           f"nominal ray samples, FP64 C oracle with OpenMP over rows, every pixel reconstructed)"
     return samples / dt, cores, desc, rows, dt
 
 
@@ -162,7 +180,7 @@ def oracle_params(lf_params):
     p = lf_params
     return O.Params(beta=float(np.float32(p.beta)), gamma=float(np.float32(p.gamma)),
                     sigma=float(np.float32(p.sigma)), seg_threshold=float(np.float32(p.seg_threshold)),
-                    eps=float(np.float32(p.eps)), mstep_seg_term=int(p.mstep_seg_term))
+                    eps=float(np.float32(p.eps)), mstep_seg_term=int(p.mstep_seg_term), em_mode=int(p.em_mode))
 
 
 def run_reference(args, world, rank):
@@ -372,6 +390,10 @@ def main():
     ap.add_argument("--rates", default="50,100,200,400", help="serve: arrival rates (requests/s)")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals per rate")
     ap.add_argument("--autotune", type=int, default=1, help="batch: tile shapes chosen by timing")
+    ap.add_argument("--em-mode", default="hard", choices=["hard", "soft", "joint"],
+                    help="street: the paper's hard EM, soft EM or joint MAP over (d, S)")
+    ap.add_argument("--dynamic-only", action="store_true",
+                    help="street: reconstruct only the reference pixels with P(dynamic) >= 0.7")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -391,7 +413,9 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     s = scenes.street_rgb(rank)
-    params = lf.default_params(precision={"f32": 0, "f16": 1, "bf16": 2}[args.precision])
+    mode = {"hard": 0, "soft": 1, "joint": 2}[args.em_mode]
+    params = lf.default_params(precision={"f32": 0, "f16": 1, "bf16": 2}[args.precision], em_mode=mode,
+                               dynamic_only=int(args.dynamic_only))
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     img_d = torch.from_numpy(s.images).to(dev)
@@ -438,7 +462,7 @@ def main():
     assert st["runs"] == args.steps
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
     total_s = max_over_ranks(sum(step_ms) / 1e3)
-    nominal = H * W * K * D * iters
+    nominal = H * W * K * D * (1 if mode == 2 else iters)
     value = whole_job_value(nominal * args.steps, world, total_s)
     kernels_per_step = st["kernels_launched"]
 
@@ -471,7 +495,17 @@ def main():
         n_sm = props.multi_processor_count
         exec_mean = st["executed_ray_samples"] / st["runs"]
         pix_iters = exec_mean / (K * D)
-        ops = pix_iters * sweep_ops_per_pixel_iter(K, D)
+        if mode == 0:
+            ops = pix_iters * sweep_ops_per_pixel_iter(K, D)
+            ops_desc = {"ops_per_pixel_iteration": sweep_ops_per_pixel_iter(K, D)}
+        elif mode == 1:  # every swept pixel's first iteration is the EM's first M-step
+            first = min(pix_iters, H * W * (float(np.mean(s.seg_prior[int(np.argmin(np.abs(s.baselines)))] >= 0.7)) if args.dynamic_only else 1))
+            ops = first * sweep_ops_per_pixel_iter(K, D) + (pix_iters - first) * soft_ops_per_pixel_iter(K, D)
+            ops_desc = {"ops_first_iteration": sweep_ops_per_pixel_iter(K, D),
+                        "ops_per_later_iteration": soft_ops_per_pixel_iter(K, D)}
+        else:
+            ops = pix_iters * joint_ops_per_pixel(K, D)
+            ops_desc = {"ops_per_pixel": joint_ops_per_pixel(K, D)}
         sweep_s = st["ms_sweep"] / 1e3
         achieved = ops / sweep_s / 1e9
         f_mhz = clk.get("sm_mhz") or 2070.0
@@ -483,13 +517,15 @@ def main():
                 if "=" in line and not line.lstrip().startswith("#"):
                     k, v = line.split("=", 1)
                     kv[k.strip()] = v.strip()
-            if kv.get("kernel_sha") == sweep_source_hash():
+            if mode == 0 and not args.dynamic_only and kv.get("kernel_sha") == sweep_source_hash():
                 traffic = float(kv["dram_bytes_per_launch"])
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "parallelism": f"replicas{world}" if world > 1 else "single",
+            "config": {"workload": WORKLOAD + ("" if mode == 0 else f", {args.em_mode} EM mode")
+                       + (", dynamic-only" if args.dynamic_only else ""),
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
                        "staged_maps": args.precision,
                        "frames_per_s": args.steps * world / total_s,
                        "executed_ray_samples_per_frame": exec_mean,
@@ -498,11 +534,10 @@ def main():
                                      "refocus": st["ms_refocus"]},
                        "l2": "flushed between steps (256 MB write outside the per-step events)",
                        "tile": [st["tile_rows"], st["tile_cols"]]},
-            "roofline": {"bound": "alu", "kernel": "em_sweep", "achieved": achieved,
+            "roofline": {"bound": "alu", "kernel": "em_sweep" if mode == 0 else "em_variant", "achieved": achieved,
                          "peak": peak, "unit": "Gop/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {f_mhz:.0f} MHz (median sampled SM clock "
-                                       f"during the timed region)",
-                         "ops_per_pixel_iteration": sweep_ops_per_pixel_iter(K, D)},
+                                       f"during the timed region)", **ops_desc},
             "e2e": {"value": whole_job_value(nominal * e2e_steps, world, e2e_s), "unit": UNIT,
                     "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s / e2e_steps},

@@ -71,12 +71,33 @@ typedef enum lf_precision {
 } lf_precision;
 
 /*
+ * How the hidden labels S are treated (Sec. III-B formulates EM over them;
+ * Sec. III-C/III-D run it with hard assignments):
+ *   LF_EM_HARD   the paper's EM: M-step at the labels of the last E-step,
+ *                E-step = arg-max over the 2^K label vectors.
+ *   LF_EM_SOFT   soft EM: the E-step keeps the posterior q(S) proportional to
+ *                exp J(d_t, S) over all label vectors and every M-step after
+ *                the first maximises sum_S q(S) J(d, S); the labels reported
+ *                are the arg-max of J(d_T, S).  At most 8 cameras.
+ *   LF_EM_JOINT  joint MAP: (d, S) = arg-max of J(d, S) over every candidate
+ *                and label vector (lowest candidate, then smallest mask); the
+ *                iteration count is not used.
+ * The two variants stage float32 maps (precision must be LF_PREC_F32) and run
+ * through lf_run_em only (not the batch API nor lf_run_em_static).
+ */
+typedef enum lf_em_mode {
+    LF_EM_HARD = 0,
+    LF_EM_SOFT = 1,
+    LF_EM_JOINT = 2
+} lf_em_mode;
+
+/*
  * Model and run parameters.  The paper names beta, gamma, sigma and the
  * initial threshold (Sec. III-C energy, Sec. III-F) but prints a value only
  * for the threshold (0.7); the defaults of lf_default_params are
  * beta = 200, gamma = 0.1, sigma = 2, seg_threshold = 0.7, eps = 1e-4,
  * mstep_seg_term = 1, median = 0, precision = LF_PREC_F32, early_exit = 1,
- * dynamic_only = 0.
+ * dynamic_only = 0, em_mode = LF_EM_HARD.
  */
 typedef struct lf_params {
     float beta;          /* weight of the static rays' descriptor variance */
@@ -95,6 +116,8 @@ typedef struct lf_params {
                             P(dynamic) >= seg_threshold (Sec. III-F: the other
                             pixels already show the static background); see
                             lf_run_em for what the other pixels receive */
+    int em_mode;         /* lf_em_mode: the paper's hard EM, or one of the two
+                            variants of its formulation (see lf_em_mode) */
 } lf_params;
 
 /* Statistics accumulated over the lf_run_em calls since the previous

@@ -638,14 +638,14 @@ constexpr int sweep_min_blocks() {
   return K <= 8 ? 2 : 1;
 }
 
-// One tile (tile_x, tile_y) of one frame: stage, run the EM, write the
-// outputs.  The CTA's mbarrier (initialised by the caller) completes phase
-// `phase` for this tile's copies.  load_tables: the frame differs from the
-// previous tile's (tables and constants must be staged again).  Ends with a
-// __syncthreads so that the next tile may reuse the shared memory.  Returns
-// false (same in every thread) when the staging wait timed out.
+// Phases 1-2 for tile (tile_x, tile_y) of one frame: raw rows by TMA, then
+// descriptors and log priors in shared memory.  The CTA's mbarrier
+// (initialised by the caller) completes phase `phase` for this tile's copies.
+// load_tables: the frame differs from the previous tile's (tables and
+// constants must be staged again).  Returns false (same in every thread) when
+// the staging wait timed out; ends with a __syncthreads either way.
 template <int K, typename TS>
-__device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap* img_map,
+__device__ __forceinline__ bool stage_tile(const SweepArgs& a, const CUtensorMap* img_map,
                                            const CUtensorMap* p_map, int tile_x, int tile_y, uint8_t* smem,
                                            unsigned phase, bool load_tables, bool maps_in_global) {
   const SmemLayout Ly = sweep_layout(K, a);
@@ -745,6 +745,32 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     stf(F + kMapZ * a.SWp + c, ld - ls);
   }
   __syncthreads();
+  return true;
+}
+
+// One tile (tile_x, tile_y) of one frame: stage, run the EM, write the
+// outputs.  Staging as in stage_tile.  Ends with a __syncthreads so that the
+// next tile may reuse the shared memory.  Returns false (same in every
+// thread) when the staging wait timed out.
+template <int K, typename TS>
+__device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap* img_map,
+                                           const CUtensorMap* p_map, int tile_x, int tile_y, uint8_t* smem,
+                                           unsigned phase, bool load_tables, bool maps_in_global) {
+  if (!stage_tile<K, TS>(a, img_map, p_map, tile_x, tile_y, smem, phase, load_tables, maps_in_global))
+    return false;
+  const SmemLayout Ly = sweep_layout(K, a);
+  const float* s_p = reinterpret_cast<const float*>(smem + Ly.raw_p);
+  TS* s_feat = reinterpret_cast<TS*>(smem + Ly.feat);
+  float* s_w = reinterpret_cast<float*>(smem + Ly.wtab);
+  int* s_o = reinterpret_cast<int*>(smem + Ly.otab);
+  unsigned* s_chg = reinterpret_cast<unsigned*>(smem + Ly.chg);
+  float* s_d = reinterpret_cast<float*>(smem + Ly.dval);
+  float* s_rcp = reinterpret_cast<float*>(smem + Ly.rcp);
+  const int tid = threadIdx.x;
+  const int u0 = tile_x * a.TW, v0 = tile_y * a.TR;
+  const int cs = floor16(u0 - a.L - 1);
+  const int W = a.W, H = a.H, RW = a.RW;
+  const int cam_stride = a.TR * kMaps * a.SWp;
 
   // ---- 3-5. per-pixel EM.  The pixels still iterating are regrouped into
   // dense warps before every pass (exact per-pixel early exit), and in the

@@ -1,0 +1,286 @@
+// Variants of the per-pixel EM, on the same staged tile as the sweep kernel
+// (Sec. III-B formulates EM over the hidden labels S; the paper runs it with
+// hard assignments, Sec. III-C/III-D):
+//
+//   soft EM    the E-step keeps the whole posterior q(S) ~ exp J(d_t, S) over
+//              the 2^K label vectors, and every M-step after the first
+//              maximises the expected complete-data objective
+//                Q(d) = sum_S q(S) J(d, S).
+//              With Var_S = (1/|S|^2) sum_{k<l in S} |f_k - f_l|^2 this is
+//                Q(d) = log p(d) + sum_k [pi_k ls_k + (1 - pi_k) ld_k]
+//                       - beta * sum_{k<l} w_kl |f_k(d) - f_l(d)|^2
+//              with pi_k = P(ray k static) and w_kl = sum_{S contains k,l}
+//              q(S) / |S|^2, both taken from q once per iteration, so one
+//              candidate costs K(K-1)/2 descriptor distances instead of 2^K
+//              label vectors.  A pixel whose M-step returns the previous
+//              candidate has reached its fixed point (q depends on d only).
+//   joint MAP  (d, S) = arg-max of J(d, S) over every candidate and every
+//              label vector (lowest candidate first, then smallest mask):
+//              the E-step enumeration run at each of the D candidates.
+//
+// Both modes write the same outputs as the EM: candidate index and value,
+// the labels at the final candidate (the arg-max over S), the per-ray
+// marginals of q(S) at the final candidate, and in dynamic-only mode the
+// stand-in outputs of the pixels it skips.
+#pragma once
+
+#include "em_sweep.cuh"
+
+namespace lf {
+namespace dev {
+
+constexpr int kModeSoft = 1, kModeJoint = 2;
+constexpr int kSoftMaxCams = 8;  // K(K-1)/2 pair weights live in registers
+
+template <int K>
+constexpr int kNumPairs = K * (K - 1) / 2 > 0 ? K * (K - 1) / 2 : 1;
+
+// q(S) ~ exp J(d, S) at the candidate the rays were sampled at (emax = the
+// maximum of J over S, without the prior, which q does not depend on).
+// pi[k] = sum over S containing k of q(S); pw[pair (k, l)] = sum over S
+// containing k and l of q(S) / |S|^2 (pairs in order (0,1), (0,2), ...,
+// (1,2), ...).
+template <int K>
+__device__ __forceinline__ void soft_posterior(const Rays& r, const float* s_rcp, float beta, float emax,
+                                               float (&pi)[K], float (&pw)[kNumPairs<K>]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) pi[k] = 0.f;
+#pragma unroll
+  for (int i = 0; i < kNumPairs<K>; ++i) pw[i] = 0.f;
+  float Z = 0.f;
+  for (unsigned m = 0; m < (1u << K); ++m) {
+    Acc acc{0.f, 0.f, 0.f, 0.f, 0.f};
+    int n = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (m >> k & 1u) {
+        acc.sy += r.gy[k]; acc.sx += r.gx[k]; acc.sz += r.gz[k];
+        acc.q += r.qk[k]; acc.sa += r.ak[k];
+        ++n;
+      }
+    }
+    const float rn = s_rcp[n];
+    const float e = expf(leaf_objective(acc, rn, r.base, beta) - emax);
+    Z += e;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (m >> k & 1u) pi[k] += e;
+    const float c = e * rn * rn;
+    int p = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int l = k + 1; l < K; ++l) {
+        if ((m >> k) & (m >> l) & 1u) pw[p] += c;
+        ++p;
+      }
+  }
+  const float inv = 1.f / Z;
+#pragma unroll
+  for (int k = 0; k < K; ++k) pi[k] *= inv;
+#pragma unroll
+  for (int i = 0; i < kNumPairs<K>; ++i) pw[i] *= inv;
+}
+
+// Soft-EM M-step: arg-max over the candidates of Q(d_j) (lowest j on ties).
+template <int K>
+__device__ __forceinline__ int m_step_soft(const SweepArgs& a, const Staged<float>& st, const float* s_w,
+                                           const int* s_o, const float* s_d, float cy, float cx, float cz,
+                                           float mu, bool inside, const float (&pi)[K],
+                                           const float (&pw)[kNumPairs<K>]) {
+  const int SWp = st.SWp;
+  float best = -INFINITY;
+  int jb = 0;
+  for (int j = 0; j < a.D; ++j) {
+    float gy[K], gx[K], gz[K];
+    float seg = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float w = s_w[j * a.KP + k];
+      const int c = st.cbase + s_o[j * a.KP + k];
+      const float* Fk = st.F + k * st.cam_stride;
+      const float Y0 = Fk[c], X0 = Fk[SWp + c], Z0 = Fk[2 * SWp + c];
+      gy[k] = fmaf(w, Fk[c + 1] - Y0, Y0 - cy);
+      gx[k] = fmaf(w, Fk[SWp + c + 1] - X0, X0 - cx);
+      gz[k] = fmaf(w, Fk[2 * SWp + c + 1] - Z0, Z0 - cz);
+      const float S0 = Fk[kMapLs * SWp + c], D0 = Fk[kMapLd * SWp + c];
+      const float ls = fmaf(w, Fk[kMapLs * SWp + c + 1] - S0, S0);
+      const float ld = fmaf(w, Fk[kMapLd * SWp + c + 1] - D0, D0);
+      seg += fmaf(pi[k], ls - ld, ld);
+    }
+    float pv = 0.f;
+    int p = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int l = k + 1; l < K; ++l) {
+        const float dy = gy[k] - gy[l], dx = gx[k] - gx[l], dz = gz[k] - gz[l];
+        pv = fmaf(pw[p], fmaf(dz, dz, fmaf(dx, dx, dy * dy)), pv);
+        ++p;
+      }
+    float J = a.mseg ? seg : 0.f;
+    if (inside) {
+      const float t = s_d[j] - mu;
+      J += __logf(a.gamma + __expf(-(t * t) * a.inv2s2));
+    }
+    J = fmaf(-a.beta, pv, J);
+    if (J > best) { best = J; jb = j; }
+  }
+  return jb;
+}
+
+// Joint MAP over (d, S): the E-step's subset-tree arg-max at every candidate
+// plus the candidate's prior.  Returns j; S and emax (J at (j, S) without the
+// prior) through the references.
+template <int K>
+__device__ __forceinline__ int joint_map(const SweepArgs& a, const Staged<float>& st, const float* s_w,
+                                         const int* s_o, const float* s_d, const float* s_rcp, float cy, float cx,
+                                         float cz, float mu, bool inside, unsigned& S, float& emax) {
+  float best = -INFINITY;
+  int jb = 0;
+  unsigned Sb = 0;
+  float eb = 0.f;
+  for (int j = 0; j < a.D; ++j) {
+    Rays r;
+    sample_rays<K, float>(a, st, s_w, s_o, j, cy, cx, cz, r);
+    unsigned m = 0;
+    float e = 0.f;
+    enumerate<0, K>(r, s_rcp, a.beta, 0.f, m, e, nullptr);
+    float J = e;
+    if (inside) {
+      const float t = s_d[j] - mu;
+      J += __logf(a.gamma + __expf(-(t * t) * a.inv2s2));
+    }
+    if (J > best) { best = J; jb = j; Sb = m; eb = e; }
+  }
+  S = Sb;
+  emax = eb;
+  return jb;
+}
+
+// One tile, one thread per pixel (no compaction: a pixel stops at its own
+// fixed point and its warp waits for the others).
+template <int K, int MODE>
+__device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorMap* img_map,
+                                             const CUtensorMap* p_map, int tile_x, int tile_y, uint8_t* smem) {
+  if (!stage_tile<K, float>(a, img_map, p_map, tile_x, tile_y, smem, 0u, true, false)) return;
+  const SmemLayout Ly = sweep_layout(K, a);
+  const float* s_p = reinterpret_cast<const float*>(smem + Ly.raw_p);
+  const float* s_feat = reinterpret_cast<const float*>(smem + Ly.feat);
+  const float* s_w = reinterpret_cast<const float*>(smem + Ly.wtab);
+  const int* s_o = reinterpret_cast<const int*>(smem + Ly.otab);
+  const unsigned* s_chg = reinterpret_cast<const unsigned*>(smem + Ly.chg);
+  const float* s_d = reinterpret_cast<const float*>(smem + Ly.dval);
+  const float* s_rcp = reinterpret_cast<const float*>(smem + Ly.rcp);
+  const int tid = threadIdx.x;
+  const int u0 = tile_x * a.TW, v0 = tile_y * a.TR;
+  const int cs = floor16(u0 - a.L - 1);
+  const int cam_stride = a.TR * kMaps * a.SWp;
+
+  const PixelCtx<float> me = load_pixel(a, s_feat, u0, v0, cam_stride, tid);
+  bool run = me.valid;
+  if (a.dyn_only && run) {  // Sec. III-F: only the reference pixels flagged dynamic
+    const int r = tid / a.TW;
+    const float Pref = s_p[(static_cast<size_t>(a.ref) * a.TR + r) * a.RW + (me.u - cs)];
+    if (!(Pref >= a.seg_threshold)) {
+      write_static_pixel<K>(a, me.u, me.v);
+      run = false;
+    }
+  }
+  unsigned executed = 0;
+  if (run) {
+    int jb;
+    unsigned S = 0;
+    float emax = 0.f;
+    float post[K];
+    Rays rays;
+    if constexpr (MODE == kModeJoint) {
+      jb = joint_map<K>(a, me.st, s_w, s_o, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu, me.inside, S, emax);
+      executed = 1;
+      if (a.post) {
+        sample_rays<K, float>(a, me.st, s_w, s_o, jb, me.cy, me.cx, me.cz, rays);
+        unsigned dummy;
+        float dummyf;
+        enumerate<1, K>(rays, s_rcp, a.beta, emax, dummy, dummyf, post);
+      }
+    } else {
+      // t = 1: the EM's first M-step (labels thresholded per candidate)
+      unsigned S0 = 0;
+      const bool f0 = constant_initial_labels<K, float>(a, me.st, &S0);
+      jb = f0 ? m_step_fixed<K, float>(a, me.st, s_w, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu, me.inside,
+                                       S0)
+              : m_step<K, true, float>(a, me.st, s_w, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu,
+                                       me.inside, 0u);
+      executed = 1;
+      float pw[kNumPairs<K>];
+      sample_rays<K, float>(a, me.st, s_w, s_o, jb, me.cy, me.cx, me.cz, rays);
+      enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
+      soft_posterior<K>(rays, s_rcp, a.beta, emax, post, pw);
+      for (int t = 2; t <= a.iters; ++t) {
+        const int jn = m_step_soft<K>(a, me.st, s_w, s_o, s_d, me.cy, me.cx, me.cz, me.mu, me.inside, post, pw);
+        ++executed;
+        if (a.early_exit && jn == jb) break;  // q_t would equal q_{t-1}: fixed point
+        jb = jn;
+        sample_rays<K, float>(a, me.st, s_w, s_o, jb, me.cy, me.cx, me.cz, rays);
+        enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
+        soft_posterior<K>(rays, s_rcp, a.beta, emax, post, pw);
+      }
+    }
+    const size_t pix = static_cast<size_t>(me.v) * a.W + me.u;
+    a.d_idx[pix] = jb;
+    if (a.d_out) a.d_out[pix] = s_d[jb];
+    if (a.labels) a.labels[pix] = static_cast<uint16_t>(S);
+    if (a.post) {
+      const size_t HW = static_cast<size_t>(a.H) * a.W;
+#pragma unroll
+      for (int k = 0; k < K; ++k) a.post[k * HW + pix] = post[k];
+    }
+  }
+  const unsigned warp_sum = __reduce_add_sync(0xffffffffu, executed);
+  if ((tid & 31) == 0 && warp_sum) atomicAdd(a.counter, static_cast<unsigned long long>(warp_sum));
+}
+
+template <int K, int MODE>
+__global__ void __launch_bounds__(256) em_variant_kernel(const __grid_constant__ CUtensorMap img_map,
+                                                         const __grid_constant__ CUtensorMap p_map,
+                                                         const SweepArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  if ((smem_u32(smem) & 127u) != 0u) {  // TMA destinations must be 128-byte aligned
+    if (threadIdx.x == 0) atomicOr(a.status, kStatusSmemMisaligned);
+    return;
+  }
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kSmemBar);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  int tx = blockIdx.x, ty = blockIdx.y;
+  if (a.tile_list) {  // dynamic-only: this CTA's tile comes from the classified list
+    if (static_cast<int>(blockIdx.x) >= *a.n_tiles) return;
+    const int id = a.tile_list[blockIdx.x], tiles_x = (a.W + a.TW - 1) / a.TW;
+    tx = id % tiles_x;
+    ty = id / tiles_x;
+  }
+  variant_tile<K, MODE>(a, &img_map, &p_map, tx, ty, smem);
+}
+
+template <int K, int MODE>
+cudaError_t launch_em_variant_k(const CUtensorMap& img_map, const CUtensorMap& p_map, const SweepArgs& a,
+                                cudaStream_t s) {
+  const size_t smem = sweep_layout(K, a).total;
+  static int configured = -1;  // largest dynamic shared size set so far (per process)
+  if (static_cast<int>(smem) > configured) {
+    cudaError_t e = cudaFuncSetAttribute(em_variant_kernel<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    configured = static_cast<int>(smem);
+  }
+  dim3 grid((a.W + a.TW - 1) / a.TW, (a.H + a.TR - 1) / a.TR);
+  if (a.tile_list) grid = dim3(grid.x * grid.y, 1);
+  em_variant_kernel<K, MODE><<<grid, a.TR * a.TW, smem, s>>>(img_map, p_map, a);
+  return cudaGetLastError();
+}
+
+}  // namespace dev
+}  // namespace lf

@@ -39,7 +39,25 @@ LF_DECL_CLASSIFY(11) LF_DECL_CLASSIFY(12)
 #undef LF_DECL_SWEEPS
 #undef LF_DECL_SWEEP
 
+#define LF_DECL_VARIANT(k) \
+  cudaError_t launch_em_variant_k##k(int, const CUtensorMap&, const CUtensorMap&, const SweepArgs&, cudaStream_t);
+LF_DECL_VARIANT(1) LF_DECL_VARIANT(2) LF_DECL_VARIANT(3) LF_DECL_VARIANT(4) LF_DECL_VARIANT(5)
+LF_DECL_VARIANT(6) LF_DECL_VARIANT(7) LF_DECL_VARIANT(8) LF_DECL_VARIANT(9) LF_DECL_VARIANT(10)
+LF_DECL_VARIANT(11) LF_DECL_VARIANT(12)
+#undef LF_DECL_VARIANT
+
 size_t sweep_smem_bytes(int K, const SweepArgs& a) { return dev::sweep_layout(K, a).total; }
+
+cudaError_t launch_em_variant(int K, int mode, const CUtensorMap& i, const CUtensorMap& p, const SweepArgs& a,
+                              cudaStream_t s) {
+  typedef cudaError_t (*VariantLaunch)(int, const CUtensorMap&, const CUtensorMap&, const SweepArgs&, cudaStream_t);
+  static const VariantLaunch table[kMaxCams] = {
+      launch_em_variant_k1, launch_em_variant_k2, launch_em_variant_k3,  launch_em_variant_k4,
+      launch_em_variant_k5, launch_em_variant_k6, launch_em_variant_k7,  launch_em_variant_k8,
+      launch_em_variant_k9, launch_em_variant_k10, launch_em_variant_k11, launch_em_variant_k12};
+  if (K < 1 || K > kMaxCams) return cudaErrorInvalidValue;
+  return table[K - 1](mode, i, p, a, s);
+}
 
 typedef cudaError_t (*SweepLaunch)(const CUtensorMap&, const CUtensorMap&, const SweepArgs&, cudaStream_t);
 
@@ -402,6 +420,7 @@ void lf_default_params(lf_params* p) {
   p->precision = LF_PREC_F32;
   p->early_exit = 1;
   p->dynamic_only = 0;
+  p->em_mode = LF_EM_HARD;
 }
 
 const char* lf_last_error(const lf_ctx*) { return g_err.c_str(); }
@@ -442,6 +461,11 @@ lf_status lf_create(lf_ctx** out, int n_cams, const float* baselines, int H, int
     return fail(LF_EINVAL, "invalid lf_params");
   if (prm.precision != LF_PREC_F32 && prm.precision != LF_PREC_F16 && prm.precision != LF_PREC_BF16)
     return fail(LF_EINVAL, "precision must be LF_PREC_F32, LF_PREC_F16 or LF_PREC_BF16");
+  if (prm.em_mode != LF_EM_HARD && prm.em_mode != LF_EM_SOFT && prm.em_mode != LF_EM_JOINT)
+    return fail(LF_EINVAL, "em_mode must be LF_EM_HARD, LF_EM_SOFT or LF_EM_JOINT");
+  if (prm.em_mode != LF_EM_HARD && prm.precision != LF_PREC_F32)
+    return fail(LF_EINVAL, "the soft-EM and joint-MAP modes stage float32 maps only (LF_PREC_F32)");
+  if (prm.em_mode == LF_EM_SOFT && n_cams > 8) return fail(LF_EINVAL, "soft EM supports at most 8 cameras");
 
   lf_ctx* c = new (std::nothrow) lf_ctx();
   if (!c) return fail(LF_ENOMEM, "host allocation failed");
@@ -684,7 +708,10 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
     a.tile_list = c->d_tiles;
     a.n_tiles = c->d_tiles + tiles;
   }
-  LF_CUDA(launch_em_sweep(c->K, c->img_map, c->p_map, a, c->stream), "em_sweep launch");
+  if (c->p.em_mode == LF_EM_HARD)
+    LF_CUDA(launch_em_sweep(c->K, c->img_map, c->p_map, a, c->stream), "em_sweep launch");
+  else
+    LF_CUDA(launch_em_variant(c->K, c->p.em_mode, c->img_map, c->p_map, a, c->stream), "em_variant launch");
   ++launched;
   LF_CUDA(mark(2), "event");
   if (refo) {
@@ -700,7 +727,9 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
     }
   }
   ++c->runs;
-  c->stats.nominal_ray_samples = static_cast<uint64_t>(HW) * c->K * c->D * iters;
+  // joint MAP sweeps the candidates once, whatever the iteration count
+  c->stats.nominal_ray_samples =
+      static_cast<uint64_t>(HW) * c->K * c->D * (c->p.em_mode == LF_EM_JOINT ? 1 : iters);
   c->stats.halo_left = c->L;
   c->stats.halo_right = c->R;
   c->stats.tile_rows = c->TR;

@@ -386,6 +386,7 @@ lf_status lf_batch_create(lf_batch** out, const lf_params* p, int autotune) {
       prm.eps <= 0.f || prm.seg_threshold <= 0.f || prm.seg_threshold >= 1.f || prm.beta < 0.f ||
       prm.precision < LF_PREC_F32 || prm.precision > LF_PREC_BF16)
     return fail(LF_EINVAL, "invalid lf_params");
+  if (prm.em_mode != LF_EM_HARD) return fail(LF_EINVAL, "batches run the hard EM only (em_mode = LF_EM_HARD)");
   lf_batch* b = new (std::nothrow) lf_batch();
   if (!b) return fail(LF_ENOMEM, "host allocation failed");
   b->p = prm;

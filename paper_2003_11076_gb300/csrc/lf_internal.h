@@ -110,6 +110,9 @@ cudaError_t launch_tile_classify(int K, const SweepArgs& a, const float* seg_pri
                                  int* tile_list, int* n_tiles, cudaStream_t s);
 cudaError_t launch_em_sweep(int K, const CUtensorMap& img_map, const CUtensorMap& p_map,
                             const SweepArgs& a, cudaStream_t s);
+// Soft EM (mode 1, K <= 8) or joint MAP (mode 2) on float32 staged maps.
+cudaError_t launch_em_variant(int K, int mode, const CUtensorMap& img_map, const CUtensorMap& p_map,
+                              const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_refocus(const RefocusArgs& a, cudaStream_t s);
 cudaError_t launch_median3(const float* in, float* out, int H, int W, int C, cudaStream_t s);
 cudaError_t launch_prior_raster_batched(const PriorArgs* frames, const RowItem* items, const int* n_items,

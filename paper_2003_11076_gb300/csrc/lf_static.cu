@@ -117,6 +117,7 @@ extern "C" lf_status lf_run_em_static(int n_cams, const float* baselines, int H,
   lf_default_params(&prm);
   if (p) prm = *p;
   if (prm.precision != LF_PREC_F32) return fail(LF_EINVAL, "the allocation-free sweep stages float32 maps only (LF_PREC_F32)");
+  if (prm.em_mode != LF_EM_HARD) return fail(LF_EINVAL, "the allocation-free sweep runs the hard EM only (LF_EM_HARD)");
   const size_t bpp = static_cast<size_t>(C) * (dtype == LF_U8 ? 1 : 4);
   // Without staging buffers the inputs are read in place by TMA: rows must
   // start on 16-byte boundaries.

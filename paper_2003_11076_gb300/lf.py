@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "lib
 LF_OK, LF_EINVAL, LF_ENOMEM, LF_ECUDA, LF_ESTATE, LF_ETIMEOUT = range(6)
 LF_U8, LF_F32, LF_F16, LF_BF16 = 0, 1, 2, 3
 LF_PREC_F32, LF_PREC_F16, LF_PREC_BF16 = 0, 1, 2
+LF_EM_HARD, LF_EM_SOFT, LF_EM_JOINT = 0, 1, 2
 
 EXPORTS = ("lf_default_params", "lf_create", "lf_set_stream", "lf_set_inputs", "lf_run_em",
            "lf_synchronize", "lf_get_prior", "lf_get_stats", "lf_last_error", "lf_destroy",
@@ -37,7 +38,8 @@ class Params(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_float), ("gamma", ctypes.c_float), ("sigma", ctypes.c_float),
                 ("seg_threshold", ctypes.c_float), ("eps", ctypes.c_float),
                 ("mstep_seg_term", ctypes.c_int), ("median", ctypes.c_int), ("precision", ctypes.c_int),
-                ("early_exit", ctypes.c_int), ("dynamic_only", ctypes.c_int)]
+                ("early_exit", ctypes.c_int), ("dynamic_only", ctypes.c_int),
+                ("em_mode", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
