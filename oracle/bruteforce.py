@@ -6,7 +6,9 @@ C core uses --
 
 * descriptors: Sobel through ``scipy.ndimage.correlate`` (mode 'nearest');
 * ray sampling: ``numpy.interp``, whose end-point clamping is the
-  clamp-to-edge reading of out-of-image rays;
+  clamp-to-edge reading of out-of-image rays; for a calibrated array,
+  ``scipy.ndimage.map_coordinates`` (order 1, mode 'nearest') at positions
+  from the camera matrices;
 * variance of the static rays: the pairwise form
   ``Var = (1 / n^2) * sum_{i<j} |f_i - f_j|^2`` instead of mean-then-deviations;
 * disparity prior: ``logaddexp(log gamma, -(d - mu)^2 / (2 sigma^2))``;
@@ -44,6 +46,16 @@ def _interp(row: np.ndarray, x: float) -> float:
     return float(np.interp(x, np.arange(row.shape[0], dtype=np.float64), row))
 
 
+def _interp2(img: np.ndarray, x: float, y: float) -> float:
+    return float(ndimage.map_coordinates(img, [[y], [x]], order=1, mode="nearest")[0])
+
+
+def _position(cam, u, v, d):
+    """(x, y) in a calibrated camera: dehomogenised cam @ (u, v, 1, d)."""
+    X = np.asarray(cam, np.float64) @ np.array([u, v, 1.0, d])
+    return X[0] / X[2], X[1] / X[2]
+
+
 def pairwise_variance(f: np.ndarray) -> float:
     n = f.shape[0]
     if n <= 1:
@@ -61,7 +73,7 @@ def log_prior(d, mu, inside, gamma, sigma):
     return float(np.logaddexp(np.log(gamma), -((d - mu) ** 2) / (2.0 * sigma * sigma)))
 
 
-def em_pixel_table(feat, ls, ld, images, baselines, u, v, dvals, mu, inside, p):
+def em_pixel_table(feat, ls, ld, images, baselines, u, v, dvals, mu, inside, p, cameras=None):
     """J[d_j, S] for every candidate and every label vector, plus the
     per-candidate initial label vector S(d_j) and the sampled images."""
     K = feat.shape[0]
@@ -71,10 +83,16 @@ def em_pixel_table(feat, ls, ld, images, baselines, u, v, dvals, mu, inside, p):
     S_init = np.zeros(D, dtype=np.int64)
     thr = p.seg_threshold
     for j, d in enumerate(dvals):
-        xs = [u - d * float(baselines[k]) for k in range(K)]
-        f = np.array([[_interp(feat[k, c, v], xs[k]) for c in range(3)] for k in range(K)])
-        sls = np.array([_interp(ls[k, v], xs[k]) for k in range(K)])
-        sld = np.array([_interp(ld[k, v], xs[k]) for k in range(K)])
+        if cameras is None:
+            xs = [u - d * float(baselines[k]) for k in range(K)]
+            f = np.array([[_interp(feat[k, c, v], xs[k]) for c in range(3)] for k in range(K)])
+            sls = np.array([_interp(ls[k, v], xs[k]) for k in range(K)])
+            sld = np.array([_interp(ld[k, v], xs[k]) for k in range(K)])
+        else:
+            pos = [_position(cameras[k], u, v, d) for k in range(K)]
+            f = np.array([[_interp2(feat[k, c], *pos[k]) for c in range(3)] for k in range(K)])
+            sls = np.array([_interp2(ls[k], *pos[k]) for k in range(K)])
+            sld = np.array([_interp2(ld[k], *pos[k]) for k in range(K)])
         lp = log_prior(d, mu, inside, p.gamma, p.sigma)
         # initial threshold: static iff the normalised dynamic probability of
         # the two interpolated log-priors is below thr
@@ -93,7 +111,8 @@ def _softmax(row: np.ndarray) -> np.ndarray:
     return q / q.sum()
 
 
-def run(images, seg_prior, baselines, mu, inside, d_min, d_max, D, iters, p, mode: str = "hard"):
+def run(images, seg_prior, baselines, mu, inside, d_min, d_max, D, iters, p, mode: str = "hard",
+        cameras=None):
     """EM on every pixel of a tiny frame from the full J[d, S] table.
 
     mode "hard": the paper's EM (M-step down the column of the current S,
@@ -102,7 +121,8 @@ def run(images, seg_prior, baselines, mu, inside, d_min, d_max, D, iters, p, mod
     previous row's softmax, ``J @ q``.  "joint": the arg-max of the whole
     table.  Returns dict like the oracle's (d_idx, labels, post, refocus)
     plus ``joint_max`` = max over (d, S) and, per iteration, ``L_t`` = the
-    log-sum-exp of the row of d_t."""
+    log-sum-exp of the row of d_t.  ``cameras`` ([K,3,4]): a calibrated array
+    (the reference is the camera whose matrix is [I | 0])."""
     imgs = np.asarray(images)
     K, H, W = imgs.shape[:3]
     feat = descriptors(imgs)
@@ -115,7 +135,11 @@ def run(images, seg_prior, baselines, mu, inside, d_min, d_max, D, iters, p, mod
     if x.ndim == 3:
         x = x[..., None]
     C = x.shape[3]
-    ref = int(np.flatnonzero(np.asarray(baselines) == 0)[0])
+    if cameras is None:
+        ref = int(np.flatnonzero(np.asarray(baselines) == 0)[0])
+    else:
+        eye = np.hstack([np.eye(3), np.zeros((3, 1))])
+        ref = next(k for k in range(K) if np.array_equal(np.asarray(cameras[k], np.float64), eye))
     out = {k: None for k in ("d_idx", "labels", "post", "refocus", "J_final", "joint_max")}
     d_idx = np.zeros((H, W), np.int64)
     labels = np.zeros((H, W), np.int64)
@@ -126,7 +150,8 @@ def run(images, seg_prior, baselines, mu, inside, d_min, d_max, D, iters, p, mod
     L_t = np.zeros((iters, H, W))
     for v in range(H):
         for u in range(W):
-            J, S_init = em_pixel_table(feat, ls, ld, imgs, baselines, u, v, dvals, mu[v, u], inside[v, u], p)
+            J, S_init = em_pixel_table(feat, ls, ld, imgs, baselines, u, v, dvals, mu[v, u], inside[v, u], p,
+                                       cameras)
             if not p.mstep_seg_term:
                 raise NotImplementedError
             S = None
@@ -156,9 +181,13 @@ def run(images, seg_prior, baselines, mu, inside, d_min, d_max, D, iters, p, mod
             members = [k for k in range(K) if S >> k & 1]
             if not members:
                 refocus[v, u] = x[ref, v, u]
-            else:
+            elif cameras is None:
                 for c in range(C):
                     refocus[v, u, c] = np.mean([_interp(x[k, v, :, c], u - dvals[j] * float(baselines[k]))
+                                                for k in members])
+            else:
+                for c in range(C):
+                    refocus[v, u, c] = np.mean([_interp2(x[k, :, :, c], *_position(cameras[k], u, v, dvals[j]))
                                                 for k in members])
     out.update(d_idx=d_idx, labels=labels, post=post, refocus=refocus[..., 0] if C == 1 else refocus,
                J_final=J_final, joint_max=joint, L_t=L_t)

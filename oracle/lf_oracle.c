@@ -17,7 +17,11 @@
  *                 with the border replicated (Sec. III-C "Pixel Likelihood")
  *   ray sampling  x_k = u - d * b_k on row v, column clamped to the image,
  *                 linear interpolation for non-integral shifts (Eq. 1 for a
- *                 rectified linear array; Sec. III-F non-integral disparities)
+ *                 rectified linear array; Sec. III-F non-integral disparities);
+ *                 for a calibrated array, the homography of the plane at
+ *                 generalized disparity d (a 3x4 matrix per camera, Eq. 1 and
+ *                 the warping function of Sec. III-C), bilinear interpolation
+ *                 with both coordinates clamped
  *   likelihood    -beta * Var_S(f): population variance over the static rays,
  *                 0 when at most one ray is static (Sec. III-C)
  *   prior         log(gamma + exp(-(d - mu)^2 / (2 sigma^2))) inside the
@@ -190,7 +194,9 @@ static double objective(int K, const double f[][3], const double *ls, const doub
 
 typedef struct {
     int K, H, W, C, dtype, D;
-    const double *b;      /* [K] baselines */
+    const double *b;      /* [K] baselines (rectified linear array) */
+    const double *P;      /* [K][3][4] camera matrices (calibrated array), or NULL */
+    int ref;              /* reference camera */
     const double *dval;   /* [D] candidate disparities */
     const double *feat;   /* [K][3][H][W] */
     const double *ls, *ld;/* [K][H][W] */
@@ -198,19 +204,64 @@ typedef struct {
     const orc_params *p;
 } orc_frame;
 
-/* Sample the K rays of reference pixel (u, v) at disparity d (Eq. 1 for a
- * rectified linear array: x_k = u - d * b_k on the same row, b_k the camera
- * position relative to the reference camera). */
+/* Where the ray of reference pixel (u, v) at disparity d meets camera k
+ * (Eq. 1).  Calibrated array: the 3x4 matrix M_k maps (u, v, 1, d) to
+ * homogeneous pixel coordinates of camera k -- in generalized disparity space
+ * this is the homography of the plane at disparity d (the warping function
+ * W_k of Sec. III-C).  Rectified linear array (no matrices): x = u - d b_k on
+ * row v. */
+static void ray_position(const orc_frame *F, int k, int u, int v, double d, double *x, double *y)
+{
+    if (!F->P) {
+        *x = (double)u - d * F->b[k];
+        *y = (double)v;
+        return;
+    }
+    const double *M = F->P + 12 * (size_t)k;
+    double X = M[0] * u + M[1] * v + M[2] + M[3] * d;
+    double Y = M[4] * u + M[5] * v + M[6] + M[7] * d;
+    double Z = M[8] * u + M[9] * v + M[10] + M[11] * d;
+    *x = X / Z;
+    *y = Y / Z;
+}
+
+/* Bilinear interpolation of an H x W map at (x, y) with each coordinate
+ * clamped to the image: the two-dimensional form of sample_row. */
+static double sample_2d(const double *map, int H, int W, double x, double y)
+{
+    if (x < 0.0) x = 0.0;
+    if (x > (double)(W - 1)) x = (double)(W - 1);
+    if (y < 0.0) y = 0.0;
+    if (y > (double)(H - 1)) y = (double)(H - 1);
+    int i0 = (int)floor(x), j0 = (int)floor(y);
+    int i1 = i0 + 1 < W ? i0 + 1 : W - 1;
+    int j1 = j0 + 1 < H ? j0 + 1 : H - 1;
+    double wx = x - (double)i0, wy = y - (double)j0;
+    double top = (1.0 - wx) * map[(size_t)j0 * W + i0] + wx * map[(size_t)j0 * W + i1];
+    double bot = (1.0 - wx) * map[(size_t)j1 * W + i0] + wx * map[(size_t)j1 * W + i1];
+    return (1.0 - wy) * top + wy * bot;
+}
+
+/* Sample the K rays of reference pixel (u, v) at disparity d (Eq. 1; see
+ * ray_position). */
 static void sample_rays(const orc_frame *F, int u, int v, double d,
                         double f[][3], double *ls, double *ld)
 {
     size_t HW = (size_t)F->H * F->W;
     for (int k = 0; k < F->K; ++k) {
-        double x = (double)u - d * F->b[k];
-        for (int c = 0; c < 3; ++c)
-            f[k][c] = sample_row(F->feat + (size_t)k * 3 * HW + (size_t)c * HW + (size_t)v * F->W, F->W, x);
-        ls[k] = sample_row(F->ls + (size_t)k * HW + (size_t)v * F->W, F->W, x);
-        ld[k] = sample_row(F->ld + (size_t)k * HW + (size_t)v * F->W, F->W, x);
+        double x, y;
+        ray_position(F, k, u, v, d, &x, &y);
+        if (!F->P) {
+            for (int c = 0; c < 3; ++c)
+                f[k][c] = sample_row(F->feat + (size_t)k * 3 * HW + (size_t)c * HW + (size_t)v * F->W, F->W, x);
+            ls[k] = sample_row(F->ls + (size_t)k * HW + (size_t)v * F->W, F->W, x);
+            ld[k] = sample_row(F->ld + (size_t)k * HW + (size_t)v * F->W, F->W, x);
+        } else {
+            for (int c = 0; c < 3; ++c)
+                f[k][c] = sample_2d(F->feat + (size_t)k * 3 * HW + (size_t)c * HW, F->H, F->W, x, y);
+            ls[k] = sample_2d(F->ls + (size_t)k * HW, F->H, F->W, x, y);
+            ld[k] = sample_2d(F->ld + (size_t)k * HW, F->H, F->W, x, y);
+        }
     }
 }
 
@@ -378,8 +429,7 @@ static void em_pixel(const orc_frame *F, int u, int v, double mu, int inside, in
     /* refocused static image, Eq. 2; no static ray keeps the reference pixel */
     int n = 0;
     for (int k = 0; k < K; ++k) n += (S >> k) & 1u;
-    int ref = 0;
-    for (int k = 0; k < K; ++k) if (F->b[k] == 0.0) { ref = k; break; }
+    const int ref = F->ref;
     for (int c = 0; c < F->C; ++c) {
         double acc = 0.0;
         if (n == 0) {
@@ -387,14 +437,28 @@ static void em_pixel(const orc_frame *F, int u, int v, double mu, int inside, in
         } else {
             for (int k = 0; k < K; ++k) {
                 if (!(S >> k & 1u)) continue;
-                double x = (double)u - d * F->b[k];
+                double x, y;
+                ray_position(F, k, u, v, d, &x, &y);
                 if (x < 0.0) x = 0.0;
                 if (x > (double)(W - 1)) x = (double)(W - 1);
                 int i0 = (int)floor(x);
                 int i1 = i0 + 1 < W ? i0 + 1 : W - 1;
                 double w = x - (double)i0;
-                acc += (1.0 - w) * img_at(F->images, F->dtype, H, W, F->C, k, v, i0, c)
-                     + w * img_at(F->images, F->dtype, H, W, F->C, k, v, i1, c);
+                if (!F->P) {
+                    acc += (1.0 - w) * img_at(F->images, F->dtype, H, W, F->C, k, v, i0, c)
+                         + w * img_at(F->images, F->dtype, H, W, F->C, k, v, i1, c);
+                } else {
+                    if (y < 0.0) y = 0.0;
+                    if (y > (double)(H - 1)) y = (double)(H - 1);
+                    int j0 = (int)floor(y);
+                    int j1 = j0 + 1 < H ? j0 + 1 : H - 1;
+                    double wy = y - (double)j0;
+                    double top = (1.0 - w) * img_at(F->images, F->dtype, H, W, F->C, k, j0, i0, c)
+                               + w * img_at(F->images, F->dtype, H, W, F->C, k, j0, i1, c);
+                    double bot = (1.0 - w) * img_at(F->images, F->dtype, H, W, F->C, k, j1, i0, c)
+                               + w * img_at(F->images, F->dtype, H, W, F->C, k, j1, i1, c);
+                    acc += (1.0 - wy) * top + wy * bot;
+                }
             }
             acc /= (double)n;
         }
@@ -412,29 +476,46 @@ static void em_pixel(const orc_frame *F, int u, int v, double mu, int inside, in
  * Candidate disparities d_j = d_min + j (d_max - d_min) / (D - 1) (D = 1: d_min).
  * Returns 0, or -1 on invalid arguments.
  */
-int orc_run(int K, const float *baselines, int H, int W, int C, int dtype,
-            const void *images, const float *seg_prior, const double *mu,
-            const uint8_t *inside, float d_min, float d_max, int D, int iters,
-            const orc_params *p, int row_begin, int row_end, int nthreads,
-            int32_t *d_idx, double *d_val, uint16_t *labels, double *post,
-            double *refocus, double *m_margin, double *e_margin, double *J_t,
-            double *init_margin)
+static int run_frame(int K, const float *baselines, const float *cameras, int H, int W, int C, int dtype,
+                     const void *images, const float *seg_prior, const double *mu,
+                     const uint8_t *inside, float d_min, float d_max, int D, int iters,
+                     const orc_params *p, int row_begin, int row_end, int nthreads,
+                     int32_t *d_idx, double *d_val, uint16_t *labels, double *post,
+                     double *refocus, double *m_margin, double *e_margin, double *J_t,
+                     double *init_margin)
 {
     if (K < 1 || K > ORC_MAXK || H < 1 || W < 1 || D < 1 || iters < 1) return -1;
     if (p->em_mode < 0 || p->em_mode > 2) return -1;
     if (C != 1 && C != 3) return -1;
+    double b[ORC_MAXK], P[ORC_MAXK * 12];
+    int ref = -1;
+    for (int k = 0; k < K; ++k) {
+        if (cameras) {
+            int identity = 1;
+            for (int i = 0; i < 12; ++i) {
+                P[12 * k + i] = (double)cameras[12 * k + i];
+                double want = (i == 0 || i == 5 || i == 10) ? 1.0 : 0.0;
+                if (P[12 * k + i] != want) identity = 0;
+            }
+            b[k] = 0.0;
+            if (identity && ref < 0) ref = k;
+        } else {
+            b[k] = (double)baselines[k];
+            if (b[k] == 0.0 && ref < 0) ref = k;
+        }
+    }
+    if (ref < 0) return -1;
     size_t HW = (size_t)H * W;
     double *feat = (double *)malloc(sizeof(double) * 3 * K * HW);
     double *ls = (double *)malloc(sizeof(double) * K * HW);
     double *ld = (double *)malloc(sizeof(double) * K * HW);
-    double b[ORC_MAXK], *dval = (double *)malloc(sizeof(double) * D);
-    for (int k = 0; k < K; ++k) b[k] = (double)baselines[k];
+    double *dval = (double *)malloc(sizeof(double) * D);
     for (int j = 0; j < D; ++j)
         dval[j] = D == 1 ? (double)d_min
                          : (double)d_min + (double)j * (((double)d_max - (double)d_min) / (double)(D - 1));
     orc_features(K, H, W, C, dtype, images, feat);
     orc_log_seg(K, H, W, seg_prior, p->eps, ls, ld);
-    orc_frame F = {K, H, W, C, dtype, D, b, dval, feat, ls, ld, images, p};
+    orc_frame F = {K, H, W, C, dtype, D, b, cameras ? P : NULL, ref, dval, feat, ls, ld, images, p};
     if (row_begin < 0) row_begin = 0;
     if (row_end > H) row_end = H;
 #ifdef _OPENMP
@@ -447,6 +528,39 @@ int orc_run(int K, const float *baselines, int H, int W, int C, int dtype,
                      d_idx, d_val, labels, post, refocus, m_margin, e_margin, J_t, init_margin);
     free(feat); free(ls); free(ld); free(dval);
     return 0;
+}
+
+/* Rectified linear array: baselines [K], one exactly 0 (the reference). */
+int orc_run(int K, const float *baselines, int H, int W, int C, int dtype,
+            const void *images, const float *seg_prior, const double *mu,
+            const uint8_t *inside, float d_min, float d_max, int D, int iters,
+            const orc_params *p, int row_begin, int row_end, int nthreads,
+            int32_t *d_idx, double *d_val, uint16_t *labels, double *post,
+            double *refocus, double *m_margin, double *e_margin, double *J_t,
+            double *init_margin)
+{
+    return run_frame(K, baselines, NULL, H, W, C, dtype, images, seg_prior, mu, inside, d_min, d_max, D, iters,
+                     p, row_begin, row_end, nthreads, d_idx, d_val, labels, post, refocus, m_margin, e_margin,
+                     J_t, init_margin);
+}
+
+/* Calibrated array (Eq. 1): cameras [K][3][4] row-major, mapping the
+ * reference pixel (u, v) at generalized disparity d, as (u, v, 1, d), to
+ * homogeneous pixel coordinates of camera k; the reference camera is the
+ * first whose matrix is exactly [I | 0].  Rays are sampled by bilinear
+ * interpolation with both coordinates clamped to the image. */
+int orc_run_general(int K, const float *cameras, int H, int W, int C, int dtype,
+                    const void *images, const float *seg_prior, const double *mu,
+                    const uint8_t *inside, float d_min, float d_max, int D, int iters,
+                    const orc_params *p, int row_begin, int row_end, int nthreads,
+                    int32_t *d_idx, double *d_val, uint16_t *labels, double *post,
+                    double *refocus, double *m_margin, double *e_margin, double *J_t,
+                    double *init_margin)
+{
+    if (!cameras) return -1;
+    return run_frame(K, NULL, cameras, H, W, C, dtype, images, seg_prior, mu, inside, d_min, d_max, D, iters,
+                     p, row_begin, row_end, nthreads, d_idx, d_val, labels, post, refocus, m_margin, e_margin,
+                     J_t, init_margin);
 }
 
 /* Number of OpenMP threads a parallel region would use (1 without OpenMP). */
@@ -473,7 +587,7 @@ double orc_objective_at(int K, const float *baselines, int H, int W, int C, int 
     for (int k = 0; k < K; ++k) b[k] = (double)baselines[k];
     orc_features(K, H, W, C, dtype, images, feat);
     orc_log_seg(K, H, W, seg_prior, p->eps, ls, ld);
-    orc_frame F = {K, H, W, C, dtype, 1, b, &d, feat, ls, ld, images, p};
+    orc_frame F = {K, H, W, C, dtype, 1, b, NULL, 0, &d, feat, ls, ld, images, p};
     double f[ORC_MAXK][3], sls[ORC_MAXK], sld[ORC_MAXK];
     sample_rays(&F, u, v, d, f, sls, sld);
     double J = objective(K, (const double(*)[3])f, sls, sld, S, log_prior(d, mu, inside, p), with_seg, p);

@@ -82,6 +82,8 @@ def _load():
                                 P, P, P, P, ctypes.c_float, ctypes.c_float, ctypes.c_int, ctypes.c_int,
                                 ctypes.POINTER(_CParams), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                 P, P, P, P, P, P, P, P, P]
+        lib.orc_run_general.restype = ctypes.c_int
+        lib.orc_run_general.argtypes = lib.orc_run.argtypes
         lib.orc_max_threads.restype = ctypes.c_int
         lib.orc_objective_at.restype = ctypes.c_double
         lib.orc_objective_at.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -177,12 +179,14 @@ def prior_raster(points: np.ndarray, H: int, W: int):
 
 def run(images: np.ndarray, seg_prior: np.ndarray, baselines: np.ndarray, points: np.ndarray,
         d_min: float, d_max: float, D: int, iters: int, params: Optional[Params] = None,
-        rows: Optional[tuple] = None, threads: int = 0, mu=None, inside=None) -> dict:
+        rows: Optional[tuple] = None, threads: int = 0, mu=None, inside=None, cameras=None) -> dict:
     """Run the oracle on one frame.
 
     images: [K,H,W] or [K,H,W,C] uint8 (scaled 1/255) or float32 in [0,1].
     seg_prior: [K,H,W] P(dynamic).  baselines: [K], one entry 0.
     rows: optional (begin, end) subset of rows (other rows stay zero).
+    cameras: optional [K,3,4] matrices of a calibrated array (Eq. 1 in
+    generalized disparity space); then the baselines are not used.
     """
     lib = _load()
     imgs = np.ascontiguousarray(images)
@@ -213,7 +217,12 @@ def run(images: np.ndarray, seg_prior: np.ndarray, baselines: np.ndarray, points
         "init_margin": np.zeros((H, W), np.float64),
     }
     cp = _cparams(params)
-    rc = lib.orc_run(K, _ptr(b), H, W, C, dtype, _ptr(imgs), _ptr(seg), _ptr(mu), _ptr(inside),
+    if cameras is not None:
+        cams = np.ascontiguousarray(cameras, dtype=np.float32).reshape(K, 3, 4)
+        fn, geo = lib.orc_run_general, cams
+    else:
+        fn, geo = lib.orc_run, b
+    rc = fn(K, _ptr(geo), H, W, C, dtype, _ptr(imgs), _ptr(seg), _ptr(mu), _ptr(inside),
                      float(d_min), float(d_max), int(D), int(iters), ctypes.byref(cp), int(r0), int(r1),
                      int(threads), _ptr(out["d_idx"]), _ptr(out["d"]), _ptr(out["labels"]),
                      _ptr(out["post"]), _ptr(out["refocus"]), _ptr(out["m_margin"]),
@@ -228,7 +237,8 @@ def run(images: np.ndarray, seg_prior: np.ndarray, baselines: np.ndarray, points
 
 def run_scene(scene, params: Optional[Params] = None, rows=None, threads: int = 0, iters=None) -> dict:
     return run(scene.images, scene.seg_prior, scene.baselines, scene.points, scene.d_min, scene.d_max,
-               scene.D, scene.iters if iters is None else iters, params, rows, threads)
+               scene.D, scene.iters if iters is None else iters, params, rows, threads,
+               cameras=getattr(scene, "cameras", None))
 
 
 def features(images: np.ndarray) -> np.ndarray:

@@ -49,6 +49,7 @@ __all__ = [
     "street_rgb",
     "random_frame",
     "plane_scene",
+    "calibrated_cameras",
 ]
 
 
@@ -157,6 +158,7 @@ class Scene:
     gt_static: np.ndarray        # [H,W] or [H,W,3] float32 in [0,1]
     dynamic_mask: np.ndarray     # [K,H,W] bool, pixels showing a dynamic surface
     halo: int = 0                # border (px) affected by rays leaving the image
+    cameras: Optional[np.ndarray] = None  # [K,3,4] calibrated (non-rectified) array, else None
 
     @property
     def K(self) -> int:
@@ -183,8 +185,53 @@ class Scene:
         return self.H * self.W * self.K * self.D * self.iters
 
 
-def render_scene(surfaces: List[Surface], baselines: np.ndarray, H: int, W: int, C: int):
-    """Render every view by parallax.
+def _ref_coords(cam: np.ndarray, d: float, uu: np.ndarray, vv: np.ndarray):
+    """Reference coordinates of the point at disparity d that the calibrated
+    camera ``cam`` (3x4, (u, v, 1, d) -> homogeneous pixel) sees at (uu, vv):
+    the inverse of the homography of the plane at disparity d."""
+    G = np.asarray(cam, np.float64)[:, :3].copy()
+    G[:, 2] += d * np.asarray(cam, np.float64)[:, 3]
+    Gi = np.linalg.inv(G)
+    X = Gi[0, 0] * uu + Gi[0, 1] * vv + Gi[0, 2]
+    Y = Gi[1, 0] * uu + Gi[1, 1] * vv + Gi[1, 2]
+    Z = Gi[2, 0] * uu + Gi[2, 1] * vv + Gi[2, 2]
+    return X / Z, Y / Z
+
+
+def calibrated_cameras(rng: np.random.Generator, baselines, H: int, W: int, rot_deg: float = 0.6,
+                       shift_y: float = 0.02, shift_z: float = 0.03, focal_jitter: float = 0.01) -> np.ndarray:
+    """[K,3,4] camera matrices of a calibrated, non-rectified array in
+    generalized disparity space (Eq. 1): camera k at (b_k, ty, tz) relative
+    to the reference with a small random rotation and its own intrinsics, so
+    that a reference pixel (u, v) at disparity d = f / depth appears at
+    M_k (u, v, 1, d).  The reference matrix is exactly [I | 0]; with no
+    rotation, equal intrinsics and ty = tz = 0 the matrix reduces to the
+    rectified shift u - d b_k."""
+    b = np.asarray(baselines, np.float64)
+    f = 1.2 * W
+    Kr = np.array([[f, 0.0, (W - 1) / 2.0], [0.0, f, (H - 1) / 2.0], [0.0, 0.0, 1.0]])
+    Kr_inv = np.linalg.inv(Kr)
+    out = np.zeros((len(b), 3, 4))
+    for k, bk in enumerate(b):
+        if bk == 0.0:
+            out[k, :, :3] = np.eye(3)
+            continue
+        fk = f * (1.0 + rng.uniform(-focal_jitter, focal_jitter))
+        Kk = np.array([[fk, 0.0, (W - 1) / 2.0 + rng.uniform(-1, 1)],
+                       [0.0, fk, (H - 1) / 2.0 + rng.uniform(-1, 1)], [0.0, 0.0, 1.0]])
+        ax, ay, az = np.deg2rad(rng.uniform(-rot_deg, rot_deg, size=3))
+        Rx = np.array([[1, 0, 0], [0, np.cos(ax), -np.sin(ax)], [0, np.sin(ax), np.cos(ax)]])
+        Ry = np.array([[np.cos(ay), 0, np.sin(ay)], [0, 1, 0], [-np.sin(ay), 0, np.cos(ay)]])
+        Rz = np.array([[np.cos(az), -np.sin(az), 0], [np.sin(az), np.cos(az), 0], [0, 0, 1]])
+        t = np.array([-bk, rng.uniform(-shift_y, shift_y), rng.uniform(-shift_z, shift_z)])
+        out[k, :, :3] = Kk @ (Rz @ Ry @ Rx) @ Kr_inv
+        out[k, :, 3] = Kk @ t / f
+    return out.astype(np.float32)
+
+
+def render_scene(surfaces: List[Surface], baselines: np.ndarray, H: int, W: int, C: int, cameras=None):
+    """Render every view by parallax (or, with ``cameras``, through the
+    inverse plane homographies of a calibrated array).
 
     Returns (images [K,H,W,C] float64, dynamic mask [K,H,W], static reference
     image [H,W,C], static reference disparity [H,W]).
@@ -202,21 +249,24 @@ def render_scene(surfaces: List[Surface], baselines: np.ndarray, H: int, W: int,
         st_done = np.zeros((H, W), dtype=bool)
         for i in order:
             s = surfaces[i]
-            ur = uu + s.disparity * float(baselines[k])
-            hit = s.covers(ur, vv)
+            if cameras is None:
+                ur, vr = uu + s.disparity * float(baselines[k]), vv
+            else:
+                ur, vr = _ref_coords(cameras[k], s.disparity, uu, vv)
+            hit = s.covers(ur, vr)
             drawn = s.views is None or k in s.views
             if drawn:
                 m = hit & ~done
                 if m.any():
                     for c in range(C):
-                        images[k, :, :, c][m] = s.tex[c](ur[m], vv[m])
+                        images[k, :, :, c][m] = s.tex[c](ur[m], vr[m])
                     dyn[k][m] = s.dynamic
                     done |= m
             if k == ref and not s.dynamic:
                 m = hit & ~st_done
                 if m.any():
                     for c in range(C):
-                        st_img[:, :, c][m] = s.tex[c](ur[m], vv[m])
+                        st_img[:, :, c][m] = s.tex[c](ur[m], vr[m])
                     st_disp[m] = s.disparity
                     st_done |= m
         assert done.all(), "scene must have a background surface covering every ray"
@@ -246,8 +296,8 @@ def _sparse_points(rng, surfaces, H, W, M, sigma):
 
 
 def _finish(name, seed, rng, surfaces, baselines, H, W, C, u8, noise, prior_fn,
-            M, point_sigma, d_min, d_max, D, iters):
-    images, dyn, st_img, st_disp = render_scene(surfaces, baselines, H, W, C)
+            M, point_sigma, d_min, d_max, D, iters, cameras=None):
+    images, dyn, st_img, st_disp = render_scene(surfaces, baselines, H, W, C, cameras)
     if noise > 0:
         images = images + rng.normal(0.0, noise, size=images.shape)
     images = np.clip(images, 0.0, 1.0)
@@ -262,11 +312,12 @@ def _finish(name, seed, rng, surfaces, baselines, H, W, C, u8, noise, prior_fn,
     pts = _sparse_points(rng, surfaces, H, W, M, point_sigma)
     bmax = float(np.max(np.abs(baselines)))
     halo = int(np.ceil(bmax * max(abs(d_min), abs(d_max)))) + 2
-    return Scene(name=name, seed=seed, baselines=np.asarray(baselines, np.float32),
+    return Scene(name=name if cameras is None else name + "_calibrated", seed=seed,
+                 baselines=np.asarray(baselines, np.float32),
                  images=images_out, seg_prior=seg, points=pts, d_min=float(d_min),
                  d_max=float(d_max), D=int(D), iters=int(iters),
                  gt_disparity=st_disp.astype(np.float32), gt_static=st_img.astype(np.float32),
-                 dynamic_mask=dyn, halo=halo)
+                 dynamic_mask=dyn, halo=halo, cameras=cameras)
 
 
 def _two_level_prior(p_dyn, p_static, jitter):
@@ -288,8 +339,10 @@ FIVE_CAMERAS = np.array([-0.2, -0.1, 0.0, 0.1, 0.2], dtype=np.float32)
 def small_gray(frame: int = 0, *, H: int = 48, W: int = 64, baselines=None, D: int = 32,
                iters: int = 5, noise: float = 0.01, occluder: bool = True,
                planes=(4.0, 9.0), occluder_disparity: float = 20.0, M: int = 40,
-               point_sigma: float = 0.3) -> Scene:
-    """5 cameras, gray float32, two planes + one occluder seen by 3 of 5 views."""
+               point_sigma: float = 0.3, calibrated: bool = False, rot_deg: float = 1.5) -> Scene:
+    """5 cameras, gray float32, two planes + one occluder seen by 3 of 5 views.
+    calibrated: a non-rectified array (``calibrated_cameras``, rotations up to
+    rot_deg), cameras drawn from their own seeded stream."""
     seed = 1 * 1000 + frame
     rng = np.random.default_rng(seed)
     b = FIVE_CAMERAS if baselines is None else np.asarray(baselines, np.float32)
@@ -307,14 +360,15 @@ def small_gray(frame: int = 0, *, H: int = 48, W: int = 64, baselines=None, D: i
         surfaces.append(Surface(occluder_disparity, (ou, ov, ou + ow, ov + oh),
                                 [pixel_noise(rng, (ou - 2, ov - 2, ou + ow + 2, ov + oh + 2))],
                                 dynamic=True, views=central))
+    cams = calibrated_cameras(np.random.default_rng(seed + 500), b, H, W, rot_deg) if calibrated else None
     return _finish("small_gray", seed, rng, surfaces, b, H, W, 1, False, noise,
-                   _two_level_prior(0.9, 0.05, 0.03), M, point_sigma, 0.0, float(D - 1), D, iters)
+                   _two_level_prior(0.9, 0.05, 0.03), M, point_sigma, 0.0, float(D - 1), D, iters, cams)
 
 
 def plane_scene(seed: int, *, H: int, W: int, baselines, planes, D: int, d_min: float = 0.0,
                 d_max: Optional[float] = None, iters: int = 5, noise: float = 0.0,
                 M: int = 40, point_sigma: float = 0.0, texture_cells=(6.0, 3.0, 1.5),
-                p_static: float = 0.05) -> Scene:
+                p_static: float = 0.05, cameras=None) -> Scene:
     """Occluder-free scene: a far plane everywhere plus nearer planes as
     vertical bands.  ``planes`` = disparities, far first."""
     rng = np.random.default_rng(seed)
@@ -329,13 +383,14 @@ def plane_scene(seed: int, *, H: int, W: int, baselines, planes, D: int, d_min: 
         surfaces.append(Surface(d, (u0, -1e9, u1, 1e9), [value_noise(rng, texture_cells, (0.5, 0.3, 0.2), ext)]))
     dm = float(D - 1) if d_max is None else float(d_max)
     return _finish("plane_scene", seed, rng, surfaces, b, H, W, 1, False, noise,
-                   _two_level_prior(0.9, p_static, 0.0), M, point_sigma, d_min, dm, D, iters)
+                   _two_level_prior(0.9, p_static, 0.0), M, point_sigma, d_min, dm, D, iters, cameras)
 
 
 def street_rgb(frame: int = 0, *, H: int = 600, W: int = 960, baselines=None, D: int = 64,
                iters: int = 10, noise: float = 0.01, M: int = 300, point_sigma: float = 0.5,
-               n_boxes: Optional[int] = None) -> Scene:
-    """Paper-shaped frame: 5 cameras, RGB uint8, 3 planes, 1-4 person boxes."""
+               n_boxes: Optional[int] = None, calibrated: bool = False, rot_deg: float = 0.6) -> Scene:
+    """Paper-shaped frame: 5 cameras, RGB uint8, 3 planes, 1-4 person boxes.
+    calibrated: the same scene seen by a non-rectified array."""
     seed = 2 * 1000 + frame
     rng = np.random.default_rng(seed)
     b = FIVE_CAMERAS if baselines is None else np.asarray(baselines, np.float32)
@@ -374,8 +429,9 @@ def street_rgb(frame: int = 0, *, H: int = 600, W: int = 960, baselines=None, D:
             break
     for (u0, v0, u1, v1, d) in boxes:
         surfaces.append(Surface(d, (u0, v0, u1, v1), rgb_tex((10.0, 4.0, 1.5)), dynamic=True))
+    cams = calibrated_cameras(np.random.default_rng(seed + 500), b, H, W, rot_deg) if calibrated else None
     return _finish("street_rgb", seed, rng, surfaces, b, H, W, 3, True, noise,
-                   _beta_prior(8.0, 2.0, 1.0, 15.0), M, point_sigma, 0.0, dmax, D, iters)
+                   _beta_prior(8.0, 2.0, 1.0, 15.0), M, point_sigma, 0.0, dmax, D, iters, cams)
 
 
 def random_frame(index: int, *, workload_id: int = 3, size_range=((320, 240), (1280, 1024)),
