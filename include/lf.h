@@ -152,6 +152,29 @@ void lf_default_params(lf_params *p);
 lf_status lf_create(lf_ctx **out, int n_cams, const float *baselines, int H, int W,
                     float d_min, float d_max, int D, const lf_params *p);
 
+/*
+ * Create a context for a calibrated, non-rectified camera array (Eq. 1:
+ * x_k = pi_k [R_k | t_k] pi_ref^-1 (x_ref, d), written in generalized
+ * disparity space so that the warping function of Sec. III-C is the
+ * homography of the plane at disparity d).  cameras: [n_cams][3][4] host
+ * floats, row-major; camera k sees reference pixel (u, v) at candidate
+ * disparity d at (X / Z, Y / Z) with (X, Y, Z) = M_k (u, v, 1, d).  The
+ * reference camera is the first whose matrix is exactly [I | 0]; the
+ * rectified array is the special case M_k = [I | (-b_k, 0, 0)].  Rays are
+ * sampled by bilinear interpolation with both coordinates clamped to the
+ * image; everything else (inputs, outputs, lf_set_inputs, lf_run_em) is as
+ * for lf_create.  The descriptor maps of all cameras are kept on the device
+ * (20 bytes per camera pixel, allocated at the first lf_run_em).
+ * Supports the hard EM on float32 maps only (em_mode = LF_EM_HARD,
+ * precision = LF_PREC_F32), dynamic_only and median included.
+ * Errors: as lf_create, and LF_EINVAL if cameras is NULL or non-finite, no
+ * matrix is [I | 0], another em_mode or precision is asked for, or some ray
+ * of the frame at a candidate disparity projects behind its camera (Z <= 0
+ * at a corner of [0, W-1] x [0, H-1] x [d_min, d_max]).
+ */
+lf_status lf_create_calibrated(lf_ctx **out, int n_cams, const float *cameras, int H, int W,
+                               float d_min, float d_max, int D, const lf_params *p);
+
 /* Use `stream` (a cudaStream_t; NULL = the legacy default stream) for every
  * later call on this context. */
 lf_status lf_set_stream(lf_ctx *ctx, void *stream);

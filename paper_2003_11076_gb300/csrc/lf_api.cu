@@ -215,6 +215,13 @@ struct lf_ctx {
   size_t own_img16_cap = 0;
   int* d_tiles = nullptr;        // dynamic-only: list of tiles to sweep, then its length
   size_t tiles_cap = 0;
+  // calibrated array: camera matrices and the per-run descriptor maps
+  bool calibrated = false;
+  float cams[kMaxCams * 12] = {};
+  float4* d_fa = nullptr;
+  size_t fa_cap = 0;
+  float* d_fb = nullptr;
+  size_t fb_cap = 0;
   // prior
   std::vector<PriorTri> h_tris;
   std::vector<int> h_bins;  // [nbins + 1] starts, then items
@@ -436,22 +443,53 @@ int lf_triangulate(const float* points, int M, int32_t* tris, int max_tris) {
   return lf::delaunay(xy.data(), M, tris, max_tris);
 }
 
-lf_status lf_create(lf_ctx** out, int n_cams, const float* baselines, int H, int W, float d_min, float d_max,
-                    int D, const lf_params* p) {
+}  // extern "C"
+
+namespace {
+// Both constructors: a rectified array (baselines) or a calibrated one
+// (cameras, [K][3][4]; the sampling tables of the rectified sweep are then
+// built for zero baselines and not used by the calibrated kernels).
+lf_status create_ctx(lf_ctx** out, int n_cams, const float* baselines, const float* cameras, int H, int W,
+                     float d_min, float d_max, int D, const lf_params* p) {
   g_err.clear();
   if (!out) return fail(LF_EINVAL, "out is NULL");
   *out = nullptr;
   if (n_cams < 1 || n_cams > kMaxCams) return fail(LF_EINVAL, "n_cams must be in [1, 12]");
-  if (!baselines) return fail(LF_EINVAL, "baselines is NULL");
+  if (!baselines && !cameras) return fail(LF_EINVAL, cameras ? "cameras is NULL" : "baselines is NULL");
   if (H < 3 || W < 3) return fail(LF_EINVAL, "H and W must be >= 3");
   if (D < 1 || D > kMaxD) return fail(LF_EINVAL, "D must be in [1, 1024]");
   if (!finite(d_min) || !finite(d_max) || d_max < d_min) return fail(LF_EINVAL, "need finite d_min <= d_max");
   int ref = -1;
-  for (int k = 0; k < n_cams; ++k) {
-    if (!finite(baselines[k])) return fail(LF_EINVAL, "non-finite baseline");
-    if (baselines[k] == 0.f && ref < 0) ref = k;
+  std::vector<float> zero_b;
+  if (cameras) {
+    for (int k = 0; k < n_cams; ++k) {
+      bool identity = true;
+      for (int i = 0; i < 12; ++i) {
+        if (!finite(cameras[12 * k + i])) return fail(LF_EINVAL, "non-finite camera matrix entry");
+        if (cameras[12 * k + i] != ((i == 0 || i == 5 || i == 10) ? 1.f : 0.f)) identity = false;
+      }
+      if (identity && ref < 0) ref = k;
+      // the homogeneous coordinate is affine in (u, v, d): positive at the 8
+      // corners of the pixel box x [d_min, d_max] means positive everywhere
+      const float* M = cameras + 12 * k;
+      for (int corner = 0; corner < 8; ++corner) {
+        const double u = (corner & 1) ? W - 1 : 0, v = (corner & 2) ? H - 1 : 0, d = (corner & 4) ? d_max : d_min;
+        if (!(static_cast<double>(M[8]) * u + static_cast<double>(M[9]) * v + M[10] + static_cast<double>(M[11]) * d >
+              0.0))
+          return fail(LF_EINVAL, "camera " + std::to_string(k) +
+                                     ": a ray of the frame at a candidate disparity projects behind the camera");
+      }
+    }
+    if (ref < 0) return fail(LF_EINVAL, "no camera matrix equals [I | 0] (reference camera)");
+    zero_b.assign(n_cams, 0.f);
+    baselines = zero_b.data();
+  } else {
+    for (int k = 0; k < n_cams; ++k) {
+      if (!finite(baselines[k])) return fail(LF_EINVAL, "non-finite baseline");
+      if (baselines[k] == 0.f && ref < 0) ref = k;
+    }
+    if (ref < 0) return fail(LF_EINVAL, "no baseline equals 0 (reference camera)");
   }
-  if (ref < 0) return fail(LF_EINVAL, "no baseline equals 0 (reference camera)");
   lf_params prm;
   lf_default_params(&prm);
   if (p) prm = *p;
@@ -466,8 +504,14 @@ lf_status lf_create(lf_ctx** out, int n_cams, const float* baselines, int H, int
   if (prm.em_mode != LF_EM_HARD && prm.precision != LF_PREC_F32)
     return fail(LF_EINVAL, "the soft-EM and joint-MAP modes stage float32 maps only (LF_PREC_F32)");
   if (prm.em_mode == LF_EM_SOFT && n_cams > 8) return fail(LF_EINVAL, "soft EM supports at most 8 cameras");
+  if (cameras && (prm.em_mode != LF_EM_HARD || prm.precision != LF_PREC_F32))
+    return fail(LF_EINVAL, "calibrated arrays run the hard EM on float32 maps (LF_EM_HARD, LF_PREC_F32)");
 
   lf_ctx* c = new (std::nothrow) lf_ctx();
+  if (cameras) {
+    c->calibrated = true;
+    std::copy(cameras, cameras + 12 * n_cams, c->cams);
+  }
   if (!c) return fail(LF_ENOMEM, "host allocation failed");
   c->K = n_cams;
   c->H = H;
@@ -541,6 +585,29 @@ lf_status lf_create(lf_ctx** out, int n_cams, const float* baselines, int H, int
   *out = c;
   return LF_OK;
 }
+}  // namespace
+
+extern "C" {
+
+lf_status lf_create(lf_ctx** out, int n_cams, const float* baselines, int H, int W, float d_min, float d_max,
+                    int D, const lf_params* p) {
+  if (!baselines) {
+    g_err.clear();
+    if (out) *out = nullptr;
+    return fail(LF_EINVAL, "baselines is NULL");
+  }
+  return create_ctx(out, n_cams, baselines, nullptr, H, W, d_min, d_max, D, p);
+}
+
+lf_status lf_create_calibrated(lf_ctx** out, int n_cams, const float* cameras, int H, int W, float d_min,
+                               float d_max, int D, const lf_params* p) {
+  if (!cameras) {
+    g_err.clear();
+    if (out) *out = nullptr;
+    return fail(LF_EINVAL, "cameras is NULL");
+  }
+  return create_ctx(out, n_cams, nullptr, cameras, H, W, d_min, d_max, D, p);
+}
 
 lf_status lf_set_stream(lf_ctx* c, void* stream) {
   g_err.clear();
@@ -606,6 +673,37 @@ lf_status lf_set_inputs(lf_ctx* c, const void* images, int C, int dtype, const f
   return LF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// Statistics of a run and, for host outputs, the copies back (the call then
+// waits for them).
+lf_status finish_run(lf_ctx* c, int iters, int launched, bool dev, size_t HW, int32_t* disparity_idx,
+                     float* disparity, uint16_t* labels, float* posteriors, float* refocused, const int32_t* didx,
+                     const float* dout, const uint16_t* lab, const float* post, const float* refo) {
+  ++c->runs;
+  // joint MAP sweeps the candidates once, whatever the iteration count
+  c->stats.nominal_ray_samples =
+      static_cast<uint64_t>(HW) * c->K * c->D * (c->p.em_mode == LF_EM_JOINT ? 1 : iters);
+  c->stats.halo_left = c->L;
+  c->stats.halo_right = c->R;
+  c->stats.tile_rows = c->calibrated ? 16 : c->TR;
+  c->stats.tile_cols = c->calibrated ? 16 : c->TW;
+  c->stats.kernels_launched = launched;
+  if (dev) return LF_OK;
+  LF_CUDA(cudaMemcpyAsync(disparity_idx, didx, HW * 4, cudaMemcpyDeviceToHost, c->stream), "output copy");
+  if (disparity) LF_CUDA(cudaMemcpyAsync(disparity, dout, HW * 4, cudaMemcpyDeviceToHost, c->stream), "output copy");
+  if (labels) LF_CUDA(cudaMemcpyAsync(labels, lab, HW * 2, cudaMemcpyDeviceToHost, c->stream), "output copy");
+  if (posteriors)
+    LF_CUDA(cudaMemcpyAsync(posteriors, post, HW * 4 * c->K, cudaMemcpyDeviceToHost, c->stream), "output copy");
+  if (refocused)
+    LF_CUDA(cudaMemcpyAsync(refocused, refo, HW * 4 * c->C, cudaMemcpyDeviceToHost, c->stream), "output copy");
+  return lf_synchronize(c);
+}
+}  // namespace
+
+extern "C" {
+
 lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* disparity, float* posteriors,
                     uint16_t* labels, float* refocused, int outputs_on_device) {
   g_err.clear();
@@ -668,6 +766,41 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
   LF_CUDA(launch_prior_raster(pa, c->stream), "prior_raster launch");
   ++launched;
   LF_CUDA(mark(1), "event");
+  if (c->calibrated) {  // Eq. 1 with per-camera homographies: maps in HBM, gathered by the sweep
+    const size_t KHW = HW * c->K;
+    if ((s = grow(&c->d_fa, &c->fa_cap, KHW, "descriptor maps")) != LF_OK) return s;
+    if ((s = grow(&c->d_fb, &c->fb_cap, KHW, "descriptor maps")) != LF_OK) return s;
+    CalibArgs g{};
+    g.K = c->K; g.H = c->H; g.W = c->W; g.C = c->C; g.D = c->D; g.ref = c->ref; g.dtype = c->dtype;
+    g.iters = iters; g.early_exit = c->p.early_exit; g.mseg = c->p.mstep_seg_term;
+    g.dyn_only = c->p.dynamic_only != 0;
+    g.seg_threshold = c->p.seg_threshold; g.beta = c->p.beta; g.gamma = c->p.gamma;
+    g.inv2s2 = static_cast<float>(1.0 / (2.0 * static_cast<double>(c->p.sigma) * c->p.sigma));
+    g.log_thr = static_cast<float>(std::log(static_cast<double>(c->p.seg_threshold) / (1.0 - c->p.seg_threshold)));
+    g.eps = c->p.eps;
+    for (int k = 0; k < c->K; ++k)
+      for (int i = 0; i < 12; ++i) g.cam[k][i] = c->cams[12 * k + i];
+    g.img = c->img; g.img_pitch = c->img_pitch; g.P = c->P; g.p_pitch = c->p_pitch;
+    g.fa = c->d_fa; g.fb = c->d_fb; g.dval = c->d_dval; g.mu = c->d_mu;
+    g.d_idx = didx; g.d_out = dout; g.labels = lab; g.post = post; g.refocus = refo_stage;
+    g.counter = c->d_counter;
+    LF_CUDA(launch_calib_features(g, c->stream), "calibrated features launch");
+    LF_CUDA(launch_calib_sweep(g, c->stream), "calibrated sweep launch");
+    launched += 2;
+    LF_CUDA(mark(2), "event");
+    if (refo) {
+      LF_CUDA(launch_calib_refocus(g, c->stream), "calibrated refocus launch");
+      ++launched;
+      LF_CUDA(mark(3), "event");
+      if (c->p.median) {
+        LF_CUDA(launch_median3(refo_stage, refo, c->H, c->W, c->C, c->stream), "median launch");
+        ++launched;
+        LF_CUDA(mark(4), "event");
+      }
+    }
+    return finish_run(c, iters, launched, dev, HW, disparity_idx, disparity, labels, posteriors, refocused,
+                      didx, dout, lab, post, refo);
+  }
   SweepArgs a{};
   a.H = c->H; a.W = c->W; a.C = c->C; a.D = c->D; a.ref = c->ref; a.dtype = c->dtype; a.bpp = c->bpp;
   a.TR = c->TR; a.TW = c->TW; a.L = c->L; a.R = c->R; a.SW = c->SW; a.SWp = c->SWp; a.RW = c->RW; a.KP = c->KP;
@@ -726,24 +859,8 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
       LF_CUDA(mark(4), "event");
     }
   }
-  ++c->runs;
-  // joint MAP sweeps the candidates once, whatever the iteration count
-  c->stats.nominal_ray_samples =
-      static_cast<uint64_t>(HW) * c->K * c->D * (c->p.em_mode == LF_EM_JOINT ? 1 : iters);
-  c->stats.halo_left = c->L;
-  c->stats.halo_right = c->R;
-  c->stats.tile_rows = c->TR;
-  c->stats.tile_cols = c->TW;
-  c->stats.kernels_launched = launched;
-  if (dev) return LF_OK;
-  LF_CUDA(cudaMemcpyAsync(disparity_idx, didx, HW * 4, cudaMemcpyDeviceToHost, c->stream), "output copy");
-  if (disparity) LF_CUDA(cudaMemcpyAsync(disparity, dout, HW * 4, cudaMemcpyDeviceToHost, c->stream), "output copy");
-  if (labels) LF_CUDA(cudaMemcpyAsync(labels, lab, HW * 2, cudaMemcpyDeviceToHost, c->stream), "output copy");
-  if (posteriors)
-    LF_CUDA(cudaMemcpyAsync(posteriors, post, HW * 4 * c->K, cudaMemcpyDeviceToHost, c->stream), "output copy");
-  if (refocused)
-    LF_CUDA(cudaMemcpyAsync(refocused, refo, HW * 4 * c->C, cudaMemcpyDeviceToHost, c->stream), "output copy");
-  return lf_synchronize(c);
+  return finish_run(c, iters, launched, dev, HW, disparity_idx, disparity, labels, posteriors, refocused, didx, dout,
+                    lab, post, refo);
 }
 
 lf_status lf_synchronize(lf_ctx* c) {
@@ -828,7 +945,7 @@ void lf_destroy(lf_ctx* c) {
   cudaStreamSynchronize(c->stream);
   void* bufs[] = {c->d_wtab, c->d_otab, c->d_chg, c->d_dval, c->d_mu, c->d_counter, c->d_status,
                   c->own_img, c->own_P, c->own_img16, c->d_tiles, c->d_tris, c->d_bins, c->o_didx, c->o_d, c->o_labels,
-                  c->o_post, c->o_ref, c->o_tmp};
+                  c->o_post, c->o_ref, c->o_tmp, c->d_fa, c->d_fb};
   for (void* p : bufs)
     if (p) cudaFree(p);
   for (auto& re : c->events)

@@ -398,13 +398,11 @@ lf_status lf_batch_create(lf_batch** out, const lf_params* p, int autotune) {
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
   for (cudaEvent_t& ev : b->ev)
     if (e == cudaSuccess) e = cudaEventCreate(&ev);
-  size_t cap = 0;
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_counts), sizeof(int) * (2 * kGroups + 1));
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_heads), sizeof(unsigned) * kGroups);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_counter), sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_status), sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(unsigned));
-  (void)cap;
   if (e != cudaSuccess) {
     lf_batch_destroy(b);
     return cuda_fail(e, "batch setup");

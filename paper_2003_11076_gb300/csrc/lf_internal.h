@@ -65,12 +65,13 @@ struct SweepArgs {
 };
 
 // Per-frame arguments of the persistent sweep, in global memory (TMA
-// descriptors must be 64-byte aligned).
-struct alignas(64) FrameDesc {
+// descriptors must be 64-byte aligned; CUtensorMap's own alignment gives it).
+struct FrameDesc {
   CUtensorMap img_map;
   CUtensorMap p_map;
   SweepArgs args;
 };
+static_assert(alignof(FrameDesc) >= 64 && sizeof(FrameDesc) % 64 == 0, "TMA descriptors need 64-byte alignment");
 
 struct RefocusArgs {
   int H, W, C, K, ref, dtype, KP;
@@ -81,6 +82,30 @@ struct RefocusArgs {
   const int32_t* d_idx;
   const uint16_t* labels;
   float* out;                      // [H][W][C]
+};
+
+// Calibrated (non-rectified) array, Eq. 1 in generalized disparity space:
+// camera k sees reference pixel (u, v) at disparity d at the dehomogenised
+// cam[k] * (u, v, 1, d).  The descriptor maps of every camera are written to
+// HBM once per run (fa, fb) and sampled bilinearly by the sweep.
+struct CalibArgs {
+  int K, H, W, C, D, ref, dtype, iters, early_exit, mseg, dyn_only;
+  float seg_threshold, beta, gamma, inv2s2, log_thr, eps;
+  float cam[kMaxCams][12];         // row-major 3x4 per camera
+  const uint8_t* img;              // [K][H] rows of img_pitch bytes ([W][C] pixels)
+  size_t img_pitch;
+  const float* P;                  // [K][H] rows of p_pitch bytes, P(dynamic)
+  size_t p_pitch;
+  float4* fa;                      // [K][H][W] {Y, Sobel-x/8, Sobel-y/8, log max(1-P, eps)}
+  float* fb;                       // [K][H][W] log max(P, eps)
+  const float* dval;               // [D]
+  const float* mu;                 // [H][W] prior centre, NaN outside
+  int32_t* d_idx;                  // [H][W]
+  float* d_out;                    // [H][W] or null
+  uint16_t* labels;                // [H][W]
+  float* post;                     // [K][H][W] or null
+  float* refocus;                  // [H][W][C] or null
+  unsigned long long* counter;     // executed pixel-sweeps
 };
 
 struct MedianArgs {
@@ -114,6 +139,10 @@ cudaError_t launch_em_sweep(int K, const CUtensorMap& img_map, const CUtensorMap
 cudaError_t launch_em_variant(int K, int mode, const CUtensorMap& img_map, const CUtensorMap& p_map,
                               const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_refocus(const RefocusArgs& a, cudaStream_t s);
+// Calibrated array: descriptor maps, the per-pixel EM, the refocus.
+cudaError_t launch_calib_features(const CalibArgs& a, cudaStream_t s);
+cudaError_t launch_calib_sweep(const CalibArgs& a, cudaStream_t s);
+cudaError_t launch_calib_refocus(const CalibArgs& a, cudaStream_t s);
 cudaError_t launch_median3(const float* in, float* out, int H, int W, int C, cudaStream_t s);
 cudaError_t launch_prior_raster_batched(const PriorArgs* frames, const RowItem* items, const int* n_items,
                                         int grid, cudaStream_t s);

@@ -25,7 +25,7 @@ EXPORTS = ("lf_default_params", "lf_create", "lf_set_stream", "lf_set_inputs", "
            "lf_synchronize", "lf_get_prior", "lf_get_stats", "lf_last_error", "lf_destroy",
            "lf_triangulate", "lf_set_timing", "lf_run_em_static", "lf_batch_create", "lf_batch_set_stream",
            "lf_batch_add", "lf_batch_run", "lf_batch_synchronize", "lf_batch_clear", "lf_batch_get_stats",
-           "lf_batch_destroy", "lf_set_tile")
+           "lf_batch_destroy", "lf_set_tile", "lf_create_calibrated")
 
 
 class LfError(RuntimeError):
@@ -70,6 +70,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lf_default_params.restype = None
     lib.lf_create.argtypes = [ctypes.POINTER(P), I, P, I, I, ctypes.c_float, ctypes.c_float, I,
                               ctypes.POINTER(Params)]
+    lib.lf_create_calibrated.argtypes = lib.lf_create.argtypes
     lib.lf_set_stream.argtypes = [P, P]
     lib.lf_set_inputs.argtypes = [P, P, I, I, P, P, I, I]
     lib.lf_run_em.argtypes = [P, I, P, P, P, P, P, I]
@@ -101,7 +102,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         getattr(lib, name).restype = I
     lib.lf_triangulate.argtypes = [P, I, P, I]
     lib.lf_triangulate.restype = I
-    for name in ("lf_create", "lf_set_stream", "lf_set_inputs", "lf_run_em", "lf_synchronize",
+    for name in ("lf_create", "lf_create_calibrated", "lf_set_stream", "lf_set_inputs", "lf_run_em", "lf_synchronize",
                  "lf_get_prior", "lf_get_stats", "lf_set_timing"):
         getattr(lib, name).restype = I
     _lib = lib
@@ -162,17 +163,26 @@ def _is_torch(x) -> bool:
 
 
 class Context:
-    """One camera array / image size; owns the library's device buffers."""
+    """One camera array / image size; owns the library's device buffers.
+    ``cameras`` ([K,3,4]): a calibrated, non-rectified array (lf_create_calibrated);
+    the baselines are then not used (may be None)."""
 
     def __init__(self, baselines, H: int, W: int, d_min: float, d_max: float, D: int,
-                 params: Optional[Params] = None, stream=None):
+                 params: Optional[Params] = None, stream=None, cameras=None):
         lib = load()
-        self.K = len(baselines)
         self.H, self.W, self.D = int(H), int(W), int(D)
-        b = np.ascontiguousarray(baselines, np.float32)
         h = ctypes.c_void_p()
-        _check(lib.lf_create(ctypes.byref(h), self.K, b.ctypes.data, self.H, self.W, float(d_min), float(d_max),
-                             self.D, ctypes.byref(params) if params is not None else None))
+        prm = ctypes.byref(params) if params is not None else None
+        if cameras is not None:
+            cams = np.ascontiguousarray(cameras, np.float32).reshape(-1, 3, 4)
+            self.K = int(cams.shape[0])
+            _check(lib.lf_create_calibrated(ctypes.byref(h), self.K, cams.ctypes.data, self.H, self.W,
+                                            float(d_min), float(d_max), self.D, prm))
+        else:
+            self.K = len(baselines)
+            b = np.ascontiguousarray(baselines, np.float32)
+            _check(lib.lf_create(ctypes.byref(h), self.K, b.ctypes.data, self.H, self.W, float(d_min),
+                                 float(d_max), self.D, prm))
         self._h = h
         self.C = None
         if stream is not None:
@@ -372,7 +382,8 @@ def device_outputs(K: int, H: int, W: int, C: int, device=None) -> dict:
 
 def run_scene(scene, params: Optional[Params] = None, iters: Optional[int] = None, **kw) -> dict:
     """Convenience: one frame of a ``scenes.Scene`` through host buffers."""
-    with Context(scene.baselines, scene.H, scene.W, scene.d_min, scene.d_max, scene.D, params) as ctx:
+    with Context(scene.baselines, scene.H, scene.W, scene.d_min, scene.d_max, scene.D, params,
+                 cameras=getattr(scene, "cameras", None)) as ctx:
         ctx.set_inputs(scene.images, scene.seg_prior, scene.points)
         out = ctx.run(scene.iters if iters is None else iters, **kw)
         out["stats"] = ctx.stats()

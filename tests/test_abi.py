@@ -118,3 +118,39 @@ def test_package_never_imports_the_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", src, re.M), f
                 assert "lf_oracle" not in src and "orc_" not in src, f
+
+
+def _rect_cams(b):
+    cams = np.zeros((len(b), 3, 4), np.float32)
+    for k, bk in enumerate(b):
+        cams[k, :, :3] = np.eye(3)
+        cams[k, 0, 3] = -bk
+    return cams
+
+
+@pytest.mark.parametrize("case,expect", [
+    ("no_reference", "[I | 0]"), ("nan", "non-finite"), ("behind", "behind the camera"),
+    ("soft", "hard EM"), ("f16", "hard EM"),
+])
+def test_create_calibrated_rejects_invalid_arguments(lib, case, expect):
+    """Argument checks of lf_create_calibrated run before any device work."""
+    from paper_2003_11076_gb300 import lf
+    cams = _rect_cams([-0.2, 0.0, 0.2])
+    p = lf.default_params()
+    if case == "no_reference":
+        cams[1, 0, 3] = 0.01
+    elif case == "nan":
+        cams[2, 1, 1] = np.nan
+    elif case == "behind":
+        cams[2, 2, 3] = -1.0  # Z = 1 - d: negative for d > 1
+    elif case == "soft":
+        p = lf.default_params(em_mode=lf.LF_EM_SOFT)
+    elif case == "f16":
+        p = lf.default_params(precision=lf.LF_PREC_F16)
+    h = ctypes.c_void_p()
+    s = lib.lf_create_calibrated(ctypes.byref(h), 3, np.ascontiguousarray(cams).ctypes.data, 16, 16, 0.0, 7.0, 8,
+                                 ctypes.byref(p))
+    assert s == lf.LF_EINVAL
+    assert not h.value
+    assert expect in lib.lf_last_error(None).decode()
+    assert lib.lf_create_calibrated(ctypes.byref(h), 3, None, 16, 16, 0.0, 7.0, 8, None) == lf.LF_EINVAL
