@@ -196,3 +196,109 @@ def run(images, seg_prior, baselines, mu, inside, d_min, d_max, D, iters, p, mod
 
 def all_label_vectors(K):
     return list(itertools.product((0, 1), repeat=K))
+
+
+# ------------------------------------------------------------ support points
+
+def support_points(images, seg_prior, baselines, d_min, d_max, D, sp):
+    """The support points of support_oracle.c restated with array operations
+    (scipy integer Sobel, padded descriptor windows, the whole cost table per
+    point).  Returns the per-cell arrays like ``oracle.support_points``."""
+    imgs = np.asarray(images)
+    K, H, W = imgs.shape[:3]
+    if imgs.dtype == np.uint8:
+        q = imgs.astype(np.int64)
+    else:
+        q = np.clip(np.rint(np.float32(255.0) * imgs.astype(np.float32)), 0, 255).astype(np.int64)
+    Y = q if q.ndim == 3 else (77 * q[..., 0] + 150 * q[..., 1] + 29 * q[..., 2] + 128) >> 8
+    kx = np.array([[-1, 0, 1], [-2, 0, 2], [-1, 0, 1]])
+    gx = np.stack([ndimage.correlate(Y[k], kx, mode="nearest") for k in range(K)])
+    gy = np.stack([ndimage.correlate(Y[k], kx.T, mode="nearest") for k in range(K)])
+    # descriptor windows: [K, H, W, 18]
+    pad = lambda a: np.pad(a, ((0, 0), (1, 1), (1, 1)), mode="edge")
+    gxp, gyp = pad(gx), pad(gy)
+    desc = np.concatenate([np.stack([gxp[:, 1 + dy:1 + dy + H, 1 + dx:1 + dx + W] for dy in (-1, 0, 1)
+                                     for dx in (-1, 0, 1)], -1),
+                           np.stack([gyp[:, 1 + dy:1 + dy + H, 1 + dx:1 + dx + W] for dy in (-1, 0, 1)
+                                     for dx in (-1, 0, 1)], -1)], -1)
+    tex = np.abs(desc).sum(-1)
+    P = np.asarray(seg_prior, np.float32)
+    Pp = np.pad(P, ((0, 0), (1, 1), (1, 1)), mode="edge")
+    win_static = np.all(np.stack([Pp[:, 1 + dy:1 + dy + H, 1 + dx:1 + dx + W] for dy in (-1, 0, 1)
+                                  for dx in (-1, 0, 1)], -1) < np.float32(sp.seg_threshold), -1)
+    b = np.asarray(baselines, np.float32).astype(np.float64)
+    ref = int(np.flatnonzero(b == 0)[0])
+    dval = np.array([float(d_min)] if D == 1 else
+                    [float(d_min) + j * ((float(d_max) - float(d_min)) / (D - 1)) for j in range(D)])
+    step = (float(d_max) - float(d_min)) / (D - 1) if D > 1 else 0.0
+    g, h = sp.grid, sp.grid // 2
+    nx, ny = (W + g - 1) // g, (H + g - 1) // g
+    cell_j = np.full((ny, nx), -1, np.int64)
+    cell_src = np.full((ny, nx), -1, np.int64)
+    cell_u = np.zeros((ny, nx))
+    cell_v = np.zeros((ny, nx))
+
+    def match(s, targets, u, v):
+        if tex[s, v, u] < sp.texture or D < 2 or step <= 0:
+            return -1
+        bmax = max(abs(b[t] - b[s]) for t in targets)
+        if bmax <= 0:
+            return -1
+        delta = int(np.ceil(1.0 / (bmax * step)))
+        costs = np.full(D, -1, np.int64)
+        for j in range(D):
+            xs = [u + int(np.floor(-dval[j] * (b[t] - b[s]) + 0.5)) for t in targets]
+            if any(x < 0 or x > W - 1 for x in xs):
+                continue
+            costs[j] = sum(int(np.abs(desc[s, v, u] - desc[t, v, x]).sum()) for t, x in zip(targets, xs))
+        valid = np.flatnonzero(costs >= 0)
+        if valid.size == 0:
+            return -1
+        best = int(valid[np.argmin(costs[valid])])      # first minimum
+        far = valid[np.abs(valid - best) >= delta]
+        if far.size == 0:
+            return -1
+        return best if 100 * costs[best] < sp.ratio_pct * costs[far].min() else -1
+
+    others = [t for t in range(K) if t != ref]
+    for cj in range(ny):
+        for ci in range(nx):
+            u, v = g * ci + h, g * cj + h
+            if u > W - 1 or v > H - 1 or not win_static[ref, v, u]:
+                continue
+            j = match(ref, others, u, v)
+            if j >= 0:
+                cell_j[cj, ci], cell_src[cj, ci], cell_u[cj, ci], cell_v[cj, ci] = j, ref, u, v
+    for s in others:
+        targets = [t for t in others if t != s]
+        if not targets:
+            continue
+        for cj in range(ny):
+            for ci in range(nx):
+                u, v = g * ci + h, g * cj + h
+                if u > W - 1 or v > H - 1 or not win_static[s, v, u]:
+                    continue
+                j = match(s, targets, u, v)
+                if j < 0:
+                    continue
+                ur = u + dval[j] * b[s]
+                if ur < 0 or ur > W - 1 or P[ref, v, int(np.floor(ur + 0.5))] < np.float32(sp.seg_threshold):
+                    continue
+                c = (cj, int(np.floor(ur / g)))
+                if cell_j[c] >= 0:
+                    continue
+                cell_j[c], cell_src[c], cell_u[c], cell_v[c] = j, s, ur, v
+    keep = np.zeros_like(cell_j, bool)
+    for cj in range(ny):
+        for ci in range(nx):
+            if cell_j[cj, ci] < 0:
+                continue
+            win = cell_j[max(cj - sp.window, 0):cj + sp.window + 1, max(ci - sp.window, 0):ci + sp.window + 1]
+            near = win[win >= 0]
+            agree = np.sum(np.abs(dval[near] - dval[cell_j[cj, ci]]) <= sp.delta) - 1  # not itself
+            keep[cj, ci] = agree >= sp.min_support
+    cell_j[~keep] = -1
+    cell_src[~keep] = -1
+    cell_u[~keep] = 0.0
+    cell_v[~keep] = 0.0
+    return {"cell_j": cell_j, "cell_src": cell_src, "cell_u": cell_u, "cell_v": cell_v}

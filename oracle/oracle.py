@@ -29,6 +29,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "lf_oracle.c")
+SUPPORT_SRC = os.path.join(HERE, "support_oracle.c")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liblf_oracle.so")
 
@@ -54,13 +55,34 @@ class _CParams(ctypes.Structure):
                 ("mstep_seg_term", ctypes.c_int), ("em_mode", ctypes.c_int)]
 
 
+@dataclasses.dataclass
+class SupportParams:
+    """Support-point detection (see support_oracle.c for the reading)."""
+
+    grid: int = 5
+    ratio_pct: int = 85
+    texture: int = 120
+    window: int = 3
+    delta: float = 3.0
+    min_support: int = 2
+    seg_threshold: float = 0.7
+
+
+class _CSupport(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_int), ("ratio_pct", ctypes.c_int), ("texture", ctypes.c_int),
+                ("window", ctypes.c_int), ("delta", ctypes.c_double), ("min_support", ctypes.c_int),
+                ("seg_threshold", ctypes.c_float)]
+
+
 def build(force: bool = False) -> str:
     """Compile the C core with gcc (OpenMP when available).  FP contraction is
     off so that x86 and Arm builds round identically."""
     os.makedirs(BUILD_DIR, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+    if not force and os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(s)
+                                                  for s in (SRC, SUPPORT_SRC)):
         return LIB
-    base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", SRC, "-o", LIB + ".tmp", "-lm"]
+    base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", SRC, SUPPORT_SRC,
+            "-o", LIB + ".tmp", "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
@@ -84,6 +106,10 @@ def _load():
                                 P, P, P, P, P, P, P, P, P]
         lib.orc_run_general.restype = ctypes.c_int
         lib.orc_run_general.argtypes = lib.orc_run.argtypes
+        lib.orc_support_points.restype = ctypes.c_int
+        lib.orc_support_points.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           P, P, ctypes.c_float, ctypes.c_float, ctypes.c_int,
+                                           ctypes.POINTER(_CSupport), P, P, P, P]
         lib.orc_max_threads.restype = ctypes.c_int
         lib.orc_objective_at.restype = ctypes.c_double
         lib.orc_objective_at.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -239,6 +265,39 @@ def run_scene(scene, params: Optional[Params] = None, rows=None, threads: int = 
     return run(scene.images, scene.seg_prior, scene.baselines, scene.points, scene.d_min, scene.d_max,
                scene.D, scene.iters if iters is None else iters, params, rows, threads,
                cameras=getattr(scene, "cameras", None))
+
+
+def support_points(images, seg_prior, baselines, d_min: float, d_max: float, D: int,
+                   params: Optional[SupportParams] = None) -> dict:
+    """Support points of the disparity prior (Sec. III-C).  Returns the
+    per-cell arrays (cell_j: candidate index or -1, cell_src: source camera,
+    cell_u / cell_v: reference coordinates) and ``points`` [M,3] (u, v, d) in
+    cell raster order."""
+    lib = _load()
+    sp = params or SupportParams()
+    imgs = np.ascontiguousarray(images)
+    dtype = 0 if imgs.dtype == np.uint8 else 1
+    if dtype == 1 and imgs.dtype != np.float32:
+        imgs = imgs.astype(np.float32)
+    K, H, W = imgs.shape[:3]
+    C = 1 if imgs.ndim == 3 else imgs.shape[3]
+    seg = np.ascontiguousarray(seg_prior, np.float32)
+    b = np.ascontiguousarray(baselines, np.float32)
+    nx, ny = (W + sp.grid - 1) // sp.grid, (H + sp.grid - 1) // sp.grid
+    out = {"cell_j": np.zeros((ny, nx), np.int32), "cell_src": np.zeros((ny, nx), np.int32),
+           "cell_u": np.zeros((ny, nx), np.float64), "cell_v": np.zeros((ny, nx), np.float64)}
+    cs = _CSupport(sp.grid, sp.ratio_pct, sp.texture, sp.window, sp.delta, sp.min_support, sp.seg_threshold)
+    n = lib.orc_support_points(K, _ptr(b), H, W, C, dtype, _ptr(imgs), _ptr(seg), float(d_min), float(d_max),
+                               int(D), ctypes.byref(cs), _ptr(out["cell_j"]), _ptr(out["cell_src"]),
+                               _ptr(out["cell_u"]), _ptr(out["cell_v"]))
+    if n < 0:
+        raise ValueError("oracle rejected the arguments")
+    dval = np.array([float(d_min)] if D == 1 else
+                    [float(d_min) + j * ((float(d_max) - float(d_min)) / (D - 1)) for j in range(D)])
+    m = out["cell_j"] >= 0
+    out["points"] = np.stack([out["cell_u"][m], out["cell_v"][m], dval[out["cell_j"][m]]], 1)
+    assert out["points"].shape[0] == n
+    return out
 
 
 def features(images: np.ndarray) -> np.ndarray:
