@@ -191,15 +191,76 @@ lf_status lf_set_stream(lf_ctx *ctx, void *stream);
  *                pixel units; triangulated on the host (Delaunay), repeated
  *                (u, v) keep their first occurrence; fewer than 3
  *                non-collinear points give a uniform prior everywhere.
+ *                sparse_points = NULL with M = LF_DETECT_SUPPORT: the
+ *                support points are detected on the device from these
+ *                images and segmentation probabilities (Sec. III-C; see
+ *                lf_support_params) and the call waits for them; they can
+ *                be read back with lf_get_support_points.  Rectified arrays
+ *                only.
  *   on_device    1: images and seg_prior are device pointers (borrowed until
  *                the stream passes the next lf_run_em); 0: host pointers
  *                (copied now, synchronously with respect to the caller).
- * Errors: LF_EINVAL (NULL pointer, C not 1 or 3, bad dtype, M < 0,
- * non-finite point), LF_ECUDA.
+ * Errors: LF_EINVAL (NULL pointer, C not 1 or 3, bad dtype, M < 0 other than
+ * LF_DETECT_SUPPORT, non-finite point, detection on a calibrated array),
+ * LF_ENOMEM, LF_ECUDA.
  */
 lf_status lf_set_inputs(lf_ctx *ctx, const void *images, int C, int dtype,
                         const float *seg_prior, const float *sparse_points, int M,
                         int on_device);
+
+#define LF_DETECT_SUPPORT (-1)
+
+/*
+ * Support-point detection (Sec. III-C "Disparity Prior": points matched along
+ * the epipolar lines over the full disparity range as in ELAS, points on
+ * dynamic objects dropped, points of other views that re-project onto the
+ * reference's occluded background added, duplicates and inconsistent points
+ * removed).  The paper gives the steps, not their details; this library's
+ * reading, all in integer or double arithmetic so that results are exact:
+ *   - 8-bit luminance (uint8 RGB: (77 R + 150 G + 29 B + 128) >> 8; float
+ *     inputs quantised per channel to rint(255 x) first), integer 3x3 Sobel
+ *     responses, descriptor = both responses over the 3x3 window;
+ *   - candidate pixels on a grid of step `grid` (offset grid / 2); a source
+ *     camera is matched against target cameras at every candidate d_j, the
+ *     target column being u + floor(-d_j (b_t - b_s) + 1/2); cost = summed
+ *     L1 descriptor distance; candidates whose target leaves the image are
+ *     skipped;
+ *   - accepted iff the window texture (sum |Gx| + |Gy|) >= texture and
+ *     100 * best < ratio_pct * (best cost at least one pixel of shift away
+ *     on the widest pair);
+ *   - reference points: the reference against all other cameras, the 3x3
+ *     window static (P < seg_threshold); other views: each other camera
+ *     against all cameras but itself and the reference, static in that view,
+ *     kept where they re-project (u + d b_s, same row) onto a reference pixel
+ *     with P >= seg_threshold;
+ *   - one point per grid cell (the reference's own first, then other views
+ *     in camera and raster order), then a point is kept iff at least
+ *     min_support other points within `window` cells have |d - d'| <= delta;
+ *   - each point is placed at its position plus a fixed offset of at most
+ *     0.01 px that depends on its cell ((7 i + 13 j) mod 17 + 1) / 1800 in u,
+ *     ((11 i + 5 j) mod 19 + 1) / 2000 in v), so that the grid's points are
+ *     not cocircular and their Delaunay triangulation is unique.
+ */
+typedef struct lf_support_params {
+    int grid;        /* grid step in pixels (default 5) */
+    int ratio_pct;   /* uniqueness ratio, percent (85) */
+    int texture;     /* minimum window texture (120) */
+    int window;      /* consistency radius in cells (3) */
+    float delta;     /* consistency tolerance, disparity units (3) */
+    int min_support; /* agreeing neighbours needed (2) */
+} lf_support_params;
+
+/* Fill *p with the defaults listed above. */
+void lf_default_support_params(lf_support_params *p);
+
+/* Parameters of the next detections on this context (NULL = defaults).
+ * Errors: LF_EINVAL on a NULL ctx or out-of-range values. */
+lf_status lf_set_support_params(lf_ctx *ctx, const lf_support_params *p);
+
+/* The points of the last detection: *n_points = their number; up to
+ * max_points (u, v, d) triples are copied to the host array points (may be
+ * NULL to query the count).  Points come in grid-cell raster order. */
+lf_status lf_get_support_points(const lf_ctx *ctx, float *points, int max_points, int *n_points);
 
 /*
  * Run the whole hot path on the last inputs: prior raster, `iters` EM

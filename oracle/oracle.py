@@ -295,7 +295,13 @@ def support_points(images, seg_prior, baselines, d_min: float, d_max: float, D: 
     dval = np.array([float(d_min)] if D == 1 else
                     [float(d_min) + j * ((float(d_max) - float(d_min)) / (D - 1)) for j in range(D)])
     m = out["cell_j"] >= 0
-    out["points"] = np.stack([out["cell_u"][m], out["cell_v"][m], dval[out["cell_j"][m]]], 1)
+    # points sit at their cell's position plus a fixed sub-pixel offset per
+    # cell (at most 0.01 px) that keeps grid points off common circles: the
+    # Delaunay triangulation of the prior is then unique
+    cj, ci = np.nonzero(m)
+    ju = 0.01 * ((7 * ci + 13 * cj) % 17 + 1).astype(np.float64) / 18.0
+    jv = 0.01 * ((11 * ci + 5 * cj) % 19 + 1).astype(np.float64) / 20.0
+    out["points"] = np.stack([out["cell_u"][m] + ju, out["cell_v"][m] + jv, dval[out["cell_j"][m]]], 1)
     assert out["points"].shape[0] == n
     return out
 

@@ -46,6 +46,10 @@
  *               the other views in camera order, raster order within a view
  *   consistency a point is kept iff at least min_support other points within
  *               a Chebyshev radius of `window` cells have |d - d'| <= delta
+ *   position    the point list (oracle.py) places each point at its cell
+ *               position plus a fixed offset below 0.01 px per cell, so that
+ *               points of the regular grid are not cocircular and the
+ *               Delaunay triangulation of the prior is unique
  */
 #include <math.h>
 #include <stdint.h>

@@ -215,6 +215,17 @@ struct lf_ctx {
   size_t own_img16_cap = 0;
   int* d_tiles = nullptr;        // dynamic-only: list of tiles to sweep, then its length
   size_t tiles_cap = 0;
+  // support-point detection (lf_set_inputs with M = LF_DETECT_SUPPORT)
+  lf_support_params sp{};
+  std::vector<float> support_pts;  // the last detected points, (u, v, d) triples
+  int16_t* d_sgrad = nullptr;      // gx then gy
+  size_t sgrad_cap = 0;
+  int* d_sint = nullptr;           // offsets, match, claim, pre_j, pre_src, cell_j, cell_src, count
+  size_t sint_cap = 0;
+  double* d_sdbl = nullptr;        // pre_u, pre_v, cell_u, cell_v
+  size_t sdbl_cap = 0;
+  float* d_spts = nullptr;
+  size_t spts_cap = 0;
   // calibrated array: camera matrices and the per-run descriptor maps
   bool calibrated = false;
   float cams[kMaxCams * 12] = {};
@@ -508,11 +519,12 @@ lf_status create_ctx(lf_ctx** out, int n_cams, const float* baselines, const flo
     return fail(LF_EINVAL, "calibrated arrays run the hard EM on float32 maps (LF_EM_HARD, LF_PREC_F32)");
 
   lf_ctx* c = new (std::nothrow) lf_ctx();
+  if (!c) return fail(LF_ENOMEM, "host allocation failed");
+  lf_default_support_params(&c->sp);
   if (cameras) {
     c->calibrated = true;
     std::copy(cameras, cameras + 12 * n_cams, c->cams);
   }
-  if (!c) return fail(LF_ENOMEM, "host allocation failed");
   c->K = n_cams;
   c->H = H;
   c->W = W;
@@ -585,9 +597,125 @@ lf_status create_ctx(lf_ctx** out, int n_cams, const float* baselines, const flo
   *out = c;
   return LF_OK;
 }
+// Support points of the current inputs into c->support_pts (Sec. III-C): the
+// kernels of support.cu, then the points and their count back to the host.
+lf_status detect_support(lf_ctx* c) {
+  const int K = c->K, D = c->D, H = c->H, W = c->W;
+  const lf_support_params& q = c->sp;
+  SupportArgs a{};
+  a.K = K; a.H = H; a.W = W; a.C = c->C; a.dtype = c->dtype; a.ref = c->ref; a.D = D;
+  a.d_min = c->d_min; a.d_max = c->d_max; a.seg_threshold = c->p.seg_threshold;
+  a.grid = q.grid; a.ratio_pct = q.ratio_pct; a.texture = q.texture; a.window = q.window;
+  a.min_support = q.min_support; a.delta = q.delta;
+  for (int k = 0; k < K; ++k) a.b[k] = c->b[k];
+  a.img = c->img; a.img_pitch = c->img_pitch; a.P = c->P; a.p_pitch = c->p_pitch;
+  a.nx = (W + q.grid - 1) / q.grid;
+  a.ny = (H + q.grid - 1) / q.grid;
+  const int ncell = a.nx * a.ny;
+  // sources: the reference against every other camera, then each other camera
+  // against every camera but itself and the reference
+  unsigned others = 0;
+  for (int t = 0; t < K; ++t)
+    if (t != c->ref) others |= 1u << t;
+  a.n_src = 0;
+  a.src[a.n_src] = c->ref;
+  a.tmask[a.n_src++] = others;
+  for (int s = 0; s < K; ++s)
+    if (s != c->ref) {
+      a.src[a.n_src] = s;
+      a.tmask[a.n_src++] = others & ~(1u << s);
+    }
+  // target offsets floor(-d_j (b_t - b_s) + 1/2) and the uniqueness spans, in double
+  const double step = D > 1 ? (static_cast<double>(c->d_max) - static_cast<double>(c->d_min)) / (D - 1) : 0.0;
+  std::vector<int> off(static_cast<size_t>(a.n_src) * K * D, 0);
+  for (int si = 0; si < a.n_src; ++si) {
+    const int s = a.src[si];
+    double bmax = 0.0;
+    for (int t = 0; t < K; ++t) {
+      if (!(a.tmask[si] >> t & 1u)) continue;
+      const double db = static_cast<double>(c->b[t]) - static_cast<double>(c->b[s]);
+      bmax = std::max(bmax, std::fabs(db));
+      for (int j = 0; j < D; ++j) {
+        const double dj = D == 1 ? static_cast<double>(c->d_min)
+                                 : static_cast<double>(c->d_min) + static_cast<double>(j) * step;
+        off[(static_cast<size_t>(si) * K + t) * D + j] = static_cast<int>(std::floor(-dj * db + 0.5));
+      }
+    }
+    a.delta_c[si] = (D >= 2 && step > 0.0 && bmax > 0.0) ? static_cast<int>(std::ceil(1.0 / (bmax * step))) : 0;
+  }
+  const size_t HWK = static_cast<size_t>(H) * W * K;
+  const size_t n_int = off.size() + static_cast<size_t>(a.n_src) * ncell + 5 * static_cast<size_t>(ncell) + 1;
+  lf_status s;
+  if ((s = grow(&c->d_sgrad, &c->sgrad_cap, 2 * HWK, "support buffers")) != LF_OK) return s;
+  if ((s = grow(&c->d_sint, &c->sint_cap, n_int, "support buffers")) != LF_OK) return s;
+  if ((s = grow(&c->d_sdbl, &c->sdbl_cap, 4 * static_cast<size_t>(ncell), "support buffers")) != LF_OK) return s;
+  if ((s = grow(&c->d_spts, &c->spts_cap, 3 * static_cast<size_t>(ncell), "support buffers")) != LF_OK) return s;
+  a.gx = c->d_sgrad;
+  a.gy = c->d_sgrad + HWK;
+  int* ip = c->d_sint;
+  a.offsets = ip; ip += off.size();
+  a.match = ip; ip += static_cast<size_t>(a.n_src) * ncell;
+  a.claim = ip; ip += ncell;
+  a.pre_j = ip; ip += ncell;
+  a.pre_src = ip; ip += ncell;
+  a.cell_j = ip; ip += ncell;
+  a.cell_src = ip; ip += ncell;
+  a.n_points = ip;
+  a.pre_u = c->d_sdbl;
+  a.pre_v = c->d_sdbl + ncell;
+  a.cell_u = c->d_sdbl + 2 * ncell;
+  a.cell_v = c->d_sdbl + 3 * ncell;
+  a.points = c->d_spts;
+  a.max_points = ncell;
+  LF_CUDA(cudaMemcpyAsync(const_cast<int*>(a.offsets), off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice,
+                          c->stream),
+          "support offsets upload");
+  LF_CUDA(launch_support(a, c->stream), "support-point kernels");
+  int n = 0;
+  LF_CUDA(cudaMemcpyAsync(&n, a.n_points, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "support count");
+  LF_CUDA(cudaStreamSynchronize(c->stream), "support points");
+  c->support_pts.resize(static_cast<size_t>(3) * n);
+  if (n > 0)
+    LF_CUDA(cudaMemcpy(c->support_pts.data(), c->d_spts, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost),
+            "support points");
+  return LF_OK;
+}
 }  // namespace
 
 extern "C" {
+
+void lf_default_support_params(lf_support_params* q) {
+  if (!q) return;
+  q->grid = 5;
+  q->ratio_pct = 85;
+  q->texture = 120;
+  q->window = 3;
+  q->delta = 3.f;
+  q->min_support = 2;
+}
+
+lf_status lf_set_support_params(lf_ctx* c, const lf_support_params* q) {
+  g_err.clear();
+  if (!c) return fail(LF_EINVAL, "ctx is NULL");
+  lf_support_params v;
+  lf_default_support_params(&v);
+  if (q) v = *q;
+  if (v.grid < 1 || v.grid > 64 || v.ratio_pct < 1 || v.ratio_pct > 100 || v.texture < 0 || v.window < 0 ||
+      v.window > 32 || !(v.delta >= 0.f) || !std::isfinite(v.delta) || v.min_support < 0)
+    return fail(LF_EINVAL, "invalid lf_support_params");
+  c->sp = v;
+  return LF_OK;
+}
+
+lf_status lf_get_support_points(const lf_ctx* c, float* points, int max_points, int* n_points) {
+  g_err.clear();
+  if (!c || !n_points) return fail(LF_EINVAL, "ctx and n_points must not be NULL");
+  const int n = static_cast<int>(c->support_pts.size() / 3);
+  *n_points = n;
+  if (points && max_points > 0)
+    std::copy(c->support_pts.begin(), c->support_pts.begin() + 3 * std::min(n, max_points), points);
+  return LF_OK;
+}
 
 lf_status lf_create(lf_ctx** out, int n_cams, const float* baselines, int H, int W, float d_min, float d_max,
                     int D, const lf_params* p) {
@@ -624,7 +752,10 @@ lf_status lf_set_inputs(lf_ctx* c, const void* images, int C, int dtype, const f
   if (C != 1 && C != 3) return fail(LF_EINVAL, "C must be 1 or 3");
   if (dtype != LF_U8 && dtype != LF_F32 && dtype != LF_F16 && dtype != LF_BF16)
     return fail(LF_EINVAL, "dtype must be LF_U8, LF_F32, LF_F16 or LF_BF16");
-  if (M < 0 || (M > 0 && !sparse_points)) return fail(LF_EINVAL, "bad sparse points");
+  const bool detect = M == LF_DETECT_SUPPORT;
+  if (detect && sparse_points) return fail(LF_EINVAL, "M = LF_DETECT_SUPPORT takes sparse_points = NULL");
+  if (detect && c->calibrated) return fail(LF_EINVAL, "support-point detection needs a rectified array");
+  if ((M < 0 && !detect) || (M > 0 && !sparse_points)) return fail(LF_EINVAL, "bad sparse points");
   for (int i = 0; i < 3 * M; ++i)
     if (!std::isfinite(sparse_points[i])) return fail(LF_EINVAL, "non-finite sparse point");
   c->have_inputs = false;
@@ -634,6 +765,20 @@ lf_status lf_set_inputs(lf_ctx* c, const void* images, int C, int dtype, const f
   lf_status s = copy_plane(c, images, static_cast<size_t>(c->W) * c->bpp, on_device != 0, &c->own_img,
                            &c->own_img_cap, &c->img, &c->img_pitch);
   if (s != LF_OK) return s;
+  {
+    const uint8_t* pp = nullptr;
+    uint8_t* ownP = reinterpret_cast<uint8_t*>(c->own_P);
+    s = copy_plane(c, seg_prior, static_cast<size_t>(c->W) * 4, on_device != 0, &ownP, &c->own_P_cap, &pp,
+                   &c->p_pitch);
+    c->own_P = reinterpret_cast<float*>(ownP);
+    if (s != LF_OK) return s;
+    c->P = reinterpret_cast<const float*>(pp);
+  }
+  if (detect) {  // Sec. III-C: support points from the inputs themselves (before any 16-bit conversion)
+    if ((s = detect_support(c)) != LF_OK) return s;
+    sparse_points = c->support_pts.data();
+    M = static_cast<int>(c->support_pts.size() / 3);
+  }
   if (dtype == LF_F32 && c->p.precision != LF_PREC_F32) {
     // reduced precision: the images are stored on the device in 16 bits
     const int to_bf16 = c->p.precision == LF_PREC_BF16;
@@ -650,13 +795,6 @@ lf_status lf_set_inputs(lf_ctx* c, const void* images, int C, int dtype, const f
   }
   s = choose_tiles(c);
   if (s != LF_OK) return s;
-  const uint8_t* pp = nullptr;
-  uint8_t* ownP = reinterpret_cast<uint8_t*>(c->own_P);
-  s = copy_plane(c, seg_prior, static_cast<size_t>(c->W) * 4, on_device != 0, &ownP, &c->own_P_cap, &pp,
-                 &c->p_pitch);
-  c->own_P = reinterpret_cast<float*>(ownP);
-  if (s != LF_OK) return s;
-  c->P = reinterpret_cast<const float*>(pp);
   build_prior(c, sparse_points, M);
   if ((s = grow(&c->d_tris, &c->tris_cap, std::max<size_t>(c->h_tris.size(), 1), "prior")) != LF_OK) return s;
   if ((s = grow(&c->d_bins, &c->bins_cap, c->h_bins.size(), "prior")) != LF_OK) return s;
@@ -945,7 +1083,8 @@ void lf_destroy(lf_ctx* c) {
   cudaStreamSynchronize(c->stream);
   void* bufs[] = {c->d_wtab, c->d_otab, c->d_chg, c->d_dval, c->d_mu, c->d_counter, c->d_status,
                   c->own_img, c->own_P, c->own_img16, c->d_tiles, c->d_tris, c->d_bins, c->o_didx, c->o_d, c->o_labels,
-                  c->o_post, c->o_ref, c->o_tmp, c->d_fa, c->d_fb};
+                  c->o_post, c->o_ref, c->o_tmp, c->d_fa, c->d_fb, c->d_sgrad, c->d_sint, c->d_sdbl,
+                  c->d_spts};
   for (void* p : bufs)
     if (p) cudaFree(p);
   for (auto& re : c->events)

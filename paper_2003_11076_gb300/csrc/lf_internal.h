@@ -108,6 +108,40 @@ struct CalibArgs {
   unsigned long long* counter;     // executed pixel-sweeps
 };
 
+// Support points of the disparity prior (rectified arrays).
+struct SupportArgs {
+  int K, H, W, C, dtype, ref, D;
+  float d_min, d_max, seg_threshold;
+  int grid, ratio_pct, texture, window, min_support;
+  float delta;
+  float b[kMaxCams];
+  const uint8_t* img;              // [K][H] rows of img_pitch bytes
+  size_t img_pitch;
+  const float* P;                  // [K][H] rows of p_pitch bytes, P(dynamic)
+  size_t p_pitch;
+  int n_src;                       // sources: the reference, then every other camera in order
+  int src[kMaxCams];
+  unsigned tmask[kMaxCams];        // per source: the target cameras
+  int delta_c[kMaxCams];           // per source: candidates spanning one pixel on the widest pair (0: none)
+  const int* offsets;              // [n_src][K][D] target column offsets (double rounding on the host)
+  int nx, ny;                      // cells
+  int16_t* gx;                     // [K][H][W] integer Sobel responses
+  int16_t* gy;
+  int* match;                      // [n_src][ny*nx] accepted candidate or -1
+  int* claim;                      // [ny*nx] first other-view claimant
+  int* pre_j;                      // [ny*nx] before the consistency test
+  int* pre_src;
+  double* pre_u;
+  double* pre_v;
+  int* cell_j;                     // [ny*nx] final
+  int* cell_src;
+  double* cell_u;
+  double* cell_v;
+  float* points;                   // [max_points][3]
+  int max_points;
+  int* n_points;
+};
+
 struct MedianArgs {
   int H, W, C;
   const float* in;
@@ -139,6 +173,7 @@ cudaError_t launch_em_sweep(int K, const CUtensorMap& img_map, const CUtensorMap
 cudaError_t launch_em_variant(int K, int mode, const CUtensorMap& img_map, const CUtensorMap& p_map,
                               const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_refocus(const RefocusArgs& a, cudaStream_t s);
+cudaError_t launch_support(const SupportArgs& a, cudaStream_t s);
 // Calibrated array: descriptor maps, the per-pixel EM, the refocus.
 cudaError_t launch_calib_features(const CalibArgs& a, cudaStream_t s);
 cudaError_t launch_calib_sweep(const CalibArgs& a, cudaStream_t s);

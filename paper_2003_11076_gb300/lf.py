@@ -25,7 +25,9 @@ EXPORTS = ("lf_default_params", "lf_create", "lf_set_stream", "lf_set_inputs", "
            "lf_synchronize", "lf_get_prior", "lf_get_stats", "lf_last_error", "lf_destroy",
            "lf_triangulate", "lf_set_timing", "lf_run_em_static", "lf_batch_create", "lf_batch_set_stream",
            "lf_batch_add", "lf_batch_run", "lf_batch_synchronize", "lf_batch_clear", "lf_batch_get_stats",
-           "lf_batch_destroy", "lf_set_tile", "lf_create_calibrated")
+           "lf_batch_destroy", "lf_set_tile", "lf_create_calibrated", "lf_default_support_params",
+           "lf_set_support_params", "lf_get_support_points")
+LF_DETECT_SUPPORT = -1
 
 
 class LfError(RuntimeError):
@@ -40,6 +42,12 @@ class Params(ctypes.Structure):
                 ("mstep_seg_term", ctypes.c_int), ("median", ctypes.c_int), ("precision", ctypes.c_int),
                 ("early_exit", ctypes.c_int), ("dynamic_only", ctypes.c_int),
                 ("em_mode", ctypes.c_int)]
+
+
+class SupportParams(ctypes.Structure):
+    """lf_support_params (support-point detection, see include/lf.h)."""
+    _fields_ = [("grid", ctypes.c_int), ("ratio_pct", ctypes.c_int), ("texture", ctypes.c_int),
+                ("window", ctypes.c_int), ("delta", ctypes.c_float), ("min_support", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -71,6 +79,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lf_create.argtypes = [ctypes.POINTER(P), I, P, I, I, ctypes.c_float, ctypes.c_float, I,
                               ctypes.POINTER(Params)]
     lib.lf_create_calibrated.argtypes = lib.lf_create.argtypes
+    lib.lf_default_support_params.argtypes = [ctypes.POINTER(SupportParams)]
+    lib.lf_default_support_params.restype = None
+    lib.lf_set_support_params.argtypes = [P, ctypes.POINTER(SupportParams)]
+    lib.lf_set_support_params.restype = I
+    lib.lf_get_support_points.argtypes = [P, P, I, ctypes.POINTER(I)]
+    lib.lf_get_support_points.restype = I
     lib.lf_set_stream.argtypes = [P, P]
     lib.lf_set_inputs.argtypes = [P, P, I, I, P, P, I, I]
     lib.lf_run_em.argtypes = [P, I, P, P, P, P, P, I]
@@ -107,6 +121,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         getattr(lib, name).restype = I
     _lib = lib
     return lib
+
+
+def default_support_params(**overrides) -> SupportParams:
+    p = SupportParams()
+    load().lf_default_support_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
 
 
 def default_params(**overrides) -> Params:
@@ -214,9 +236,13 @@ class Context:
     # -- the path
     def set_inputs(self, images, seg_prior, points):
         """images [K,H,W] / [K,H,W,3] uint8 or float32; seg_prior [K,H,W]
-        float32 P(dynamic); points [M,3] float32 (host).  numpy arrays are
-        host inputs, torch CUDA tensors device inputs."""
-        pts = np.ascontiguousarray(points, np.float32).reshape(-1, 3)
+        float32 P(dynamic); points [M,3] float32 (host), or None to detect
+        the support points on the device (LF_DETECT_SUPPORT).  numpy arrays
+        are host inputs, torch CUDA tensors device inputs."""
+        detect = points is None
+        pts = np.zeros((0, 3), np.float32) if detect else np.ascontiguousarray(points, np.float32).reshape(-1, 3)
+        pptr = None if detect else pts.ctypes.data
+        M = LF_DETECT_SUPPORT if detect else pts.shape[0]
         if _is_torch(images):
             import torch
             assert images.is_cuda and seg_prior.is_cuda and images.is_contiguous() and seg_prior.is_contiguous()
@@ -225,8 +251,7 @@ class Context:
                   torch.bfloat16: LF_BF16}[images.dtype]
             assert seg_prior.dtype == torch.float32
             self._keep = (images, seg_prior)
-            _check(load().lf_set_inputs(self._h, images.data_ptr(), C, dt, seg_prior.data_ptr(),
-                                        pts.ctypes.data, pts.shape[0], 1))
+            _check(load().lf_set_inputs(self._h, images.data_ptr(), C, dt, seg_prior.data_ptr(), pptr, M, 1))
         else:
             imgs = np.ascontiguousarray(images)
             if imgs.dtype not in (np.uint8, np.float32):
@@ -234,8 +259,7 @@ class Context:
             C = 1 if imgs.ndim == 3 else int(imgs.shape[3])
             dt = LF_U8 if imgs.dtype == np.uint8 else LF_F32
             seg = np.ascontiguousarray(seg_prior, np.float32)
-            _check(load().lf_set_inputs(self._h, imgs.ctypes.data, C, dt, seg.ctypes.data,
-                                        pts.ctypes.data, pts.shape[0], 0))
+            _check(load().lf_set_inputs(self._h, imgs.ctypes.data, C, dt, seg.ctypes.data, pptr, M, 0))
         self.C = C
 
     def run(self, iters: int, *, posteriors: bool = True, refocus: bool = True, disparity: bool = True,
@@ -280,6 +304,18 @@ class Context:
         _check(lib.lf_run_em(self._h, int(iters), ptr("d_idx"), ptr("d"), ptr("post"), ptr("labels"),
                              ptr("refocus"), 0))
         return res
+
+    def set_support_params(self, params: Optional[SupportParams] = None):
+        _check(load().lf_set_support_params(self._h, ctypes.byref(params) if params is not None else None))
+
+    def support_points(self) -> np.ndarray:
+        """[M,3] (u, v, d) of the last detection."""
+        n = ctypes.c_int(0)
+        _check(load().lf_get_support_points(self._h, None, 0, ctypes.byref(n)))
+        out = np.zeros((n.value, 3), np.float32)
+        if n.value:
+            _check(load().lf_get_support_points(self._h, out.ctypes.data, n.value, ctypes.byref(n)))
+        return out
 
     def set_tile(self, tile_rows: int, tile_cols: int):
         _check(load().lf_set_tile(self._h, int(tile_rows), int(tile_cols)))
@@ -380,12 +416,21 @@ def device_outputs(K: int, H: int, W: int, C: int, device=None) -> dict:
             "refocus": torch.empty((H, W, C) if C > 1 else (H, W), dtype=torch.float32, device=dev)}
 
 
-def run_scene(scene, params: Optional[Params] = None, iters: Optional[int] = None, **kw) -> dict:
-    """Convenience: one frame of a ``scenes.Scene`` through host buffers."""
+def run_scene(scene, params: Optional[Params] = None, iters: Optional[int] = None,
+              support: Optional[SupportParams] = None, detect_support: bool = False, **kw) -> dict:
+    """Convenience: one frame of a ``scenes.Scene`` through host buffers.
+    detect_support: support points detected on the device instead of the
+    scene's points (``support`` = their parameters)."""
     with Context(scene.baselines, scene.H, scene.W, scene.d_min, scene.d_max, scene.D, params,
                  cameras=getattr(scene, "cameras", None)) as ctx:
-        ctx.set_inputs(scene.images, scene.seg_prior, scene.points)
+        if support is not None:
+            ctx.set_support_params(support)
+        ctx.set_inputs(scene.images, scene.seg_prior, None if detect_support else scene.points)
+        if detect_support:
+            out_pts = ctx.support_points()
         out = ctx.run(scene.iters if iters is None else iters, **kw)
         out["stats"] = ctx.stats()
         out["mu"] = ctx.prior()
+        if detect_support:
+            out["support_points"] = out_pts
     return out

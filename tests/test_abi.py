@@ -154,3 +154,16 @@ def test_create_calibrated_rejects_invalid_arguments(lib, case, expect):
     assert not h.value
     assert expect in lib.lf_last_error(None).decode()
     assert lib.lf_create_calibrated(ctypes.byref(h), 3, None, 16, 16, 0.0, 7.0, 8, None) == lf.LF_EINVAL
+
+
+def test_host_delaunay_of_grid_support_points_matches_qhull(lib):
+    """Support points sit on a regular grid plus a fixed per-cell sub-pixel
+    offset; with the offset the triangulation is unique, so the library's
+    host Delaunay and Qhull agree on it."""
+    from scipy.spatial import Delaunay
+    from oracle import oracle as O
+    from paper_2003_11076_gb300 import lf, scenes
+    s = scenes.street_rgb(1, H=240, W=384, D=64, M=20)
+    pts = O.support_points(s.images, s.seg_prior, s.baselines, s.d_min, s.d_max, s.D)["points"].astype(np.float32)
+    assert pts.shape[0] > 1000
+    assert _tri_set(lf.triangulate(pts)) == _tri_set(Delaunay(pts[:, :2].astype(np.float64)).simplices)
