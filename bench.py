@@ -555,7 +555,9 @@ def main():
                        "kernel_ms": {"prior_raster": st["ms_prior"], "em_sweep": st["ms_sweep"],
                                      "refocus": st["ms_refocus"]},
                        "l2": "flushed between steps (256 MB write outside the per-step events)",
-                       "tile": [st["tile_rows"], st["tile_cols"]]},
+                       "tile": [st["tile_rows"], st["tile_cols"]],
+                       "host_ms_set_inputs": st["ms_set_inputs"],
+                       **({"support_ms": st["ms_support"]} if args.detect_support else {})},
             "roofline": {"bound": "alu", "kernel": "calib_sweep" if args.calibrated else
                          ("em_sweep" if mode == 0 else "em_variant"), "achieved": achieved,
                          "peak": peak, "unit": "Gop/s", "frac": achieved / peak, "traffic": traffic,

@@ -133,6 +133,9 @@ typedef struct lf_stats {
                                       of each kernel (lf_set_timing on), else 0 */
     int graph_captures;            /* batches: CUDA graphs captured so far */
     int tuned_signatures;          /* batches: tile shapes chosen by timing so far */
+    float ms_support;              /* device time of the last support-point detection */
+    float ms_set_inputs;           /* mean host time of lf_set_inputs (copies, detection,
+                                      Delaunay, bins) over the calls covered */
 } lf_stats;
 
 /* Fill *p with the documented defaults. */

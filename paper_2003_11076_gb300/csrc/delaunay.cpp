@@ -179,14 +179,14 @@ class Mesh {
   int last_ = 0;
 
   void next_stamp() {
-    if (mark_.size() < tris_.size()) mark_.resize(tris_.size() + 64, 0u);
+    if (mark_.size() < tris_.size()) mark_.resize(2 * tris_.size() + 64, 0u);  // geometric growth
     if (++stamp_ == 0) {
       std::fill(mark_.begin(), mark_.end(), 0u);
       stamp_ = 1;
     }
   }
   void mark(int t) {
-    if (static_cast<size_t>(t) >= mark_.size()) mark_.resize(tris_.size() + 64, 0u);
+    if (static_cast<size_t>(t) >= mark_.size()) mark_.resize(2 * tris_.size() + 64, 0u);
     mark_[t] = stamp_;
   }
   bool marked(int t) const { return static_cast<size_t>(t) < mark_.size() && mark_[t] == stamp_; }

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -226,6 +227,9 @@ struct lf_ctx {
   size_t sdbl_cap = 0;
   float* d_spts = nullptr;
   size_t spts_cap = 0;
+  cudaEvent_t sup_ev[2] = {nullptr, nullptr};
+  double set_inputs_ms = 0.0;      // host time of lf_set_inputs since the last lf_get_stats
+  int set_inputs_calls = 0;
   // calibrated array: camera matrices and the per-run descriptor maps
   bool calibrated = false;
   float cams[kMaxCams * 12] = {};
@@ -670,10 +674,17 @@ lf_status detect_support(lf_ctx* c) {
   LF_CUDA(cudaMemcpyAsync(const_cast<int*>(a.offsets), off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice,
                           c->stream),
           "support offsets upload");
+  if (!c->sup_ev[0]) {
+    LF_CUDA(cudaEventCreate(&c->sup_ev[0]), "event create");
+    LF_CUDA(cudaEventCreate(&c->sup_ev[1]), "event create");
+  }
+  LF_CUDA(cudaEventRecord(c->sup_ev[0], c->stream), "event");
   LF_CUDA(launch_support(a, c->stream), "support-point kernels");
+  LF_CUDA(cudaEventRecord(c->sup_ev[1], c->stream), "event");
   int n = 0;
   LF_CUDA(cudaMemcpyAsync(&n, a.n_points, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "support count");
   LF_CUDA(cudaStreamSynchronize(c->stream), "support points");
+  LF_CUDA(cudaEventElapsedTime(&c->stats.ms_support, c->sup_ev[0], c->sup_ev[1]), "event time");
   c->support_pts.resize(static_cast<size_t>(3) * n);
   if (n > 0)
     LF_CUDA(cudaMemcpy(c->support_pts.data(), c->d_spts, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost),
@@ -744,10 +755,30 @@ lf_status lf_set_stream(lf_ctx* c, void* stream) {
   return LF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+lf_status set_inputs_impl(lf_ctx* c, const void* images, int C, int dtype, const float* seg_prior,
+                          const float* sparse_points, int M, int on_device);
+}  // namespace
+
+extern "C" {
+
 lf_status lf_set_inputs(lf_ctx* c, const void* images, int C, int dtype, const float* seg_prior,
                         const float* sparse_points, int M, int on_device) {
   g_err.clear();
   if (!c) return fail(LF_EINVAL, "ctx is NULL");
+  const auto t0 = std::chrono::steady_clock::now();
+  const lf_status st = set_inputs_impl(c, images, C, dtype, seg_prior, sparse_points, M, on_device);
+  c->set_inputs_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  ++c->set_inputs_calls;
+  return st;
+}
+}  // extern "C"
+
+namespace {
+lf_status set_inputs_impl(lf_ctx* c, const void* images, int C, int dtype, const float* seg_prior,
+                          const float* sparse_points, int M, int on_device) {
   if (!images || !seg_prior) return fail(LF_EINVAL, "images and seg_prior must not be NULL");
   if (C != 1 && C != 3) return fail(LF_EINVAL, "C must be 1 or 3");
   if (dtype != LF_U8 && dtype != LF_F32 && dtype != LF_F16 && dtype != LF_BF16)
@@ -810,8 +841,7 @@ lf_status lf_set_inputs(lf_ctx* c, const void* images, int C, int dtype, const f
   c->have_inputs = true;
   return LF_OK;
 }
-
-}  // extern "C"
+}  // namespace
 
 namespace {
 // Statistics of a run and, for host outputs, the copies back (the call then
@@ -1072,9 +1102,12 @@ lf_status lf_get_stats(lf_ctx* c, lf_stats* out) {
     }
     *ms[i] = c->events_used ? static_cast<float>(acc / c->events_used) : 0.f;
   }
+  c->stats.ms_set_inputs = c->set_inputs_calls ? static_cast<float>(c->set_inputs_ms / c->set_inputs_calls) : 0.f;
   *out = c->stats;
   c->events_used = 0;
   c->runs = 0;
+  c->set_inputs_ms = 0.0;
+  c->set_inputs_calls = 0;
   return LF_OK;
 }
 
@@ -1087,6 +1120,8 @@ void lf_destroy(lf_ctx* c) {
                   c->d_spts};
   for (void* p : bufs)
     if (p) cudaFree(p);
+  for (cudaEvent_t e : c->sup_ev)
+    if (e) cudaEventDestroy(e);
   for (auto& re : c->events)
     for (cudaEvent_t e : re.ev)
       if (e) cudaEventDestroy(e);

@@ -58,7 +58,8 @@ class Stats(ctypes.Structure):
                 ("kernels_launched", ctypes.c_int),
                 ("ms_prior", ctypes.c_float), ("ms_sweep", ctypes.c_float), ("ms_refocus", ctypes.c_float),
                 ("ms_median", ctypes.c_float), ("graph_captures", ctypes.c_int),
-                ("tuned_signatures", ctypes.c_int)]
+                ("tuned_signatures", ctypes.c_int), ("ms_support", ctypes.c_float),
+                ("ms_set_inputs", ctypes.c_float)]
 
 
 _lib = None
