@@ -483,15 +483,19 @@ def main():
     kernels_per_step = st["kernels_launched"]
 
     # ---- end to end through the public API with pinned host buffers
-    img_h = torch.empty(s.images.shape, dtype=torch.uint8, pin_memory=True).numpy()
+    img_pin = torch.empty(s.images.shape, dtype=torch.uint8, pin_memory=True)
+    img_h = img_pin.numpy()
     img_h[...] = s.images
-    seg_h = torch.empty(s.seg_prior.shape, dtype=torch.float32, pin_memory=True).numpy()
+    seg_pin = torch.empty(s.seg_prior.shape, dtype=torch.float32, pin_memory=True)
+    seg_h = seg_pin.numpy()
     seg_h[...] = s.seg_prior
     out_h = {"d_idx": torch.empty((H, W), dtype=torch.int32, pin_memory=True).numpy(),
              "d": torch.empty((H, W), dtype=torch.float32, pin_memory=True).numpy(),
              "post": torch.empty((K, H, W), dtype=torch.float32, pin_memory=True).numpy(),
              "labels": torch.empty((H, W), dtype=torch.int16, pin_memory=True).numpy().view(np.uint16),
              "refocus": torch.empty((H, W, C), dtype=torch.float32, pin_memory=True).numpy()}
+    # (a) blocking calls with host pointers: lf_set_inputs copies the inputs
+    # in, lf_run_em copies the results out and waits
     e2e_steps = max(3, min(args.steps, 20))
     for _ in range(2):
         ctx.set_inputs(img_h, seg_h, step_points)
@@ -502,9 +506,43 @@ def main():
     for _ in range(e2e_steps):
         ctx.set_inputs(img_h, seg_h, step_points)
         ctx.run(iters, out=out_h)
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_sync_s = max_over_ranks(time.perf_counter() - t0)
     h2d = img_h.nbytes + seg_h.nbytes + s.points.nbytes
     d2h = sum(v.nbytes for v in out_h.values())
+    # (b) the same per-step copies, double buffered: two contexts on two
+    # streams, so one frame's host<->device copies overlap the other's kernels
+    pipes = []
+    for _ in range(2):
+        st_i = torch.cuda.Stream()
+        c_i = lf.Context(s.baselines, s.H, s.W, s.d_min, s.d_max, s.D, params, cameras=s.cameras)
+        c_i.set_stream(st_i)
+        o_dev = lf.device_outputs(K, H, W, C)
+        pipes.append((st_i, c_i, torch.empty_like(img_pin, device=dev), torch.empty_like(seg_pin, device=dev),
+                      o_dev, {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in o_dev.items()}))
+
+    def e2e_step(i):
+        st_i, c_i, img_dev, seg_dev, o_dev, o_pin = pipes[i % 2]
+        with torch.cuda.stream(st_i):
+            img_dev.copy_(img_pin, non_blocking=True)
+            seg_dev.copy_(seg_pin, non_blocking=True)
+            c_i.set_inputs(img_dev, seg_dev, step_points)
+            c_i.run(iters, device=True, out=o_dev)
+            for k, v in o_dev.items():
+                o_pin[k].copy_(v, non_blocking=True)
+
+    e2e_pipe_steps = max(4, min(args.steps, 200))
+    for i in range(4):
+        e2e_step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(e2e_pipe_steps):
+        e2e_step(i)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    for p_ in pipes:
+        p_[1].close()
 
     if rank == 0:
         props = torch.cuda.get_device_properties(dev)
@@ -563,9 +601,14 @@ def main():
                          "peak": peak, "unit": "Gop/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {f_mhz:.0f} MHz (median sampled SM clock "
                                        f"during the timed region)", **ops_desc},
-            "e2e": {"value": whole_job_value(nominal * e2e_steps, world, e2e_s), "unit": UNIT,
-                    "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s / e2e_steps},
+            "e2e": {"value": whole_job_value(nominal * e2e_pipe_steps, world, e2e_s), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": 1e3 * e2e_s / e2e_pipe_steps,
+                    "how": "public API, pinned host inputs copied in and every output copied out each step; "
+                           "two contexts on two streams (double buffering)",
+                    "blocking_host_pointer_calls": {
+                        "value": whole_job_value(nominal * e2e_steps, world, e2e_sync_s),
+                        "ms_per_step": 1e3 * e2e_sync_s / e2e_steps}},
             "gpu_launches": kernels_per_step * args.steps,
             "clocks": clk,
         }

@@ -275,11 +275,12 @@ namespace {
 
 bool finite(float x) { return std::isfinite(x); }
 
-// Pick the sweep tile: the widest tile whose staged rows fit one TMA box
-// (256 eight-byte words per row) and whose shared memory allows at least
-// two CTAs per SM, else at least one.
+// Pick the sweep tile: the first candidate (in order of measured sweep time
+// on a 960x600 five-camera frame) whose staged rows fit one TMA box (256
+// eight-byte words per row) and whose shared memory allows at least two CTAs
+// per SM, else at least one.
 lf_status choose_tiles(lf_ctx* c) {
-  static const int cand[][2] = {{2, 128}, {1, 128}, {4, 64}, {2, 64}, {1, 64}, {2, 32}, {1, 32}};
+  static const int cand[][2] = {{4, 64}, {2, 128}, {1, 128}, {2, 64}, {1, 64}, {2, 32}, {1, 32}};
   const int forced[1][2] = {{c->force_TR, c->force_TW}};
   int dev_smem = 0;
   cudaError_t e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
