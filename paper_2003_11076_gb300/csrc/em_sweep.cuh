@@ -35,6 +35,7 @@
 #include <cstdint>
 
 #include "lf_internal.h"
+#include "prior_pixel.cuh"
 
 namespace lf {
 namespace dev {
@@ -110,7 +111,7 @@ __host__ __device__ inline size_t align_up(size_t x, size_t n) { return (x + n -
 
 // Shared-memory carve-up, identical on host (size) and device (offsets).
 struct SmemLayout {
-  size_t raw_img, raw_p, luma, feat, wtab, otab, chg, dval, rcp, pix, wcnt, bar, total;
+  size_t raw_img, raw_p, luma, feat, wtab, otab, chg, dval, rcp, mu, pix, wcnt, bar, total;
 };
 
 // Per-pixel EM state of one tile, kept in shared memory between iterations
@@ -154,6 +155,8 @@ __host__ __device__ inline SmemLayout sweep_layout(int K, const SweepArgs& a) {
   o = align_up(o + static_cast<size_t>(a.D) * 4, 16);
   L.rcp = o;
   o = align_up(o + 16 * 4, 16);
+  L.mu = o;  // fused prior: the tile's prior centres
+  o = align_up(o + static_cast<size_t>(a.TR) * a.TW * 4, 16);
   L.pix = o;
   o = align_up(o + static_cast<size_t>(a.TR) * a.TW * 14, 16);
   L.wcnt = o;
@@ -588,15 +591,16 @@ struct PixelCtx {
   Staged<TS> st;
 };
 
+// s_mu: the tile's prior centres when the prior is fused, else NULL (read mu).
 template <typename TS>
 __device__ __forceinline__ PixelCtx<TS> load_pixel(const SweepArgs& a, const TS* s_feat, int u0, int v0,
-                                                   int cam_stride, int p) {
+                                                   int cam_stride, int p, const float* s_mu = nullptr) {
   PixelCtx<TS> c;
   const int r = p / a.TW, tx = p - r * a.TW;
   c.u = u0 + tx;
   c.v = v0 + r;
   c.valid = (c.u < a.W) && (c.v < a.H);
-  c.mu = a.mu[static_cast<size_t>(min(c.v, a.H - 1)) * a.W + min(c.u, a.W - 1)];
+  c.mu = s_mu ? s_mu[p] : a.mu[static_cast<size_t>(min(c.v, a.H - 1)) * a.W + min(c.u, a.W - 1)];
   c.inside = !isnan(c.mu);
   c.st.F = s_feat + static_cast<size_t>(r) * kMaps * a.SWp;
   c.st.cam_stride = cam_stride;
@@ -687,6 +691,15 @@ __device__ __forceinline__ bool stage_tile(const SweepArgs& a, const CUtensorMap
     }
     if (tid < 16) s_rcp[tid] = tid >= 2 ? 1.f / static_cast<float>(tid) : 0.f;
   }
+  if (a.ptris) {  // fused prior, computed while the copies are in flight (one thread per tile pixel)
+    const int u = u0 + tid % a.TW, v = v0 + tid / a.TW;
+    float m = __int_as_float(0x7fc00000);
+    if (u < W && v < H) {
+      m = prior::prior_pixel(a.ptris, a.pbin_start, a.pbin_items, a.pnbx, u, v);
+      a.mu_out[static_cast<size_t>(v) * W + u] = m;
+    }
+    reinterpret_cast<float*>(smem + Ly.mu)[tid] = m;
+  }
   const bool ok = mbar_wait_bounded(bar, phase, a.timeout_ns);
   if (__syncthreads_or(!ok)) {
     if (!ok) {
@@ -771,6 +784,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
   const int cs = floor16(u0 - a.L - 1);
   const int W = a.W, H = a.H, RW = a.RW;
   const int cam_stride = a.TR * kMaps * a.SWp;
+  const float* s_mu = a.ptris ? reinterpret_cast<const float*>(smem + Ly.mu) : nullptr;
 
   // ---- 3-5. per-pixel EM.  The pixels still iterating are regrouped into
   // dense warps before every pass (exact per-pixel early exit), and in the
@@ -801,7 +815,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     }
   }
   {
-    const PixelCtx<TS> me = load_pixel(a, s_feat, u0, v0, cam_stride, tid);
+    const PixelCtx<TS> me = load_pixel(a, s_feat, u0, v0, cam_stride, tid, s_mu);
     unsigned S0 = 0;
     const bool f0 = me.valid && constant_initial_labels<K, TS>(a, me.st, &S0);
     ps.fixed0[tid] = f0;
@@ -816,7 +830,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
   if (warp * 32 < nact) {
     const bool active = tid < nact;
     const int p = ps.list[active ? tid : nact - 1];
-    const PixelCtx<TS> c = load_pixel(a, s_feat, u0, v0, cam_stride, p);
+    const PixelCtx<TS> c = load_pixel(a, s_feat, u0, v0, cam_stride, p, s_mu);
     const bool f0 = ps.fixed0[p];
     const unsigned S0 = ps.S0[p];
     const bool fast = __all_sync(0xffffffffu, f0);
@@ -844,7 +858,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     if (warp * 32 < n) {
       const bool active = tid < n;
       const int p = ps.list[active ? tid : n - 1];
-      const PixelCtx<TS> c = load_pixel(a, s_feat, u0, v0, cam_stride, p);
+      const PixelCtx<TS> c = load_pixel(a, s_feat, u0, v0, cam_stride, p, s_mu);
       const unsigned Sp = ps.S[p];
       const int jb = m_step_fixed<K, TS>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, Sp);
       Rays rays;
@@ -864,7 +878,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
 
   // posteriors and outputs, one thread per pixel
   if (my_valid) {
-    const PixelCtx<TS> me = load_pixel(a, s_feat, u0, v0, cam_stride, tid);
+    const PixelCtx<TS> me = load_pixel(a, s_feat, u0, v0, cam_stride, tid, s_mu);
     const int jb = ps.jb[tid];
     const unsigned S = ps.S[tid];
     const size_t pix = static_cast<size_t>(me.v) * W + me.u;

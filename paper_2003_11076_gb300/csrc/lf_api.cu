@@ -931,9 +931,14 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
     return cudaEventRecord(re->ev[i], c->stream);
   };
   LF_CUDA(mark(0), "event");
+  // the single-frame hard EM computes the prior inside the sweep kernel, while
+  // its staging copies are in flight; every other path rasterises it first
+  const bool fused_prior = !c->calibrated && c->p.em_mode == LF_EM_HARD && !c->p.dynamic_only;
   PriorArgs pa{c->H, c->W, c->nbx, c->nby, c->d_tris, c->d_bins, c->d_bins + (c->nbx * c->nby + 1), c->d_mu};
-  LF_CUDA(launch_prior_raster(pa, c->stream), "prior_raster launch");
-  ++launched;
+  if (!fused_prior) {
+    LF_CUDA(launch_prior_raster(pa, c->stream), "prior_raster launch");
+    ++launched;
+  }
   LF_CUDA(mark(1), "event");
   if (c->calibrated) {  // Eq. 1 with per-camera homographies: maps in HBM, gathered by the sweep
     const size_t KHW = HW * c->K;
@@ -1000,6 +1005,13 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
   }
   a.d_idx = didx; a.d_out = dout; a.labels = lab; a.post = post;
   a.counter = c->d_counter; a.status = c->d_status; a.timeout_ns = kTimeoutNs;
+  if (fused_prior) {
+    a.ptris = pa.tris;
+    a.pbin_start = pa.bin_start;
+    a.pbin_items = pa.bin_items;
+    a.pnbx = pa.nbx;
+    a.mu_out = c->d_mu;
+  }
   if (a.dyn_only) {  // Sec. III-F: sweep only the tiles with dynamic reference pixels
     const int tiles = ((c->W + c->TW - 1) / c->TW) * ((c->H + c->TR - 1) / c->TR);
     if ((s = grow(&c->d_tiles, &c->tiles_cap, static_cast<size_t>(tiles) + 1, "tile list")) != LF_OK) return s;

@@ -54,6 +54,14 @@ struct SweepArgs {
   const unsigned* chg;             // [D] bit k: otab[j][k] != otab[j-1][k] (j = 0: all)
   const float* dval;               // [D] d_j
   const float* mu;                 // [H][W] prior centre, NaN outside
+  // fused prior (single-frame hard EM): non-null ptris means the sweep kernel
+  // computes the prior centre of its own pixels while its TMA copies are in
+  // flight (and writes it to mu_out) instead of reading mu
+  const PriorTri* ptris;
+  const int* pbin_start;
+  const int* pbin_items;
+  int pnbx;
+  float* mu_out;
   int omin[kMaxCams], omax[kMaxCams];  // per camera: min / max over j of otab[j][k]
   int32_t* d_idx;                  // [H][W]
   float* d_out;                    // [H][W] or null
