@@ -593,6 +593,8 @@ def main():
                        "kernel_ms": {"prior_raster": st["ms_prior"], "em_sweep": st["ms_sweep"],
                                      "refocus": st["ms_refocus"]},
                        "l2": "flushed between steps (256 MB write outside the per-step events)",
+                       "fused": "prior raster and refocus inside the sweep kernel" if st["kernels_launched"] == 1
+                                else "separate prior / refocus kernels",
                        "tile": [st["tile_rows"], st["tile_cols"]],
                        "host_ms_set_inputs": st["ms_set_inputs"],
                        **({"support_ms": st["ms_support"]} if args.detect_support else {})},

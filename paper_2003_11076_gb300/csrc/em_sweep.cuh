@@ -896,6 +896,44 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
 #pragma unroll
       for (int k = 0; k < K; ++k) a.post[k * HW + pix] = post[k];
     }
+    if (a.refocus_out) {  // Eq. 2 from the staged raw rows (they hold every tap of every candidate)
+      const uint8_t* s_img = smem + Ly.raw_img;
+      const size_t LR = static_cast<size_t>(a.TR) + 2;
+      const int row = me.v - v0 + 1;  // staged rows start one above the tile
+      const float scale = a.dtype == 0 ? (1.f / 255.f) : 1.f;
+      float* out = a.refocus_out + pix * a.C;
+      auto px = [&](int k, int x, int c) {
+        const uint8_t* p = s_img + ((k * LR + row) * RW + (x - cs)) * a.bpp;
+        if (a.dtype == 0) return static_cast<float>(p[c]);
+        if (a.dtype == 1) return reinterpret_cast<const float*>(p)[c];
+        if (a.dtype == 2) return __half2float(reinterpret_cast<const __half*>(p)[c]);
+        return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(p)[c]);
+      };
+      if (S == 0u) {
+        for (int c = 0; c < a.C; ++c) out[c] = px(a.ref, me.u, c) * scale;
+      } else {
+        float acc[3] = {0.f, 0.f, 0.f};
+        int n = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          if (!(S >> k & 1u)) continue;
+          ++n;
+          const int o = s_o[jb * a.KP + k];
+          const float w = s_w[jb * a.KP + k];
+          const int x0 = min(max(me.u + o, 0), W - 1), x1 = min(max(me.u + o + 1, 0), W - 1);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            if (c >= a.C) break;
+            const float g0 = px(k, x0, c), g1 = px(k, x1, c);
+            acc[c] += fmaf(w, g1 - g0, g0) * scale;
+          }
+        }
+        const float inv = 1.f / static_cast<float>(n);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (c < a.C) out[c] = acc[c] * inv;
+      }
+    }
   }
   if (tid == 0) atomicAdd(a.counter, executed);
   __syncthreads();

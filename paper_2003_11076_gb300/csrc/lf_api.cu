@@ -1005,12 +1005,13 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
   }
   a.d_idx = didx; a.d_out = dout; a.labels = lab; a.post = post;
   a.counter = c->d_counter; a.status = c->d_status; a.timeout_ns = kTimeoutNs;
-  if (fused_prior) {
+  if (fused_prior) {  // and the refocus: the sweep writes Eq. 2 from the rows it staged
     a.ptris = pa.tris;
     a.pbin_start = pa.bin_start;
     a.pbin_items = pa.bin_items;
     a.pnbx = pa.nbx;
     a.mu_out = c->d_mu;
+    a.refocus_out = refo_stage;
   }
   if (a.dyn_only) {  // Sec. III-F: sweep only the tiles with dynamic reference pixels
     const int tiles = ((c->W + c->TW - 1) / c->TW) * ((c->H + c->TR - 1) / c->TR);
@@ -1029,10 +1030,12 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
   ++launched;
   LF_CUDA(mark(2), "event");
   if (refo) {
-    RefocusArgs r{c->H, c->W, c->C, c->K, c->ref, c->dtype, c->KP, c->img_pitch, c->img, c->d_wtab, c->d_otab,
-                  didx, lab, refo_stage};
-    LF_CUDA(launch_refocus(r, c->stream), "refocus launch");
-    ++launched;
+    if (!fused_prior) {
+      RefocusArgs r{c->H, c->W, c->C, c->K, c->ref, c->dtype, c->KP, c->img_pitch, c->img, c->d_wtab, c->d_otab,
+                    didx, lab, refo_stage};
+      LF_CUDA(launch_refocus(r, c->stream), "refocus launch");
+      ++launched;
+    }
     LF_CUDA(mark(3), "event");
     if (c->p.median) {
       LF_CUDA(launch_median3(refo_stage, refo, c->H, c->W, c->C, c->stream), "median launch");

@@ -62,6 +62,9 @@ struct SweepArgs {
   const int* pbin_items;
   int pnbx;
   float* mu_out;
+  // fused refocus (same mode): non-null means the sweep kernel also writes
+  // Eq. 2 for its pixels from the raw rows it staged, [H][W][C] float32
+  float* refocus_out;
   int omin[kMaxCams], omax[kMaxCams];  // per camera: min / max over j of otab[j][k]
   int32_t* d_idx;                  // [H][W]
   float* d_out;                    // [H][W] or null
