@@ -593,8 +593,10 @@ def main():
                        "kernel_ms": {"prior_raster": st["ms_prior"], "em_sweep": st["ms_sweep"],
                                      "refocus": st["ms_refocus"]},
                        "l2": "flushed between steps (256 MB write outside the per-step events)",
-                       "fused": "prior raster and refocus inside the sweep kernel" if st["kernels_launched"] == 1
-                                else "separate prior / refocus kernels",
+                       "fused": "prior raster and refocus inside the sweep kernel (kernel_ms.em_sweep covers "
+                                "them)" if mode == 0 and not args.calibrated and not args.dynamic_only
+                                else "separate prior / refocus kernels" if mode != 0 or args.calibrated
+                                else "prior raster in the tile classifier, refocus in the sweep",
                        "tile": [st["tile_rows"], st["tile_cols"]],
                        "host_ms_set_inputs": st["ms_set_inputs"],
                        **({"support_ms": st["ms_support"]} if args.detect_support else {})},

@@ -283,11 +283,12 @@ lf_status lf_get_support_points(const lf_ctx *ctx, float *points, int max_points
  * = the reference image; every other pixel gets exactly the full-mode result.
  * Tiles without such a pixel are filled by a classification kernel and never
  * staged.
- * The hard EM on a rectified array outside dynamic_only runs as one kernel:
- * the sweep computes the prior of its pixels while its staging copies are in
- * flight and the refocus from the raw rows it staged (lf_stats: ms_prior and
- * ms_refocus ~ 0, ms_sweep includes them); the other modes rasterise the
- * prior and refocus in kernels of their own.
+ * The hard EM on a rectified array runs as one kernel: the sweep computes
+ * the prior of its pixels while its staging copies are in flight and the
+ * refocus from the raw rows it staged (lf_stats: ms_prior and ms_refocus ~ 0,
+ * ms_sweep includes them); in dynamic_only mode the tile classifier
+ * rasterises the prior and fills the static tiles before the sweep.  The
+ * other modes run prior, sweep and refocus kernels in order.
  * outputs_on_device: 1 = device pointers (the call returns once the work is
  * enqueued; lf_synchronize waits and reports device errors); 0 = host pointers
  * (the call waits for the results).

@@ -523,13 +523,22 @@ __device__ __forceinline__ void enumerate(const Rays& r, const float* s_rcp, flo
   }
 }
 
+// Element c of the pixel at p (an image of dtype a.dtype), unscaled.
+__device__ __forceinline__ float pixel_element(const uint8_t* p, int c, int dtype) {
+  if (dtype == 0) return static_cast<float>(p[c]);
+  if (dtype == 1) return reinterpret_cast<const float*>(p)[c];
+  if (dtype == 2) return __half2float(reinterpret_cast<const __half*>(p)[c]);
+  return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(p)[c]);
+}
+
 // Outputs of a reference pixel that the dynamic-only mode does not
-// reconstruct: disparity from the prior (nearest candidate, lower on a tie;
-// -1 / NaN outside the triangulation), no static ray, no posteriors (NaN).
+// reconstruct: disparity from the prior centre mu (nearest candidate, lower
+// on a tie; -1 / NaN outside the triangulation), no static ray, no
+// posteriors (NaN).  The refocused value (the reference image) is written by
+// the caller when the refocus is fused.
 template <int K>
-__device__ __forceinline__ void write_static_pixel(const SweepArgs& a, int u, int v) {
+__device__ __forceinline__ void write_static_pixel(const SweepArgs& a, int u, int v, float mu) {
   const size_t pix = static_cast<size_t>(v) * a.W + u;
-  const float mu = a.mu[pix];
   int j = -1;
   if (!isnan(mu)) {
     j = 0;
@@ -561,15 +570,29 @@ __global__ void tile_classify_kernel(const SweepArgs a, const float* seg_prior, 
   const int u = u0 + threadIdx.x % a.TW, v = v0 + threadIdx.x / a.TW;
   const bool valid = u < a.W && v < a.H;
   bool dyn = false;
+  float mu = __int_as_float(0x7fc00000);
   if (valid) {
     const float* row = reinterpret_cast<const float*>(reinterpret_cast<const uint8_t*>(seg_prior) +
                                                       (static_cast<size_t>(a.ref) * a.H + v) * p_pitch);
     dyn = row[u] >= a.seg_threshold;
+    const size_t pix = static_cast<size_t>(v) * a.W + u;
+    if (a.ptris) {  // fused prior: this kernel rasterises it for the whole frame
+      mu = prior::prior_pixel(a.ptris, a.pbin_start, a.pbin_items, a.pnbx, u, v);
+      a.mu_out[pix] = mu;
+    } else {
+      mu = a.mu[pix];
+    }
   }
   if (__syncthreads_or(dyn)) {
     if (threadIdx.x == 0) tile_list[atomicAdd(n_tiles, 1)] = tile;
   } else if (valid) {
-    write_static_pixel<K>(a, u, v);
+    write_static_pixel<K>(a, u, v, mu);
+    if (a.refocus_out) {  // fused refocus: a pixel with no static ray keeps the reference image
+      const uint8_t* p = a.img + (static_cast<size_t>(a.ref) * a.H + v) * a.img_pitch + static_cast<size_t>(u) * a.bpp;
+      const float scale = a.dtype == 0 ? (1.f / 255.f) : 1.f;
+      for (int c = 0; c < a.C; ++c)
+        a.refocus_out[(static_cast<size_t>(v) * a.W + u) * a.C + c] = pixel_element(p, c, a.dtype) * scale;
+    }
   }
 }
 
@@ -810,7 +833,13 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     const int r = tid / a.TW, u = u0 + tid % a.TW;
     const float Pref = s_p[(static_cast<size_t>(a.ref) * a.TR + r) * RW + (u - cs)];
     if (!(Pref >= a.seg_threshold)) {
-      write_static_pixel<K>(a, u, v0 + r);
+      const size_t pix = static_cast<size_t>(v0 + r) * W + u;
+      write_static_pixel<K>(a, u, v0 + r, s_mu ? s_mu[tid] : a.mu[pix]);
+      if (a.refocus_out) {  // no static ray: the reference image, from the staged rows
+        const uint8_t* p = smem + Ly.raw_img + ((static_cast<size_t>(a.ref) * (a.TR + 2) + r + 1) * RW + (u - cs)) * a.bpp;
+        const float scale = a.dtype == 0 ? (1.f / 255.f) : 1.f;
+        for (int c = 0; c < a.C; ++c) a.refocus_out[pix * a.C + c] = pixel_element(p, c, a.dtype) * scale;
+      }
       my_valid = false;
     }
   }
@@ -903,11 +932,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
       const float scale = a.dtype == 0 ? (1.f / 255.f) : 1.f;
       float* out = a.refocus_out + pix * a.C;
       auto px = [&](int k, int x, int c) {
-        const uint8_t* p = s_img + ((k * LR + row) * RW + (x - cs)) * a.bpp;
-        if (a.dtype == 0) return static_cast<float>(p[c]);
-        if (a.dtype == 1) return reinterpret_cast<const float*>(p)[c];
-        if (a.dtype == 2) return __half2float(reinterpret_cast<const __half*>(p)[c]);
-        return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(p)[c]);
+        return pixel_element(s_img + ((k * LR + row) * RW + (x - cs)) * a.bpp, c, a.dtype);
       };
       if (S == 0u) {
         for (int c = 0; c < a.C; ++c) out[c] = px(a.ref, me.u, c) * scale;

@@ -183,7 +183,7 @@ __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorM
     const int r = tid / a.TW;
     const float Pref = s_p[(static_cast<size_t>(a.ref) * a.TR + r) * a.RW + (me.u - cs)];
     if (!(Pref >= a.seg_threshold)) {
-      write_static_pixel<K>(a, me.u, me.v);
+      write_static_pixel<K>(a, me.u, me.v, me.mu);
       run = false;
     }
   }

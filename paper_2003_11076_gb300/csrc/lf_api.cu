@@ -275,12 +275,16 @@ namespace {
 
 bool finite(float x) { return std::isfinite(x); }
 
-// Pick the sweep tile: the first candidate (in order of measured sweep time
-// on a 960x600 five-camera frame) whose staged rows fit one TMA box (256
-// eight-byte words per row) and whose shared memory allows at least two CTAs
-// per SM, else at least one.
+// Pick the sweep tile: the first candidate whose staged rows fit one TMA box
+// (256 eight-byte words per row) and whose shared memory allows at least two
+// CTAs per SM, else at least one.  With a narrow disparity halo (L + R <= 32
+// columns) 4 x 64 tiles come first (measured fastest on the 960x600
+// five-camera frame, halo 26); wider halos favour wider tiles, which stage
+// fewer redundant columns per pixel.
 lf_status choose_tiles(lf_ctx* c) {
-  static const int cand[][2] = {{4, 64}, {2, 128}, {1, 128}, {2, 64}, {1, 64}, {2, 32}, {1, 32}};
+  static const int narrow[][2] = {{4, 64}, {2, 128}, {1, 128}, {2, 64}, {1, 64}, {2, 32}, {1, 32}};
+  static const int wide[][2] = {{2, 128}, {1, 128}, {4, 64}, {2, 64}, {1, 64}, {2, 32}, {1, 32}};
+  const auto& cand = c->L + c->R <= 32 ? narrow : wide;
   const int forced[1][2] = {{c->force_TR, c->force_TW}};
   int dev_smem = 0;
   cudaError_t e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
@@ -931,11 +935,14 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
     return cudaEventRecord(re->ev[i], c->stream);
   };
   LF_CUDA(mark(0), "event");
-  // the single-frame hard EM computes the prior inside the sweep kernel, while
-  // its staging copies are in flight; every other path rasterises it first
-  const bool fused_prior = !c->calibrated && c->p.em_mode == LF_EM_HARD && !c->p.dynamic_only;
+  // The hard EM on a rectified array fuses the prior raster and the refocus
+  // into its kernels: the sweep computes its pixels' prior centres while its
+  // staging copies are in flight and writes Eq. 2 from the rows it staged (in
+  // dynamic-only mode the tile classifier rasterises the prior).  The other
+  // paths run prior, sweep and refocus kernels in order.
+  const bool fused = !c->calibrated && c->p.em_mode == LF_EM_HARD;
   PriorArgs pa{c->H, c->W, c->nbx, c->nby, c->d_tris, c->d_bins, c->d_bins + (c->nbx * c->nby + 1), c->d_mu};
-  if (!fused_prior) {
+  if (!fused) {
     LF_CUDA(launch_prior_raster(pa, c->stream), "prior_raster launch");
     ++launched;
   }
@@ -1005,19 +1012,31 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
   }
   a.d_idx = didx; a.d_out = dout; a.labels = lab; a.post = post;
   a.counter = c->d_counter; a.status = c->d_status; a.timeout_ns = kTimeoutNs;
-  if (fused_prior) {  // and the refocus: the sweep writes Eq. 2 from the rows it staged
-    a.ptris = pa.tris;
-    a.pbin_start = pa.bin_start;
-    a.pbin_items = pa.bin_items;
-    a.pnbx = pa.nbx;
-    a.mu_out = c->d_mu;
+  if (fused) {
     a.refocus_out = refo_stage;
+    a.img = c->img;
+    a.img_pitch = c->img_pitch;
+    if (!c->p.dynamic_only) {  // (in dynamic-only mode the classifier has written mu by then)
+      a.ptris = pa.tris;
+      a.pbin_start = pa.bin_start;
+      a.pbin_items = pa.bin_items;
+      a.pnbx = pa.nbx;
+      a.mu_out = c->d_mu;
+    }
   }
   if (a.dyn_only) {  // Sec. III-F: sweep only the tiles with dynamic reference pixels
     const int tiles = ((c->W + c->TW - 1) / c->TW) * ((c->H + c->TR - 1) / c->TR);
     if ((s = grow(&c->d_tiles, &c->tiles_cap, static_cast<size_t>(tiles) + 1, "tile list")) != LF_OK) return s;
     LF_CUDA(cudaMemsetAsync(c->d_tiles + tiles, 0, sizeof(int), c->stream), "memset");
-    LF_CUDA(launch_tile_classify(c->K, a, c->P, c->p_pitch, c->d_tiles, c->d_tiles + tiles, c->stream),
+    SweepArgs ca = a;  // the classifier also rasterises the prior when the refocus is fused
+    if (fused) {
+      ca.ptris = pa.tris;
+      ca.pbin_start = pa.bin_start;
+      ca.pbin_items = pa.bin_items;
+      ca.pnbx = pa.nbx;
+      ca.mu_out = c->d_mu;
+    }
+    LF_CUDA(launch_tile_classify(c->K, ca, c->P, c->p_pitch, c->d_tiles, c->d_tiles + tiles, c->stream),
             "tile_classify launch");
     ++launched;
     a.tile_list = c->d_tiles;
@@ -1030,7 +1049,7 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
   ++launched;
   LF_CUDA(mark(2), "event");
   if (refo) {
-    if (!fused_prior) {
+    if (!fused) {
       RefocusArgs r{c->H, c->W, c->C, c->K, c->ref, c->dtype, c->KP, c->img_pitch, c->img, c->d_wtab, c->d_otab,
                     didx, lab, refo_stage};
       LF_CUDA(launch_refocus(r, c->stream), "refocus launch");

@@ -8,6 +8,8 @@
 //   one persistent sweep launch per camera count present, each CTA pulling
 //   (frame, tile) items of that camera count from a device-side queue,
 //   batched refocus (and median) over (frame, row) items.
+// (Fusing the prior and refocus into the persistent sweep, as the
+// single-frame path does, measured slower on the uneven batch.)
 // All kernels read their work lists and counts from device memory, so the
 // captured graph stays valid while the batch contents change; it is captured
 // again only when its shape changes (camera counts present, shared-memory

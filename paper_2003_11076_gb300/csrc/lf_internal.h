@@ -54,9 +54,10 @@ struct SweepArgs {
   const unsigned* chg;             // [D] bit k: otab[j][k] != otab[j-1][k] (j = 0: all)
   const float* dval;               // [D] d_j
   const float* mu;                 // [H][W] prior centre, NaN outside
-  // fused prior (single-frame hard EM): non-null ptris means the sweep kernel
-  // computes the prior centre of its own pixels while its TMA copies are in
-  // flight (and writes it to mu_out) instead of reading mu
+  // fused prior (single-frame hard EM): non-null ptris means the kernel
+  // computes the prior centre of its own pixels (the sweep while its TMA
+  // copies are in flight, the dynamic-only tile classifier for the whole
+  // frame) and writes it to mu_out instead of reading mu
   const PriorTri* ptris;
   const int* pbin_start;
   const int* pbin_items;
@@ -64,7 +65,10 @@ struct SweepArgs {
   float* mu_out;
   // fused refocus (same mode): non-null means the sweep kernel also writes
   // Eq. 2 for its pixels from the raw rows it staged, [H][W][C] float32
+  // (the dynamic-only tile classifier reads the reference image from img)
   float* refocus_out;
+  const uint8_t* img;              // [K][H] rows of img_pitch bytes
+  size_t img_pitch;
   int omin[kMaxCams], omax[kMaxCams];  // per camera: min / max over j of otab[j][k]
   int32_t* d_idx;                  // [H][W]
   float* d_out;                    // [H][W] or null
