@@ -245,13 +245,6 @@ struct lf_ctx {
   int* d_bins = nullptr;
   size_t bins_cap = 0;
   int nbx = 0, nby = 0;
-  // page-locked staging of the prior upload, two slots: a copy from pageable
-  // memory would wait for the stream to drain and keep the host from
-  // preparing the next frame while the current one runs
-  uint8_t* h_stage[2] = {nullptr, nullptr};
-  size_t h_stage_cap[2] = {0, 0};
-  cudaEvent_t h_stage_ev[2] = {nullptr, nullptr};
-  int h_slot = 0;
   // staging for host outputs
   int32_t* o_didx = nullptr;
   float* o_d = nullptr;
@@ -841,27 +834,13 @@ lf_status set_inputs_impl(lf_ctx* c, const void* images, int C, int dtype, const
   build_prior(c, sparse_points, M);
   if ((s = grow(&c->d_tris, &c->tris_cap, std::max<size_t>(c->h_tris.size(), 1), "prior")) != LF_OK) return s;
   if ((s = grow(&c->d_bins, &c->bins_cap, c->h_bins.size(), "prior")) != LF_OK) return s;
-  {
-    const size_t tb = c->h_tris.size() * sizeof(PriorTri), bb = c->h_bins.size() * sizeof(int);
-    const int slot = c->h_slot;
-    c->h_slot ^= 1;
-    if (!c->h_stage_ev[slot]) LF_CUDA(cudaEventCreateWithFlags(&c->h_stage_ev[slot], cudaEventDisableTiming), "event");
-    LF_CUDA(cudaEventSynchronize(c->h_stage_ev[slot]), "prior staging");  // this slot's previous upload is done
-    if (c->h_stage_cap[slot] < tb + bb) {
-      if (c->h_stage[slot]) cudaFreeHost(c->h_stage[slot]);
-      c->h_stage[slot] = nullptr;
-      c->h_stage_cap[slot] = 0;
-      const size_t cap = 2 * (tb + bb) + 4096;
-      LF_CUDA(cudaMallocHost(reinterpret_cast<void**>(&c->h_stage[slot]), cap), "prior staging");
-      c->h_stage_cap[slot] = cap;
-    }
-    uint8_t* h = c->h_stage[slot];
-    if (tb) std::memcpy(h, c->h_tris.data(), tb);
-    std::memcpy(h + tb, c->h_bins.data(), bb);
-    if (tb) LF_CUDA(cudaMemcpyAsync(c->d_tris, h, tb, cudaMemcpyHostToDevice, c->stream), "prior upload");
-    LF_CUDA(cudaMemcpyAsync(c->d_bins, h + tb, bb, cudaMemcpyHostToDevice, c->stream), "prior upload");
-    LF_CUDA(cudaEventRecord(c->h_stage_ev[slot], c->stream), "event");
-  }
+  if (!c->h_tris.empty())
+    LF_CUDA(cudaMemcpyAsync(c->d_tris, c->h_tris.data(), c->h_tris.size() * sizeof(PriorTri),
+                            cudaMemcpyHostToDevice, c->stream),
+            "prior upload");
+  LF_CUDA(cudaMemcpyAsync(c->d_bins, c->h_bins.data(), c->h_bins.size() * sizeof(int), cudaMemcpyHostToDevice,
+                          c->stream),
+          "prior upload");
   if ((s = encode_maps(c)) != LF_OK) return s;
   if (!on_device) LF_CUDA(cudaStreamSynchronize(c->stream), "input copy");
   c->have_inputs = true;
@@ -1178,10 +1157,6 @@ void lf_destroy(lf_ctx* c) {
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->sup_ev)
     if (e) cudaEventDestroy(e);
-  for (int i = 0; i < 2; ++i) {
-    if (c->h_stage_ev[i]) cudaEventDestroy(c->h_stage_ev[i]);
-    if (c->h_stage[i]) cudaFreeHost(c->h_stage[i]);
-  }
   for (auto& re : c->events)
     for (cudaEvent_t e : re.ev)
       if (e) cudaEventDestroy(e);
