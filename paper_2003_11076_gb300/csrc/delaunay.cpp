@@ -116,16 +116,22 @@ class Mesh {
     }
     for (int u : cavity_) tris_[u].dead = true;
     // boundary of the cavity: edge (a -> b) of a dead triangle whose
-    // neighbour across it survives
+    // neighbour across it survives (and the slot of that neighbour which
+    // points back into the cavity)
     bedges_.clear();
     for (int u : cavity_)
       for (int i = 0; i < 3; ++i) {
         const int n = tris_[u].nb[i];
         if (n >= 0 && tris_[n].dead) continue;
-        bedges_.push_back(Edge{tris_[u].v[(i + 1) % 3], tris_[u].v[(i + 2) % 3], n});
+        int back = -1;
+        if (n >= 0)
+          for (int j = 0; j < 3; ++j)
+            if (tris_[n].nb[j] == u) back = j;
+        bedges_.push_back(Edge{tris_[u].v[(i + 1) % 3], tris_[u].v[(i + 2) % 3], n, back});
       }
     // fan the boundary to p: triangle (a, b, p), rotated so that a symbolic
-    // vertex sits in slot 2; dead slots are reused
+    // vertex sits in slot 2; dead slots are reused.  Slot of the edge
+    // (a, b): 2 for (a, b, p), 1 for (b, p, inf), 0 for (p, a, inf).
     made_.clear();
     size_t reuse = 0;
     for (const Edge& e : bedges_) {
@@ -137,16 +143,17 @@ class Mesh {
         tris_.push_back(Tri{});
       }
       Tri& T = tris_[slot];
-      if (e.a == kInf) { T.v[0] = e.b; T.v[1] = p; T.v[2] = kInf; }
-      else if (e.b == kInf) { T.v[0] = p; T.v[1] = e.a; T.v[2] = kInf; }
-      else { T.v[0] = e.a; T.v[1] = e.b; T.v[2] = p; }
+      int s_ab;
+      if (e.a == kInf) { T.v[0] = e.b; T.v[1] = p; T.v[2] = kInf; s_ab = 1; }
+      else if (e.b == kInf) { T.v[0] = p; T.v[1] = e.a; T.v[2] = kInf; s_ab = 0; }
+      else { T.v[0] = e.a; T.v[1] = e.b; T.v[2] = p; s_ab = 2; }
       T.nb[0] = T.nb[1] = T.nb[2] = -1;
       T.dead = false;
-      set_nb_across(slot, e.a, e.b, e.out);
-      if (e.out >= 0) set_nb_across(e.out, e.a, e.b, slot);
+      T.nb[s_ab] = e.out;
+      if (e.out >= 0) tris_[e.out].nb[e.back] = slot;
       made_.push_back(slot);
     }
-    link_fan(p);
+    link_fan();
     last_ = made_.empty() ? last_ : made_.back();
     return true;
   }
@@ -167,7 +174,7 @@ class Mesh {
 
  private:
   struct Edge {
-    int a, b, out;
+    int a, b, out, back;  // back: the slot of `out` across this edge
   };
 
   const double* P_;
@@ -198,14 +205,6 @@ class Mesh {
     return -1;
   }
 
-  // in triangle t, the neighbour across its edge with endpoints {a, b}
-  void set_nb_across(int t, int a, int b, int n) {
-    Tri& T = tris_[t];
-    int i = edge_slot(T, a, b);
-    if (i < 0) i = edge_slot(T, b, a);
-    if (i >= 0) T.nb[i] = n;
-  }
-
   void link_all() {
     for (size_t t = 0; t < tris_.size(); ++t)
       for (int i = 0; i < 3; ++i) {
@@ -218,15 +217,19 @@ class Mesh {
   }
 
   // The new triangle made from boundary edge (a_i -> b_i) meets, across its
-  // edge (b_i, p), the new triangle whose boundary edge starts at b_i.
-  void link_fan(int p) {
+  // edge (b_i, p), the new triangle whose boundary edge starts at b_i, across
+  // that one's edge (p, a_j).  Slots of (b, p): 0 for (a, b, p), 2 for
+  // (b, p, inf), 1 for (p, a, inf); of (p, a): 1, 0 and 2.
+  void link_fan() {
     const size_t m = made_.size();
+    auto slot_bp = [&](const Edge& e) { return e.a == kInf ? 2 : (e.b == kInf ? 1 : 0); };
+    auto slot_pa = [&](const Edge& e) { return e.a == kInf ? 0 : (e.b == kInf ? 2 : 1); };
     for (size_t i = 0; i < m; ++i) {
       const int bi = bedges_[i].b;
       for (size_t j = 0; j < m; ++j) {
         if (j == i || bedges_[j].a != bi) continue;
-        set_nb_across(made_[i], bi, p, made_[j]);
-        set_nb_across(made_[j], bi, p, made_[i]);
+        tris_[made_[i]].nb[slot_bp(bedges_[i])] = made_[j];
+        tris_[made_[j]].nb[slot_pa(bedges_[j])] = made_[i];
         break;
       }
     }
