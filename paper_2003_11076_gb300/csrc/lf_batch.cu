@@ -169,6 +169,13 @@ struct lf_batch {
   cudaGraphExec_t exec = nullptr;
   std::vector<long long> key;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // the persistent sweeps of different launch groups are captured as parallel
+  // branches (so that one group's tail overlaps the others): branch streams
+  // and the fork / join events between them
+  static constexpr int kBranches = 4;
+  cudaStream_t branch[kBranches] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kBranches] = {nullptr, nullptr, nullptr, nullptr};
   bool ran = false;
   uint64_t runs = 0, nominal = 0;
   int graph_captures = 0;
@@ -400,6 +407,11 @@ lf_status lf_batch_create(lf_batch** out, const lf_params* p, int autotune) {
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
   for (cudaEvent_t& ev : b->ev)
     if (e == cudaSuccess) e = cudaEventCreate(&ev);
+  for (int i = 0; i < lf_batch::kBranches; ++i) {
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_counts), sizeof(int) * (2 * kGroups + 1));
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_heads), sizeof(unsigned) * kGroups);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_counter), sizeof(unsigned long long));
@@ -726,11 +738,24 @@ lf_status lf_batch_run(lf_batch* b) {
     chk(cudaMemsetAsync(b->d_heads, 0, sizeof(unsigned) * kGroups, c));
     chk(cudaMemsetAsync(b->d_fcount, 0, sizeof(unsigned long long) * b->frames_cap, c));
     chk(cudaEventRecordWithFlags(b->ev[1], c, cudaEventRecordExternal));
+    chk(cudaEventRecord(b->fork, c));
+    bool used[lf_batch::kBranches] = {false, false, false, false};
+    int nb = 0;
     for (int g = 0; g < kGroups; ++g) {
       if (!smem[g]) continue;
+      const int br = nb++ % lf_batch::kBranches;
+      if (!used[br]) {
+        chk(cudaStreamWaitEvent(b->branch[br], b->fork, 0));
+        used[br] = true;
+      }
       chk(launch_em_sweep_persistent(g / kThreadClasses + 1, b->p.precision, b->d_frames, b->d_items,
                                      b->d_counts + kGroups + 1 + g, b->d_counts + g, b->d_heads + g, smem[g],
-                                     grid[g], kThreadsOf[g % kThreadClasses], c));
+                                     grid[g], kThreadsOf[g % kThreadClasses], b->branch[br]));
+    }
+    for (int br = 0; br < lf_batch::kBranches; ++br) {
+      if (!used[br]) continue;
+      chk(cudaEventRecord(b->join[br], b->branch[br]));
+      chk(cudaStreamWaitEvent(c, b->join[br], 0));
     }
     chk(cudaEventRecordWithFlags(b->ev[2], c, cudaEventRecordExternal));
     chk(launch_refocus_batched(b->d_refocus, b->d_rows, b->d_counts + kGroups, rgrid, c));
@@ -805,6 +830,11 @@ void lf_batch_destroy(lf_batch* b) {
   for (cudaEvent_t e : b->ev)
     if (e) cudaEventDestroy(e);
   if (b->capture) cudaStreamDestroy(b->capture);
+  for (int i = 0; i < lf_batch::kBranches; ++i) {
+    if (b->branch[i]) cudaStreamDestroy(b->branch[i]);
+    if (b->join[i]) cudaEventDestroy(b->join[i]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   delete b;
 }
 
