@@ -44,21 +44,21 @@ def params_pair(**kw):
     return gp, op
 
 
-def check_parity(g, o, rows=None, what=""):
+def check_parity(g, o, rows=None, what="", d_frac=D_FRAC):
     sl = slice(None) if rows is None else rows
     gd, od = g["d_idx"][sl], o["d_idx"][sl]
     exc = O.excused({k: (v[:, sl] if k in ("m_margin", "e_margin", "J_t") else v[sl])
                      for k, v in o.items() if k in ("m_margin", "e_margin", "J_t", "init_margin")})
     same = gd == od
     frac = same.mean()
-    assert frac >= D_FRAC, f"{what}: disparity agreement {frac:.5f}"
+    assert frac >= d_frac, f"{what}: disparity agreement {frac:.5f}"
     bad = ~same & ~exc
     assert not bad.any(), f"{what}: {bad.sum()} non-excused disparity mismatches at {np.argwhere(bad)[:5]}"
     gl, ol = g["labels"][sl].astype(np.int64), o["labels"][sl].astype(np.int64)
     agree = same & (gl == ol)
     badl = ~agree & ~exc
     assert not badl.any(), f"{what}: {badl.sum()} non-excused label mismatches"
-    assert agree.mean() >= D_FRAC - 0.002
+    assert agree.mean() >= d_frac - 0.002
     if "post" in g:
         err = np.abs(g["post"][:, sl] - o["post"][:, sl])[:, agree]
         assert err.size == 0 or err.max() <= POST_TOL, f"{what}: posterior err {err.max()}"
@@ -243,3 +243,58 @@ def test_street_rgb_full_size_sampled_rows():
         check_parity(g, o, rows=slice(r0, r1), what=f"street rows {r0}-{r1}")
     post = g["post"]
     assert np.all((post >= 0) & (post <= 1))
+
+
+def test_without_support_points_the_prior_is_uniform():
+    """No points, two points and collinear points: no triangulation, the
+    prior is uniform everywhere (NaN map), and the EM still matches."""
+    base = scenes.small_gray(4)
+    for pts in (np.zeros((0, 3), np.float32), base.points[:2],
+                np.array([[5, 5, 4], [10, 10, 4], [20, 20, 4], [30, 30, 4]], np.float32)):
+        s = scenes.small_gray(4)
+        s.points = np.ascontiguousarray(pts, np.float32)
+        g, o = run_both(s)
+        assert np.all(np.isnan(g["mu"]))
+        assert not o["inside"].any()
+        check_parity(g, o, what=f"{len(pts)} support points")
+
+
+def test_negative_disparity_range():
+    """Candidates on both sides of zero (d from -8 to 8): the warp runs in
+    both directions for every camera."""
+    s = scenes.small_gray(5, D=33)
+    s.d_min, s.d_max = -8.0, 8.0
+    g, o = run_both(s)
+    check_parity(g, o, what="d in [-8, 8]")
+
+
+def test_maximum_candidate_count():
+    """D = 1024, the largest the library accepts (tables of 1024 x K in
+    shared memory: one CTA per SM).  Candidates 0.03 apart put far more
+    pixels within float32 rounding of an arg-max tie than a 1-unit grid does,
+    so the agreement floor is 99 % here; every mismatch must still be an
+    excused near-tie."""
+    s = scenes.small_gray(6, H=24, W=40, D=1024, iters=3, M=12)
+    s.d_min, s.d_max = 0.0, 31.0
+    g, o = run_both(s)
+    check_parity(g, o, what="D = 1024", d_frac=0.99)
+
+
+def test_wide_baselines_wide_halo():
+    """Baselines up to +-1 with D = 48 need a 48-column halo on each side:
+    the tile choice falls back to wide tiles."""
+    s = scenes.small_gray(7, H=40, W=160, baselines=[-1.0, -0.5, 0.0, 0.5, 1.0], D=48, iters=4)
+    g, o = run_both(s)
+    assert g["stats"]["halo_left"] >= 40 and g["stats"]["halo_right"] >= 40
+    check_parity(g, o, what="halo 48")
+
+
+def test_large_frame_sampled_rows():
+    """A 1920 x 1088 RGB frame (D = 96); the oracle checks two bands."""
+    s = scenes.street_rgb(4, H=1088, W=1920, D=96, iters=6, M=400)
+    lf = _lf()
+    gp, op = params_pair()
+    g = lf.run_scene(s, params=gp)
+    for rows in ((0, 4), (600, 606)):
+        o = O.run_scene(s, params=op, rows=rows)
+        check_parity(g, o, rows=slice(*rows), what=f"1920x1088 rows {rows}")
