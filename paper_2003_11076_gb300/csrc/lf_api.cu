@@ -653,7 +653,9 @@ lf_status detect_support(lf_ctx* c) {
     a.delta_c[si] = (D >= 2 && step > 0.0 && bmax > 0.0) ? static_cast<int>(std::ceil(1.0 / (bmax * step))) : 0;
   }
   const size_t HWK = static_cast<size_t>(H) * W * K;
-  const size_t n_int = off.size() + static_cast<size_t>(a.n_src) * ncell + 5 * static_cast<size_t>(ncell) + 1;
+  const size_t n_chunks = (static_cast<size_t>(ncell) + 1023) / 1024;
+  const size_t n_int =
+      off.size() + static_cast<size_t>(a.n_src) * ncell + 5 * static_cast<size_t>(ncell) + 1 + n_chunks;
   lf_status s;
   if ((s = grow(&c->d_sgrad, &c->sgrad_cap, 2 * HWK, "support buffers")) != LF_OK) return s;
   if ((s = grow(&c->d_sint, &c->sint_cap, n_int, "support buffers")) != LF_OK) return s;
@@ -670,6 +672,7 @@ lf_status detect_support(lf_ctx* c) {
   a.cell_j = ip; ip += ncell;
   a.cell_src = ip; ip += ncell;
   a.n_points = ip;
+  a.chunk_count = ip + 1;
   a.pre_u = c->d_sdbl;
   a.pre_v = c->d_sdbl + ncell;
   a.cell_u = c->d_sdbl + 2 * ncell;

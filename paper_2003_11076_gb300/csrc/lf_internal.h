@@ -155,6 +155,7 @@ struct SupportArgs {
   float* points;                   // [max_points][3]
   int max_points;
   int* n_points;
+  int* chunk_count;                // [ceil(ny*nx / 1024)] kept cells per chunk
 };
 
 struct MedianArgs {

@@ -20,7 +20,9 @@
 //                           raster order wins through atomicMin)
 //   support_fill_kernel     the claimants that won write their cell
 //   support_check_kernel    neighbourhood consistency
-//   support_compact_kernel  the surviving points in cell raster order
+//   support_count_kernel /  the surviving points in cell raster order (per
+//   support_compact_kernel  1024-cell chunk: count, then write after the
+//                           earlier chunks' points)
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -237,41 +239,44 @@ __global__ void support_check_kernel(const SupportArgs a) {
   a.cell_v[cell] = keep ? a.pre_v[cell] : 0.0;
 }
 
-// One CTA: the kept points in cell raster order as float (u, v, d) triples.
+// The kept points in cell raster order as float (u, v, d) triples: every
+// CTA counts the kept cells of its chunk of 1024 cells, then writes its
+// points after the points of all earlier chunks.
+__global__ void __launch_bounds__(1024) support_count_kernel(const SupportArgs a) {
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = __syncthreads_count(cell < a.nx * a.ny && a.cell_j[cell] >= 0);
+  if (threadIdx.x == 0) a.chunk_count[blockIdx.x] = n;
+}
+
 __global__ void __launch_bounds__(1024) support_compact_kernel(const SupportArgs a) {
   __shared__ int s_warp[32];
   __shared__ int s_base;
   const int ncell = a.nx * a.ny;
-  if (threadIdx.x == 0) s_base = 0;
-  __syncthreads();
-  for (int start = 0; start < ncell; start += blockDim.x) {
-    const int cell = start + threadIdx.x;
-    const bool has = cell < ncell && a.cell_j[cell] >= 0;
-    const unsigned ballot = __ballot_sync(0xffffffffu, has);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s_warp[warp] = __popc(ballot);
-    __syncthreads();
-    int before = 0, total = 0;
-    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) {
-      before += w < warp ? s_warp[w] : 0;
-      total += s_warp[w];
-    }
-    const int rank = s_base + before + __popc(ballot & ((1u << lane) - 1u));
-    if (has && rank < a.max_points) {
-      // a fixed sub-pixel offset per cell (at most 0.01 px) keeps grid points
-      // off common circles, so that their Delaunay triangulation is unique
-      const int ci = cell % a.nx, cj = cell / a.nx;
-      const double ju = __ddiv_rn(__dmul_rn(0.01, static_cast<double>((7 * ci + 13 * cj) % 17 + 1)), 18.0);
-      const double jv = __ddiv_rn(__dmul_rn(0.01, static_cast<double>((11 * ci + 5 * cj) % 19 + 1)), 20.0);
-      a.points[3 * rank] = static_cast<float>(__dadd_rn(a.cell_u[cell], ju));
-      a.points[3 * rank + 1] = static_cast<float>(__dadd_rn(a.cell_v[cell], jv));
-      a.points[3 * rank + 2] = static_cast<float>(cand_d(a, a.cell_j[cell]));
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) s_base += total;
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    int base = 0;
+    for (int b = 0; b < static_cast<int>(blockIdx.x); ++b) base += a.chunk_count[b];
+    s_base = base;
+    if (blockIdx.x == gridDim.x - 1) *a.n_points = base + a.chunk_count[blockIdx.x];
   }
-  if (threadIdx.x == 0) *a.n_points = s_base;
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool has = cell < ncell && a.cell_j[cell] >= 0;
+  const unsigned ballot = __ballot_sync(0xffffffffu, has);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) s_warp[warp] = __popc(ballot);
+  __syncthreads();
+  int before = 0;
+  for (int w = 0; w < warp; ++w) before += s_warp[w];
+  const int rank = s_base + before + __popc(ballot & ((1u << lane) - 1u));
+  if (has && rank < a.max_points) {
+    // a fixed sub-pixel offset per cell (at most 0.01 px) keeps grid points
+    // off common circles, so that their Delaunay triangulation is unique
+    const int ci = cell % a.nx, cj = cell / a.nx;
+    const double ju = __ddiv_rn(__dmul_rn(0.01, static_cast<double>((7 * ci + 13 * cj) % 17 + 1)), 18.0);
+    const double jv = __ddiv_rn(__dmul_rn(0.01, static_cast<double>((11 * ci + 5 * cj) % 19 + 1)), 20.0);
+    a.points[3 * rank] = static_cast<float>(__dadd_rn(a.cell_u[cell], ju));
+    a.points[3 * rank + 1] = static_cast<float>(__dadd_rn(a.cell_v[cell], jv));
+    a.points[3 * rank + 2] = static_cast<float>(cand_d(a, a.cell_j[cell]));
+  }
 }
 
 }  // namespace
@@ -291,7 +296,10 @@ cudaError_t launch_support(const SupportArgs& a, cudaStream_t s) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   support_check_kernel<<<(ncell + 127) / 128, 128, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  support_compact_kernel<<<1, 1024, 0, s>>>(a);
+  const int chunks = (ncell + 1023) / 1024;
+  support_count_kernel<<<chunks, 1024, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  support_compact_kernel<<<chunks, 1024, 0, s>>>(a);
   return cudaGetLastError();
 }
 
