@@ -309,7 +309,9 @@ lf_status lf_synchronize(lf_ctx *ctx);
 lf_status lf_get_prior(lf_ctx *ctx, float *mu, int on_device);
 
 /* Sweep tile shape: tile_rows x tile_cols reference pixels per CTA (one
- * thread each; tile_cols a multiple of 32, rows * cols <= 256).  0, 0 restores
+ * thread each; tile_cols a multiple of 32, rows * cols <= 256 up to eight
+ * cameras, <= 128 from nine, where the sweep kernel is compiled for three
+ * 128-thread CTAs per SM).  0, 0 restores
  * the library's choice.  LF_EINVAL if the shape does not fit the staging
  * limits of the current inputs.  The batch autotuner uses this to time
  * candidate shapes. */

@@ -656,12 +656,21 @@ __device__ __forceinline__ int compact(bool pred, int16_t* list, int base, int* 
 }
 
 // ---------------------------------------------------------------- kernel
-// Minimum resident 256-thread CTAs per SM requested from the register
-// allocator: two (at most 128 registers) up to eight cameras; above that the
-// register taps and the wider E-step need more than 128 registers without
-// spilling, so one.
+// Launch shapes the sweep kernels are compiled for (minimum resident CTAs
+// per SM requested from the register allocator).  Up to eight cameras: CTAs
+// of at most 256 threads, two per SM (at most 128 registers).  From nine
+// cameras the register taps and the wider E-step need more than 128
+// registers: the single-frame kernel takes CTAs of at most 128 threads,
+// three per SM (at most 168 registers, no spills) up to eleven cameras and
+// two for twelve; the persistent kernel keeps 256-thread CTAs, one per SM,
+// because its wide-halo frames are bound by shared memory, where a 128-thread
+// CTA would leave half the warps.
 template <int K>
 constexpr int sweep_min_blocks() {
+  return K <= 8 ? 2 : K <= 11 ? 3 : 2;
+}
+template <int K>
+constexpr int persistent_min_blocks() {
   return K <= 8 ? 2 : 1;
 }
 
@@ -967,7 +976,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
 
 // One CTA per tile of one frame.
 template <int K, typename TS>
-__global__ void __launch_bounds__(256, sweep_min_blocks<K>()) em_sweep_kernel(const __grid_constant__ CUtensorMap img_map,
+__global__ void __launch_bounds__(sweep_max_threads(K), sweep_min_blocks<K>()) em_sweep_kernel(const __grid_constant__ CUtensorMap img_map,
                                                        const __grid_constant__ CUtensorMap p_map,
                                                        const SweepArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
@@ -996,7 +1005,7 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<K>()) em_sweep_kernel(co
 // adjacent, so a CTA restages the frame's tables only when the frame changes.
 // frames[] holds per-frame arguments and TMA descriptors in global memory.
 template <int K, typename TS>
-__global__ void __launch_bounds__(256, sweep_min_blocks<K>()) em_sweep_persistent(const FrameDesc* frames,
+__global__ void __launch_bounds__(256, persistent_min_blocks<K>()) em_sweep_persistent(const FrameDesc* frames,
                                                                                 const TileItem* items,
                                                                                 const int* first_item,
                                                                                 const int* n_items,
@@ -1050,6 +1059,7 @@ cudaError_t launch_em_sweep_k(const CUtensorMap& img_map, const CUtensorMap& p_m
     if (e != cudaSuccess) return e;
     configured = static_cast<int>(smem);
   }
+  if (a.TR * a.TW > sweep_max_threads(K)) return cudaErrorInvalidConfiguration;
   dim3 grid((a.W + a.TW - 1) / a.TW, (a.H + a.TR - 1) / a.TR);
   if (a.tile_list) grid = dim3(grid.x * grid.y, 1);  // one CTA per listed tile (at most all)
   em_sweep_kernel<K, TS><<<grid, a.TR * a.TW, smem, s>>>(img_map, p_map, a);

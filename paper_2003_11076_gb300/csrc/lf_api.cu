@@ -294,6 +294,7 @@ lf_status choose_tiles(lf_ctx* c) {
     const int ncand = c->force_TR > 0 ? 1 : static_cast<int>(sizeof(cand) / sizeof(cand[0]));
     for (int ci = 0; ci < ncand; ++ci) {
       const int* t = c->force_TR > 0 ? forced[0] : cand[ci];
+      if (t[0] * t[1] > sweep_max_threads(c->K)) continue;
       SweepArgs a{};
       a.TR = t[0];
       a.TW = t[1];
@@ -1098,8 +1099,9 @@ lf_status lf_set_tile(lf_ctx* c, int tile_rows, int tile_cols) {
   if (tile_rows == 0 && tile_cols == 0) {
     c->force_TR = c->force_TW = 0;
   } else {
-    if (tile_rows < 1 || tile_cols < 32 || tile_cols % 32 != 0 || tile_rows * tile_cols > 256)
-      return fail(LF_EINVAL, "tile: columns a multiple of 32, rows * columns <= 256");
+    if (tile_rows < 1 || tile_cols < 32 || tile_cols % 32 != 0 || tile_rows * tile_cols > sweep_max_threads(c->K))
+      return fail(LF_EINVAL, c->K <= 8 ? "tile: columns a multiple of 32, rows * columns <= 256"
+                                       : "tile: columns a multiple of 32, rows * columns <= 128 from nine cameras");
     c->force_TR = tile_rows;
     c->force_TW = tile_cols;
   }

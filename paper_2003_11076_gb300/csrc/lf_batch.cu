@@ -505,7 +505,9 @@ lf_status lf_batch_run(lf_batch* b) {
   if (b->autotune) {  // time the candidate tiles of signatures not seen before
     std::map<TileKey, int> done;
     for (Frame& f : b->frames) {
-      if (!f.untuned) continue;
+      // from nine cameras the single-frame kernel the tuner times takes no
+      // 256-thread shapes: those frames keep the first shape that fits
+      if (!f.untuned || kTiles[0][0] * kTiles[0][1] > sweep_max_threads(f.K)) continue;
       auto it = done.find(f.key);
       if (it == done.end()) {
         const int t = tune_frame(f, b->p, b->stream);

@@ -176,6 +176,10 @@ struct TileItem {
 
 // Shared-memory bytes of the sweep kernel for a tile configuration.
 size_t sweep_smem_bytes(int K, const SweepArgs& a);
+// Largest CTA (tile rows x columns) the single-frame sweep kernel for K
+// cameras is compiled for (its launcher rejects larger ones); the persistent
+// kernel of uneven batches takes up to 256 threads at every K.
+constexpr int sweep_max_threads(int K) { return K <= 8 ? 256 : 128; }
 
 cudaError_t launch_prior_raster(const PriorArgs& a, cudaStream_t s);
 // Dynamic-only mode: list the tiles holding a pixel with P_ref >= threshold

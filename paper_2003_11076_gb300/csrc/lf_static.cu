@@ -176,6 +176,7 @@ extern "C" lf_status lf_run_em_static(int n_cams, const float* baselines, int H,
   static const int cand[][2] = {{2, 128}, {1, 128}, {4, 64}, {2, 64}, {1, 64}, {2, 32}, {1, 32}};
   bool found = false;
   for (auto& t : cand) {
+    if (t[0] * t[1] > sweep_max_threads(n_cams)) continue;
     a.TR = t[0];
     a.TW = t[1];
     a.L = -omin;

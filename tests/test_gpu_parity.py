@@ -298,3 +298,36 @@ def test_large_frame_sampled_rows():
     for rows in ((0, 4), (600, 606)):
         o = O.run_scene(s, params=op, rows=rows)
         check_parity(g, o, rows=slice(*rows), what=f"1920x1088 rows {rows}")
+
+
+@pytest.mark.parametrize("baselines,allowed,rejected", [
+    ([-0.2, -0.1, 0.0, 0.1, 0.2], [(4, 64), (2, 128), (1, 256), (8, 32), (1, 128), (2, 64), (1, 32)], []),
+    ([-0.4, -0.3, -0.2, -0.1, 0.0, 0.1, 0.2, 0.3, 0.4], [(1, 128), (2, 64), (4, 32), (1, 64), (1, 32)],
+     [(2, 128), (4, 64), (1, 256)]),
+])
+def test_tile_shapes_give_identical_results(baselines, allowed, rejected):
+    """Every pixel's EM is independent of the CTA it runs in, so every tile
+    shape gives bit-identical outputs; from nine cameras the sweep kernel is
+    compiled for CTAs of at most 128 threads and larger shapes are refused."""
+    lf = _lf()
+    s = scenes.small_gray(8, H=30, W=150, baselines=baselines, D=24, iters=5, M=20)
+    outs = []
+    with lf.Context(s.baselines, s.H, s.W, s.d_min, s.d_max, s.D) as ctx:
+        ctx.set_inputs(s.images, s.seg_prior, s.points)
+        for tr, tc in allowed:
+            ctx.set_tile(tr, tc)
+            out = ctx.run(s.iters)
+            st = ctx.stats()
+            assert (st["tile_rows"], st["tile_cols"]) == (tr, tc)
+            outs.append(out)
+        for tr, tc in rejected:
+            with pytest.raises(lf.LfError) as e:
+                ctx.set_tile(tr, tc)
+            assert e.value.status == lf.LF_EINVAL
+        ctx.set_tile(0, 0)
+        outs.append(ctx.run(s.iters))
+    for o in outs[1:]:
+        for k in ("d_idx", "d", "labels", "post", "refocus"):
+            assert np.array_equal(o[k], outs[0][k], equal_nan=True), k
+    _, op = params_pair()
+    check_parity(outs[0], O.run_scene(s, params=op), what=f"tiles K={len(baselines)}")
