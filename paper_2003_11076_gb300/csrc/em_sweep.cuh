@@ -292,11 +292,15 @@ __device__ __forceinline__ int m_step(const SweepArgs& a, const Staged<TS>& st, 
 // and likewise for the log priors, so one candidate costs six fused
 // multiply-adds per ray.  The base sums over k change only at candidates
 // where some camera's tap moves; they are then summed afresh (no drift).
-template <int K, typename TS>
-__device__ __forceinline__ int m_step_fixed(const SweepArgs& a, const Staged<TS>& st, const float* s_w,
-                                            const int* s_o, const unsigned* s_chg, const float* s_d,
-                                            const float* s_rcp, float cy, float cx, float cz, float mu,
-                                            bool inside, unsigned S) {
+// Candidates j0 <= j < j1 (lowest j wins ties; *best_out = the maximum).
+// RESTART: every camera's taps are loaded at j0, so a range that starts
+// mid-sweep computes each candidate's objective exactly as the whole sweep
+// does (a tap that has not moved since its last load holds the same texels).
+template <int K, typename TS, bool RESTART>
+__device__ __forceinline__ int m_step_fixed_range(const SweepArgs& a, const Staged<TS>& st, const float* s_w,
+                                                  const int* s_o, const unsigned* s_chg, const float* s_d,
+                                                  const float* s_rcp, float cy, float cx, float cz, float mu,
+                                                  bool inside, unsigned S, int j0, int j1, float* best_out) {
   float my[K], mx[K], mz[K], sy[K], sx[K], sz[K], ml[K], sl[K], A[K], C[K], q0[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -306,9 +310,9 @@ __device__ __forceinline__ int m_step_fixed(const SweepArgs& a, const Staged<TS>
   const int SWp = st.SWp;
   const float rn = s_rcp[__popc(S)];
   float best = -INFINITY;
-  int jb = 0;
-  for (int j = 0; j < a.D; ++j) {
-    const unsigned ch = s_chg[j];
+  int jb = j0;
+  for (int j = j0; j < j1; ++j) {
+    const unsigned ch = RESTART && j == j0 ? (1u << K) - 1u : s_chg[j];
     float w[K];
     {
       const float4* w4 = reinterpret_cast<const float4*>(s_w + j * a.KP);
@@ -364,7 +368,17 @@ __device__ __forceinline__ int m_step_fixed(const SweepArgs& a, const Staged<TS>
     J = fmaf(-a.beta, var, J);
     if (J > best) { best = J; jb = j; }
   }
+  if (best_out) *best_out = best;
   return jb;
+}
+
+template <int K, typename TS>
+__device__ __forceinline__ int m_step_fixed(const SweepArgs& a, const Staged<TS>& st, const float* s_w,
+                                            const int* s_o, const unsigned* s_chg, const float* s_d,
+                                            const float* s_rcp, float cy, float cx, float cz, float mu,
+                                            bool inside, unsigned S) {
+  return m_step_fixed_range<K, TS, false>(a, st, s_w, s_o, s_chg, s_d, s_rcp, cy, cx, cz, mu, inside, S, 0, a.D,
+                                          nullptr);
 }
 
 // First-iteration labels of one pixel when they are the same for every
@@ -521,6 +535,54 @@ __device__ __forceinline__ void enumerate(const Rays& r, const float* s_rcp, flo
 #pragma unroll
     for (int i = 0; i < NH; ++i) post[L + i] = ph[i] * inv;
   }
+}
+
+// Warp-cooperative forms for a pixel that runs alone (the last pixels of a
+// tile still iterating): the 32 lanes split its candidates, then its label
+// vectors, and reduce with the same tie rules as the one-thread sweep (lowest
+// candidate, smallest mask), so the result is bit-identical.
+
+// Larger objective, or on a tie the lower index, over the warp's lanes.
+__device__ __forceinline__ void warp_argmax(float& best, unsigned& idx) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+    const unsigned oi = __shfl_xor_sync(0xffffffffu, idx, off);
+    if (ob > best || (ob == best && oi < idx)) {
+      best = ob;
+      idx = oi;
+    }
+  }
+}
+
+// Arg-max of the E-step over masks m = lane, lane + 32, ...  Each leaf's sums
+// are formed from scratch in the subset tree's order (the high cameras in
+// increasing order, then the low block from its highest camera down), so the
+// objectives equal the tree's bit for bit.
+template <int K>
+__device__ __forceinline__ void enumerate_warp(const Rays& r, const float* s_rcp, float beta, int lane,
+                                               unsigned& bmask, float& best) {
+  constexpr int L = K < 6 ? K : 6;
+  float b = -INFINITY;
+  unsigned bm = static_cast<unsigned>(lane);
+  for (unsigned m = lane; m < (1u << K); m += 32) {
+    Acc acc{0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = L; k < K; ++k)
+      if (m >> k & 1u) {
+        acc.sy += r.gy[k]; acc.sx += r.gx[k]; acc.sz += r.gz[k]; acc.q += r.qk[k]; acc.sa += r.ak[k];
+      }
+#pragma unroll
+    for (int k = L - 1; k >= 0; --k)
+      if (m >> k & 1u) {
+        acc.sy += r.gy[k]; acc.sx += r.gx[k]; acc.sz += r.gz[k]; acc.q += r.qk[k]; acc.sa += r.ak[k];
+      }
+    const float E = leaf_objective(acc, s_rcp[__popc(m)], r.base, beta);
+    if (E > b) { b = E; bm = m; }
+  }
+  warp_argmax(b, bm);
+  bmask = bm;
+  best = b;
 }
 
 // Element c of the pixel at p (an image of dtype a.dtype), unscaled.
@@ -888,12 +950,36 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     }
   }
   __syncthreads();
-  // t >= 2: only the pixels not yet at their fixed point
+  // t >= 2: only the pixels not yet at their fixed point; when no more of
+  // them are left than the CTA has warps, one warp per pixel
+  const int nwarps = blockDim.x >> 5, lane = tid & 31;
   for (int t = 2; t <= a.iters; ++t) {
     const int n = compact(my_valid && !ps.conv[tid], ps.list, 0, s_wcnt);
     if (n == 0) break;
     executed += static_cast<unsigned long long>(n);
-    if (warp * 32 < n) {
+    if (n <= nwarps) {
+      if (warp < n) {
+        const int p = ps.list[warp];
+        const PixelCtx<TS> c = load_pixel(a, s_feat, u0, v0, cam_stride, p, s_mu);
+        const unsigned Sp = ps.S[p];
+        const int per = (a.D + 31) >> 5, j0 = min(lane * per, a.D), j1 = min(j0 + per, a.D);
+        float jbest;
+        unsigned jb = static_cast<unsigned>(m_step_fixed_range<K, TS, true>(
+            a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, Sp, j0, j1, &jbest));
+        warp_argmax(jbest, jb);
+        Rays rays;
+        sample_rays<K, TS>(a, c.st, s_w, s_o, static_cast<int>(jb), c.cy, c.cx, c.cz, rays);
+        unsigned S = 0;
+        float emax = 0.f;
+        enumerate_warp<K>(rays, s_rcp, a.beta, lane, S, emax);
+        if (lane == 0) {
+          ps.jb[p] = static_cast<int16_t>(jb);
+          ps.S[p] = static_cast<uint16_t>(S);
+          ps.emax[p] = emax;
+          ps.conv[p] = a.early_exit && S == Sp;
+        }
+      }
+    } else if (warp * 32 < n) {
       const bool active = tid < n;
       const int p = ps.list[active ? tid : n - 1];
       const PixelCtx<TS> c = load_pixel(a, s_feat, u0, v0, cam_stride, p, s_mu);

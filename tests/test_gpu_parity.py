@@ -174,6 +174,27 @@ def test_early_exit_is_exact():
     assert b["stats"]["executed_ray_samples"] == b["stats"]["nominal_ray_samples"]
 
 
+@pytest.mark.parametrize("make", [
+    lambda: scenes.street_rgb(0),
+    lambda: scenes.small_gray(12, D=7, iters=8),
+    lambda: scenes.small_gray(13, H=40, W=96, D=1024, iters=6),
+    lambda: scenes.small_gray(14, baselines=[-0.4, -0.3, -0.2, -0.1, 0.0, 0.1, 0.2, 0.3, 0.4], D=40, iters=8),
+    lambda: scenes.small_gray(15, H=24, W=48, D=16, iters=6,
+                              baselines=[-0.3, -0.25, -0.2, -0.15, -0.1, -0.05, 0.0, 0.05, 0.1, 0.15, 0.2, 0.25]),
+])
+def test_early_exit_is_exact_across_shapes(make):
+    """With the early exit the last pixels of a tile still iterating run one
+    per warp (lanes split the candidates and label vectors); without it every
+    pixel runs every iteration one per thread.  Both give the same bits."""
+    lf = _lf()
+    s = make()
+    a = lf.run_scene(s, params=lf.default_params(early_exit=1))
+    b = lf.run_scene(s, params=lf.default_params(early_exit=0))
+    for k in ("d_idx", "d", "labels", "post", "refocus"):
+        assert np.array_equal(a[k], b[k]), k
+    assert a["stats"]["executed_ray_samples"] < b["stats"]["executed_ray_samples"]
+
+
 def test_device_io_equals_host_io():
     import torch
     lf = _lf()
