@@ -55,15 +55,18 @@ __device__ __forceinline__ CalibRay calib_sample(const CalibArgs& a, int k, floa
   return r;
 }
 
-// M-step over the D candidates (lowest index on ties).  INIT: labels
-// thresholded at each ray's own sample (ld - ls < log(thr / (1 - thr)) means
-// static); otherwise the fixed labels S.
+// M-step over candidates j0 <= j < j1 (lowest index on ties; *best_out = the
+// maximum).  INIT: labels thresholded at each ray's own sample (ld - ls <
+// log(thr / (1 - thr)) means static); otherwise the fixed labels S.  Every
+// candidate is evaluated from scratch, so a range computes the same
+// objectives as the whole sweep.
 template <int K, bool INIT>
 __device__ __forceinline__ int calib_m_step(const CalibArgs& a, const float (&A)[K][3], float cy, float cx,
-                                            float cz, float mu, bool inside, unsigned S) {
+                                            float cz, float mu, bool inside, unsigned S, int j0, int j1,
+                                            float* best_out) {
   float best = -INFINITY;
-  int jb = 0;
-  for (int j = 0; j < a.D; ++j) {
+  int jb = j0;
+  for (int j = j0; j < j1; ++j) {
     const float d = __ldg(a.dval + j);
     float sy = 0.f, sx = 0.f, sz = 0.f, q = 0.f, seg = 0.f;
     int n = 0;
@@ -100,6 +103,7 @@ __device__ __forceinline__ int calib_m_step(const CalibArgs& a, const float (&A)
     J = fmaf(-a.beta, var, J);
     if (J > best) { best = J; jb = j; }
   }
+  if (best_out) *best_out = best;
   return jb;
 }
 
@@ -119,88 +123,162 @@ __device__ __forceinline__ void calib_rays(const CalibArgs& a, const float (&A)[
   }
 }
 
+// One CTA per 16 x 16 block of reference pixels, one thread per pixel for
+// the first iteration; afterwards only the pixels not yet at their fixed
+// point, regrouped into dense warps before every pass (exact per-pixel early
+// exit), and one warp per pixel once few are left (lanes split the
+// candidates, then the label vectors; same tie rules, same bits).
 template <int K>
 __global__ void __launch_bounds__(256) calib_sweep_kernel(const __grid_constant__ CalibArgs a) {
   __shared__ float s_rcp[16];  // 1/n for the E-step's subset sizes (0 for n < 2: Var = 0)
-  if (threadIdx.y == 0 && threadIdx.x < 16)
-    s_rcp[threadIdx.x] = threadIdx.x >= 2 ? 1.f / static_cast<float>(threadIdx.x) : 0.f;
+  __shared__ float s_emax[256];
+  __shared__ int16_t s_jb[256], s_list[256];
+  __shared__ uint16_t s_S[256];
+  __shared__ uint8_t s_conv[256];
+  __shared__ int s_wcnt[8];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  if (tid < 16) s_rcp[tid] = tid >= 2 ? 1.f / static_cast<float>(tid) : 0.f;
   __syncthreads();
-  const int u = blockIdx.x * blockDim.x + threadIdx.x, v = blockIdx.y * blockDim.y + threadIdx.y;
-  unsigned executed = 0;
-  if (u < a.W && v < a.H) {
+  const int bu = blockIdx.x * 16, bv = blockIdx.y * 16;
+  const int u = bu + (tid & 15), v = bv + (tid >> 4);
+  bool run = u < a.W && v < a.H;
+  if (run && a.dyn_only) {  // Sec. III-F: only the reference pixels flagged dynamic
     const size_t pix = static_cast<size_t>(v) * a.W + u;
-    const float mu = a.mu[pix];
-    const bool inside = !isnan(mu);
-    bool run = true;
-    if (a.dyn_only) {  // Sec. III-F: only the reference pixels flagged dynamic
-      const float Pref = reinterpret_cast<const float*>(reinterpret_cast<const uint8_t*>(a.P) +
-                                                        (static_cast<size_t>(a.ref) * a.H + v) * a.p_pitch)[u];
-      if (!(Pref >= a.seg_threshold)) {
-        int j = -1;
-        if (inside) {  // the candidate nearest the prior centre, lower index on a tie
-          j = 0;
-          float bd = fabsf(a.dval[0] - mu);
-          for (int i = 1; i < a.D; ++i) {
-            const float dd = fabsf(a.dval[i] - mu);
-            if (dd < bd) { bd = dd; j = i; }
-          }
+    const float Pref = reinterpret_cast<const float*>(reinterpret_cast<const uint8_t*>(a.P) +
+                                                      (static_cast<size_t>(a.ref) * a.H + v) * a.p_pitch)[u];
+    if (!(Pref >= a.seg_threshold)) {
+      const float mu = a.mu[pix];
+      int j = -1;
+      if (!isnan(mu)) {  // the candidate nearest the prior centre, lower index on a tie
+        j = 0;
+        float bd = fabsf(a.dval[0] - mu);
+        for (int i = 1; i < a.D; ++i) {
+          const float dd = fabsf(a.dval[i] - mu);
+          if (dd < bd) { bd = dd; j = i; }
         }
-        const float nan = __int_as_float(0x7fc00000);
-        a.d_idx[pix] = j;
-        if (a.d_out) a.d_out[pix] = j >= 0 ? a.dval[j] : nan;
-        a.labels[pix] = 0;
-        if (a.post)
-          for (int k = 0; k < K; ++k) a.post[k * static_cast<size_t>(a.H) * a.W + pix] = nan;
-        run = false;
       }
+      const float nan = __int_as_float(0x7fc00000);
+      a.d_idx[pix] = j;
+      if (a.d_out) a.d_out[pix] = j >= 0 ? a.dval[j] : nan;
+      a.labels[pix] = 0;
+      if (a.post)
+        for (int k = 0; k < K; ++k) a.post[k * static_cast<size_t>(a.H) * a.W + pix] = nan;
+      run = false;
     }
-    if (run) {
-      float A[K][3];
+  }
+  // everything the EM of block pixel p needs, recomputed per pass
+  struct Px {
+    float A[K][3];
+    float mu, cy, cx, cz;
+    bool inside;
+  };
+  auto load = [&](int p) {
+    Px x;
+    const int pu = bu + (p & 15), pv = bv + (p >> 4);
+    const size_t pix = static_cast<size_t>(pv) * a.W + pu;
 #pragma unroll
-      for (int k = 0; k < K; ++k)
+    for (int k = 0; k < K; ++k)
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
-          A[k][r] = fmaf(a.cam[k][4 * r], static_cast<float>(u),
-                         fmaf(a.cam[k][4 * r + 1], static_cast<float>(v), a.cam[k][4 * r + 2]));
-      const float4 fr = a.fa[static_cast<size_t>(a.ref) * a.H * a.W + pix];
-      const float cy = fr.x, cx = fr.y, cz = fr.z;
-      int jb = calib_m_step<K, true>(a, A, cy, cx, cz, mu, inside, 0u);
+      for (int r = 0; r < 3; ++r)
+        x.A[k][r] = fmaf(a.cam[k][4 * r], static_cast<float>(pu),
+                         fmaf(a.cam[k][4 * r + 1], static_cast<float>(pv), a.cam[k][4 * r + 2]));
+    x.mu = a.mu[pix];
+    x.inside = !isnan(x.mu);
+    const float4 fr = a.fa[static_cast<size_t>(a.ref) * a.H * a.W + pix];
+    x.cy = fr.x; x.cx = fr.y; x.cz = fr.z;
+    return x;
+  };
+  unsigned long long executed = 0;
+  // t = 1
+  {
+    const int n = compact(run, s_list, 0, s_wcnt);
+    executed += static_cast<unsigned long long>(n);
+    if (tid < n) {
+      const int p = s_list[tid];
+      const Px x = load(p);
+      const int jb = calib_m_step<K, true>(a, x.A, x.cy, x.cx, x.cz, x.mu, x.inside, 0u, 0, a.D, nullptr);
       Rays rays;
-      calib_rays<K>(a, A, jb, cy, cx, cz, rays);
+      calib_rays<K>(a, x.A, jb, x.cy, x.cx, x.cz, rays);
       unsigned S = 0;
       float emax = 0.f;
       enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
-      executed = 1;
-      for (int t = 2; t <= a.iters; ++t) {
-        const unsigned Sp = S;
-        jb = calib_m_step<K, false>(a, A, cy, cx, cz, mu, inside, Sp);
-        ++executed;
-        calib_rays<K>(a, A, jb, cy, cx, cz, rays);
-        enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
-        if (a.early_exit && S == Sp) break;  // the next M-step would repeat this one exactly
+      s_jb[p] = static_cast<int16_t>(jb);
+      s_S[p] = static_cast<uint16_t>(S);
+      s_emax[p] = emax;
+    }
+    s_conv[tid] = 0;
+    __syncthreads();
+  }
+  for (int t = 2; t <= a.iters; ++t) {
+    const int n = compact(run && !s_conv[tid], s_list, 0, s_wcnt);
+    if (n == 0) break;
+    executed += static_cast<unsigned long long>(n);
+    if (n <= kWarpPathPixelsPerWarp * nwarps) {
+      for (int i = warp; i < n; i += nwarps) {
+        const int p = s_list[i];
+        const Px x = load(p);
+        const unsigned Sp = s_S[p];
+        const int per = (a.D + 31) >> 5, j0 = min(lane * per, a.D), j1 = min(j0 + per, a.D);
+        float jbest;
+        unsigned jb = static_cast<unsigned>(
+            calib_m_step<K, false>(a, x.A, x.cy, x.cx, x.cz, x.mu, x.inside, Sp, j0, j1, &jbest));
+        warp_argmax(jbest, jb);
+        Rays rays;
+        calib_rays<K>(a, x.A, static_cast<int>(jb), x.cy, x.cx, x.cz, rays);
+        unsigned S = 0;
+        float emax = 0.f;
+        enumerate_warp<K>(rays, s_rcp, a.beta, lane, S, emax);
+        if (lane == 0) {
+          s_jb[p] = static_cast<int16_t>(jb);
+          s_S[p] = static_cast<uint16_t>(S);
+          s_emax[p] = emax;
+          s_conv[p] = a.early_exit && S == Sp;  // the next M-step would repeat this one exactly
+        }
       }
-      a.d_idx[pix] = jb;
-      if (a.d_out) a.d_out[pix] = a.dval[jb];
-      a.labels[pix] = static_cast<uint16_t>(S);
-      if (a.post) {
-        float post[K];
-        unsigned dummy;
-        float dummyf;
-        enumerate<1, K>(rays, s_rcp, a.beta, emax, dummy, dummyf, post);
+    } else if (tid < n) {
+      const int p = s_list[tid];
+      const Px x = load(p);
+      const unsigned Sp = s_S[p];
+      const int jb = calib_m_step<K, false>(a, x.A, x.cy, x.cx, x.cz, x.mu, x.inside, Sp, 0, a.D, nullptr);
+      Rays rays;
+      calib_rays<K>(a, x.A, jb, x.cy, x.cx, x.cz, rays);
+      unsigned S = 0;
+      float emax = 0.f;
+      enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
+      s_jb[p] = static_cast<int16_t>(jb);
+      s_S[p] = static_cast<uint16_t>(S);
+      s_emax[p] = emax;
+      s_conv[p] = a.early_exit && S == Sp;
+    }
+    __syncthreads();
+  }
+  // outputs, one thread per pixel
+  if (run) {
+    const size_t pix = static_cast<size_t>(v) * a.W + u;
+    const int jb = s_jb[tid];
+    const unsigned S = s_S[tid];
+    a.d_idx[pix] = jb;
+    if (a.d_out) a.d_out[pix] = a.dval[jb];
+    a.labels[pix] = static_cast<uint16_t>(S);
+    if (a.post) {
+      const Px x = load(tid);
+      Rays rays;
+      calib_rays<K>(a, x.A, jb, x.cy, x.cx, x.cz, rays);
+      float post[K];
+      unsigned dummy;
+      float dummyf;
+      enumerate<1, K>(rays, s_rcp, a.beta, s_emax[tid], dummy, dummyf, post);
 #pragma unroll
-        for (int k = 0; k < K; ++k) a.post[k * static_cast<size_t>(a.H) * a.W + pix] = post[k];
-      }
+      for (int k = 0; k < K; ++k) a.post[k * static_cast<size_t>(a.H) * a.W + pix] = post[k];
     }
   }
-  const unsigned warp_sum = __reduce_add_sync(0xffffffffu, executed);
-  if (((threadIdx.y * blockDim.x + threadIdx.x) & 31) == 0 && warp_sum)
-    atomicAdd(a.counter, static_cast<unsigned long long>(warp_sum));
+  if (tid == 0 && executed) atomicAdd(a.counter, executed);
 }
 
 template <int K>
 cudaError_t launch_calib_sweep_k(const CalibArgs& a, cudaStream_t s) {
-  const dim3 block(16, 16), grid((a.W + 15) / 16, (a.H + 15) / 16);
-  calib_sweep_kernel<K><<<grid, block, 0, s>>>(a);
+  const dim3 grid((a.W + 15) / 16, (a.H + 15) / 16);
+  calib_sweep_kernel<K><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -542,6 +542,11 @@ __device__ __forceinline__ void enumerate(const Rays& r, const float* s_rcp, flo
 // vectors, and reduce with the same tie rules as the one-thread sweep (lowest
 // candidate, smallest mask), so the result is bit-identical.
 
+// A CTA takes the warp-per-pixel path when at most this many pixels per warp
+// are still iterating (each warp then runs its pixels one after another; at
+// four a warp's pixels take about as long as one one-thread-per-pixel pass).
+constexpr int kWarpPathPixelsPerWarp = 4;
+
 // Larger objective, or on a tie the lower index, over the warp's lanes.
 __device__ __forceinline__ void warp_argmax(float& best, unsigned& idx) {
 #pragma unroll
@@ -950,16 +955,16 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     }
   }
   __syncthreads();
-  // t >= 2: only the pixels not yet at their fixed point; when no more of
-  // them are left than the CTA has warps, one warp per pixel
+  // t >= 2: only the pixels not yet at their fixed point; when few of them
+  // are left, one warp per pixel
   const int nwarps = blockDim.x >> 5, lane = tid & 31;
   for (int t = 2; t <= a.iters; ++t) {
     const int n = compact(my_valid && !ps.conv[tid], ps.list, 0, s_wcnt);
     if (n == 0) break;
     executed += static_cast<unsigned long long>(n);
-    if (n <= nwarps) {
-      if (warp < n) {
-        const int p = ps.list[warp];
+    if (n <= kWarpPathPixelsPerWarp * nwarps) {
+      for (int i = warp; i < n; i += nwarps) {
+        const int p = ps.list[i];
         const PixelCtx<TS> c = load_pixel(a, s_feat, u0, v0, cam_stride, p, s_mu);
         const unsigned Sp = ps.S[p];
         const int per = (a.D + 31) >> 5, j0 = min(lane * per, a.D), j1 = min(j0 + per, a.D);
