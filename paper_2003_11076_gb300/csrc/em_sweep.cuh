@@ -832,10 +832,14 @@ __device__ __forceinline__ bool stage_tile(const SweepArgs& a, const CUtensorMap
   }
   __syncthreads();
   const int cam_stride = a.TR * kMaps * a.SWp;
-  for (int i = tid; i < K * a.TR * a.SW; i += nthr) {
-    const int c = i % a.SW;
-    const int r = (i / a.SW) % a.TR;
-    const int k = i / (a.SW * a.TR);
+  // element (k, r, c) of the K x TR x SW staged maps, walked with a
+  // mixed-radix counter (one step = nthr elements; no division in the loop)
+  int c = tid % a.SW, r = (tid / a.SW) % a.TR, k = tid / (a.SW * a.TR);
+  const int dc = nthr % a.SW, dr = (nthr / a.SW) % a.TR, dk = nthr / (a.SW * a.TR);
+  for (; k < K; c += dc, r += dr, k += dk) {
+    if (c >= a.SW) { c -= a.SW; ++r; }
+    if (r >= a.TR) { r -= a.TR; ++k; }
+    if (k >= K) break;
     const int Xc = min(max(u0 - a.L + c, 0), W - 1);
     const int V = min(v0 + r, H - 1);
     const int rm = max(V - 1, 0) - (v0 - 1), r0 = V - (v0 - 1), rp = min(V + 1, H - 1) - (v0 - 1);
