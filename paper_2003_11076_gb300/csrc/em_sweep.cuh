@@ -166,6 +166,11 @@ __host__ __device__ inline SmemLayout sweep_layout(int K, const SweepArgs& a) {
   return L;
 }
 
+// The soft-EM variant keeps its per-pixel state after the sweep layout.
+__host__ __device__ inline size_t soft_state_offset(int K, const SweepArgs& a) {
+  return align_up(sweep_layout(K, a).total, 16);
+}
+
 // Staged descriptor maps are float32, or float16 / bfloat16 in the reduced-
 // precision modes; all arithmetic is float32.
 __device__ __forceinline__ float ldf(const float* p) { return *p; }

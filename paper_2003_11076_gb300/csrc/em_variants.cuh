@@ -82,16 +82,18 @@ __device__ __forceinline__ void soft_posterior(const Rays& r, const float* s_rcp
   for (int i = 0; i < kNumPairs<K>; ++i) pw[i] *= inv;
 }
 
-// Soft-EM M-step: arg-max over the candidates of Q(d_j) (lowest j on ties).
+// Soft-EM M-step: arg-max of Q(d_j) over candidates j0 <= j < j1 (lowest j
+// on ties; *best_out = the maximum).  Each candidate is evaluated from
+// scratch, so a range computes the same objectives as the whole sweep.
 template <int K>
 __device__ __forceinline__ int m_step_soft(const SweepArgs& a, const Staged<float>& st, const float* s_w,
                                            const int* s_o, const float* s_d, float cy, float cx, float cz,
-                                           float mu, bool inside, const float (&pi)[K],
-                                           const float (&pw)[kNumPairs<K>]) {
+                                           float mu, bool inside, const float* pi, const float* pw, int j0,
+                                           int j1, float* best_out) {
   const int SWp = st.SWp;
   float best = -INFINITY;
-  int jb = 0;
-  for (int j = 0; j < a.D; ++j) {
+  int jb = j0;
+  for (int j = j0; j < j1; ++j) {
     float gy[K], gx[K], gz[K];
     float seg = 0.f;
 #pragma unroll
@@ -126,6 +128,7 @@ __device__ __forceinline__ int m_step_soft(const SweepArgs& a, const Staged<floa
     J = fmaf(-a.beta, pv, J);
     if (J > best) { best = J; jb = j; }
   }
+  if (best_out) *best_out = best;
   return jb;
 }
 
@@ -158,8 +161,19 @@ __device__ __forceinline__ int joint_map(const SweepArgs& a, const Staged<float>
   return jb;
 }
 
-// One tile, one thread per pixel (no compaction: a pixel stops at its own
-// fixed point and its warp waits for the others).
+// Soft-EM state of one pixel between iterations, in shared memory after the
+// sweep layout: pi[K] then the pair weights, per tile pixel.
+template <int K>
+constexpr int kSoftStateFloats = K + kNumPairs<K>;
+static_assert(kSoftStateFloats<1> == soft_state_floats(1) && kSoftStateFloats<2> == soft_state_floats(2) &&
+                  kSoftStateFloats<8> == soft_state_floats(8),
+              "device and host sizes of the soft-EM state must agree");
+
+// One tile.  Joint MAP: one thread per pixel (every pixel does the same
+// work).  Soft EM: the first iteration one thread per pixel, then only the
+// pixels not yet at their fixed point, regrouped into dense warps before
+// every pass, and one warp per pixel once few are left (lanes split the
+// candidates; same tie rule, same bits).
 template <int K, int MODE>
 __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorMap* img_map,
                                              const CUtensorMap* p_map, int tile_x, int tile_y, uint8_t* smem) {
@@ -172,10 +186,11 @@ __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorM
   const unsigned* s_chg = reinterpret_cast<const unsigned*>(smem + Ly.chg);
   const float* s_d = reinterpret_cast<const float*>(smem + Ly.dval);
   const float* s_rcp = reinterpret_cast<const float*>(smem + Ly.rcp);
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int u0 = tile_x * a.TW, v0 = tile_y * a.TR;
   const int cs = floor16(u0 - a.L - 1);
   const int cam_stride = a.TR * kMaps * a.SWp;
+  const size_t HW = static_cast<size_t>(a.H) * a.W;
 
   const PixelCtx<float> me = load_pixel(a, s_feat, u0, v0, cam_stride, tid);
   bool run = me.valid;
@@ -187,61 +202,153 @@ __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorM
       run = false;
     }
   }
-  unsigned executed = 0;
-  if (run) {
-    int jb;
-    unsigned S = 0;
-    float emax = 0.f;
-    float post[K];
-    Rays rays;
-    if constexpr (MODE == kModeJoint) {
-      jb = joint_map<K>(a, me.st, s_w, s_o, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu, me.inside, S, emax);
+  if constexpr (MODE == kModeJoint) {
+    unsigned executed = 0;
+    if (run) {
+      unsigned S = 0;
+      float emax = 0.f;
+      const int jb = joint_map<K>(a, me.st, s_w, s_o, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu, me.inside, S, emax);
       executed = 1;
+      const size_t pix = static_cast<size_t>(me.v) * a.W + me.u;
+      a.d_idx[pix] = jb;
+      if (a.d_out) a.d_out[pix] = s_d[jb];
+      if (a.labels) a.labels[pix] = static_cast<uint16_t>(S);
       if (a.post) {
+        Rays rays;
         sample_rays<K, float>(a, me.st, s_w, s_o, jb, me.cy, me.cx, me.cz, rays);
+        float post[K];
         unsigned dummy;
         float dummyf;
         enumerate<1, K>(rays, s_rcp, a.beta, emax, dummy, dummyf, post);
+#pragma unroll
+        for (int k = 0; k < K; ++k) a.post[k * HW + pix] = post[k];
       }
-    } else {
-      // t = 1: the EM's first M-step (labels thresholded per candidate)
+    }
+    const unsigned warp_sum = __reduce_add_sync(0xffffffffu, executed);
+    if (lane == 0 && warp_sum) atomicAdd(a.counter, static_cast<unsigned long long>(warp_sum));
+  } else {
+    PixelState ps;
+    {
+      uint8_t* b = smem + Ly.pix;
+      const int P = a.TR * a.TW;
+      ps.emax = reinterpret_cast<float*>(b);
+      ps.S = reinterpret_cast<uint16_t*>(b + 4 * P);
+      ps.S0 = ps.S + P;
+      ps.jb = reinterpret_cast<int16_t*>(ps.S0 + P);
+      ps.list = ps.jb + P;
+      ps.fixed0 = reinterpret_cast<uint8_t*>(ps.list + P);
+      ps.conv = ps.fixed0 + P;
+    }
+    int* s_wcnt = reinterpret_cast<int*>(smem + Ly.wcnt);
+    float* s_soft = reinterpret_cast<float*>(smem + soft_state_offset(K, a));
+    constexpr int NS = kSoftStateFloats<K>;
+    static_assert(NS == soft_state_floats(K), "soft-EM state size");
+    // E-step at candidate j (q(S) from the rays there) into pixel p's state
+    auto e_step = [&](const PixelCtx<float>& c, int p, int j) {
+      Rays rays;
+      sample_rays<K, float>(a, c.st, s_w, s_o, j, c.cy, c.cx, c.cz, rays);
+      unsigned S = 0;
+      float emax = 0.f;
+      enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
+      float pi[K], pw[kNumPairs<K>];
+      soft_posterior<K>(rays, s_rcp, a.beta, emax, pi, pw);
+      float* st = s_soft + p * NS;
+#pragma unroll
+      for (int k = 0; k < K; ++k) st[k] = pi[k];
+#pragma unroll
+      for (int i = 0; i < kNumPairs<K>; ++i) st[K + i] = pw[i];
+      ps.jb[p] = static_cast<int16_t>(j);
+      ps.S[p] = static_cast<uint16_t>(S);
+      ps.emax[p] = emax;
+    };
+    unsigned long long executed = 0;
+    // t = 1: the EM's first M-step (labels thresholded per candidate)
+    if (run) {
       unsigned S0 = 0;
       const bool f0 = constant_initial_labels<K, float>(a, me.st, &S0);
-      jb = f0 ? m_step_fixed<K, float>(a, me.st, s_w, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu, me.inside,
-                                       S0)
-              : m_step<K, true, float>(a, me.st, s_w, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu,
-                                       me.inside, 0u);
-      executed = 1;
-      float pw[kNumPairs<K>];
-      sample_rays<K, float>(a, me.st, s_w, s_o, jb, me.cy, me.cx, me.cz, rays);
-      enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
-      soft_posterior<K>(rays, s_rcp, a.beta, emax, post, pw);
-      for (int t = 2; t <= a.iters; ++t) {
-        const int jn = m_step_soft<K>(a, me.st, s_w, s_o, s_d, me.cy, me.cx, me.cz, me.mu, me.inside, post, pw);
-        ++executed;
-        if (a.early_exit && jn == jb) break;  // q_t would equal q_{t-1}: fixed point
-        jb = jn;
-        sample_rays<K, float>(a, me.st, s_w, s_o, jb, me.cy, me.cx, me.cz, rays);
-        enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
-        soft_posterior<K>(rays, s_rcp, a.beta, emax, post, pw);
+      const int jb = f0 ? m_step_fixed<K, float>(a, me.st, s_w, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu,
+                                                 me.inside, S0)
+                        : m_step<K, true, float>(a, me.st, s_w, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu,
+                                                 me.inside, 0u);
+      e_step(me, tid, jb);
+    }
+    ps.conv[tid] = 0;
+    executed = static_cast<unsigned long long>(__syncthreads_count(run));
+    for (int t = 2; t <= a.iters; ++t) {
+      const int n = compact(run && !ps.conv[tid], ps.list, 0, s_wcnt);
+      if (n == 0) break;
+      executed += static_cast<unsigned long long>(n);
+      if (n <= kWarpPathPixelsPerWarp * nwarps) {
+        for (int i = warp; i < n; i += nwarps) {
+          const int p = ps.list[i];
+          const PixelCtx<float> c = load_pixel(a, s_feat, u0, v0, cam_stride, p);
+          const float* st = s_soft + p * NS;
+          const int per = (a.D + 31) >> 5, j0 = min(lane * per, a.D), j1 = min(j0 + per, a.D);
+          float jbest;
+          unsigned jn = static_cast<unsigned>(m_step_soft<K>(a, c.st, s_w, s_o, s_d, c.cy, c.cx, c.cz, c.mu,
+                                                             c.inside, st, st + K, j0, j1, &jbest));
+          warp_argmax(jbest, jn);
+          const int jp = ps.jb[p];
+          __syncwarp();
+          if (a.early_exit && static_cast<int>(jn) == jp) {  // q_t would equal q_{t-1}: fixed point
+            if (lane == 0) ps.conv[p] = 1;
+          } else {
+            // every lane computes the same E-step; lane 0 keeps it
+            Rays rays;
+            sample_rays<K, float>(a, c.st, s_w, s_o, static_cast<int>(jn), c.cy, c.cx, c.cz, rays);
+            unsigned S = 0;
+            float emax = 0.f;
+            enumerate_warp<K>(rays, s_rcp, a.beta, lane, S, emax);
+            float pi[K], pw[kNumPairs<K>];
+            soft_posterior<K>(rays, s_rcp, a.beta, emax, pi, pw);
+            __syncwarp();
+            if (lane == 0) {
+              float* sto = s_soft + p * NS;
+#pragma unroll
+              for (int k = 0; k < K; ++k) sto[k] = pi[k];
+#pragma unroll
+              for (int q = 0; q < kNumPairs<K>; ++q) sto[K + q] = pw[q];
+              ps.jb[p] = static_cast<int16_t>(jn);
+              ps.S[p] = static_cast<uint16_t>(S);
+              ps.emax[p] = emax;
+            }
+          }
+        }
+      } else if (tid < n) {
+        const int p = ps.list[tid];
+        const PixelCtx<float> c = load_pixel(a, s_feat, u0, v0, cam_stride, p);
+        const float* st = s_soft + p * NS;
+        const int jn = m_step_soft<K>(a, c.st, s_w, s_o, s_d, c.cy, c.cx, c.cz, c.mu, c.inside, st, st + K, 0,
+                                      a.D, nullptr);
+        if (a.early_exit && jn == ps.jb[p]) ps.conv[p] = 1;  // q_t would equal q_{t-1}: fixed point
+        else e_step(c, p, jn);
+      }
+      __syncthreads();
+    }
+    if (run) {
+      const size_t pix = static_cast<size_t>(me.v) * a.W + me.u;
+      const int jb = ps.jb[tid];
+      a.d_idx[pix] = jb;
+      if (a.d_out) a.d_out[pix] = s_d[jb];
+      if (a.labels) a.labels[pix] = ps.S[tid];
+      if (a.post) {
+        const float* st = s_soft + tid * NS;
+#pragma unroll
+        for (int k = 0; k < K; ++k) a.post[k * HW + pix] = st[k];
       }
     }
-    const size_t pix = static_cast<size_t>(me.v) * a.W + me.u;
-    a.d_idx[pix] = jb;
-    if (a.d_out) a.d_out[pix] = s_d[jb];
-    if (a.labels) a.labels[pix] = static_cast<uint16_t>(S);
-    if (a.post) {
-      const size_t HW = static_cast<size_t>(a.H) * a.W;
-#pragma unroll
-      for (int k = 0; k < K; ++k) a.post[k * HW + pix] = post[k];
-    }
+    if (tid == 0 && executed) atomicAdd(a.counter, executed);
   }
-  const unsigned warp_sum = __reduce_add_sync(0xffffffffu, executed);
-  if ((tid & 31) == 0 && warp_sum) atomicAdd(a.counter, static_cast<unsigned long long>(warp_sum));
+}
+
+// Soft EM up to seven cameras in 128 registers: two CTAs per SM.
+template <int K, int MODE>
+constexpr int variant_min_blocks() {
+  return MODE == kModeSoft && K <= 7 ? 2 : 1;
 }
 
 template <int K, int MODE>
-__global__ void __launch_bounds__(256) em_variant_kernel(const __grid_constant__ CUtensorMap img_map,
+__global__ void __launch_bounds__(256, variant_min_blocks<K, MODE>()) em_variant_kernel(const __grid_constant__ CUtensorMap img_map,
                                                          const __grid_constant__ CUtensorMap p_map,
                                                          const SweepArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
@@ -268,7 +375,8 @@ __global__ void __launch_bounds__(256) em_variant_kernel(const __grid_constant__
 template <int K, int MODE>
 cudaError_t launch_em_variant_k(const CUtensorMap& img_map, const CUtensorMap& p_map, const SweepArgs& a,
                                 cudaStream_t s) {
-  const size_t smem = sweep_layout(K, a).total;
+  const size_t smem = MODE == kModeSoft ? soft_state_offset(K, a) + soft_state_bytes(K, a.TR * a.TW)
+                                        : sweep_layout(K, a).total;
   static int configured = -1;  // largest dynamic shared size set so far (per process)
   if (static_cast<int>(smem) > configured) {
     cudaError_t e = cudaFuncSetAttribute(em_variant_kernel<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,

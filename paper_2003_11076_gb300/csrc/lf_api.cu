@@ -306,7 +306,9 @@ lf_status choose_tiles(lf_ctx* c) {
       a.KP = c->KP;
       a.prec = c->p.precision;
       if (a.RW * a.bpp / 8 > 256 || a.RW / 2 > 256) continue;
-      if (sweep_smem_bytes(c->K, a) > limit) continue;
+      const size_t need = c->p.em_mode == LF_EM_SOFT ? dev::soft_state_offset(c->K, a) + soft_state_bytes(c->K, a.TR * a.TW)
+                                                     : sweep_smem_bytes(c->K, a);
+      if (need > limit) continue;
       c->TR = a.TR;
       c->TW = a.TW;
       c->SW = a.SW;

@@ -180,6 +180,13 @@ size_t sweep_smem_bytes(int K, const SweepArgs& a);
 // cameras is compiled for (its launcher rejects larger ones); the persistent
 // kernel of uneven batches takes up to 256 threads at every K.
 constexpr int sweep_max_threads(int K) { return K <= 8 ? 256 : 128; }
+// The soft-EM state kept per tile pixel between iterations: P(ray static)
+// per camera, then the K(K-1)/2 pair weights (one slot, unused, for a single
+// camera); floats per pixel and shared-memory bytes per tile.
+__host__ __device__ constexpr int soft_state_floats(int K) { return K + (K * (K - 1) / 2 > 0 ? K * (K - 1) / 2 : 1); }
+__host__ __device__ inline size_t soft_state_bytes(int K, int pixels) {
+  return static_cast<size_t>(pixels) * static_cast<size_t>(soft_state_floats(K)) * 4;
+}
 
 cudaError_t launch_prior_raster(const PriorArgs& a, cudaStream_t s);
 // Dynamic-only mode: list the tiles holding a pixel with P_ref >= threshold

@@ -118,9 +118,18 @@ def test_variant_dynamic_only_equals_full_mode_on_dynamic_pixels(mode):
     assert np.all(np.isnan(dyn["post"][:, ~m])) and np.all(dyn["labels"][~m] == 0)
 
 
-def test_soft_em_early_exit_is_exact():
+@pytest.mark.parametrize("make", [
+    lambda: scenes.small_gray(2),
+    lambda: scenes.street_rgb(0),
+    lambda: scenes.small_gray(16, D=7),
+    lambda: scenes.small_gray(17, baselines=[-0.35, -0.25, -0.15, -0.05, 0.0, 0.1, 0.2, 0.3], D=40),
+])
+def test_soft_em_early_exit_is_exact(make):
+    """With the early exit only the pixels still iterating run, regrouped into
+    dense warps and, once few are left, one warp per pixel; without it every
+    pixel runs every iteration.  Both give the same bits."""
     from paper_2003_11076_gb300 import lf
-    s = scenes.small_gray(2)
+    s = make()
     a = lf.run_scene(s, params=lf.default_params(em_mode=1, early_exit=1), iters=8)
     b = lf.run_scene(s, params=lf.default_params(em_mode=1, early_exit=0), iters=8)
     for k in ("d_idx", "labels", "d", "post", "refocus"):
