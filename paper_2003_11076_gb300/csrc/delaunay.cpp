@@ -13,8 +13,11 @@
 //     left -- conflicts with p when p is strictly left of a->b, or on the
 //     line a-b strictly between a and b.
 // Each point is located by a visibility walk from the last inserted
-// triangle (points are inserted in Morton order of their coordinates, so the
-// walks are short); the conflict cavity is grown from the located triangle
+// triangle.  Points are inserted in a biased randomised order: rounds of
+// doubling size drawn by a fixed hash of the point index (the same order on
+// every machine), each round in Morton order of the coordinates, so the
+// walks are short and most points land inside the current hull, where the
+// cavities are small.  The conflict cavity is grown from the located triangle
 // by breadth-first search over neighbours (it is connected), deleted, and its
 // boundary fanned to the new point.  Repeated (x, y) keep their first
 // occurrence.  With points in general position the result is the unique
@@ -83,7 +86,8 @@ uint32_t spread16(uint32_t x) {
 
 class Mesh {
  public:
-  explicit Mesh(const double* P) : P_(P) {}
+  // n: number of input points (vertex ids are 0 .. n-1)
+  Mesh(const double* P, int n) : P_(P), fan_at_(static_cast<size_t>(n) + 1, 0), fan_stamp_(static_cast<size_t>(n) + 1, 0u) {}
 
   void seed(int a, int b, int c) {
     // finite (a, b, c) ccw plus three ghosts on its outside
@@ -184,6 +188,11 @@ class Mesh {
   std::vector<uint32_t> mark_;
   uint32_t stamp_ = 0;
   int last_ = 0;
+  // per vertex (slot 0: the vertex at infinity): index of the boundary edge
+  // that starts there in the current fan, valid when its stamp is current
+  std::vector<int> fan_at_;
+  std::vector<uint32_t> fan_stamp_;
+  uint32_t fan_now_ = 0;
 
   void next_stamp() {
     if (mark_.size() < tris_.size()) mark_.resize(2 * tris_.size() + 64, 0u);  // geometric growth
@@ -220,18 +229,28 @@ class Mesh {
   // edge (b_i, p), the new triangle whose boundary edge starts at b_i, across
   // that one's edge (p, a_j).  Slots of (b, p): 0 for (a, b, p), 2 for
   // (b, p, inf), 1 for (p, a, inf); of (p, a): 1, 0 and 2.
+  // The cavity boundary is a closed cycle, so every vertex starts exactly
+  // one boundary edge: index them by start vertex, then link in one pass.
   void link_fan() {
     const size_t m = made_.size();
     auto slot_bp = [&](const Edge& e) { return e.a == kInf ? 2 : (e.b == kInf ? 1 : 0); };
     auto slot_pa = [&](const Edge& e) { return e.a == kInf ? 0 : (e.b == kInf ? 2 : 1); };
+    if (++fan_now_ == 0) {
+      std::fill(fan_stamp_.begin(), fan_stamp_.end(), 0u);
+      fan_now_ = 1;
+    }
+    for (size_t j = 0; j < m; ++j) {
+      const size_t va = static_cast<size_t>(bedges_[j].a + 1);
+      fan_at_[va] = static_cast<int>(j);
+      fan_stamp_[va] = fan_now_;
+    }
     for (size_t i = 0; i < m; ++i) {
-      const int bi = bedges_[i].b;
-      for (size_t j = 0; j < m; ++j) {
-        if (j == i || bedges_[j].a != bi) continue;
-        tris_[made_[i]].nb[slot_bp(bedges_[i])] = made_[j];
-        tris_[made_[j]].nb[slot_pa(bedges_[j])] = made_[i];
-        break;
-      }
+      const size_t vb = static_cast<size_t>(bedges_[i].b + 1);
+      if (fan_stamp_[vb] != fan_now_) continue;
+      const size_t j = static_cast<size_t>(fan_at_[vb]);
+      if (j == i) continue;
+      tris_[made_[i]].nb[slot_bp(bedges_[i])] = made_[j];
+      tris_[made_[j]].nb[slot_pa(bedges_[j])] = made_[i];
     }
   }
 
@@ -280,38 +299,65 @@ class Mesh {
 
 int delaunay(const double* P, int n, int* out, int max_tris) {
   if (n < 3) return 0;
-  // keep the first occurrence of every (x, y)
-  std::vector<int> idx(static_cast<size_t>(n));
-  for (int i = 0; i < n; ++i) idx[i] = i;
-  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
-    if (P[2 * a] != P[2 * b]) return P[2 * a] < P[2 * b];
-    return P[2 * a + 1] < P[2 * b + 1];
-  });
-  std::vector<int> keep;
-  keep.reserve(idx.size());
-  for (size_t i = 0; i < idx.size(); ++i) {
-    if (i > 0 && P[2 * idx[i]] == P[2 * idx[i - 1]] && P[2 * idx[i] + 1] == P[2 * idx[i - 1] + 1]) continue;
-    keep.push_back(idx[i]);  // stable sort: the first of equal keys is the first occurrence
-  }
-  if (keep.size() < 3) return 0;
-  // Morton order for short walks
-  double x0 = P[2 * keep[0]], x1 = x0, y0 = P[2 * keep[0] + 1], y1 = y0;
-  for (int i : keep) {
+  // Morton order (for short walks) in one sort that also brings repeated
+  // (x, y) together: key, then x, then y, then index; the first of a run of
+  // repeats is the first occurrence
+  double x0 = P[0], x1 = x0, y0 = P[1], y1 = y0;
+  for (int i = 1; i < n; ++i) {
     x0 = std::min(x0, P[2 * i]); x1 = std::max(x1, P[2 * i]);
     y0 = std::min(y0, P[2 * i + 1]); y1 = std::max(y1, P[2 * i + 1]);
   }
   const double sx = x1 > x0 ? 65535.0 / (x1 - x0) : 0.0, sy = y1 > y0 ? 65535.0 / (y1 - y0) : 0.0;
   std::vector<std::pair<uint32_t, int>> order;
-  order.reserve(keep.size());
-  for (int i : keep) {
+  order.reserve(static_cast<size_t>(n));
+  for (int i = 0; i < n; ++i) {
     const uint32_t qx = static_cast<uint32_t>((P[2 * i] - x0) * sx);
     const uint32_t qy = static_cast<uint32_t>((P[2 * i + 1] - y0) * sy);
     order.emplace_back(spread16(qx) | (spread16(qy) << 1), i);
   }
-  std::sort(order.begin(), order.end());
+  std::sort(order.begin(), order.end(), [&](const std::pair<uint32_t, int>& u, const std::pair<uint32_t, int>& w) {
+    if (u.first != w.first) return u.first < w.first;
+    const int a = u.second, b = w.second;
+    if (P[2 * a] != P[2 * b]) return P[2 * a] < P[2 * b];
+    if (P[2 * a + 1] != P[2 * b + 1]) return P[2 * a + 1] < P[2 * b + 1];
+    return a < b;
+  });
   std::vector<int> pts;
   pts.reserve(order.size());
-  for (auto& o : order) pts.push_back(o.second);
+  for (size_t i = 0; i < order.size(); ++i) {
+    const int q = order[i].second;
+    if (i > 0) {
+      const int r = order[i - 1].second;
+      if (P[2 * q] == P[2 * r] && P[2 * q + 1] == P[2 * r + 1]) continue;
+    }
+    pts.push_back(q);
+  }
+  if (pts.size() < 3) return 0;
+  {
+    auto mix = [](uint64_t z) {  // SplitMix64 finaliser
+      z += 0x9e3779b97f4a7c15ull;
+      z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+      z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+      return z ^ (z >> 31);
+    };
+    std::vector<std::pair<uint64_t, int>> byh;  // (hash, Morton position)
+    byh.reserve(pts.size());
+    for (size_t i = 0; i < pts.size(); ++i) byh.emplace_back(mix(static_cast<uint64_t>(pts[i])), static_cast<int>(i));
+    std::sort(byh.begin(), byh.end());
+    // hash rank r -> round floor(log2(r + 1)); inside a round, Morton order
+    std::vector<std::pair<int, int>> rk;
+    rk.reserve(pts.size());
+    for (size_t r = 0; r < byh.size(); ++r) {
+      int lv = 0;
+      while ((2ull << lv) <= r + 1) ++lv;
+      rk.emplace_back(lv, byh[r].second);
+    }
+    std::sort(rk.begin(), rk.end());
+    std::vector<int> brio;
+    brio.reserve(pts.size());
+    for (const auto& q : rk) brio.push_back(pts[q.second]);
+    pts.swap(brio);
+  }
   // seed: first point, next point, first point off their line
   const int a = pts[0], b = pts[1];
   int c = -1;
@@ -319,7 +365,7 @@ int delaunay(const double* P, int n, int* out, int max_tris) {
   for (size_t i = 2; i < pts.size(); ++i)
     if (orient(P, a, b, pts[i]) != 0.0) { c = pts[i]; ci = i; break; }
   if (c < 0) return 0;  // all points collinear
-  Mesh mesh(P);
+  Mesh mesh(P, n);
   if (orient(P, a, b, c) > 0.0) mesh.seed(a, b, c);
   else mesh.seed(a, c, b);
   for (size_t i = 2; i < pts.size(); ++i) {
