@@ -542,20 +542,21 @@ __device__ __forceinline__ void enumerate(const Rays& r, const float* s_rcp, flo
   }
 }
 
-// Warp-cooperative forms for a pixel that runs alone (the last pixels of a
-// tile still iterating): the 32 lanes split its candidates, then its label
-// vectors, and reduce with the same tie rules as the one-thread sweep (lowest
-// candidate, smallest mask), so the result is bit-identical.
+// Cooperative forms for the last pixels of a tile still iterating: a group
+// of G lanes (G a power of two, up to the warp) takes one pixel, splits its
+// candidates and then its label vectors, and reduces with the same tie
+// rules as the one-thread sweep (lowest candidate, smallest mask), so the
+// result is bit-identical.
 
-// A CTA takes the warp-per-pixel path when at most this many pixels per warp
-// are still iterating (each warp then runs its pixels one after another; at
-// four a warp's pixels take about as long as one one-thread-per-pixel pass).
+// A CTA in the calibrated and soft-EM kernels takes the warp-per-pixel path
+// when at most this many pixels per warp are still iterating (each warp then
+// runs its pixels one after another).
 constexpr int kWarpPathPixelsPerWarp = 4;
 
-// Larger objective, or on a tie the lower index, over the warp's lanes.
-__device__ __forceinline__ void warp_argmax(float& best, unsigned& idx) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
+// Larger objective, or on a tie the lower index, over the G lanes of each
+// aligned group (every lane of the warp takes part).
+__device__ __forceinline__ void group_argmax(float& best, unsigned& idx, int G) {
+  for (int off = G >> 1; off > 0; off >>= 1) {
     const float ob = __shfl_xor_sync(0xffffffffu, best, off);
     const unsigned oi = __shfl_xor_sync(0xffffffffu, idx, off);
     if (ob > best || (ob == best && oi < idx)) {
@@ -564,35 +565,64 @@ __device__ __forceinline__ void warp_argmax(float& best, unsigned& idx) {
     }
   }
 }
+__device__ __forceinline__ void warp_argmax(float& best, unsigned& idx) { group_argmax(best, idx, 32); }
 
-// Arg-max of the E-step over masks m = lane, lane + 32, ...  Each leaf's sums
-// are formed from scratch in the subset tree's order (the high cameras in
-// increasing order, then the low block from its highest camera down), so the
-// objectives equal the tree's bit for bit.
+// Arg-max of the E-step by lane gl of a group of G.  Up to six cameras each
+// lane takes masks gl, gl + G, ... and forms their sums from scratch in the
+// subset tree's order (the low block from its highest camera down); from
+// seven, each lane takes high masks gl, gl + G, ... of the tree's outer loop
+// and runs its inner subset tree as is.  Either way the objectives equal the
+// one-thread enumeration's bit for bit.
+template <int K>
+__device__ __forceinline__ void enumerate_group(const Rays& r, const float* s_rcp, float beta, int gl, int G,
+                                                unsigned& bmask, float& best) {
+  constexpr int L = K < 6 ? K : 6;
+  constexpr int NH = K - L;
+  float b = -INFINITY;
+  unsigned bm = gl == 0 ? 0u : 0xffffffffu;  // all objectives -inf: mask 0, as the one-thread form
+  if constexpr (NH == 0) {
+    for (unsigned m = gl; m < (1u << K); m += G) {
+      Acc acc{0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int k = L - 1; k >= 0; --k)
+        if (m >> k & 1u) {
+          acc.sy += r.gy[k]; acc.sx += r.gx[k]; acc.sz += r.gz[k]; acc.q += r.qk[k]; acc.sa += r.ak[k];
+        }
+      const float E = leaf_objective(acc, s_rcp[__popc(m)], r.base, beta);
+      if (E > b) { b = E; bm = m; }
+    }
+  } else {
+    EnumState<L> s;
+    s.best = -INFINITY;
+    s.bmask = bm;
+    s.emax = 0.f;
+    for (unsigned h = gl; h < (1u << NH); h += G) {
+      Acc acc{0.f, 0.f, 0.f, 0.f, 0.f};
+      int nh = 0;
+#pragma unroll
+      for (int i = 0; i < NH; ++i) {
+        if (h >> i & 1u) {
+          acc.sy += r.gy[L + i]; acc.sx += r.gx[L + i]; acc.sz += r.gz[L + i];
+          acc.q += r.qk[L + i]; acc.sa += r.ak[L + i];
+          ++nh;
+        }
+      }
+      float rnv[L + 1];
+#pragma unroll
+      for (int i = 0; i <= L; ++i) rnv[i] = s_rcp[nh + i];
+      enum_low<0, L, L - 1, 0, 0u>(r, acc, rnv, h << L, beta, s);
+    }
+    b = s.best;
+    bm = s.bmask;
+  }
+  group_argmax(b, bm, G);
+  bmask = bm;
+  best = b;
+}
 template <int K>
 __device__ __forceinline__ void enumerate_warp(const Rays& r, const float* s_rcp, float beta, int lane,
                                                unsigned& bmask, float& best) {
-  constexpr int L = K < 6 ? K : 6;
-  float b = -INFINITY;
-  unsigned bm = static_cast<unsigned>(lane);
-  for (unsigned m = lane; m < (1u << K); m += 32) {
-    Acc acc{0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int k = L; k < K; ++k)
-      if (m >> k & 1u) {
-        acc.sy += r.gy[k]; acc.sx += r.gx[k]; acc.sz += r.gz[k]; acc.q += r.qk[k]; acc.sa += r.ak[k];
-      }
-#pragma unroll
-    for (int k = L - 1; k >= 0; --k)
-      if (m >> k & 1u) {
-        acc.sy += r.gy[k]; acc.sx += r.gx[k]; acc.sz += r.gz[k]; acc.q += r.qk[k]; acc.sa += r.ak[k];
-      }
-    const float E = leaf_objective(acc, s_rcp[__popc(m)], r.base, beta);
-    if (E > b) { b = E; bm = m; }
-  }
-  warp_argmax(b, bm);
-  bmask = bm;
-  best = b;
+  enumerate_group<K>(r, s_rcp, beta, lane, 32, bmask, best);
 }
 
 // Element c of the pixel at p (an image of dtype a.dtype), unscaled.
@@ -964,29 +994,36 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     }
   }
   __syncthreads();
-  // t >= 2: only the pixels not yet at their fixed point; when few of them
-  // are left, one warp per pixel
+  // t >= 2: only the pixels not yet at their fixed point; when fewer than a
+  // CTA's threads are left, groups of lanes per pixel
   const int nwarps = blockDim.x >> 5, lane = tid & 31;
   for (int t = 2; t <= a.iters; ++t) {
     const int n = compact(my_valid && !ps.conv[tid], ps.list, 0, s_wcnt);
     if (n == 0) break;
     executed += static_cast<unsigned long long>(n);
-    if (n <= kWarpPathPixelsPerWarp * nwarps) {
-      for (int i = warp; i < n; i += nwarps) {
-        const int p = ps.list[i];
+    // lanes per pixel: the largest power of two that still fits every
+    // remaining pixel into one round of the CTA's warps
+    int G = 1;
+    while (G < 32 && n * (G << 1) <= nwarps * 32) G <<= 1;
+    if (G > 1) {
+      const int gpw = 32 / G, gl = lane & (G - 1);
+      const int slot = warp * gpw + lane / G;  // this group's pixel among the n
+      if (warp * gpw < n) {
+        const bool act = slot < n;
+        const int p = ps.list[act ? slot : n - 1];  // idle groups repeat the last pixel
         const PixelCtx<TS> c = load_pixel(a, s_feat, u0, v0, cam_stride, p, s_mu);
         const unsigned Sp = ps.S[p];
-        const int per = (a.D + 31) >> 5, j0 = min(lane * per, a.D), j1 = min(j0 + per, a.D);
+        const int per = (a.D + G - 1) / G, j0 = min(gl * per, a.D), j1 = min(j0 + per, a.D);
         float jbest;
         unsigned jb = static_cast<unsigned>(m_step_fixed_range<K, TS, true>(
             a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, Sp, j0, j1, &jbest));
-        warp_argmax(jbest, jb);
+        group_argmax(jbest, jb, G);
         Rays rays;
         sample_rays<K, TS>(a, c.st, s_w, s_o, static_cast<int>(jb), c.cy, c.cx, c.cz, rays);
         unsigned S = 0;
         float emax = 0.f;
-        enumerate_warp<K>(rays, s_rcp, a.beta, lane, S, emax);
-        if (lane == 0) {
+        enumerate_group<K>(rays, s_rcp, a.beta, gl, G, S, emax);
+        if (act && gl == 0) {
           ps.jb[p] = static_cast<int16_t>(jb);
           ps.S[p] = static_cast<uint16_t>(S);
           ps.emax[p] = emax;
