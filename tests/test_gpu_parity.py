@@ -179,13 +179,18 @@ def test_early_exit_is_exact():
     lambda: scenes.small_gray(12, D=7, iters=8),
     lambda: scenes.small_gray(13, H=40, W=96, D=1024, iters=6),
     lambda: scenes.small_gray(14, baselines=[-0.4, -0.3, -0.2, -0.1, 0.0, 0.1, 0.2, 0.3, 0.4], D=40, iters=8),
+    lambda: scenes.small_gray(18, H=40, W=200, baselines=[-0.3, -0.2, -0.1, 0.0, 0.1, 0.2, 0.3], D=33, iters=8),
+    lambda: scenes.small_gray(19, H=30, W=130, baselines=[-0.35, -0.25, -0.15, -0.05, 0.0, 0.1, 0.2, 0.3], D=50,
+                              iters=8),
+    lambda: scenes.random_frame(5, scale=0.3),
     lambda: scenes.small_gray(15, H=24, W=48, D=16, iters=6,
                               baselines=[-0.3, -0.25, -0.2, -0.15, -0.1, -0.05, 0.0, 0.05, 0.1, 0.15, 0.2, 0.25]),
 ])
 def test_early_exit_is_exact_across_shapes(make):
-    """With the early exit the last pixels of a tile still iterating run one
-    per warp (lanes split the candidates and label vectors); without it every
-    pixel runs every iteration one per thread.  Both give the same bits."""
+    """With the early exit the last pixels of a tile still iterating run in
+    groups of lanes (2 to 32 per pixel: lanes split the candidates and label
+    vectors); without it every pixel runs every iteration one per thread.
+    Both give the same bits (five to twelve cameras, D from 7 to 1024)."""
     lf = _lf()
     s = make()
     a = lf.run_scene(s, params=lf.default_params(early_exit=1))
