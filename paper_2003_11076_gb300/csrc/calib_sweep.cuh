@@ -66,7 +66,14 @@ __device__ __forceinline__ int calib_m_step(const CalibArgs& a, const float (&A)
                                             float* best_out) {
   float best = -INFINITY;
   int jb = j0;
+  auto prior_at = [&](int j) {
+    const float t = __ldg(a.dval + j) - mu;
+    return __logf(a.gamma + __expf(-(t * t) * a.inv2s2));
+  };
+  float pr_next = j0 < j1 ? prior_at(j0) : 0.f;
   for (int j = j0; j < j1; ++j) {
+    const float pr = pr_next;
+    pr_next = prior_at(min(j + 1, j1 - 1));  // the next candidate's prior, off this one's critical path
     const float d = __ldg(a.dval + j);
     float sy = 0.f, sx = 0.f, sz = 0.f, q = 0.f, seg = 0.f;
     int n = 0;
@@ -96,10 +103,7 @@ __device__ __forceinline__ int calib_m_step(const CalibArgs& a, const float (&A)
     const float ss = fmaf(sz, sz, fmaf(sx, sx, sy * sy));
     const float var = fmaf(-ss, rn, q) * rn;
     float J = a.mseg ? seg : 0.f;
-    if (inside) {
-      const float t = d - mu;
-      J += __logf(a.gamma + __expf(-(t * t) * a.inv2s2));
-    }
+    if (inside) J += pr;
     J = fmaf(-a.beta, var, J);
     if (J > best) { best = J; jb = j; }
   }

@@ -195,8 +195,11 @@ struct Staged {
 
 // ---------------------------------------------------------------- M-step
 // Arg-max over the D candidates of J(d_j, S) for one pixel (lowest j wins
-// ties).  INIT: first iteration, where each ray's label is thresholded at the
-// ray's own sample (ld - ls < log(thr / (1 - thr)) means static).
+// ties).  INIT: first iteration, where each ray's label is thresholded at
+// the ray's own sample (ld - ls < log(thr / (1 - thr)) means static).  Here
+// and in the other M-steps the log prior of candidate j + 1 (two dependent
+// special-function operations) is evaluated while candidate j's sums are
+// formed, off the loop's critical path; the values are the same.
 template <int K, bool INIT, typename TS>
 __device__ __forceinline__ int m_step(const SweepArgs& a, const Staged<TS>& st, const float* s_w,
                                       const int* s_o, const unsigned* s_chg, const float* s_d,
@@ -214,7 +217,14 @@ __device__ __forceinline__ int m_step(const SweepArgs& a, const Staged<TS>& st, 
   const float rn_fixed = s_rcp[__popc(S)];
   float best = -INFINITY;
   int jb = 0;
+  auto prior_at = [&](int j) {
+    const float t = s_d[j] - mu;
+    return __logf(a.gamma + __expf(-(t * t) * a.inv2s2));
+  };
+  float pr_next = prior_at(0);
   for (int j = 0; j < a.D; ++j) {
+    const float pr = pr_next;
+    pr_next = prior_at(min(j + 1, a.D - 1));  // the next candidate's prior, off this one's critical path
     const unsigned ch = s_chg[j];
     float w[K];
     {
@@ -277,10 +287,7 @@ __device__ __forceinline__ int m_step(const SweepArgs& a, const Staged<TS>& st, 
     const float ss = fmaf(sz, sz, fmaf(sx, sx, sy * sy));
     const float var = fmaf(-ss, rn, q) * rn;
     float J = a.mseg ? seg : 0.f;
-    if (inside) {
-      const float t = s_d[j] - mu;
-      J += __logf(a.gamma + __expf(-(t * t) * a.inv2s2));
-    }
+    if (inside) J += pr;
     J = fmaf(-a.beta, var, J);
     if (J > best) { best = J; jb = j; }
   }
@@ -316,7 +323,14 @@ __device__ __forceinline__ int m_step_fixed_range(const SweepArgs& a, const Stag
   const float rn = s_rcp[__popc(S)];
   float best = -INFINITY;
   int jb = j0;
+  auto prior_at = [&](int j) {
+    const float t = s_d[j] - mu;
+    return __logf(a.gamma + __expf(-(t * t) * a.inv2s2));
+  };
+  float pr_next = j0 < j1 ? prior_at(j0) : 0.f;
   for (int j = j0; j < j1; ++j) {
+    const float pr = pr_next;
+    pr_next = prior_at(min(j + 1, j1 - 1));  // the next candidate's prior, off this one's critical path
     const unsigned ch = RESTART && j == j0 ? (1u << K) - 1u : s_chg[j];
     float w[K];
     {
@@ -366,10 +380,7 @@ __device__ __forceinline__ int m_step_fixed_range(const SweepArgs& a, const Stag
     const float ss = fmaf(SZ, SZ, fmaf(SX, SX, SY * SY));
     const float var = fmaf(-ss, rn, Q) * rn;
     float J = a.mseg ? SL : 0.f;
-    if (inside) {
-      const float t = s_d[j] - mu;
-      J += __logf(a.gamma + __expf(-(t * t) * a.inv2s2));
-    }
+    if (inside) J += pr;
     J = fmaf(-a.beta, var, J);
     if (J > best) { best = J; jb = j; }
   }

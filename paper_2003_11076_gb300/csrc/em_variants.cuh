@@ -93,7 +93,14 @@ __device__ __forceinline__ int m_step_soft(const SweepArgs& a, const Staged<floa
   const int SWp = st.SWp;
   float best = -INFINITY;
   int jb = j0;
+  auto prior_at = [&](int j) {
+    const float t = s_d[j] - mu;
+    return __logf(a.gamma + __expf(-(t * t) * a.inv2s2));
+  };
+  float pr_next = j0 < j1 ? prior_at(j0) : 0.f;
   for (int j = j0; j < j1; ++j) {
+    const float pr = pr_next;
+    pr_next = prior_at(min(j + 1, j1 - 1));  // the next candidate's prior, off this one's critical path
     float gy[K], gx[K], gz[K];
     float seg = 0.f;
 #pragma unroll
@@ -121,10 +128,7 @@ __device__ __forceinline__ int m_step_soft(const SweepArgs& a, const Staged<floa
         ++p;
       }
     float J = a.mseg ? seg : 0.f;
-    if (inside) {
-      const float t = s_d[j] - mu;
-      J += __logf(a.gamma + __expf(-(t * t) * a.inv2s2));
-    }
+    if (inside) J += pr;
     J = fmaf(-a.beta, pv, J);
     if (J > best) { best = J; jb = j; }
   }
@@ -341,10 +345,11 @@ __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorM
   }
 }
 
-// Soft EM up to seven cameras in 128 registers: two CTAs per SM.
+// Two CTAs per SM (at most 128 registers) for soft EM up to seven cameras
+// and joint MAP up to eight; one above.
 template <int K, int MODE>
 constexpr int variant_min_blocks() {
-  return MODE == kModeSoft && K <= 7 ? 2 : 1;
+  return (MODE == kModeSoft && K <= 7) || (MODE == kModeJoint && K <= 8) ? 2 : 1;
 }
 
 template <int K, int MODE>
