@@ -413,6 +413,19 @@ lf_status lf_run_em_static(int n_cams, const float *baselines, int H, int W, flo
                            float *disparity, float *posteriors, uint16_t *labels, void *stream);
 
 /*
+ * Self-test of the bounded device waits (no fault is involved).  Every wait
+ * of the sweep kernels on their TMA copies gives up after a time limit and
+ * reports it through the context's status word, which lf_run_em turns into
+ * LF_ETIMEOUT.  This call launches one CTA on the current device that arms
+ * an mbarrier for bytes no copy will deliver and waits on it with the same
+ * bounded wait for timeout_ns nanoseconds (0 < timeout_ns <= 1e10).
+ * Returns LF_ETIMEOUT when the wait expired and was reported (the expected
+ * outcome), LF_OK if it completed, LF_EINVAL / LF_ECUDA otherwise.  Nothing
+ * stays in flight and the device stays usable.
+ */
+lf_status lf_selftest_bounded_wait(unsigned long long timeout_ns);
+
+/*
  * Host utility (no GPU needed): Delaunay triangulation of the (u, v) of
  * `points` ([M][3] float32, (u, v, d)) as used for the prior (Sec. III-C,
  * triangulation of the support points, as in ELAS).  Writes up to max_tris

@@ -436,6 +436,25 @@ lf_status copy_plane(lf_ctx* c, const void* src, size_t row_bytes, bool on_devic
 
 }  // namespace
 
+namespace {
+// Self-test of the bounded wait the sweep kernels use on their TMA copies:
+// thread 0 arms the CTA's mbarrier for `bytes` of transaction that no copy
+// will deliver, every thread waits with the sweep's bounded wait, and the
+// expiry is reported through the status word as in the sweep.  No copy is
+// ever issued, so nothing is in flight when the CTA leaves.
+__global__ void bounded_wait_selftest_kernel(unsigned* status, unsigned bytes, unsigned long long timeout_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    dev::mbar_init(&bar, 1);
+    dev::fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) dev::mbar_arrive_expect_tx(&bar, bytes);
+  const bool ok = dev::mbar_wait_bounded(&bar, 0u, timeout_ns);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(status, kStatusTmaTimeout);
+}
+}  // namespace
+
 extern "C" {
 
 void lf_default_params(lf_params* p) {
@@ -1114,6 +1133,28 @@ lf_status lf_set_tile(lf_ctx* c, int tile_rows, int tile_cols) {
     return s;
   }
   return encode_maps(c);
+}
+
+lf_status lf_selftest_bounded_wait(unsigned long long timeout_ns) {
+  g_err.clear();
+  if (timeout_ns == 0 || timeout_ns > 10000000000ull) return fail(LF_EINVAL, "timeout_ns must be in (0, 1e10]");
+  unsigned* d_status = nullptr;
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&d_status), sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) {
+    bounded_wait_selftest_kernel<<<1, 64, 0, s>>>(d_status, 1024u, timeout_ns);
+    e = cudaGetLastError();
+  }
+  unsigned st = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (s) cudaStreamDestroy(s);
+  if (d_status) cudaFree(d_status);
+  if (e != cudaSuccess) return fail(LF_ECUDA, std::string("bounded-wait self-test: ") + cudaGetErrorString(e));
+  if (st & kStatusTmaTimeout) return fail(LF_ETIMEOUT, "bounded-wait self-test: the wait expired and was reported");
+  return LF_OK;
 }
 
 lf_status lf_set_timing(lf_ctx* c, int enable) {

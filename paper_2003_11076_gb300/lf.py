@@ -26,7 +26,7 @@ EXPORTS = ("lf_default_params", "lf_create", "lf_set_stream", "lf_set_inputs", "
            "lf_triangulate", "lf_set_timing", "lf_run_em_static", "lf_batch_create", "lf_batch_set_stream",
            "lf_batch_add", "lf_batch_run", "lf_batch_synchronize", "lf_batch_clear", "lf_batch_get_stats",
            "lf_batch_destroy", "lf_set_tile", "lf_create_calibrated", "lf_default_support_params",
-           "lf_set_support_params", "lf_get_support_points")
+           "lf_set_support_params", "lf_get_support_points", "lf_selftest_bounded_wait")
 LF_DETECT_SUPPORT = -1
 
 
@@ -117,6 +117,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         getattr(lib, name).restype = I
     lib.lf_triangulate.argtypes = [P, I, P, I]
     lib.lf_triangulate.restype = I
+    lib.lf_selftest_bounded_wait.argtypes = [ctypes.c_ulonglong]
+    lib.lf_selftest_bounded_wait.restype = I
     for name in ("lf_create", "lf_create_calibrated", "lf_set_stream", "lf_set_inputs", "lf_run_em", "lf_synchronize",
                  "lf_get_prior", "lf_get_stats", "lf_set_timing"):
         getattr(lib, name).restype = I
@@ -144,6 +146,13 @@ def _check(status: int):
     if status != LF_OK:
         msg = load().lf_last_error(None)
         raise LfError(status, msg.decode() if msg else "")
+
+
+def selftest_bounded_wait(timeout_ns: int) -> int:
+    """Run the device's bounded-wait self-test (one CTA waits for bytes no
+    copy delivers); returns the status, LF_ETIMEOUT when the expiry was
+    detected and reported."""
+    return int(load().lf_selftest_bounded_wait(int(timeout_ns)))
 
 
 def triangulate(points: np.ndarray) -> np.ndarray:

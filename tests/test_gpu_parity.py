@@ -357,3 +357,21 @@ def test_tile_shapes_give_identical_results(baselines, allowed, rejected):
             assert np.array_equal(o[k], outs[0][k], equal_nan=True), k
     _, op = params_pair()
     check_parity(outs[0], O.run_scene(s, params=op), what=f"tiles K={len(baselines)}")
+
+
+def test_bounded_wait_expiry_is_reported_and_the_device_stays_usable():
+    """Failure detection without a fault: one CTA waits (with the sweep's
+    bounded wait) for bytes no copy delivers; the expiry comes back as
+    LF_ETIMEOUT within the limit, and the next frame runs normally."""
+    import time
+    lf = _lf()
+    t0 = time.perf_counter()
+    st = lf.selftest_bounded_wait(20_000_000)  # 20 ms
+    dt = time.perf_counter() - t0
+    assert st == lf.LF_ETIMEOUT
+    assert "expired" in lf.load().lf_last_error(None).decode()
+    assert dt < 5.0
+    assert lf.selftest_bounded_wait(0) == lf.LF_EINVAL
+    s = scenes.small_gray(0)
+    g, o = run_both(s)
+    check_parity(g, o, what="after the bounded-wait self-test")
