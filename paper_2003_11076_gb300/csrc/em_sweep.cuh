@@ -194,19 +194,19 @@ struct Staged {
 };
 
 // ---------------------------------------------------------------- M-step
-// Arg-max over the D candidates of J(d_j, S) for one pixel (lowest j wins
-// ties).  INIT: first iteration, where each ray's label is thresholded at
-// the ray's own sample (ld - ls < log(thr / (1 - thr)) means static).  Here
-// and in the other M-steps the log prior of candidate j + 1 (two dependent
+// First M-step: arg-max over the D candidates of J(d_j, S_j) for one pixel
+// (lowest j wins ties), where each ray's label S_j is thresholded at the
+// ray's own sample (ld - ls < log(thr / (1 - thr)) means static).  Here and
+// in the other M-steps the log prior of candidate j + 1 (two dependent
 // special-function operations) is evaluated while candidate j's sums are
 // formed, off the loop's critical path; the values are the same.
-template <int K, bool INIT, typename TS>
-__device__ __forceinline__ int m_step(const SweepArgs& a, const Staged<TS>& st, const float* s_w,
-                                      const int* s_o, const unsigned* s_chg, const float* s_d,
-                                      const float* s_rcp, float cy, float cx, float cz, float mu,
-                                      bool inside, unsigned S) {
-  // per camera: shifted descriptor taps (value at i0, slope to i1), the
-  // selected (or, INIT, both) log-prior taps and, INIT, the Z taps
+template <int K, typename TS>
+__device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>& st, const float* s_w,
+                                           const int* s_o, const unsigned* s_chg, const float* s_d,
+                                           const float* s_rcp, float cy, float cx, float cz, float mu,
+                                           bool inside) {
+  // per camera: shifted descriptor taps (value at i0, slope to i1), both
+  // log-prior taps and the Z taps
   float y0[K], dy[K], x0[K], dx[K], z0[K], dz[K], l0[K], dl[K], m0[K], dm[K], q0[K], dq[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -214,7 +214,6 @@ __device__ __forceinline__ int m_step(const SweepArgs& a, const Staged<TS>& st, 
     l0[k] = dl[k] = m0[k] = dm[k] = q0[k] = dq[k] = 0.f;
   }
   const int SWp = st.SWp;
-  const float rn_fixed = s_rcp[__popc(S)];
   float best = -INFINITY;
   int jb = 0;
   auto prior_at = [&](int j) {
@@ -248,42 +247,23 @@ __device__ __forceinline__ int m_step(const SweepArgs& a, const Staged<TS>& st, 
         const float Y0 = ldf(Fk + (c)), Y1 = ldf(Fk + (c + 1));
         const float X0 = ldf(Fk + (SWp + c)), X1 = ldf(Fk + (SWp + c + 1));
         const float Z0 = ldf(Fk + (2 * SWp + c)), Z1 = ldf(Fk + (2 * SWp + c + 1));
-        if (INIT) {
-          y0[k] = Y0 - cy; dy[k] = Y1 - Y0;
-          x0[k] = X0 - cx; dx[k] = X1 - X0;
-          z0[k] = Z0 - cz; dz[k] = Z1 - Z0;
-          l0[k] = ldf(Fk + (kMapLs * SWp + c)); dl[k] = ldf(Fk + (kMapLs * SWp + c + 1)) - l0[k];
-          m0[k] = ldf(Fk + (kMapLd * SWp + c)); dm[k] = ldf(Fk + (kMapLd * SWp + c + 1)) - m0[k];
-          q0[k] = ldf(Fk + (kMapZ * SWp + c)); dq[k] = ldf(Fk + (kMapZ * SWp + c + 1)) - q0[k];
-        } else {
-          const bool stat = (S >> k) & 1u;
-          const float s = stat ? 1.f : 0.f;
-          y0[k] = s * (Y0 - cy); dy[k] = s * (Y1 - Y0);
-          x0[k] = s * (X0 - cx); dx[k] = s * (X1 - X0);
-          z0[k] = s * (Z0 - cz); dz[k] = s * (Z1 - Z0);
-          const TS* Lk = Fk + (stat ? kMapLs : kMapLd) * SWp;
-          l0[k] = ldf(Lk + c); dl[k] = ldf(Lk + c + 1) - l0[k];
-        }
+        y0[k] = Y0 - cy; dy[k] = Y1 - Y0;
+        x0[k] = X0 - cx; dx[k] = X1 - X0;
+        z0[k] = Z0 - cz; dz[k] = Z1 - Z0;
+        l0[k] = ldf(Fk + (kMapLs * SWp + c)); dl[k] = ldf(Fk + (kMapLs * SWp + c + 1)) - l0[k];
+        m0[k] = ldf(Fk + (kMapLd * SWp + c)); dm[k] = ldf(Fk + (kMapLd * SWp + c + 1)) - m0[k];
+        q0[k] = ldf(Fk + (kMapZ * SWp + c)); dq[k] = ldf(Fk + (kMapZ * SWp + c + 1)) - q0[k];
       }
-      if (INIT) {
-        const bool stat = fmaf(w[k], dq[k], q0[k]) < a.log_thr;
-        const float gy = stat ? fmaf(w[k], dy[k], y0[k]) : 0.f;
-        const float gx = stat ? fmaf(w[k], dx[k], x0[k]) : 0.f;
-        const float gz = stat ? fmaf(w[k], dz[k], z0[k]) : 0.f;
-        seg += fmaf(w[k], stat ? dl[k] : dm[k], stat ? l0[k] : m0[k]);
-        n += stat ? 1 : 0;
-        sy += gy; sx += gx; sz += gz;
-        q = fmaf(gy, gy, q); q = fmaf(gx, gx, q); q = fmaf(gz, gz, q);
-      } else {
-        const float gy = fmaf(w[k], dy[k], y0[k]);
-        const float gx = fmaf(w[k], dx[k], x0[k]);
-        const float gz = fmaf(w[k], dz[k], z0[k]);
-        seg += fmaf(w[k], dl[k], l0[k]);
-        sy += gy; sx += gx; sz += gz;
-        q = fmaf(gy, gy, q); q = fmaf(gx, gx, q); q = fmaf(gz, gz, q);
-      }
+      const bool stat = fmaf(w[k], dq[k], q0[k]) < a.log_thr;
+      const float gy = stat ? fmaf(w[k], dy[k], y0[k]) : 0.f;
+      const float gx = stat ? fmaf(w[k], dx[k], x0[k]) : 0.f;
+      const float gz = stat ? fmaf(w[k], dz[k], z0[k]) : 0.f;
+      seg += fmaf(w[k], stat ? dl[k] : dm[k], stat ? l0[k] : m0[k]);
+      n += stat ? 1 : 0;
+      sy += gy; sx += gx; sz += gz;
+      q = fmaf(gy, gy, q); q = fmaf(gx, gx, q); q = fmaf(gz, gz, q);
     }
-    const float rn = INIT ? s_rcp[n] : rn_fixed;
+    const float rn = s_rcp[n];
     const float ss = fmaf(sz, sz, fmaf(sx, sx, sy * sy));
     const float var = fmaf(-ss, rn, q) * rn;
     float J = a.mseg ? seg : 0.f;
@@ -990,7 +970,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     const unsigned S0 = ps.S0[p];
     const bool fast = __all_sync(0xffffffffu, f0);
     const int jb = fast ? m_step_fixed<K, TS>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, S0)
-                        : m_step<K, true, TS>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, 0u);
+                        : m_step_init<K, TS>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside);
     Rays rays;
     sample_rays<K, TS>(a, c.st, s_w, s_o, jb, c.cy, c.cx, c.cz, rays);
     unsigned S = 0;

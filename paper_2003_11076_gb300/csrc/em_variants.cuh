@@ -272,8 +272,8 @@ __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorM
       const bool f0 = constant_initial_labels<K, float>(a, me.st, &S0);
       const int jb = f0 ? m_step_fixed<K, float>(a, me.st, s_w, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu,
                                                  me.inside, S0)
-                        : m_step<K, true, float>(a, me.st, s_w, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu,
-                                                 me.inside, 0u);
+                        : m_step_init<K, float>(a, me.st, s_w, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu,
+                                                 me.inside);
       e_step(me, tid, jb);
     }
     ps.conv[tid] = 0;
