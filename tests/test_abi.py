@@ -167,3 +167,69 @@ def test_host_delaunay_of_grid_support_points_matches_qhull(lib):
     pts = O.support_points(s.images, s.seg_prior, s.baselines, s.d_min, s.d_max, s.D)["points"].astype(np.float32)
     assert pts.shape[0] > 1000
     assert _tri_set(lf.triangulate(pts)) == _tri_set(Delaunay(pts[:, :2].astype(np.float64)).simplices)
+
+
+def _check_delaunay_valid(pts_xy, tris):
+    """Exact validity of a Delaunay triangulation of integer points: every
+    triangle counter-clockwise and non-degenerate, no input point strictly
+    inside any circumcircle, triangle areas summing to the convex hull's,
+    every edge shared by at most two triangles (hull edges by one)."""
+    from scipy.spatial import ConvexHull
+    P = [(int(x), int(y)) for x, y in pts_xy]
+    uniq = sorted(set(P))
+    area2 = 0
+    edges = {}
+    for a, b, c in np.asarray(tris).tolist():
+        (ax, ay), (bx, by), (cx, cy) = P[a], P[b], P[c]
+        o = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax)
+        assert o > 0, "triangle not counter-clockwise"
+        area2 += o
+        for dx, dy in uniq:
+            adx, ady, bdx, bdy, cdx, cdy = ax - dx, ay - dy, bx - dx, by - dy, cx - dx, cy - dy
+            det = ((adx * adx + ady * ady) * (bdx * cdy - cdx * bdy) + (bdx * bdx + bdy * bdy) * (cdx * ady - adx * cdy)
+                   + (cdx * cdx + cdy * cdy) * (adx * bdy - bdx * ady))
+            assert det <= 0, f"point {(dx, dy)} strictly inside the circumcircle of {(P[a], P[b], P[c])}"
+        for e in ((a, b), (b, c), (c, a)):
+            key = tuple(sorted((P[e[0]], P[e[1]])))
+            edges[key] = edges.get(key, 0) + 1
+    assert all(n <= 2 for n in edges.values())
+    hull = ConvexHull(np.array(uniq, np.float64))
+    assert area2 == int(round(2 * hull.volume))
+    used = {P[i] for t in np.asarray(tris).tolist() for i in t}
+    assert used == set(uniq)
+
+
+@pytest.mark.parametrize("case", ["lattice", "lattice_holes", "circle", "lattice_repeats", "collinear_rows"])
+def test_host_delaunay_degenerate_sets_are_valid(lib, case):
+    """Sets whose Delaunay triangulation is not unique (cocircular lattice
+    squares, lattice points on one circle, repeats, long collinear runs on
+    the hull): the host triangulation is a valid one, checked exactly."""
+    from paper_2003_11076_gb300 import lf
+    rng = np.random.default_rng(7)
+    if case == "lattice":
+        xy = [(x, y) for y in range(0, 60, 5) for x in range(0, 90, 5)]
+    elif case == "lattice_holes":
+        xy = [(x, y) for y in range(0, 60, 5) for x in range(0, 90, 5) if rng.uniform() > 0.3]
+    elif case == "circle":  # the 12 lattice points at distance 5 from the origin, the origin, a far point
+        xy = [(5, 0), (4, 3), (3, 4), (0, 5), (-3, 4), (-4, 3), (-5, 0), (-4, -3), (-3, -4), (0, -5), (3, -4),
+              (4, -3), (0, 0), (20, 1)]
+    elif case == "lattice_repeats":
+        base = [(x, y) for y in range(0, 40, 4) for x in range(0, 40, 4)]
+        xy = base + [base[i] for i in rng.integers(0, len(base), 30)]
+    else:
+        xy = [(x, 0) for x in range(0, 100, 2)] + [(x, 50) for x in range(0, 100, 2)] + [(50, 25), (10, 30)]
+    pts = np.array([(x, y, 1.0) for x, y in xy], np.float32)
+    tris = lf.triangulate(pts)
+    assert len(tris) > 0
+    _check_delaunay_valid(pts[:, :2], tris)
+
+
+def test_delaunay_validity_check_catches_a_wrong_flip():
+    """The exact checker above rejects a triangulation with a non-Delaunay
+    edge (the long diagonal of a thin quadrilateral)."""
+    xy = np.array([(0, 0), (10, 0), (12, 3), (0, 2)], np.float64)
+    good = np.array([(0, 1, 3), (1, 2, 3)])   # diagonal 1-3 (short)
+    bad = np.array([(0, 1, 2), (0, 2, 3)])    # diagonal 0-2 (long)
+    _check_delaunay_valid(xy, good)
+    with pytest.raises(AssertionError):
+        _check_delaunay_valid(xy, bad)
