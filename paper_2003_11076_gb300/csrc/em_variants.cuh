@@ -282,31 +282,37 @@ __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorM
       const int n = compact(run && !ps.conv[tid], ps.list, 0, s_wcnt);
       if (n == 0) break;
       executed += static_cast<unsigned long long>(n);
-      if (n <= kWarpPathPixelsPerWarp * nwarps) {
-        for (int i = warp; i < n; i += nwarps) {
-          const int p = ps.list[i];
+      // lanes per pixel: the largest power of two that still fits every
+      // remaining pixel into one round of the CTA's warps
+      int G = 1;
+      while (G < 32 && n * (G << 1) <= nwarps * 32) G <<= 1;
+      if (G > 1) {
+        const int gpw = 32 / G, gl = lane & (G - 1);
+        const int slot = warp * gpw + lane / G;
+        if (warp * gpw < n) {
+          const bool act = slot < n;
+          const int p = ps.list[act ? slot : n - 1];  // idle groups repeat the last pixel
           const PixelCtx<float> c = load_pixel(a, s_feat, u0, v0, cam_stride, p);
           const float* st = s_soft + p * NS;
-          const int per = (a.D + 31) >> 5, j0 = min(lane * per, a.D), j1 = min(j0 + per, a.D);
+          const int per = (a.D + G - 1) / G, j0 = min(gl * per, a.D), j1 = min(j0 + per, a.D);
           float jbest;
           unsigned jn = static_cast<unsigned>(m_step_soft<K>(a, c.st, s_w, s_o, s_d, c.cy, c.cx, c.cz, c.mu,
                                                              c.inside, st, st + K, j0, j1, &jbest));
-          warp_argmax(jbest, jn);
-          const int jp = ps.jb[p];
+          group_argmax(jbest, jn, G);
+          const bool conv = a.early_exit && static_cast<int>(jn) == ps.jb[p];  // q_t would equal q_{t-1}
           __syncwarp();
-          if (a.early_exit && static_cast<int>(jn) == jp) {  // q_t would equal q_{t-1}: fixed point
-            if (lane == 0) ps.conv[p] = 1;
-          } else {
-            // every lane computes the same E-step; lane 0 keeps it
+          // the E-step whenever some group of the warp goes on (every lane
+          // takes part in its shuffles; the converged groups discard it)
+          if (!__all_sync(0xffffffffu, conv)) {
             Rays rays;
             sample_rays<K, float>(a, c.st, s_w, s_o, static_cast<int>(jn), c.cy, c.cx, c.cz, rays);
             unsigned S = 0;
             float emax = 0.f;
-            enumerate_warp<K>(rays, s_rcp, a.beta, lane, S, emax);
+            enumerate_group<K>(rays, s_rcp, a.beta, gl, G, S, emax);
             float pi[K], pw[kNumPairs<K>];
             soft_posterior<K>(rays, s_rcp, a.beta, emax, pi, pw);
             __syncwarp();
-            if (lane == 0) {
+            if (act && gl == 0 && !conv) {
               float* sto = s_soft + p * NS;
 #pragma unroll
               for (int k = 0; k < K; ++k) sto[k] = pi[k];
@@ -317,6 +323,7 @@ __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorM
               ps.emax[p] = emax;
             }
           }
+          if (act && gl == 0 && conv) ps.conv[p] = 1;
         }
       } else if (tid < n) {
         const int p = ps.list[tid];
