@@ -130,8 +130,9 @@ __device__ __forceinline__ void calib_rays(const CalibArgs& a, const float (&A)[
 // One CTA per 16 x 16 block of reference pixels, one thread per pixel for
 // the first iteration; afterwards only the pixels not yet at their fixed
 // point, regrouped into dense warps before every pass (exact per-pixel early
-// exit), and one warp per pixel once few are left (lanes split the
-// candidates, then the label vectors; same tie rules, same bits).
+// exit), and groups of 2 to 32 lanes per pixel once fewer are left than the
+// CTA has threads (lanes split the candidates, then the label vectors; same
+// tie rules, same bits).
 template <int K>
 __global__ void __launch_bounds__(256) calib_sweep_kernel(const __grid_constant__ CalibArgs a) {
   __shared__ float s_rcp[16];  // 1/n for the E-step's subset sizes (0 for n < 2: Var = 0)
@@ -217,22 +218,29 @@ __global__ void __launch_bounds__(256) calib_sweep_kernel(const __grid_constant_
     const int n = compact(run && !s_conv[tid], s_list, 0, s_wcnt);
     if (n == 0) break;
     executed += static_cast<unsigned long long>(n);
-    if (n <= kWarpPathPixelsPerWarp * nwarps) {
-      for (int i = warp; i < n; i += nwarps) {
-        const int p = s_list[i];
+    // lanes per pixel: the largest power of two that still fits every
+    // remaining pixel into one round of the CTA's warps
+    int G = 1;
+    while (G < 32 && n * (G << 1) <= nwarps * 32) G <<= 1;
+    if (G > 1) {
+      const int gpw = 32 / G, gl = lane & (G - 1);
+      const int slot = warp * gpw + lane / G;
+      if (warp * gpw < n) {
+        const bool act = slot < n;
+        const int p = s_list[act ? slot : n - 1];  // idle groups repeat the last pixel
         const Px x = load(p);
         const unsigned Sp = s_S[p];
-        const int per = (a.D + 31) >> 5, j0 = min(lane * per, a.D), j1 = min(j0 + per, a.D);
+        const int per = (a.D + G - 1) / G, j0 = min(gl * per, a.D), j1 = min(j0 + per, a.D);
         float jbest;
         unsigned jb = static_cast<unsigned>(
             calib_m_step<K, false>(a, x.A, x.cy, x.cx, x.cz, x.mu, x.inside, Sp, j0, j1, &jbest));
-        warp_argmax(jbest, jb);
+        group_argmax(jbest, jb, G);
         Rays rays;
         calib_rays<K>(a, x.A, static_cast<int>(jb), x.cy, x.cx, x.cz, rays);
         unsigned S = 0;
         float emax = 0.f;
-        enumerate_warp<K>(rays, s_rcp, a.beta, lane, S, emax);
-        if (lane == 0) {
+        enumerate_group<K>(rays, s_rcp, a.beta, gl, G, S, emax);
+        if (act && gl == 0) {
           s_jb[p] = static_cast<int16_t>(jb);
           s_S[p] = static_cast<uint16_t>(S);
           s_emax[p] = emax;

@@ -539,11 +539,6 @@ __device__ __forceinline__ void enumerate(const Rays& r, const float* s_rcp, flo
 // rules as the one-thread sweep (lowest candidate, smallest mask), so the
 // result is bit-identical.
 
-// A CTA in the calibrated and soft-EM kernels takes the warp-per-pixel path
-// when at most this many pixels per warp are still iterating (each warp then
-// runs its pixels one after another).
-constexpr int kWarpPathPixelsPerWarp = 4;
-
 // Larger objective, or on a tie the lower index, over the G lanes of each
 // aligned group (every lane of the warp takes part).
 __device__ __forceinline__ void group_argmax(float& best, unsigned& idx, int G) {
@@ -556,7 +551,6 @@ __device__ __forceinline__ void group_argmax(float& best, unsigned& idx, int G) 
     }
   }
 }
-__device__ __forceinline__ void warp_argmax(float& best, unsigned& idx) { group_argmax(best, idx, 32); }
 
 // Arg-max of the E-step by lane gl of a group of G.  Up to six cameras each
 // lane takes masks gl, gl + G, ... and forms their sums from scratch in the
@@ -609,11 +603,6 @@ __device__ __forceinline__ void enumerate_group(const Rays& r, const float* s_rc
   group_argmax(b, bm, G);
   bmask = bm;
   best = b;
-}
-template <int K>
-__device__ __forceinline__ void enumerate_warp(const Rays& r, const float* s_rcp, float beta, int lane,
-                                               unsigned& bmask, float& best) {
-  enumerate_group<K>(r, s_rcp, beta, lane, 32, bmask, best);
 }
 
 // Element c of the pixel at p (an image of dtype a.dtype), unscaled.
