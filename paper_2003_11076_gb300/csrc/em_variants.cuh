@@ -176,8 +176,9 @@ static_assert(kSoftStateFloats<1> == soft_state_floats(1) && kSoftStateFloats<2>
 // One tile.  Joint MAP: one thread per pixel (every pixel does the same
 // work).  Soft EM: the first iteration one thread per pixel, then only the
 // pixels not yet at their fixed point, regrouped into dense warps before
-// every pass, and one warp per pixel once few are left (lanes split the
-// candidates; same tie rule, same bits).
+// every pass, and groups of 2 to 32 lanes per pixel once fewer are left than
+// the CTA has threads (lanes split the candidates; same tie rule, same
+// bits).
 template <int K, int MODE>
 __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorMap* img_map,
                                              const CUtensorMap* p_map, int tile_x, int tile_y, uint8_t* smem) {
