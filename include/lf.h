@@ -398,13 +398,16 @@ void lf_batch_destroy(lf_batch *b);
  * allocating routine.
  *   Limits: D <= 256 (the tables the array holds); images and seg_prior rows
  *   must start on 16-byte boundaries (W * bytes per pixel a multiple of 16),
- *   because they are read in place; otherwise LF_EINVAL.
- *   The first call on a device looks up the array's device address with that
- *   device current; make that first call before any stream capture.
+ *   because they are read in place; hard EM on float32 maps, every pixel
+ *   (em_mode = LF_EM_HARD, precision = LF_PREC_F32, dynamic_only = 0);
+ *   p is checked as lf_create checks it.  Otherwise LF_EINVAL.
+ *   Every call looks up the array's device address for the current device
+ *   (nothing is cached between calls).
+ *   The call is synchronous: it waits for `stream` (a cudaStream_t, NULL =
+ *   legacy default stream) before returning.
  *   All calls share the one array and leave their contents in it (each call
  *   clears the counter and status it needs); calls whose GPU work overlaps
- *   would race on it, so the call serialises its callers and waits for
- *   `stream` (a cudaStream_t, NULL = legacy default stream) before returning.
+ *   would race on it, so the call serialises its callers.
  * Errors as lf_run_em (message in lf_last_error).
  */
 lf_status lf_run_em_static(int n_cams, const float *baselines, int H, int W, float d_min, float d_max,

@@ -182,6 +182,31 @@ constexpr unsigned long long kTimeoutNs = 2000000000ull;  // 2 s bounded device 
 
 void lf::set_error_message(const std::string& msg) { g_err = msg; }
 
+bool lf::check_params(const lf_params& p, std::string* why) {
+  const char* msg = nullptr;
+  if (!std::isfinite(p.beta) || !std::isfinite(p.gamma) || !std::isfinite(p.sigma) ||
+      !std::isfinite(p.seg_threshold) || !std::isfinite(p.eps))
+    msg = "invalid lf_params: non-finite constant";
+  else if (p.sigma <= 0.f)
+    msg = "invalid lf_params: sigma must be > 0";
+  else if (p.gamma < 0.f)
+    msg = "invalid lf_params: gamma must be >= 0";
+  else if (p.eps <= 0.f)
+    msg = "invalid lf_params: eps must be > 0";
+  else if (p.beta < 0.f)
+    msg = "invalid lf_params: beta must be >= 0";
+  else if (p.seg_threshold <= 0.f || p.seg_threshold >= 1.f)
+    msg = "invalid lf_params: seg_threshold must be in (0, 1)";
+  else if (p.precision != LF_PREC_F32 && p.precision != LF_PREC_F16 && p.precision != LF_PREC_BF16)
+    msg = "precision must be LF_PREC_F32, LF_PREC_F16 or LF_PREC_BF16";
+  else if (p.em_mode != LF_EM_HARD && p.em_mode != LF_EM_SOFT && p.em_mode != LF_EM_JOINT)
+    msg = "em_mode must be LF_EM_HARD, LF_EM_SOFT or LF_EM_JOINT";
+  else if (p.em_mode != LF_EM_HARD && p.precision != LF_PREC_F32)
+    msg = "the soft-EM and joint-MAP modes stage float32 maps only (LF_PREC_F32)";
+  if (msg && why) *why = msg;
+  return msg == nullptr;
+}
+
 struct lf_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -535,16 +560,8 @@ lf_status create_ctx(lf_ctx** out, int n_cams, const float* baselines, const flo
   lf_params prm;
   lf_default_params(&prm);
   if (p) prm = *p;
-  if (!finite(prm.beta) || !finite(prm.gamma) || !finite(prm.sigma) || !finite(prm.seg_threshold) ||
-      !finite(prm.eps) || prm.sigma <= 0.f || prm.gamma < 0.f || prm.eps <= 0.f || prm.seg_threshold <= 0.f ||
-      prm.seg_threshold >= 1.f || prm.beta < 0.f)
-    return fail(LF_EINVAL, "invalid lf_params");
-  if (prm.precision != LF_PREC_F32 && prm.precision != LF_PREC_F16 && prm.precision != LF_PREC_BF16)
-    return fail(LF_EINVAL, "precision must be LF_PREC_F32, LF_PREC_F16 or LF_PREC_BF16");
-  if (prm.em_mode != LF_EM_HARD && prm.em_mode != LF_EM_SOFT && prm.em_mode != LF_EM_JOINT)
-    return fail(LF_EINVAL, "em_mode must be LF_EM_HARD, LF_EM_SOFT or LF_EM_JOINT");
-  if (prm.em_mode != LF_EM_HARD && prm.precision != LF_PREC_F32)
-    return fail(LF_EINVAL, "the soft-EM and joint-MAP modes stage float32 maps only (LF_PREC_F32)");
+  std::string why;
+  if (!check_params(prm, &why)) return fail(LF_EINVAL, why);
   if (prm.em_mode == LF_EM_SOFT && n_cams > 8) return fail(LF_EINVAL, "soft EM supports at most 8 cameras");
   if (cameras && (prm.em_mode != LF_EM_HARD || prm.precision != LF_PREC_F32))
     return fail(LF_EINVAL, "calibrated arrays run the hard EM on float32 maps (LF_EM_HARD, LF_PREC_F32)");

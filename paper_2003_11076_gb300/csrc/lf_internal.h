@@ -6,6 +6,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "lf.h"
+
 namespace lf {
 
 constexpr int kMaxCams = 12;       // 2^K label vectors per E-step
@@ -221,6 +223,12 @@ int em_sweep_persistent_occupancy(int K, int prec, size_t smem, int threads);
 // float32 [rows][W*C] (pitch_in bytes) -> float16 (to_bf16 = 0) or bfloat16 rows (pitch_out bytes)
 cudaError_t launch_convert_f32(const uint8_t* in, size_t pitch_in, uint8_t* out, size_t pitch_out, int rows,
                                int cols, int to_bf16, cudaStream_t s);
+
+// Validity of the model and run parameters every entry point shares: finite
+// constants with sigma > 0, gamma >= 0, eps > 0, beta >= 0 and
+// 0 < seg_threshold < 1; precision and em_mode among their enumerators; the
+// two EM variants on float32 maps only.  False with *why set otherwise.
+bool check_params(const lf_params& p, std::string* why);
 
 // Sets the calling thread's message returned by lf_last_error.
 void set_error_message(const std::string& msg);

@@ -43,11 +43,10 @@ constexpr size_t kStaticUsed = kOffStatus + sizeof(unsigned);
 static_assert(kStaticUsed <= kStaticScratchBytes, "static scratch too small for its layout");
 
 // The scratch itself.  In host code this name is only a host-side handle;
-// the device address comes from cudaGetSymbolAddress (per device).
+// the device address comes from cudaGetSymbolAddress, on every call.
 static __device__ __align__(256) unsigned char g_lf_static_scratch[kStaticScratchBytes];
 
-std::mutex g_static_mutex;             // serialises host staging and set-up
-void* g_scratch_addr[64] = {nullptr};  // device address per device ordinal
+std::mutex g_static_mutex;                // serialises host staging and the GPU work
 unsigned char g_host_stage[kOffCounter];  // host copy of the tables (pageable)
 
 lf_status fail(lf_status s, const std::string& m) {
@@ -116,8 +115,11 @@ extern "C" lf_status lf_run_em_static(int n_cams, const float* baselines, int H,
   lf_params prm;
   lf_default_params(&prm);
   if (p) prm = *p;
+  std::string why;
+  if (!check_params(prm, &why)) return fail(LF_EINVAL, why);  // the same checks as lf_create
   if (prm.precision != LF_PREC_F32) return fail(LF_EINVAL, "the allocation-free sweep stages float32 maps only (LF_PREC_F32)");
   if (prm.em_mode != LF_EM_HARD) return fail(LF_EINVAL, "the allocation-free sweep runs the hard EM only (LF_EM_HARD)");
+  if (prm.dynamic_only) return fail(LF_EINVAL, "the allocation-free sweep reconstructs every pixel (dynamic_only = 0)");
   const size_t bpp = static_cast<size_t>(C) * (dtype == LF_U8 ? 1 : 4);
   // Without staging buffers the inputs are read in place by TMA: rows must
   // start on 16-byte boundaries.
@@ -128,14 +130,15 @@ extern "C" lf_status lf_run_em_static(int n_cams, const float* baselines, int H,
   std::lock_guard<std::mutex> lock(g_static_mutex);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= 64) return fail(LF_ECUDA, "cudaGetDevice failed");
-  if (!g_scratch_addr[dev]) {  // once per device, with that device current
-    void* addr = nullptr;
-    e = cudaGetSymbolAddress(&addr, g_lf_static_scratch);
-    if (e != cudaSuccess) return fail(LF_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_scratch_addr[dev] = addr;
-  }
-  unsigned char* scratch = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  if (e != cudaSuccess) return fail(LF_ECUDA, "cudaGetDevice failed");
+  // The array's device address, looked up on every call with the caller's
+  // device current: cheap, allocates nothing, and never stale (a cached
+  // address would outlive a cudaDeviceReset that reloads the module).
+  void* addr = nullptr;
+  e = cudaGetSymbolAddress(&addr, g_lf_static_scratch);
+  if (e != cudaSuccess || !addr)
+    return fail(LF_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  unsigned char* scratch = static_cast<unsigned char*>(addr);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   // sampling tables, as lf_create builds them

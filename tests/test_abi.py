@@ -233,3 +233,39 @@ def test_delaunay_validity_check_catches_a_wrong_flip():
     _check_delaunay_valid(xy, good)
     with pytest.raises(AssertionError):
         _check_delaunay_valid(xy, bad)
+
+
+@pytest.mark.parametrize("field,value,expect", [
+    ("sigma", 0.0, "sigma"), ("seg_threshold", 1.0, "seg_threshold"), ("seg_threshold", 0.0, "seg_threshold"),
+    ("eps", 0.0, "eps"), ("gamma", -1.0, "gamma"), ("beta", float("nan"), "non-finite"),
+    ("precision", 7, "precision"), ("em_mode", 9, "em_mode"),
+])
+def test_create_and_static_entry_check_params_alike(lib, field, value, expect):
+    """lf_create and the allocation-free lf_run_em_static share one parameter
+    check; both reject before any device work (so this runs without a GPU)."""
+    from paper_2003_11076_gb300 import lf
+    p = lf.default_params()
+    setattr(p, field, value)
+    b = np.array([-0.1, 0.0, 0.1], np.float32)
+    h = ctypes.c_void_p()
+    assert lib.lf_create(ctypes.byref(h), 3, b.ctypes.data, 16, 16, 0.0, 7.0, 8, ctypes.byref(p)) == lf.LF_EINVAL
+    assert not h.value and expect in lib.lf_last_error(None).decode()
+    img = np.zeros((3, 16, 16), np.float32)  # host stand-ins: never dereferenced on this path
+    mu = np.zeros((16, 16), np.float32)
+    didx = np.zeros((16, 16), np.int32)
+    s = lib.lf_run_em_static(3, b.ctypes.data, 16, 16, 0.0, 7.0, 8, ctypes.byref(p), 3, img.ctypes.data, 1,
+                             lf.LF_F32, img.ctypes.data, mu.ctypes.data, didx.ctypes.data, None, None, None, None)
+    assert s == lf.LF_EINVAL
+    assert expect in lib.lf_last_error(None).decode()
+
+
+def test_static_entry_rejects_dynamic_only(lib):
+    from paper_2003_11076_gb300 import lf
+    p = lf.default_params(dynamic_only=1)
+    b = np.array([-0.1, 0.0, 0.1], np.float32)
+    img = np.zeros((3, 16, 16), np.float32)
+    mu = np.zeros((16, 16), np.float32)
+    didx = np.zeros((16, 16), np.int32)
+    s = lib.lf_run_em_static(3, b.ctypes.data, 16, 16, 0.0, 7.0, 8, ctypes.byref(p), 3, img.ctypes.data, 1,
+                             lf.LF_F32, img.ctypes.data, mu.ctypes.data, didx.ctypes.data, None, None, None, None)
+    assert s == lf.LF_EINVAL and "dynamic_only" in lib.lf_last_error(None).decode()

@@ -68,3 +68,27 @@ def test_static_entry_rejects_what_it_cannot_hold():
     with pytest.raises(lf.LfError) as e:
         lf.run_em_static(s.baselines, s.d_min, s.d_max, s.D, 3, img_odd, seg_odd, mu_odd, out_odd)
     assert e.value.status == lf.LF_EINVAL and "aligned" in str(e.value)
+
+
+def test_static_entry_checks_params_as_lf_create_does():
+    """sigma = 0 or seg_threshold = 1 would make the sweep divide by zero or
+    take log(thr / (1 - thr)) = inf; the call must refuse them, not return
+    LF_OK with meaningless disparities."""
+    import torch
+    from paper_2003_11076_gb300 import build, lf, scenes
+    build.build()
+    s = scenes.small_gray(0)
+    dev = torch.device("cuda")
+    img = torch.from_numpy(s.images).to(dev)
+    seg = torch.from_numpy(s.seg_prior).to(dev)
+    mu = torch.zeros((s.H, s.W), dtype=torch.float32, device=dev)
+    out = {"d_idx": torch.empty((s.H, s.W), dtype=torch.int32, device=dev)}
+    for field, value in (("sigma", 0.0), ("seg_threshold", 1.0)):
+        p = lf.default_params(**{field: value})
+        with pytest.raises(lf.LfError) as e:
+            lf.run_em_static(s.baselines, s.d_min, s.d_max, s.D, 3, img, seg, mu, out, params=p)
+        assert e.value.status == lf.LF_EINVAL and field in str(e.value)
+    # and a valid call right after still works
+    ref = lf.run_scene(s)
+    got = _static_call(lf, s, torch.from_numpy(ref["mu"]).cuda(), torch)
+    assert np.array_equal(got["d_idx"], ref["d_idx"])
