@@ -51,6 +51,19 @@ def sweep_ops_per_pixel_iter(K: int, D: int) -> int:
     return D * (11 * K + 12) + (1 << K) * 13
 
 
+def scope_ops(pix_iters: float, static_samples: float, K: int, D: int) -> float:
+    """Algorithmic FP32/INT lane-operations of the hard EM by the op model of
+    the hot-path scope table: a static ray sample costs 29 (8 interpolations
+    of 2, 9 for the shifted sums and squares, 1 segmentation add, 3 for the
+    address and weight), a dynamic one 4, each (pixel, candidate) 12 more
+    (variance, prior, objective, compare) and each E-step label vector 20.
+    pix_iters: executed pixel-iterations; static_samples: the executed ray
+    samples whose ray was static in its M-step (counted by the kernel)."""
+    samples = pix_iters * K * D
+    return 29.0 * static_samples + 4.0 * (samples - static_samples) + 12.0 * D * pix_iters + \
+        20.0 * (1 << K) * pix_iters
+
+
 def soft_ops_per_pixel_iter(K: int, D: int) -> int:
     """Soft-EM iteration after the first: M-step per (candidate, camera) 5
     interpolations + 1 expected segmentation term, per camera pair 7 (3
@@ -553,8 +566,15 @@ def main():
             ops = pix_iters * calib_ops_per_pixel_iter(K, D)
             ops_desc = {"ops_per_pixel_iteration": calib_ops_per_pixel_iter(K, D)}
         elif mode == 0:
-            ops = pix_iters * sweep_ops_per_pixel_iter(K, D)
-            ops_desc = {"ops_per_pixel_iteration": sweep_ops_per_pixel_iter(K, D)}
+            static_mean = st["executed_static_ray_samples"] / st["runs"]
+            ops = scope_ops(pix_iters, static_mean, K, D)
+            tight = pix_iters * sweep_ops_per_pixel_iter(K, D)
+            ops_desc = {"ops_model": "scope-table op model: 29 per static ray sample, 4 per dynamic, 12 per "
+                                     "(pixel, candidate), 20 per E-step label vector",
+                        "ops_per_frame": ops, "static_ray_share": static_mean / exec_mean,
+                        "frac_tight_model": None, "tight_model": "11 per ray sample, 12 per (pixel, candidate), "
+                                                                 "13 per label vector",
+                        "ops_per_pixel_iteration_tight": sweep_ops_per_pixel_iter(K, D)}
         elif mode == 1:  # every swept pixel's first iteration is the EM's first M-step
             first = min(pix_iters, H * W * (float(np.mean(s.seg_prior[int(np.argmin(np.abs(s.baselines)))] >= 0.7)) if args.dynamic_only else 1))
             ops = first * sweep_ops_per_pixel_iter(K, D) + (pix_iters - first) * soft_ops_per_pixel_iter(K, D)
@@ -567,6 +587,8 @@ def main():
         achieved = ops / sweep_s / 1e9
         f_mhz = clk.get("sm_mhz") or 2070.0
         peak = n_sm * 128 * f_mhz * 1e6 / 1e9
+        if "frac_tight_model" in ops_desc:
+            ops_desc["frac_tight_model"] = tight / sweep_s / 1e9 / peak
         traffic = None
         if os.path.exists(TRAFFIC_FILE):
             kv = {}
@@ -589,6 +611,7 @@ def main():
                        "staged_maps": args.precision,
                        "frames_per_s": args.steps * world / total_s,
                        "executed_ray_samples_per_frame": exec_mean,
+                       "executed_ray_samples_per_s": exec_mean * args.steps * world / total_s,
                        "nominal_ray_samples_per_frame": nominal,
                        "kernel_ms": {"prior_raster": st["ms_prior"], "em_sweep": st["ms_sweep"],
                                      "refocus": st["ms_refocus"]},
@@ -603,6 +626,8 @@ def main():
             "roofline": {"bound": "alu", "kernel": "calib_sweep" if args.calibrated else
                          ("em_sweep" if mode == 0 else "em_variant"), "achieved": achieved,
                          "peak": peak, "unit": "Gop/s", "frac": achieved / peak, "traffic": traffic,
+                         "traffic_source": "recorded ncu capture of this kernel source (profiles/), not measured "
+                                           "in this run" if traffic is not None else None,
                          "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {f_mhz:.0f} MHz (median sampled SM clock "
                                        f"during the timed region)", **ops_desc},
             "e2e": {"value": whole_job_value(nominal * e2e_pipe_steps, world, e2e_s), "unit": UNIT,

@@ -136,6 +136,9 @@ typedef struct lf_stats {
     float ms_support;              /* device time of the last support-point detection */
     float ms_set_inputs;           /* mean host time of lf_set_inputs (copies, detection,
                                       Delaunay, bins) over the calls covered */
+    uint64_t executed_static_ray_samples; /* of executed_ray_samples, those whose ray was
+                                      labelled static in its M-step (hard EM on a
+                                      rectified array; 0 for the other modes) */
 } lf_stats;
 
 /* Fill *p with the documented defaults. */

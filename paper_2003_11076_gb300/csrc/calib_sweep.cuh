@@ -6,9 +6,9 @@
 // exact per-pixel early exit, posteriors of the final labels.
 //
 // What differs is the sampling.  A ray of reference pixel (u, v) at disparity
-// d lands at (X / Z, Y / Z) with (X, Y, Z) = A_k + d E_k, where A_k =
-// cam_k[:, :3] (u, v, 1) is computed once per pixel and E_k = cam_k[:, 3].  The
-// position moves along the epipolar line in both image directions, so the
+// d lands at (X / Z, Y / Z) with (X, Y, Z) = cam_k (u, v, 1, d); the kernel
+// locates it by its offset from (u, v) (calib_geom.cuh), whose pixel-constant
+// parts are computed once per pixel and pass.  The position moves along the epipolar line in both image directions, so the
 // rectified kernel's row staging with a horizontal halo does not apply: the
 // descriptor maps of all cameras are written to HBM once per run (20 bytes per
 // camera pixel, L2-resident at the paper's frame size) and each ray sample is
@@ -17,6 +17,7 @@
 // gathers of a warp share cache lines.
 #pragma once
 
+#include "calib_geom.cuh"
 #include "em_sweep.cuh"
 
 namespace lf {
@@ -26,16 +27,14 @@ struct CalibRay {
   float gy, gx, gz, ls, ld;
 };
 
-// Bilinear sample of camera k's maps at (x, y), both clamped to the image,
-// with the descriptors shifted by the reference ray's.
-__device__ __forceinline__ CalibRay calib_sample(const CalibArgs& a, int k, float X, float Y, float Z, float cy,
-                                                 float cx, float cz) {
-  const float iz = 1.f / Z;
-  const float x = fminf(fmaxf(X * iz, 0.f), static_cast<float>(a.W - 1));
-  const float y = fminf(fmaxf(Y * iz, 0.f), static_cast<float>(a.H - 1));
-  const int i0 = static_cast<int>(x), j0 = static_cast<int>(y);  // x, y >= 0: truncation = floor
-  const int i1 = min(i0 + 1, a.W - 1), j1 = min(j0 + 1, a.H - 1);
-  const float wx = x - static_cast<float>(i0), wy = y - static_cast<float>(j0);
+// Bilinear sample of camera k's maps at the ray of pixel (u, v) at disparity
+// d, both coordinates clamped to the image, with the descriptors shifted by
+// the reference ray's.
+__device__ __forceinline__ CalibRay calib_sample(const CalibArgs& a, int k, const CalibPix& cp, int u, int v,
+                                                 float d, float cy, float cx, float cz) {
+  const CalibTaps t = calib_taps(a.cam[k], cp, u, v, d, a.W, a.H);
+  const int i0 = t.i0, i1 = t.i1, j0 = t.j0, j1 = t.j1;
+  const float wx = t.wx, wy = t.wy;
   const size_t plane = static_cast<size_t>(k) * a.H * a.W;
   const size_t r0 = plane + static_cast<size_t>(j0) * a.W, r1 = plane + static_cast<size_t>(j1) * a.W;
   const float4 p00 = __ldg(a.fa + r0 + i0), p01 = __ldg(a.fa + r0 + i1);
@@ -61,7 +60,7 @@ __device__ __forceinline__ CalibRay calib_sample(const CalibArgs& a, int k, floa
 // candidate is evaluated from scratch, so a range computes the same
 // objectives as the whole sweep.
 template <int K, bool INIT>
-__device__ __forceinline__ int calib_m_step(const CalibArgs& a, const float (&A)[K][3], float cy, float cx,
+__device__ __forceinline__ int calib_m_step(const CalibArgs& a, const CalibPix (&A)[K], int u, int v, float cy, float cx,
                                             float cz, float mu, bool inside, unsigned S, int j0, int j1,
                                             float* best_out) {
   float best = -INFINITY;
@@ -81,14 +80,12 @@ __device__ __forceinline__ int calib_m_step(const CalibArgs& a, const float (&A)
     for (int k = 0; k < K; ++k) {
       if (!INIT && !(S >> k & 1u)) {  // a dynamic ray contributes its log p(dynamic) only
         if (a.mseg) {
-          const CalibRay r = calib_sample(a, k, fmaf(d, a.cam[k][3], A[k][0]), fmaf(d, a.cam[k][7], A[k][1]),
-                                          fmaf(d, a.cam[k][11], A[k][2]), cy, cx, cz);
+          const CalibRay r = calib_sample(a, k, A[k], u, v, d, cy, cx, cz);
           seg += r.ld;
         }
         continue;
       }
-      const CalibRay r = calib_sample(a, k, fmaf(d, a.cam[k][3], A[k][0]), fmaf(d, a.cam[k][7], A[k][1]),
-                                      fmaf(d, a.cam[k][11], A[k][2]), cy, cx, cz);
+      const CalibRay r = calib_sample(a, k, A[k], u, v, d, cy, cx, cz);
       const bool stat = INIT ? (r.ld - r.ls < a.log_thr) : true;
       if (stat) {
         sy += r.gy; sx += r.gx; sz += r.gz;
@@ -112,14 +109,13 @@ __device__ __forceinline__ int calib_m_step(const CalibArgs& a, const float (&A)
 }
 
 template <int K>
-__device__ __forceinline__ void calib_rays(const CalibArgs& a, const float (&A)[K][3], int j, float cy, float cx,
+__device__ __forceinline__ void calib_rays(const CalibArgs& a, const CalibPix (&A)[K], int u, int v, int j, float cy, float cx,
                                            float cz, Rays& r) {
   const float d = __ldg(a.dval + j);
   r.base = 0.f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const CalibRay s = calib_sample(a, k, fmaf(d, a.cam[k][3], A[k][0]), fmaf(d, a.cam[k][7], A[k][1]),
-                                    fmaf(d, a.cam[k][11], A[k][2]), cy, cx, cz);
+    const CalibRay s = calib_sample(a, k, A[k], u, v, d, cy, cx, cz);
     r.gy[k] = s.gy; r.gx[k] = s.gx; r.gz[k] = s.gz;
     r.qk[k] = fmaf(s.gz, s.gz, fmaf(s.gx, s.gx, s.gy * s.gy));
     r.ak[k] = s.ls - s.ld;
@@ -173,7 +169,8 @@ __global__ void __launch_bounds__(256) calib_sweep_kernel(const __grid_constant_
   }
   // everything the EM of block pixel p needs, recomputed per pass
   struct Px {
-    float A[K][3];
+    CalibPix A[K];
+    int u, v;
     float mu, cy, cx, cz;
     bool inside;
   };
@@ -182,11 +179,9 @@ __global__ void __launch_bounds__(256) calib_sweep_kernel(const __grid_constant_
     const int pu = bu + (p & 15), pv = bv + (p >> 4);
     const size_t pix = static_cast<size_t>(pv) * a.W + pu;
 #pragma unroll
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-        x.A[k][r] = fmaf(a.cam[k][4 * r], static_cast<float>(pu),
-                         fmaf(a.cam[k][4 * r + 1], static_cast<float>(pv), a.cam[k][4 * r + 2]));
+    for (int k = 0; k < K; ++k) x.A[k] = calib_pixel(a.cam[k], static_cast<float>(pu), static_cast<float>(pv));
+    x.u = pu;
+    x.v = pv;
     x.mu = a.mu[pix];
     x.inside = !isnan(x.mu);
     const float4 fr = a.fa[static_cast<size_t>(a.ref) * a.H * a.W + pix];
@@ -201,9 +196,9 @@ __global__ void __launch_bounds__(256) calib_sweep_kernel(const __grid_constant_
     if (tid < n) {
       const int p = s_list[tid];
       const Px x = load(p);
-      const int jb = calib_m_step<K, true>(a, x.A, x.cy, x.cx, x.cz, x.mu, x.inside, 0u, 0, a.D, nullptr);
+      const int jb = calib_m_step<K, true>(a, x.A, x.u, x.v, x.cy, x.cx, x.cz, x.mu, x.inside, 0u, 0, a.D, nullptr);
       Rays rays;
-      calib_rays<K>(a, x.A, jb, x.cy, x.cx, x.cz, rays);
+      calib_rays<K>(a, x.A, x.u, x.v, jb, x.cy, x.cx, x.cz, rays);
       unsigned S = 0;
       float emax = 0.f;
       enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
@@ -233,10 +228,10 @@ __global__ void __launch_bounds__(256) calib_sweep_kernel(const __grid_constant_
         const int per = (a.D + G - 1) / G, j0 = min(gl * per, a.D), j1 = min(j0 + per, a.D);
         float jbest;
         unsigned jb = static_cast<unsigned>(
-            calib_m_step<K, false>(a, x.A, x.cy, x.cx, x.cz, x.mu, x.inside, Sp, j0, j1, &jbest));
+            calib_m_step<K, false>(a, x.A, x.u, x.v, x.cy, x.cx, x.cz, x.mu, x.inside, Sp, j0, j1, &jbest));
         group_argmax(jbest, jb, G);
         Rays rays;
-        calib_rays<K>(a, x.A, static_cast<int>(jb), x.cy, x.cx, x.cz, rays);
+        calib_rays<K>(a, x.A, x.u, x.v, static_cast<int>(jb), x.cy, x.cx, x.cz, rays);
         unsigned S = 0;
         float emax = 0.f;
         enumerate_group<K>(rays, s_rcp, a.beta, gl, G, S, emax);
@@ -251,9 +246,9 @@ __global__ void __launch_bounds__(256) calib_sweep_kernel(const __grid_constant_
       const int p = s_list[tid];
       const Px x = load(p);
       const unsigned Sp = s_S[p];
-      const int jb = calib_m_step<K, false>(a, x.A, x.cy, x.cx, x.cz, x.mu, x.inside, Sp, 0, a.D, nullptr);
+      const int jb = calib_m_step<K, false>(a, x.A, x.u, x.v, x.cy, x.cx, x.cz, x.mu, x.inside, Sp, 0, a.D, nullptr);
       Rays rays;
-      calib_rays<K>(a, x.A, jb, x.cy, x.cx, x.cz, rays);
+      calib_rays<K>(a, x.A, x.u, x.v, jb, x.cy, x.cx, x.cz, rays);
       unsigned S = 0;
       float emax = 0.f;
       enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
@@ -275,7 +270,7 @@ __global__ void __launch_bounds__(256) calib_sweep_kernel(const __grid_constant_
     if (a.post) {
       const Px x = load(tid);
       Rays rays;
-      calib_rays<K>(a, x.A, jb, x.cy, x.cx, x.cz, rays);
+      calib_rays<K>(a, x.A, x.u, x.v, jb, x.cy, x.cx, x.cz, rays);
       float post[K];
       unsigned dummy;
       float dummyf;

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 
+#include "calib_geom.cuh"
 #include "lf_internal.h"
 
 namespace lf {
@@ -90,15 +91,10 @@ __global__ void calib_refocus_kernel(const CalibArgs a) {
     if (!(S >> k & 1u)) continue;
     ++n;
     const float* M = a.cam[k];
-    const float X = fmaf(d, M[3], fmaf(M[0], static_cast<float>(u), fmaf(M[1], static_cast<float>(v), M[2])));
-    const float Y = fmaf(d, M[7], fmaf(M[4], static_cast<float>(u), fmaf(M[5], static_cast<float>(v), M[6])));
-    const float Z = fmaf(d, M[11], fmaf(M[8], static_cast<float>(u), fmaf(M[9], static_cast<float>(v), M[10])));
-    const float iz = 1.f / Z;
-    const float x = fminf(fmaxf(X * iz, 0.f), static_cast<float>(a.W - 1));
-    const float y = fminf(fmaxf(Y * iz, 0.f), static_cast<float>(a.H - 1));
-    const int i0 = static_cast<int>(x), j0 = static_cast<int>(y);
-    const int i1 = min(i0 + 1, a.W - 1), j1 = min(j0 + 1, a.H - 1);
-    const float wx = x - static_cast<float>(i0), wy = y - static_cast<float>(j0);
+    const dev::CalibTaps t =
+        dev::calib_taps(M, dev::calib_pixel(M, static_cast<float>(u), static_cast<float>(v)), u, v, d, a.W, a.H);
+    const int i0 = t.i0, i1 = t.i1, j0 = t.j0, j1 = t.j1;
+    const float wx = t.wx, wy = t.wy;
     const uint8_t* r0 = a.img + (static_cast<size_t>(k) * a.H + j0) * a.img_pitch;
     const uint8_t* r1 = a.img + (static_cast<size_t>(k) * a.H + j1) * a.img_pitch;
     for (int c = 0; c < a.C; ++c) {

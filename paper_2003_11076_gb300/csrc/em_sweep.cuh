@@ -95,17 +95,119 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-// Staged maps per camera and tile row: luminance, Sobel-x/8, Sobel-y/8,
-// log p(static) = log max(1-P, eps), log p(dynamic) = log max(P, eps), and
-// their difference Z = log p(dynamic) - log p(static) (first-iteration test).
-constexpr int kMapY = 0, kMapSx = 1, kMapSy = 2, kMapLs = 3, kMapLd = 4, kMapZ = 5, kMaps = 6;
+// Staged maps per camera and tile row (Sec. III-C descriptors and the
+// segmentation prior of Sec. III-B), SWp texels each:
+//   Y   luminance
+//   X   Sobel-x / 8
+//   Zs  Sobel-y / 8
+//   ls  log p(static)  = log max(1 - P, eps)
+//   ld  log p(dynamic) = log max(P, eps)
+//   T   ld - ls, the first-iteration label test (static iff its
+//       interpolated value is below log(thr / (1 - thr)))
+// stored per precision mode as planes of register pairs, so that one load
+// gives two values the packed float32x2 arithmetic uses together:
+//   float32   (Y, X) float2 | (Zs, ld) float2 | ls float  | T float    24 B
+//   float16   Y float | (X, Zs) half2  | (ld, ls) float2 | T float     20 B
+//   bfloat16  Y float | (X, Zs) bf162  | (ld, ls) float2 | T float     20 B
+// Only the Sobel responses (differences of neighbouring luminances: small
+// numbers that keep their relative precision) are stored in 16 bits.  The
+// luminance and the log segmentation maps stay float32: rounding the
+// luminance to 16 bits moves the photometric variance, and rounding the log
+// maps moves the segmentation term and the label test, by more than the
+// arg-max margins the parity rule allows (16-bit luminance alone takes the
+// disparity agreement of a float32 gray frame to 99.84 % in float16 and
+// 98.8 % in bfloat16; bfloat16 log maps to 99.94 % on the 960 x 600 frame).
+__host__ __device__ constexpr int texel_bytes(int prec) {
+  return prec == kPrecF32 ? 24 : 20;
+}
 
-// First-iteration labels are decided on lerp(Z) < log(thr / (1 - thr)).  A
-// camera whose Z texels over the pixel's whole sample range stay at least
+// First-iteration labels are decided on lerp(T) < log(thr / (1 - thr)).  A
+// camera whose T texels over the pixel's whole sample range stay at least
 // this far on one side of the threshold has the same label for every
 // candidate (the interpolated value cannot leave [min, max] by more than a
 // few units of float32 rounding, far below this margin).
 constexpr float kThresholdMargin = 1e-4f;
+
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+template <typename TS>
+struct Texels;
+
+template <>
+struct Texels<float> {
+  static constexpr int kBytes = 24;
+  // (Y, X) and (Zs, ld) of texel c of one camera row
+  __device__ static __forceinline__ void quad(const uint8_t* R, int SWp, int c, float2& yx, float2& zd) {
+    yx = reinterpret_cast<const float2*>(R)[c];
+    zd = reinterpret_cast<const float2*>(R + 8 * SWp)[c];
+  }
+  __device__ static __forceinline__ float ls(const uint8_t* R, int SWp, int c) {
+    return reinterpret_cast<const float*>(R + 16 * SWp)[c];
+  }
+  __device__ static __forceinline__ float t(const uint8_t* R, int SWp, int c) {
+    return reinterpret_cast<const float*>(R + 20 * SWp)[c];
+  }
+  __device__ static __forceinline__ void store(uint8_t* R, int SWp, int c, float Y, float X, float Zs, float ls,
+                                               float ld) {
+    reinterpret_cast<float2*>(R)[c] = make_float2(Y, X);
+    reinterpret_cast<float2*>(R + 8 * SWp)[c] = make_float2(Zs, ld);
+    reinterpret_cast<float*>(R + 16 * SWp)[c] = ls;
+    reinterpret_cast<float*>(R + 20 * SWp)[c] = ld - ls;
+  }
+};
+
+template <>
+struct Texels<__half> {
+  static constexpr int kBytes = 20;
+  __device__ static __forceinline__ void quad(const uint8_t* R, int SWp, int c, float2& yx, float2& zd) {
+    const float2 xz = __half22float2(reinterpret_cast<const __half2*>(R + 4 * SWp)[c]);
+    yx = make_float2(reinterpret_cast<const float*>(R)[c], xz.x);
+    zd = make_float2(xz.y, reinterpret_cast<const float2*>(R + 8 * SWp)[c].x);
+  }
+  __device__ static __forceinline__ float ls(const uint8_t* R, int SWp, int c) {
+    return reinterpret_cast<const float2*>(R + 8 * SWp)[c].y;
+  }
+  __device__ static __forceinline__ float t(const uint8_t* R, int SWp, int c) {
+    return reinterpret_cast<const float*>(R + 16 * SWp)[c];
+  }
+  __device__ static __forceinline__ void store(uint8_t* R, int SWp, int c, float Y, float X, float Zs, float ls,
+                                               float ld) {
+    reinterpret_cast<float*>(R)[c] = Y;
+    reinterpret_cast<__half2*>(R + 4 * SWp)[c] = __floats2half2_rn(X, Zs);
+    reinterpret_cast<float2*>(R + 8 * SWp)[c] = make_float2(ld, ls);
+    reinterpret_cast<float*>(R + 16 * SWp)[c] = ld - ls;
+  }
+};
+
+template <>
+struct Texels<__nv_bfloat16> {
+  static constexpr int kBytes = 20;
+  __device__ static __forceinline__ void quad(const uint8_t* R, int SWp, int c, float2& yx, float2& zd) {
+    const float2 xz = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(R + 4 * SWp)[c]);
+    yx = make_float2(reinterpret_cast<const float*>(R)[c], xz.x);
+    zd = make_float2(xz.y, reinterpret_cast<const float2*>(R + 8 * SWp)[c].x);
+  }
+  __device__ static __forceinline__ float ls(const uint8_t* R, int SWp, int c) {
+    return reinterpret_cast<const float2*>(R + 8 * SWp)[c].y;
+  }
+  __device__ static __forceinline__ float t(const uint8_t* R, int SWp, int c) {
+    return reinterpret_cast<const float*>(R + 16 * SWp)[c];
+  }
+  __device__ static __forceinline__ void store(uint8_t* R, int SWp, int c, float Y, float X, float Zs, float ls,
+                                               float ld) {
+    reinterpret_cast<float*>(R)[c] = Y;
+    reinterpret_cast<__nv_bfloat162*>(R + 4 * SWp)[c] = __floats2bfloat162_rn(X, Zs);
+    reinterpret_cast<float2*>(R + 8 * SWp)[c] = make_float2(ld, ls);
+    reinterpret_cast<float*>(R + 16 * SWp)[c] = ld - ls;
+  }
+};
+
+static_assert(Texels<float>::kBytes == texel_bytes(kPrecF32) && Texels<__half>::kBytes == texel_bytes(kPrecF16) &&
+                  Texels<__nv_bfloat16>::kBytes == texel_bytes(kPrecBF16),
+              "staged texel sizes of host and device must agree");
 
 __host__ __device__ inline size_t align_up(size_t x, size_t n) { return (x + n - 1) / n * n; }
 
@@ -134,6 +236,9 @@ constexpr size_t kSmemArgs = 16;
 constexpr size_t kSmemItem = kSmemArgs + ((sizeof(SweepArgs) + 15) / 16) * 16;
 constexpr size_t kSmemHead = ((kSmemItem + 16 + 127) / 128) * 128;
 
+// The sampling tables in shared memory: per (candidate, camera) the
+// interpolation weight and its square, (w, w^2) (float2), and the tap
+// offset floor(-d_j b_k) (int).
 __host__ __device__ inline SmemLayout sweep_layout(int K, const SweepArgs& a) {
   SmemLayout L{};
   size_t o = kSmemHead;
@@ -144,9 +249,9 @@ __host__ __device__ inline SmemLayout sweep_layout(int K, const SweepArgs& a) {
   L.luma = o;
   o = align_up(o + static_cast<size_t>(K) * (a.TR + 2) * a.RW * 4, 16);
   L.feat = o;
-  o = align_up(o + static_cast<size_t>(K) * a.TR * kMaps * a.SWp * (a.prec == 0 ? 4 : 2), 16);
+  o = align_up(o + static_cast<size_t>(K) * a.TR * a.SWp * texel_bytes(a.prec), 16);
   L.wtab = o;
-  o = align_up(o + static_cast<size_t>(a.D) * a.KP * 4, 16);
+  o = align_up(o + static_cast<size_t>(a.D) * a.KP * 8, 16);
   L.otab = o;
   o = align_up(o + static_cast<size_t>(a.D) * a.KP * 4, 16);
   L.chg = o;
@@ -171,53 +276,74 @@ __host__ __device__ inline size_t soft_state_offset(int K, const SweepArgs& a) {
   return align_up(sweep_layout(K, a).total, 16);
 }
 
-// Staged descriptor maps are float32, or float16 / bfloat16 in the reduced-
-// precision modes; all arithmetic is float32.
-__device__ __forceinline__ float ldf(const float* p) { return *p; }
-__device__ __forceinline__ float ldf(const __half* p) { return __half2float(*p); }
-__device__ __forceinline__ float ldf(const __nv_bfloat16* p) { return __bfloat162float(*p); }
-__device__ __forceinline__ void stf(float* p, float v) { *p = v; }
-__device__ __forceinline__ void stf(__half* p, float v) { *p = __float2half_rn(v); }
-__device__ __forceinline__ void stf(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
-
 __device__ __forceinline__ int floor16(int x) { return x >= 0 ? (x & ~15) : -((-x + 15) & ~15); }
 
-
-
-// View of one CTA's staged descriptor maps for one thread's pixel.
+// View of one CTA's staged maps for one thread's pixel.
 template <typename TS>
 struct Staged {
-  const TS* F;          // camera 0, this thread's tile row, map kMapY
-  int cam_stride;       // floats between cameras
-  int SWp;              // floats between maps
+  const uint8_t* F;     // camera 0's maps, this thread's tile row
+  int cam_stride;       // bytes between cameras
+  int SWp;              // texels per map row
   int cbase;            // staged column of this pixel (offset 0)
+  __device__ __forceinline__ const uint8_t* row(int k) const { return F + k * cam_stride; }
 };
 
+// (w, w^2) of cameras 0..K-1 at candidate j: entries come in pairs of cameras
+// as float4 loads (the table's row stride KP is a multiple of 4).
+template <int K>
+__device__ __forceinline__ void load_weights(const float2* s_wq, int KP, int j, float2 (&w)[K]) {
+  const float4* w4 = reinterpret_cast<const float4*>(s_wq + j * KP);
+#pragma unroll
+  for (int q = 0; q < (K + 1) / 2; ++q) {
+    const float4 t = w4[q];
+    w[2 * q] = make_float2(t.x, t.y);
+    if (2 * q + 1 < K) w[(2 * q + 1) % K] = make_float2(t.z, t.w);
+  }
+}
+
 // ---------------------------------------------------------------- M-step
+// Both M-steps keep, per camera, the taps bracketing the current sample in
+// registers and reload them only where the integer part of u - d_j b_k
+// changes (the change mask s_chg[j] is the same for every pixel: the reload
+// branch is warp-uniform).  Quantities that are used together are held as
+// register pairs and combined with packed float32x2 operations; every lane
+// of a packed operation is an IEEE float32 operation.  The log prior of
+// candidate j + 1 (two dependent special-function operations) is evaluated
+// while candidate j's sums are formed, off the loop's critical path.
+
 // First M-step: arg-max over the D candidates of J(d_j, S_j) for one pixel
 // (lowest j wins ties), where each ray's label S_j is thresholded at the
-// ray's own sample (ld - ls < log(thr / (1 - thr)) means static).  Here and
-// in the other M-steps the log prior of candidate j + 1 (two dependent
-// special-function operations) is evaluated while candidate j's sums are
-// formed, off the loop's critical path; the values are the same.
+// ray's own sample (lerp(T) < log(thr / (1 - thr)) means static).  With
+// e_k in {0, 1} the ray's label, g_k its shifted descriptor, the candidate's
+// sums are
+//   sum_k e_k g_k,   sum_k e_k |g_k|^2,   n = sum_k e_k,
+//   seg = sum_k [e_k ls_k + (1 - e_k) ld_k] = sum_k ld_k - sum_k e_k T_k,
+// formed without selects.
 template <int K, typename TS>
-__device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>& st, const float* s_w,
+__device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>& st, const float2* s_wq,
                                            const int* s_o, const unsigned* s_chg, const float* s_d,
                                            const float* s_rcp, float cy, float cx, float cz, float mu,
-                                           bool inside) {
-  // per camera: shifted descriptor taps (value at i0, slope to i1), both
-  // log-prior taps and the Z taps
-  float y0[K], dy[K], x0[K], dx[K], z0[K], dz[K], l0[K], dl[K], m0[K], dm[K], q0[K], dq[K];
+                                           bool inside, unsigned* n_static) {
+  using Tx = Texels<TS>;
+  // per camera: p1 = (Y, X) at floor(x) minus the reference's, d1 the slope
+  // to the next tap; p2 = (Zs minus the reference's, ld), d2; t0, dt the
+  // label-test map
+  float2 p1[K], d1[K], p2[K], d2[K];
+  float t0[K], dt[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    y0[k] = dy[k] = x0[k] = dx[k] = z0[k] = dz[k] = 0.f;
-    l0[k] = dl[k] = m0[k] = dm[k] = q0[k] = dq[k] = 0.f;
+    p1[k] = d1[k] = p2[k] = d2[k] = make_float2(0.f, 0.f);
+    t0[k] = dt[k] = 0.f;
   }
   const int SWp = st.SWp;
-  float best = -INFINITY;
+  const float2 ref1 = make_float2(-cy, -cx), ref2 = make_float2(-cz, 0.f);
+  // outside the triangulation mu is NaN and the prior is uniform: the prior
+  // is then evaluated at a finite centre and weighted by pin = 0
+  const float lin = a.mseg ? 1.f : 0.f, pin = inside ? 1.f : 0.f, mu_in = inside ? mu : 0.f;
+  float best = -INFINITY, nsum = 0.f;  // nsum: static rays over the candidates (an exact integer)
   int jb = 0;
   auto prior_at = [&](int j) {
-    const float t = s_d[j] - mu;
+    const float t = s_d[j] - mu_in;
     return __logf(a.gamma + __expf(-(t * t) * a.inv2s2));
   };
   float pr_next = prior_at(0);
@@ -225,52 +351,55 @@ __device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>&
     const float pr = pr_next;
     pr_next = prior_at(min(j + 1, a.D - 1));  // the next candidate's prior, off this one's critical path
     const unsigned ch = s_chg[j];
-    float w[K];
-    {
-      const float4* w4 = reinterpret_cast<const float4*>(s_w + j * a.KP);
+    float2 w[K];
+    load_weights<K>(s_wq, a.KP, j, w);
+    if (ch) {  // same for every pixel: warp-uniform branch
 #pragma unroll
-      for (int q = 0; q < (K + 3) / 4; ++q) {
-        const float4 t = w4[q];
-        if (4 * q + 0 < K) w[(4 * q + 0) % K] = t.x;
-        if (4 * q + 1 < K) w[(4 * q + 1) % K] = t.y;
-        if (4 * q + 2 < K) w[(4 * q + 2) % K] = t.z;
-        if (4 * q + 3 < K) w[(4 * q + 3) % K] = t.w;
+      for (int k = 0; k < K; ++k) {
+        if (!(ch & (1u << k))) continue;
+        const int c = st.cbase + s_o[j * a.KP + k];
+        const uint8_t* R = st.row(k);
+        float2 yx0, zd0, yx1, zd1;
+        Tx::quad(R, SWp, c, yx0, zd0);
+        Tx::quad(R, SWp, c + 1, yx1, zd1);
+        const float T0 = Tx::t(R, SWp, c), T1 = Tx::t(R, SWp, c + 1);
+        p1[k] = fadd2(yx0, ref1);
+        d1[k] = fsub2(yx1, yx0);
+        p2[k] = fadd2(zd0, ref2);
+        d2[k] = fsub2(zd1, zd0);
+        t0[k] = T0;
+        dt[k] = T1 - T0;
       }
     }
-    float sy = 0.f, sx = 0.f, sz = 0.f, q = 0.f, seg = 0.f;
-    int n = 0;
+    float2 syx = make_float2(0.f, 0.f), szl = make_float2(0.f, 0.f), qq = make_float2(0.f, 0.f);
+    float2 nt = make_float2(0.f, 0.f);  // (n, sum of e_k T_k)
+    float qz = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      if (ch & (1u << k)) {  // same for every pixel: warp-uniform branch
-        const int c = st.cbase + s_o[j * a.KP + k];
-        const TS* Fk = st.F + k * st.cam_stride;
-        const float Y0 = ldf(Fk + (c)), Y1 = ldf(Fk + (c + 1));
-        const float X0 = ldf(Fk + (SWp + c)), X1 = ldf(Fk + (SWp + c + 1));
-        const float Z0 = ldf(Fk + (2 * SWp + c)), Z1 = ldf(Fk + (2 * SWp + c + 1));
-        y0[k] = Y0 - cy; dy[k] = Y1 - Y0;
-        x0[k] = X0 - cx; dx[k] = X1 - X0;
-        z0[k] = Z0 - cz; dz[k] = Z1 - Z0;
-        l0[k] = ldf(Fk + (kMapLs * SWp + c)); dl[k] = ldf(Fk + (kMapLs * SWp + c + 1)) - l0[k];
-        m0[k] = ldf(Fk + (kMapLd * SWp + c)); dm[k] = ldf(Fk + (kMapLd * SWp + c + 1)) - m0[k];
-        q0[k] = ldf(Fk + (kMapZ * SWp + c)); dq[k] = ldf(Fk + (kMapZ * SWp + c + 1)) - q0[k];
-      }
-      const bool stat = fmaf(w[k], dq[k], q0[k]) < a.log_thr;
-      const float gy = stat ? fmaf(w[k], dy[k], y0[k]) : 0.f;
-      const float gx = stat ? fmaf(w[k], dx[k], x0[k]) : 0.f;
-      const float gz = stat ? fmaf(w[k], dz[k], z0[k]) : 0.f;
-      seg += fmaf(w[k], stat ? dl[k] : dm[k], stat ? l0[k] : m0[k]);
-      n += stat ? 1 : 0;
-      sy += gy; sx += gx; sz += gz;
-      q = fmaf(gy, gy, q); q = fmaf(gx, gx, q); q = fmaf(gz, gz, q);
+      const float2 ww = make_float2(w[k].x, w[k].x);
+      const float2 g1 = ffma2(ww, d1[k], p1[k]);  // (gy, gx)
+      const float2 g2 = ffma2(ww, d2[k], p2[k]);  // (gz, ld)
+      const float tq = fmaf(w[k].x, dt[k], t0[k]);
+      const float e = tq < a.log_thr ? 1.f : 0.f;
+      const float2 ee = make_float2(e, e);
+      const float2 h1 = fmul2(ee, g1);
+      syx = fadd2(syx, h1);
+      qq = ffma2(h1, g1, qq);
+      const float2 h2 = fmul2(make_float2(e, 1.f), g2);  // (e gz, ld)
+      szl = fadd2(szl, h2);
+      qz = fmaf(h2.x, g2.x, qz);
+      nt = ffma2(ee, make_float2(1.f, tq), nt);
     }
-    const float rn = s_rcp[n];
-    const float ss = fmaf(sz, sz, fmaf(sx, sx, sy * sy));
+    const float rn = s_rcp[static_cast<int>(nt.x)];
+    nsum += nt.x;
+    const float q = qq.x + qq.y + qz;
+    const float2 sq = fmul2(syx, syx);
+    const float ss = fmaf(szl.x, szl.x, sq.x + sq.y);
     const float var = fmaf(-ss, rn, q) * rn;
-    float J = a.mseg ? seg : 0.f;
-    if (inside) J += pr;
-    J = fmaf(-a.beta, var, J);
+    const float J = fmaf(-a.beta, var, fmaf(pin, pr, lin * (szl.y - nt.y)));
     if (J > best) { best = J; jb = j; }
   }
+  *n_static = static_cast<unsigned>(nsum);
   return jb;
 }
 
@@ -280,31 +409,43 @@ __device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>&
 // the slope to the next tap; both zero for a dynamic ray) the static rays'
 // sums are
 //   sum_k g_k     = sum_k m_k     + sum_k w_jk s_k
-//   sum_k |g_k|^2 = sum_k |m_k|^2 + sum_k w_jk (2 m_k.s_k + w_jk |s_k|^2)
-// and likewise for the log priors, so one candidate costs six fused
-// multiply-adds per ray.  The base sums over k change only at candidates
-// where some camera's tap moves; they are then summed afresh (no drift).
-// Candidates j0 <= j < j1 (lowest j wins ties; *best_out = the maximum).
-// RESTART: every camera's taps are loaded at j0, so a range that starts
-// mid-sweep computes each candidate's objective exactly as the whole sweep
-// does (a tap that has not moved since its last load holds the same texels).
+//   sum_k |g_k|^2 = sum_k |m_k|^2 + sum_k (w_jk (2 m_k.s_k) + w_jk^2 |s_k|^2)
+// and likewise for the log priors of the labels, so one candidate costs
+// three packed fused multiply-adds per ray.  The base sums over k change only
+// at candidates where some camera's tap moves; they are then summed afresh
+// (no drift).  Candidates j0 <= j < j1 (lowest j wins ties; *best_out = the
+// maximum).  RESTART: every camera's taps are loaded at j0, so a range that
+// starts mid-sweep computes each candidate's objective exactly as the whole
+// sweep does (a tap that has not moved since its last load holds the same
+// texels).
 template <int K, typename TS, bool RESTART>
-__device__ __forceinline__ int m_step_fixed_range(const SweepArgs& a, const Staged<TS>& st, const float* s_w,
+__device__ __forceinline__ int m_step_fixed_range(const SweepArgs& a, const Staged<TS>& st, const float2* s_wq,
                                                   const int* s_o, const unsigned* s_chg, const float* s_d,
                                                   const float* s_rcp, float cy, float cx, float cz, float mu,
                                                   bool inside, unsigned S, int j0, int j1, float* best_out) {
-  float my[K], mx[K], mz[K], sy[K], sx[K], sz[K], ml[K], sl[K], A[K], C[K], q0[K];
+  using Tx = Texels<TS>;
+  // per camera: b1 = (m_Y, m_X), b2 = (m_Zs, m_L) with L the log prior of the
+  // ray's label; s1, s2 the slopes; ac = (2 m.s, |s|^2) and q0 = |m|^2 over
+  // the descriptor (Y, X, Zs)
+  float2 b1[K], b2[K], s1[K], s2[K], ac[K];
+  float q0[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    my[k] = mx[k] = mz[k] = sy[k] = sx[k] = sz[k] = ml[k] = sl[k] = A[k] = C[k] = q0[k] = 0.f;
+    b1[k] = b2[k] = s1[k] = s2[k] = ac[k] = make_float2(0.f, 0.f);
+    q0[k] = 0.f;
   }
-  float BY = 0.f, BX = 0.f, BZ = 0.f, BQ = 0.f, BL = 0.f;
+  float2 B1 = make_float2(0.f, 0.f), B2 = make_float2(0.f, 0.f);
+  float BQ = 0.f;
   const int SWp = st.SWp;
   const float rn = s_rcp[__popc(S)];
+  const float2 ref1 = make_float2(-cy, -cx), ref2 = make_float2(-cz, 0.f);
+  // outside the triangulation mu is NaN and the prior is uniform: the prior
+  // is then evaluated at a finite centre and weighted by pin = 0
+  const float lin = a.mseg ? 1.f : 0.f, pin = inside ? 1.f : 0.f, mu_in = inside ? mu : 0.f;
   float best = -INFINITY;
   int jb = j0;
   auto prior_at = [&](int j) {
-    const float t = s_d[j] - mu;
+    const float t = s_d[j] - mu_in;
     return __logf(a.gamma + __expf(-(t * t) * a.inv2s2));
   };
   float pr_next = j0 < j1 ? prior_at(j0) : 0.f;
@@ -312,56 +453,54 @@ __device__ __forceinline__ int m_step_fixed_range(const SweepArgs& a, const Stag
     const float pr = pr_next;
     pr_next = prior_at(min(j + 1, j1 - 1));  // the next candidate's prior, off this one's critical path
     const unsigned ch = RESTART && j == j0 ? (1u << K) - 1u : s_chg[j];
-    float w[K];
-    {
-      const float4* w4 = reinterpret_cast<const float4*>(s_w + j * a.KP);
-#pragma unroll
-      for (int q = 0; q < (K + 3) / 4; ++q) {
-        const float4 t = w4[q];
-        if (4 * q + 0 < K) w[(4 * q + 0) % K] = t.x;
-        if (4 * q + 1 < K) w[(4 * q + 1) % K] = t.y;
-        if (4 * q + 2 < K) w[(4 * q + 2) % K] = t.z;
-        if (4 * q + 3 < K) w[(4 * q + 3) % K] = t.w;
-      }
-    }
+    float2 w[K];
+    load_weights<K>(s_wq, a.KP, j, w);
     if (ch) {  // same for every pixel: warp-uniform branch
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         if (!(ch & (1u << k))) continue;
         const int c = st.cbase + s_o[j * a.KP + k];
-        const TS* Fk = st.F + k * st.cam_stride;
+        const uint8_t* R = st.row(k);
         const bool stat = (S >> k) & 1u;
-        const float s = stat ? 1.f : 0.f;
-        const float Y0 = ldf(Fk + c), X0 = ldf(Fk + SWp + c), Z0 = ldf(Fk + 2 * SWp + c);
-        my[k] = s * (Y0 - cy); sy[k] = s * (ldf(Fk + c + 1) - Y0);
-        mx[k] = s * (X0 - cx); sx[k] = s * (ldf(Fk + SWp + c + 1) - X0);
-        mz[k] = s * (Z0 - cz); sz[k] = s * (ldf(Fk + 2 * SWp + c + 1) - Z0);
-        const TS* Lk = Fk + (stat ? kMapLs : kMapLd) * SWp;
-        ml[k] = ldf(Lk + c); sl[k] = ldf(Lk + c + 1) - ml[k];
-        A[k] = 2.f * fmaf(mz[k], sz[k], fmaf(mx[k], sx[k], my[k] * sy[k]));
-        C[k] = fmaf(sz[k], sz[k], fmaf(sx[k], sx[k], sy[k] * sy[k]));
-        q0[k] = fmaf(mz[k], mz[k], fmaf(mx[k], mx[k], my[k] * my[k]));
+        float2 yx0, zd0, yx1, zd1;
+        Tx::quad(R, SWp, c, yx0, zd0);
+        Tx::quad(R, SWp, c + 1, yx1, zd1);
+        const float ls0 = Tx::ls(R, SWp, c), ls1 = Tx::ls(R, SWp, c + 1);
+        zd0.y = stat ? ls0 : zd0.y;  // (Zs, log prior of the label)
+        zd1.y = stat ? ls1 : zd1.y;
+        const float sk = stat ? 1.f : 0.f;
+        const float2 mk = make_float2(sk, sk), ml = make_float2(sk, lin);
+        b1[k] = fmul2(fadd2(yx0, ref1), mk);
+        s1[k] = fmul2(fsub2(yx1, yx0), mk);
+        b2[k] = fmul2(fadd2(zd0, ref2), ml);
+        s2[k] = fmul2(fsub2(zd1, zd0), ml);
+        const float2 bs = fmul2(b1[k], s1[k]), sq = fmul2(s1[k], s1[k]), bb = fmul2(b1[k], b1[k]);
+        ac[k] = make_float2(2.f * fmaf(b2[k].x, s2[k].x, bs.x + bs.y), fmaf(s2[k].x, s2[k].x, sq.x + sq.y));
+        q0[k] = fmaf(b2[k].x, b2[k].x, bb.x + bb.y);
       }
-      BY = my[0]; BX = mx[0]; BZ = mz[0]; BQ = q0[0]; BL = ml[0];
+      B1 = b1[0];
+      B2 = b2[0];
+      BQ = q0[0];
 #pragma unroll
       for (int k = 1; k < K; ++k) {
-        BY += my[k]; BX += mx[k]; BZ += mz[k]; BQ += q0[k]; BL += ml[k];
+        B1 = fadd2(B1, b1[k]);
+        B2 = fadd2(B2, b2[k]);
+        BQ += q0[k];
       }
     }
-    float SY = BY, SX = BX, SZ = BZ, Q = BQ, SL = BL;
+    float2 A1 = B1, A2 = B2, QQ = make_float2(BQ, 0.f);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      SY = fmaf(w[k], sy[k], SY);
-      SX = fmaf(w[k], sx[k], SX);
-      SZ = fmaf(w[k], sz[k], SZ);
-      SL = fmaf(w[k], sl[k], SL);
-      Q = fmaf(w[k], fmaf(w[k], C[k], A[k]), Q);
+      const float2 ww = make_float2(w[k].x, w[k].x);
+      A1 = ffma2(ww, s1[k], A1);
+      A2 = ffma2(ww, s2[k], A2);
+      QQ = ffma2(w[k], ac[k], QQ);
     }
-    const float ss = fmaf(SZ, SZ, fmaf(SX, SX, SY * SY));
-    const float var = fmaf(-ss, rn, Q) * rn;
-    float J = a.mseg ? SL : 0.f;
-    if (inside) J += pr;
-    J = fmaf(-a.beta, var, J);
+    const float q = QQ.x + QQ.y;
+    const float2 sq = fmul2(A1, A1);
+    const float ss = fmaf(A2.x, A2.x, sq.x + sq.y);
+    const float var = fmaf(-ss, rn, q) * rn;
+    const float J = fmaf(-a.beta, var, fmaf(pin, pr, A2.y));
     if (J > best) { best = J; jb = j; }
   }
   if (best_out) *best_out = best;
@@ -369,17 +508,17 @@ __device__ __forceinline__ int m_step_fixed_range(const SweepArgs& a, const Stag
 }
 
 template <int K, typename TS>
-__device__ __forceinline__ int m_step_fixed(const SweepArgs& a, const Staged<TS>& st, const float* s_w,
+__device__ __forceinline__ int m_step_fixed(const SweepArgs& a, const Staged<TS>& st, const float2* s_wq,
                                             const int* s_o, const unsigned* s_chg, const float* s_d,
                                             const float* s_rcp, float cy, float cx, float cz, float mu,
                                             bool inside, unsigned S) {
-  return m_step_fixed_range<K, TS, false>(a, st, s_w, s_o, s_chg, s_d, s_rcp, cy, cx, cz, mu, inside, S, 0, a.D,
+  return m_step_fixed_range<K, TS, false>(a, st, s_wq, s_o, s_chg, s_d, s_rcp, cy, cx, cz, mu, inside, S, 0, a.D,
                                           nullptr);
 }
 
 // First-iteration labels of one pixel when they are the same for every
 // candidate: bit k of *mask is camera k's label (static) and the return value
-// says whether every camera's Z texels stay clear of the threshold.
+// says whether every camera's T texels stay clear of the threshold.
 template <int K, typename TS>
 __device__ __forceinline__ bool constant_initial_labels(const SweepArgs& a, const Staged<TS>& st,
                                                         unsigned* mask) {
@@ -387,10 +526,10 @@ __device__ __forceinline__ bool constant_initial_labels(const SweepArgs& a, cons
   unsigned m = 0;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const TS* Zk = st.F + k * st.cam_stride + kMapZ * st.SWp;
+    const uint8_t* R = st.row(k);
     float lo = INFINITY, hi = -INFINITY;
     for (int c = st.cbase + a.omin[k]; c <= st.cbase + a.omax[k] + 1; ++c) {
-      const float z = ldf(Zk + (c));
+      const float z = Texels<TS>::t(R, st.SWp, c);
       lo = fminf(lo, z);
       hi = fmaxf(hi, z);
     }
@@ -409,30 +548,30 @@ struct Rays {
 };
 
 template <int K, typename TS>
-__device__ __forceinline__ void sample_rays(const SweepArgs& a, const Staged<TS>& st, const float* s_w,
+__device__ __forceinline__ void sample_rays(const SweepArgs& a, const Staged<TS>& st, const float2* s_wq,
                                             const int* s_o, int jt, float cy, float cx, float cz,
                                             Rays& r) {
+  using Tx = Texels<TS>;
   const int SWp = st.SWp;
+  const float2 ref1 = make_float2(-cy, -cx), ref2 = make_float2(-cz, 0.f);
   r.base = 0.f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const float w = s_w[jt * a.KP + k];
+    const float w = s_wq[jt * a.KP + k].x;
     const int c = st.cbase + s_o[jt * a.KP + k];
-    const TS* Fk = st.F + k * st.cam_stride;
-    const float Y0 = ldf(Fk + (c)), Y1 = ldf(Fk + (c + 1));
-    const float X0 = ldf(Fk + (SWp + c)), X1 = ldf(Fk + (SWp + c + 1));
-    const float Z0 = ldf(Fk + (2 * SWp + c)), Z1 = ldf(Fk + (2 * SWp + c + 1));
-    const float S0 = ldf(Fk + (kMapLs * SWp + c)), S1 = ldf(Fk + (kMapLs * SWp + c + 1));
-    const float D0 = ldf(Fk + (kMapLd * SWp + c)), D1 = ldf(Fk + (kMapLd * SWp + c + 1));
-    const float gy = fmaf(w, Y1 - Y0, Y0 - cy);
-    const float gx = fmaf(w, X1 - X0, X0 - cx);
-    const float gz = fmaf(w, Z1 - Z0, Z0 - cz);
+    const uint8_t* R = st.row(k);
+    float2 yx0, zd0, yx1, zd1;
+    Tx::quad(R, SWp, c, yx0, zd0);
+    Tx::quad(R, SWp, c + 1, yx1, zd1);
+    const float S0 = Tx::ls(R, SWp, c), S1 = Tx::ls(R, SWp, c + 1);
+    const float2 ww = make_float2(w, w);
+    const float2 g1 = ffma2(ww, fsub2(yx1, yx0), fadd2(yx0, ref1));  // (gy, gx)
+    const float2 g2 = ffma2(ww, fsub2(zd1, zd0), fadd2(zd0, ref2));  // (gz, ld)
     const float ls = fmaf(w, S1 - S0, S0);
-    const float ld = fmaf(w, D1 - D0, D0);
-    r.gy[k] = gy; r.gx[k] = gx; r.gz[k] = gz;
-    r.qk[k] = fmaf(gz, gz, fmaf(gx, gx, gy * gy));
-    r.ak[k] = ls - ld;
-    r.base += ld;
+    r.gy[k] = g1.x; r.gx[k] = g1.y; r.gz[k] = g2.x;
+    r.qk[k] = fmaf(g2.x, g2.x, fmaf(g1.y, g1.y, g1.x * g1.x));
+    r.ak[k] = ls - g2.y;
+    r.base += g2.y;
   }
 }
 
@@ -698,7 +837,7 @@ struct PixelCtx {
 
 // s_mu: the tile's prior centres when the prior is fused, else NULL (read mu).
 template <typename TS>
-__device__ __forceinline__ PixelCtx<TS> load_pixel(const SweepArgs& a, const TS* s_feat, int u0, int v0,
+__device__ __forceinline__ PixelCtx<TS> load_pixel(const SweepArgs& a, const uint8_t* s_feat, int u0, int v0,
                                                    int cam_stride, int p, const float* s_mu = nullptr) {
   PixelCtx<TS> c;
   const int r = p / a.TW, tx = p - r * a.TW;
@@ -707,14 +846,15 @@ __device__ __forceinline__ PixelCtx<TS> load_pixel(const SweepArgs& a, const TS*
   c.valid = (c.u < a.W) && (c.v < a.H);
   c.mu = s_mu ? s_mu[p] : a.mu[static_cast<size_t>(min(c.v, a.H - 1)) * a.W + min(c.u, a.W - 1)];
   c.inside = !isnan(c.mu);
-  c.st.F = s_feat + static_cast<size_t>(r) * kMaps * a.SWp;
+  c.st.F = s_feat + static_cast<size_t>(r) * a.SWp * texel_bytes(a.prec);
   c.st.cam_stride = cam_stride;
   c.st.SWp = a.SWp;
   c.st.cbase = tx + a.L;
-  const TS* Fr = c.st.F + a.ref * cam_stride;
-  c.cy = ldf(Fr + kMapY * a.SWp + c.st.cbase);
-  c.cx = ldf(Fr + kMapSx * a.SWp + c.st.cbase);
-  c.cz = ldf(Fr + kMapSy * a.SWp + c.st.cbase);
+  float2 yx, zd;
+  Texels<TS>::quad(c.st.row(a.ref), a.SWp, c.st.cbase, yx, zd);
+  c.cy = yx.x;
+  c.cx = yx.y;
+  c.cz = zd.x;
   return c;
 }
 
@@ -770,8 +910,8 @@ __device__ __forceinline__ bool stage_tile(const SweepArgs& a, const CUtensorMap
   uint8_t* s_img = smem + Ly.raw_img;
   const float* s_p = reinterpret_cast<const float*>(smem + Ly.raw_p);
   float* s_luma = reinterpret_cast<float*>(smem + Ly.luma);
-  TS* s_feat = reinterpret_cast<TS*>(smem + Ly.feat);
-  float* s_w = reinterpret_cast<float*>(smem + Ly.wtab);
+  uint8_t* s_feat = smem + Ly.feat;
+  float2* s_wq = reinterpret_cast<float2*>(smem + Ly.wtab);
   int* s_o = reinterpret_cast<int*>(smem + Ly.otab);
   unsigned* s_chg = reinterpret_cast<unsigned*>(smem + Ly.chg);
   float* s_d = reinterpret_cast<float*>(smem + Ly.dval);
@@ -796,7 +936,8 @@ __device__ __forceinline__ bool stage_tile(const SweepArgs& a, const CUtensorMap
   }
   if (load_tables) {
     for (int i = tid; i < a.D * a.KP; i += nthr) {
-      s_w[i] = a.wtab[i];
+      const float w = a.wtab[i];
+      s_wq[i] = make_float2(w, w * w);
       s_o[i] = a.otab[i];
     }
     for (int i = tid; i < a.D; i += nthr) {
@@ -846,7 +987,7 @@ __device__ __forceinline__ bool stage_tile(const SweepArgs& a, const CUtensorMap
     s_luma[i] = y;
   }
   __syncthreads();
-  const int cam_stride = a.TR * kMaps * a.SWp;
+  const int cam_stride = a.TR * a.SWp * texel_bytes(a.prec);
   // element (k, r, c) of the K x TR x SW staged maps, walked with a
   // mixed-radix counter (one step = nthr elements; no division in the loop)
   int c = tid % a.SW, r = (tid / a.SW) % a.TR, k = tid / (a.SW * a.TR);
@@ -866,14 +1007,9 @@ __device__ __forceinline__ bool stage_tile(const SweepArgs& a, const CUtensorMap
     const float gx = ((a02 + 2.f * a12) + a22) - ((a00 + 2.f * a10) + a20);
     const float gy = ((a20 + 2.f * a21) + a22) - ((a00 + 2.f * a01) + a02);
     const float P = s_p[(static_cast<size_t>(k) * a.TR + (V - v0)) * RW + c0];
-    TS* F = s_feat + static_cast<size_t>(k) * cam_stride + static_cast<size_t>(r) * kMaps * a.SWp;
+    uint8_t* F = s_feat + static_cast<size_t>(k) * cam_stride + static_cast<size_t>(r) * a.SWp * texel_bytes(a.prec);
     const float ls = __logf(fmaxf(1.f - P, a.eps)), ld = __logf(fmaxf(P, a.eps));
-    stf(F + kMapY * a.SWp + c, a11);
-    stf(F + kMapSx * a.SWp + c, gx * 0.125f);
-    stf(F + kMapSy * a.SWp + c, gy * 0.125f);
-    stf(F + kMapLs * a.SWp + c, ls);
-    stf(F + kMapLd * a.SWp + c, ld);
-    stf(F + kMapZ * a.SWp + c, ld - ls);
+    Texels<TS>::store(F, a.SWp, c, a11, gx * 0.125f, gy * 0.125f, ls, ld);
   }
   __syncthreads();
   return true;
@@ -891,8 +1027,8 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     return false;
   const SmemLayout Ly = sweep_layout(K, a);
   const float* s_p = reinterpret_cast<const float*>(smem + Ly.raw_p);
-  TS* s_feat = reinterpret_cast<TS*>(smem + Ly.feat);
-  float* s_w = reinterpret_cast<float*>(smem + Ly.wtab);
+  const uint8_t* s_feat = smem + Ly.feat;
+  const float2* s_wq = reinterpret_cast<const float2*>(smem + Ly.wtab);
   int* s_o = reinterpret_cast<int*>(smem + Ly.otab);
   unsigned* s_chg = reinterpret_cast<unsigned*>(smem + Ly.chg);
   float* s_d = reinterpret_cast<float*>(smem + Ly.dval);
@@ -901,7 +1037,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
   const int u0 = tile_x * a.TW, v0 = tile_y * a.TR;
   const int cs = floor16(u0 - a.L - 1);
   const int W = a.W, H = a.H, RW = a.RW;
-  const int cam_stride = a.TR * kMaps * a.SWp;
+  const int cam_stride = a.TR * a.SWp * texel_bytes(a.prec);
   const float* s_mu = a.ptris ? reinterpret_cast<const float*>(smem + Ly.mu) : nullptr;
 
   // ---- 3-5. per-pixel EM.  The pixels still iterating are regrouped into
@@ -939,7 +1075,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     }
   }
   {
-    const PixelCtx<TS> me = load_pixel(a, s_feat, u0, v0, cam_stride, tid, s_mu);
+    const PixelCtx<TS> me = load_pixel<TS>(a, s_feat, u0, v0, cam_stride, tid, s_mu);
     unsigned S0 = 0;
     const bool f0 = me.valid && constant_initial_labels<K, TS>(a, me.st, &S0);
     ps.fixed0[tid] = f0;
@@ -949,19 +1085,22 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
   const int nfast = compact(my_valid && ps.fixed0[tid], ps.list, 0, s_wcnt);
   const int nact = nfast + compact(my_valid && !ps.fixed0[tid], ps.list, nfast, s_wcnt);
   unsigned long long executed = static_cast<unsigned long long>(nact);
+  unsigned my_static = 0;  // static ray samples of the M-steps this thread ran (for the statistics)
 
   // t = 1
   if (warp * 32 < nact) {
     const bool active = tid < nact;
     const int p = ps.list[active ? tid : nact - 1];
-    const PixelCtx<TS> c = load_pixel(a, s_feat, u0, v0, cam_stride, p, s_mu);
+    const PixelCtx<TS> c = load_pixel<TS>(a, s_feat, u0, v0, cam_stride, p, s_mu);
     const bool f0 = ps.fixed0[p];
     const unsigned S0 = ps.S0[p];
     const bool fast = __all_sync(0xffffffffu, f0);
-    const int jb = fast ? m_step_fixed<K, TS>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, S0)
-                        : m_step_init<K, TS>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside);
+    unsigned ns = __popc(S0) * static_cast<unsigned>(a.D);
+    const int jb = fast ? m_step_fixed<K, TS>(a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, S0)
+                        : m_step_init<K, TS>(a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, &ns);
+    if (active) my_static += ns;
     Rays rays;
-    sample_rays<K, TS>(a, c.st, s_w, s_o, jb, c.cy, c.cx, c.cz, rays);
+    sample_rays<K, TS>(a, c.st, s_wq, s_o, jb, c.cy, c.cx, c.cz, rays);
     unsigned S = 0;
     float emax = 0.f;
     enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
@@ -991,15 +1130,16 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
       if (warp * gpw < n) {
         const bool act = slot < n;
         const int p = ps.list[act ? slot : n - 1];  // idle groups repeat the last pixel
-        const PixelCtx<TS> c = load_pixel(a, s_feat, u0, v0, cam_stride, p, s_mu);
+        const PixelCtx<TS> c = load_pixel<TS>(a, s_feat, u0, v0, cam_stride, p, s_mu);
         const unsigned Sp = ps.S[p];
         const int per = (a.D + G - 1) / G, j0 = min(gl * per, a.D), j1 = min(j0 + per, a.D);
         float jbest;
         unsigned jb = static_cast<unsigned>(m_step_fixed_range<K, TS, true>(
-            a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, Sp, j0, j1, &jbest));
+            a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, Sp, j0, j1, &jbest));
+        if (act) my_static += __popc(Sp) * static_cast<unsigned>(j1 - j0);
         group_argmax(jbest, jb, G);
         Rays rays;
-        sample_rays<K, TS>(a, c.st, s_w, s_o, static_cast<int>(jb), c.cy, c.cx, c.cz, rays);
+        sample_rays<K, TS>(a, c.st, s_wq, s_o, static_cast<int>(jb), c.cy, c.cx, c.cz, rays);
         unsigned S = 0;
         float emax = 0.f;
         enumerate_group<K>(rays, s_rcp, a.beta, gl, G, S, emax);
@@ -1013,11 +1153,12 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     } else if (warp * 32 < n) {
       const bool active = tid < n;
       const int p = ps.list[active ? tid : n - 1];
-      const PixelCtx<TS> c = load_pixel(a, s_feat, u0, v0, cam_stride, p, s_mu);
+      const PixelCtx<TS> c = load_pixel<TS>(a, s_feat, u0, v0, cam_stride, p, s_mu);
       const unsigned Sp = ps.S[p];
-      const int jb = m_step_fixed<K, TS>(a, c.st, s_w, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, Sp);
+      const int jb = m_step_fixed<K, TS>(a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, Sp);
+      if (active) my_static += __popc(Sp) * static_cast<unsigned>(a.D);
       Rays rays;
-      sample_rays<K, TS>(a, c.st, s_w, s_o, jb, c.cy, c.cx, c.cz, rays);
+      sample_rays<K, TS>(a, c.st, s_wq, s_o, jb, c.cy, c.cx, c.cz, rays);
       unsigned S = 0;
       float emax = 0.f;
       enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
@@ -1033,7 +1174,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
 
   // posteriors and outputs, one thread per pixel
   if (my_valid) {
-    const PixelCtx<TS> me = load_pixel(a, s_feat, u0, v0, cam_stride, tid, s_mu);
+    const PixelCtx<TS> me = load_pixel<TS>(a, s_feat, u0, v0, cam_stride, tid, s_mu);
     const int jb = ps.jb[tid];
     const unsigned S = ps.S[tid];
     const size_t pix = static_cast<size_t>(me.v) * W + me.u;
@@ -1042,7 +1183,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     if (a.labels) a.labels[pix] = static_cast<uint16_t>(S);
     if (a.post) {
       Rays rays;
-      sample_rays<K, TS>(a, me.st, s_w, s_o, jb, me.cy, me.cx, me.cz, rays);
+      sample_rays<K, TS>(a, me.st, s_wq, s_o, jb, me.cy, me.cx, me.cz, rays);
       float post[K];
       unsigned dummy;
       float dummyf;
@@ -1070,7 +1211,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
           if (!(S >> k & 1u)) continue;
           ++n;
           const int o = s_o[jb * a.KP + k];
-          const float w = s_w[jb * a.KP + k];
+          const float w = s_wq[jb * a.KP + k].x;
           const int x0 = min(max(me.u + o, 0), W - 1), x1 = min(max(me.u + o + 1, 0), W - 1);
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
@@ -1087,6 +1228,10 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     }
   }
   if (tid == 0) atomicAdd(a.counter, executed);
+  if (a.static_counter) {
+    const unsigned wsum = __reduce_add_sync(0xffffffffu, my_static);
+    if (lane == 0 && wsum) atomicAdd(a.static_counter, static_cast<unsigned long long>(wsum));
+  }
   __syncthreads();
   return true;
 }

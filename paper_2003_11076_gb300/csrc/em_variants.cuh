@@ -86,11 +86,13 @@ __device__ __forceinline__ void soft_posterior(const Rays& r, const float* s_rcp
 // on ties; *best_out = the maximum).  Each candidate is evaluated from
 // scratch, so a range computes the same objectives as the whole sweep.
 template <int K>
-__device__ __forceinline__ int m_step_soft(const SweepArgs& a, const Staged<float>& st, const float* s_w,
+__device__ __forceinline__ int m_step_soft(const SweepArgs& a, const Staged<float>& st, const float2* s_wq,
                                            const int* s_o, const float* s_d, float cy, float cx, float cz,
                                            float mu, bool inside, const float* pi, const float* pw, int j0,
                                            int j1, float* best_out) {
+  using Tx = Texels<float>;
   const int SWp = st.SWp;
+  const float2 ref1 = make_float2(-cy, -cx), ref2 = make_float2(-cz, 0.f);
   float best = -INFINITY;
   int jb = j0;
   auto prior_at = [&](int j) {
@@ -105,16 +107,20 @@ __device__ __forceinline__ int m_step_soft(const SweepArgs& a, const Staged<floa
     float seg = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const float w = s_w[j * a.KP + k];
+      const float w = s_wq[j * a.KP + k].x;
       const int c = st.cbase + s_o[j * a.KP + k];
-      const float* Fk = st.F + k * st.cam_stride;
-      const float Y0 = Fk[c], X0 = Fk[SWp + c], Z0 = Fk[2 * SWp + c];
-      gy[k] = fmaf(w, Fk[c + 1] - Y0, Y0 - cy);
-      gx[k] = fmaf(w, Fk[SWp + c + 1] - X0, X0 - cx);
-      gz[k] = fmaf(w, Fk[2 * SWp + c + 1] - Z0, Z0 - cz);
-      const float S0 = Fk[kMapLs * SWp + c], D0 = Fk[kMapLd * SWp + c];
-      const float ls = fmaf(w, Fk[kMapLs * SWp + c + 1] - S0, S0);
-      const float ld = fmaf(w, Fk[kMapLd * SWp + c + 1] - D0, D0);
+      const uint8_t* R = st.row(k);
+      float2 yx0, zd0, yx1, zd1;
+      Tx::quad(R, SWp, c, yx0, zd0);
+      Tx::quad(R, SWp, c + 1, yx1, zd1);
+      const float S0 = Tx::ls(R, SWp, c), S1 = Tx::ls(R, SWp, c + 1);
+      const float2 ww = make_float2(w, w);
+      const float2 g1 = ffma2(ww, fsub2(yx1, yx0), fadd2(yx0, ref1));  // (gy, gx)
+      const float2 g2 = ffma2(ww, fsub2(zd1, zd0), fadd2(zd0, ref2));  // (gz, ld)
+      gy[k] = g1.x;
+      gx[k] = g1.y;
+      gz[k] = g2.x;
+      const float ls = fmaf(w, S1 - S0, S0), ld = g2.y;
       seg += fmaf(pi[k], ls - ld, ld);
     }
     float pv = 0.f;
@@ -140,7 +146,7 @@ __device__ __forceinline__ int m_step_soft(const SweepArgs& a, const Staged<floa
 // plus the candidate's prior.  Returns j; S and emax (J at (j, S) without the
 // prior) through the references.
 template <int K>
-__device__ __forceinline__ int joint_map(const SweepArgs& a, const Staged<float>& st, const float* s_w,
+__device__ __forceinline__ int joint_map(const SweepArgs& a, const Staged<float>& st, const float2* s_wq,
                                          const int* s_o, const float* s_d, const float* s_rcp, float cy, float cx,
                                          float cz, float mu, bool inside, unsigned& S, float& emax) {
   float best = -INFINITY;
@@ -149,7 +155,7 @@ __device__ __forceinline__ int joint_map(const SweepArgs& a, const Staged<float>
   float eb = 0.f;
   for (int j = 0; j < a.D; ++j) {
     Rays r;
-    sample_rays<K, float>(a, st, s_w, s_o, j, cy, cx, cz, r);
+    sample_rays<K, float>(a, st, s_wq, s_o, j, cy, cx, cz, r);
     unsigned m = 0;
     float e = 0.f;
     enumerate<0, K>(r, s_rcp, a.beta, 0.f, m, e, nullptr);
@@ -185,8 +191,8 @@ __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorM
   if (!stage_tile<K, float>(a, img_map, p_map, tile_x, tile_y, smem, 0u, true, false)) return;
   const SmemLayout Ly = sweep_layout(K, a);
   const float* s_p = reinterpret_cast<const float*>(smem + Ly.raw_p);
-  const float* s_feat = reinterpret_cast<const float*>(smem + Ly.feat);
-  const float* s_w = reinterpret_cast<const float*>(smem + Ly.wtab);
+  const uint8_t* s_feat = smem + Ly.feat;
+  const float2* s_wq = reinterpret_cast<const float2*>(smem + Ly.wtab);
   const int* s_o = reinterpret_cast<const int*>(smem + Ly.otab);
   const unsigned* s_chg = reinterpret_cast<const unsigned*>(smem + Ly.chg);
   const float* s_d = reinterpret_cast<const float*>(smem + Ly.dval);
@@ -194,10 +200,10 @@ __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorM
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int u0 = tile_x * a.TW, v0 = tile_y * a.TR;
   const int cs = floor16(u0 - a.L - 1);
-  const int cam_stride = a.TR * kMaps * a.SWp;
+  const int cam_stride = a.TR * a.SWp * texel_bytes(a.prec);
   const size_t HW = static_cast<size_t>(a.H) * a.W;
 
-  const PixelCtx<float> me = load_pixel(a, s_feat, u0, v0, cam_stride, tid);
+  const PixelCtx<float> me = load_pixel<float>(a, s_feat, u0, v0, cam_stride, tid);
   bool run = me.valid;
   if (a.dyn_only && run) {  // Sec. III-F: only the reference pixels flagged dynamic
     const int r = tid / a.TW;
@@ -212,7 +218,7 @@ __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorM
     if (run) {
       unsigned S = 0;
       float emax = 0.f;
-      const int jb = joint_map<K>(a, me.st, s_w, s_o, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu, me.inside, S, emax);
+      const int jb = joint_map<K>(a, me.st, s_wq, s_o, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu, me.inside, S, emax);
       executed = 1;
       const size_t pix = static_cast<size_t>(me.v) * a.W + me.u;
       a.d_idx[pix] = jb;
@@ -220,7 +226,7 @@ __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorM
       if (a.labels) a.labels[pix] = static_cast<uint16_t>(S);
       if (a.post) {
         Rays rays;
-        sample_rays<K, float>(a, me.st, s_w, s_o, jb, me.cy, me.cx, me.cz, rays);
+        sample_rays<K, float>(a, me.st, s_wq, s_o, jb, me.cy, me.cx, me.cz, rays);
         float post[K];
         unsigned dummy;
         float dummyf;
@@ -251,7 +257,7 @@ __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorM
     // E-step at candidate j (q(S) from the rays there) into pixel p's state
     auto e_step = [&](const PixelCtx<float>& c, int p, int j) {
       Rays rays;
-      sample_rays<K, float>(a, c.st, s_w, s_o, j, c.cy, c.cx, c.cz, rays);
+      sample_rays<K, float>(a, c.st, s_wq, s_o, j, c.cy, c.cx, c.cz, rays);
       unsigned S = 0;
       float emax = 0.f;
       enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
@@ -269,12 +275,12 @@ __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorM
     unsigned long long executed = 0;
     // t = 1: the EM's first M-step (labels thresholded per candidate)
     if (run) {
-      unsigned S0 = 0;
+      unsigned S0 = 0, ns = 0;
       const bool f0 = constant_initial_labels<K, float>(a, me.st, &S0);
-      const int jb = f0 ? m_step_fixed<K, float>(a, me.st, s_w, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu,
+      const int jb = f0 ? m_step_fixed<K, float>(a, me.st, s_wq, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu,
                                                  me.inside, S0)
-                        : m_step_init<K, float>(a, me.st, s_w, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu,
-                                                 me.inside);
+                        : m_step_init<K, float>(a, me.st, s_wq, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu,
+                                                 me.inside, &ns);
       e_step(me, tid, jb);
     }
     ps.conv[tid] = 0;
@@ -293,11 +299,11 @@ __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorM
         if (warp * gpw < n) {
           const bool act = slot < n;
           const int p = ps.list[act ? slot : n - 1];  // idle groups repeat the last pixel
-          const PixelCtx<float> c = load_pixel(a, s_feat, u0, v0, cam_stride, p);
+          const PixelCtx<float> c = load_pixel<float>(a, s_feat, u0, v0, cam_stride, p);
           const float* st = s_soft + p * NS;
           const int per = (a.D + G - 1) / G, j0 = min(gl * per, a.D), j1 = min(j0 + per, a.D);
           float jbest;
-          unsigned jn = static_cast<unsigned>(m_step_soft<K>(a, c.st, s_w, s_o, s_d, c.cy, c.cx, c.cz, c.mu,
+          unsigned jn = static_cast<unsigned>(m_step_soft<K>(a, c.st, s_wq, s_o, s_d, c.cy, c.cx, c.cz, c.mu,
                                                              c.inside, st, st + K, j0, j1, &jbest));
           group_argmax(jbest, jn, G);
           const bool conv = a.early_exit && static_cast<int>(jn) == ps.jb[p];  // q_t would equal q_{t-1}
@@ -306,7 +312,7 @@ __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorM
           // takes part in its shuffles; the converged groups discard it)
           if (!__all_sync(0xffffffffu, conv)) {
             Rays rays;
-            sample_rays<K, float>(a, c.st, s_w, s_o, static_cast<int>(jn), c.cy, c.cx, c.cz, rays);
+            sample_rays<K, float>(a, c.st, s_wq, s_o, static_cast<int>(jn), c.cy, c.cx, c.cz, rays);
             unsigned S = 0;
             float emax = 0.f;
             enumerate_group<K>(rays, s_rcp, a.beta, gl, G, S, emax);
@@ -328,9 +334,9 @@ __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorM
         }
       } else if (tid < n) {
         const int p = ps.list[tid];
-        const PixelCtx<float> c = load_pixel(a, s_feat, u0, v0, cam_stride, p);
+        const PixelCtx<float> c = load_pixel<float>(a, s_feat, u0, v0, cam_stride, p);
         const float* st = s_soft + p * NS;
-        const int jn = m_step_soft<K>(a, c.st, s_w, s_o, s_d, c.cy, c.cx, c.cz, c.mu, c.inside, st, st + K, 0,
+        const int jn = m_step_soft<K>(a, c.st, s_wq, s_o, s_d, c.cy, c.cx, c.cz, c.mu, c.inside, st, st + K, 0,
                                       a.D, nullptr);
         if (a.early_exit && jn == ps.jb[p]) ps.conv[p] = 1;  // q_t would equal q_{t-1}: fixed point
         else e_step(c, p, jn);

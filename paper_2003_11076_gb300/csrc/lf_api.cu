@@ -237,8 +237,6 @@ struct lf_ctx {
   size_t own_img_cap = 0;
   float* own_P = nullptr;
   size_t own_P_cap = 0;
-  uint8_t* own_img16 = nullptr;  // 16-bit copy of float32 images in the reduced-precision modes
-  size_t own_img16_cap = 0;
   int* d_tiles = nullptr;        // dynamic-only: list of tiles to sweep, then its length
   size_t tiles_cap = 0;
   // support-point detection (lf_set_inputs with M = LF_DETECT_SUPPORT)
@@ -625,11 +623,11 @@ lf_status create_ctx(lf_ctx** out, int n_cams, const float* baselines, const flo
   cap = 0;
   if ((s = grow(&c->d_mu, &cap, static_cast<size_t>(H) * W, "prior")) != LF_OK) return bail(s);
   cap = 0;
-  if ((s = grow(&c->d_counter, &cap, 1, "counter")) != LF_OK) return bail(s);
+  if ((s = grow(&c->d_counter, &cap, 2, "counter")) != LF_OK) return bail(s);  // executed sweeps, static samples
   cap = 0;
   if ((s = grow(&c->d_status, &cap, 1, "status")) != LF_OK) return bail(s);
   cudaError_t e;
-  if ((e = cudaMemset(c->d_counter, 0, sizeof(unsigned long long))) != cudaSuccess ||
+  if ((e = cudaMemset(c->d_counter, 0, 2 * sizeof(unsigned long long))) != cudaSuccess ||
       (e = cudaMemset(c->d_status, 0, sizeof(unsigned))) != cudaSuccess)
     return bail(cuda_fail(e, "counter init"));
   if ((e = cudaMemcpy(c->d_wtab, c->wtab.data(), c->wtab.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -857,20 +855,6 @@ lf_status set_inputs_impl(lf_ctx* c, const void* images, int C, int dtype, const
     sparse_points = c->support_pts.data();
     M = static_cast<int>(c->support_pts.size() / 3);
   }
-  if (dtype == LF_F32 && c->p.precision != LF_PREC_F32) {
-    // reduced precision: the images are stored on the device in 16 bits
-    const int to_bf16 = c->p.precision == LF_PREC_BF16;
-    const size_t row16 = static_cast<size_t>(c->W) * C * 2, pitch16 = (row16 + 15) / 16 * 16;
-    s = grow(&c->own_img16, &c->own_img16_cap, pitch16 * c->H * c->K, "input staging");
-    if (s != LF_OK) return s;
-    LF_CUDA(launch_convert_f32(c->img, c->img_pitch, c->own_img16, pitch16, c->K * c->H, c->W * C, to_bf16,
-                               c->stream),
-            "image conversion");
-    c->img = c->own_img16;
-    c->img_pitch = pitch16;
-    c->dtype = to_bf16 ? LF_BF16 : LF_F16;
-    c->bpp = C * 2;
-  }
   s = choose_tiles(c);
   if (s != LF_OK) return s;
   build_prior(c, sparse_points, M);
@@ -1053,7 +1037,7 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
     a.omax[k] = hi;
   }
   a.d_idx = didx; a.d_out = dout; a.labels = lab; a.post = post;
-  a.counter = c->d_counter; a.status = c->d_status; a.timeout_ns = kTimeoutNs;
+  a.counter = c->d_counter; a.static_counter = c->d_counter + 1; a.status = c->d_status; a.timeout_ns = kTimeoutNs;
   if (fused) {
     a.refocus_out = refo_stage;
     a.img = c->img;
@@ -1185,11 +1169,12 @@ lf_status lf_get_stats(lf_ctx* c, lf_stats* out) {
   g_err.clear();
   if (!c || !out) return fail(LF_EINVAL, "NULL argument");
   LF_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
-  unsigned long long n = 0;
-  LF_CUDA(cudaMemcpy(&n, c->d_counter, sizeof(n), cudaMemcpyDeviceToHost), "counter read");
+  unsigned long long n[2] = {0, 0};
+  LF_CUDA(cudaMemcpy(n, c->d_counter, sizeof(n), cudaMemcpyDeviceToHost), "counter read");
   LF_CUDA(cudaMemset(c->d_counter, 0, sizeof(n)), "counter reset");
   c->stats.runs = c->runs;
-  c->stats.executed_ray_samples = static_cast<uint64_t>(n) * c->K * c->D;
+  c->stats.executed_ray_samples = static_cast<uint64_t>(n[0]) * c->K * c->D;
+  c->stats.executed_static_ray_samples = static_cast<uint64_t>(n[1]);
   float* ms[4] = {&c->stats.ms_prior, &c->stats.ms_sweep, &c->stats.ms_refocus, &c->stats.ms_median};
   for (int i = 0; i < 4; ++i) {
     double acc = 0.0;
@@ -1215,7 +1200,7 @@ void lf_destroy(lf_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   void* bufs[] = {c->d_wtab, c->d_otab, c->d_chg, c->d_dval, c->d_mu, c->d_counter, c->d_status,
-                  c->own_img, c->own_P, c->own_img16, c->d_tiles, c->d_tris, c->d_bins, c->o_didx, c->o_d, c->o_labels,
+                  c->own_img, c->own_P, c->d_tiles, c->d_tris, c->d_bins, c->o_didx, c->o_d, c->o_labels,
                   c->o_post, c->o_ref, c->o_tmp, c->d_fa, c->d_fb, c->d_sgrad, c->d_sint, c->d_sdbl,
                   c->d_spts};
   for (void* p : bufs)

@@ -126,7 +126,7 @@ struct Frame {
   int nbx = 0, nby = 0;
   // staging decisions
   int bpp = 0, stage_dtype = 0;
-  bool stage_img = false, stage_p = false, convert = false;
+  bool stage_img = false, stage_p = false;
   size_t img_pitch = 0, p_pitch = 0;
   // tile
   int tile = 0;
@@ -295,11 +295,11 @@ void prepare_frame(Frame& f, const lf_params& p, int smem_optin) {
   }
   // input staging: TMA reads rows in place when they are 16-byte aligned
   const int in_bpp = f.C * (f.dtype == LF_U8 ? 1 : f.dtype == LF_F32 ? 4 : 2);
-  f.convert = f.dtype == LF_F32 && p.precision != LF_PREC_F32;
-  f.stage_dtype = f.convert ? (p.precision == LF_PREC_BF16 ? LF_BF16 : LF_F16) : f.dtype;
-  f.bpp = f.convert ? f.C * 2 : in_bpp;
+  // (the precision mode sets the storage of the staged maps; the images stay as given)
+  f.stage_dtype = f.dtype;
+  f.bpp = in_bpp;
   const size_t in_row = static_cast<size_t>(f.W) * in_bpp;
-  f.stage_img = f.convert || in_row % 16 != 0 || reinterpret_cast<uintptr_t>(f.src_img) % 16 != 0;
+  f.stage_img = in_row % 16 != 0 || reinterpret_cast<uintptr_t>(f.src_img) % 16 != 0;
   f.img_pitch = f.stage_img ? align_up(static_cast<size_t>(f.W) * f.bpp, 16) : in_row;
   f.stage_p = (static_cast<size_t>(f.W) * 4) % 16 != 0 || reinterpret_cast<uintptr_t>(f.src_p) % 16 != 0;
   f.p_pitch = f.stage_p ? align_up(static_cast<size_t>(f.W) * 4, 16) : static_cast<size_t>(f.W) * 4;
@@ -628,15 +628,9 @@ lf_status lf_batch_run(lf_batch* b) {
     const int in_bpp = f.C * (f.dtype == LF_U8 ? 1 : f.dtype == LF_F32 ? 4 : 2);
     const size_t in_row = static_cast<size_t>(f.W) * in_bpp;
     if (f.stage_img) {
-      if (f.convert) {  // float32 rows (4-byte aligned) -> 16-bit pitched rows
-        LF_CUDA(launch_convert_f32(img, in_row, A + f.o_img, f.img_pitch, f.K * f.H, f.W * f.C,
-                                   b->p.precision == LF_PREC_BF16, st),
-                "batch conversion");
-      } else {
-        LF_CUDA(cudaMemcpy2DAsync(A + f.o_img, f.img_pitch, img, in_row, in_row, static_cast<size_t>(f.H) * f.K,
-                                  cudaMemcpyDeviceToDevice, st),
-                "batch staging");
-      }
+      LF_CUDA(cudaMemcpy2DAsync(A + f.o_img, f.img_pitch, img, in_row, in_row, static_cast<size_t>(f.H) * f.K,
+                                cudaMemcpyDeviceToDevice, st),
+              "batch staging");
       img = A + f.o_img;
     }
     const float* P = f.src_p;

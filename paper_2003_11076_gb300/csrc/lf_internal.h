@@ -77,6 +77,7 @@ struct SweepArgs {
   uint16_t* labels;                // [H][W] or null
   float* post;                     // [K][H][W] or null
   unsigned long long* counter;     // executed pixel-sweeps
+  unsigned long long* static_counter;  // static ray samples the M-steps evaluated (may be null)
   unsigned* status;                // kStatus* bits
   unsigned long long timeout_ns;   // bounded-wait limit
 };
@@ -220,9 +221,6 @@ cudaError_t launch_em_sweep_persistent(int K, int prec, const FrameDesc* frames,
                                        int grid, int threads, cudaStream_t s);
 // Resident CTAs per SM of the persistent sweep for this shared-memory size.
 int em_sweep_persistent_occupancy(int K, int prec, size_t smem, int threads);
-// float32 [rows][W*C] (pitch_in bytes) -> float16 (to_bf16 = 0) or bfloat16 rows (pitch_out bytes)
-cudaError_t launch_convert_f32(const uint8_t* in, size_t pitch_in, uint8_t* out, size_t pitch_out, int rows,
-                               int cols, int to_bf16, cudaStream_t s);
 
 // Validity of the model and run parameters every entry point shares: finite
 // constants with sigma > 0, gamma >= 0, eps > 0, beta >= 0 and

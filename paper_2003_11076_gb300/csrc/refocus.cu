@@ -18,17 +18,6 @@ __device__ __forceinline__ float load_px(const uint8_t* row, int x, int c, int C
   return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(row)[x * C + c]);
 }
 
-__global__ void convert_f32_kernel(const uint8_t* in, size_t pitch_in, uint8_t* out, size_t pitch_out, int rows,
-                                   int cols, int to_bf16) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y;
-  if (x >= cols || y >= rows) return;
-  const float v = reinterpret_cast<const float*>(in + static_cast<size_t>(y) * pitch_in)[x];
-  uint8_t* o = out + static_cast<size_t>(y) * pitch_out;
-  if (to_bf16) reinterpret_cast<__nv_bfloat16*>(o)[x] = __float2bfloat16_rn(v);
-  else reinterpret_cast<__half*>(o)[x] = __float2half_rn(v);
-}
-
 __device__ __forceinline__ void refocus_pixel(const RefocusArgs& a, int u, int v) {
   const size_t pix = static_cast<size_t>(v) * a.W + u;
   const int j = a.d_idx[pix];
@@ -127,13 +116,6 @@ cudaError_t launch_refocus(const RefocusArgs& a, cudaStream_t s) {
   dim3 block(64, 4);
   dim3 grid((a.W + 63) / 64, (a.H + 3) / 4);
   refocus_kernel<<<grid, block, 0, s>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_convert_f32(const uint8_t* in, size_t pitch_in, uint8_t* out, size_t pitch_out, int rows,
-                               int cols, int to_bf16, cudaStream_t s) {
-  dim3 grid((cols + 255) / 256, rows);
-  convert_f32_kernel<<<grid, 256, 0, s>>>(in, pitch_in, out, pitch_out, rows, cols, to_bf16);
   return cudaGetLastError();
 }
 

@@ -59,7 +59,7 @@ class Stats(ctypes.Structure):
                 ("ms_prior", ctypes.c_float), ("ms_sweep", ctypes.c_float), ("ms_refocus", ctypes.c_float),
                 ("ms_median", ctypes.c_float), ("graph_captures", ctypes.c_int),
                 ("tuned_signatures", ctypes.c_int), ("ms_support", ctypes.c_float),
-                ("ms_set_inputs", ctypes.c_float)]
+                ("ms_set_inputs", ctypes.c_float), ("executed_static_ray_samples", ctypes.c_uint64)]
 
 
 _lib = None
@@ -245,29 +245,36 @@ class Context:
 
     # -- the path
     def set_inputs(self, images, seg_prior, points):
-        """images [K,H,W] / [K,H,W,3] uint8 or float32; seg_prior [K,H,W]
-        float32 P(dynamic); points [M,3] float32 (host), or None to detect
-        the support points on the device (LF_DETECT_SUPPORT).  numpy arrays
-        are host inputs, torch CUDA tensors device inputs."""
+        """images [K,H,W] / [K,H,W,3] uint8, float32, float16 or bfloat16
+        (the library reads each type as it is); seg_prior [K,H,W] float32
+        P(dynamic); points [M,3] float32 (host), or None to detect the
+        support points on the device (LF_DETECT_SUPPORT).  numpy arrays and
+        CPU torch tensors are host inputs, torch CUDA tensors device inputs."""
         detect = points is None
         pts = np.zeros((0, 3), np.float32) if detect else np.ascontiguousarray(points, np.float32).reshape(-1, 3)
         pptr = None if detect else pts.ctypes.data
         M = LF_DETECT_SUPPORT if detect else pts.shape[0]
         if _is_torch(images):
             import torch
-            assert images.is_cuda and seg_prior.is_cuda and images.is_contiguous() and seg_prior.is_contiguous()
+            images = images.contiguous()
             C = 1 if images.dim() == 3 else int(images.shape[3])
             dt = {torch.uint8: LF_U8, torch.float32: LF_F32, torch.float16: LF_F16,
                   torch.bfloat16: LF_BF16}[images.dtype]
-            assert seg_prior.dtype == torch.float32
-            self._keep = (images, seg_prior)
-            _check(load().lf_set_inputs(self._h, images.data_ptr(), C, dt, seg_prior.data_ptr(), pptr, M, 1))
+            if images.is_cuda:
+                assert seg_prior.is_cuda and seg_prior.is_contiguous() and seg_prior.dtype == torch.float32
+                self._keep = (images, seg_prior)
+                _check(load().lf_set_inputs(self._h, images.data_ptr(), C, dt, seg_prior.data_ptr(), pptr, M, 1))
+            else:  # host tensor: copied by the library within the call
+                seg = np.ascontiguousarray(seg_prior.numpy() if _is_torch(seg_prior) else seg_prior, np.float32)
+                _check(load().lf_set_inputs(self._h, images.data_ptr(), C, dt, seg.ctypes.data, pptr, M, 0))
         else:
             imgs = np.ascontiguousarray(images)
-            if imgs.dtype not in (np.uint8, np.float32):
-                imgs = imgs.astype(np.float32)
+            dts = {np.dtype(np.uint8): LF_U8, np.dtype(np.float32): LF_F32, np.dtype(np.float16): LF_F16}
+            if imgs.dtype not in dts:
+                raise TypeError(f"images must be uint8, float32 or float16 (got {imgs.dtype}); "
+                                "pass bfloat16 images as a torch tensor")
             C = 1 if imgs.ndim == 3 else int(imgs.shape[3])
-            dt = LF_U8 if imgs.dtype == np.uint8 else LF_F32
+            dt = dts[imgs.dtype]
             seg = np.ascontiguousarray(seg_prior, np.float32)
             _check(load().lf_set_inputs(self._h, imgs.ctypes.data, C, dt, seg.ctypes.data, pptr, M, 0))
         self.C = C

@@ -99,3 +99,34 @@ def test_empty_batch_is_an_error():
         with pytest.raises(lf.LfError) as e:
             b.run()
         assert e.value.status == lf.LF_ESTATE
+
+
+# Frames of the uneven-batch workload itself (random_frame(i), the generator
+# the batch benchmark draws from): the largest (1269 x 1019, K = 5, D = 128),
+# the widest disparity halo (K = 9, D = 128, 109 columns each side), a tall
+# nine-camera frame (705 x 969), K = 7 at D = 128 and D = 32, and K = 3.
+ORACLE_FRAMES = (49, 42, 45, 19, 8, 25)
+
+
+def test_batch_frames_match_the_oracle():
+    """The persistent batch kernel (per-frame descriptors in global memory,
+    nine-camera launch group, wide halos, autotuned tiles) against the FP64
+    oracle on every pixel of uneven workload frames, with the parity rule of
+    the single-frame tests."""
+    import torch
+    from oracle import oracle as O
+    from paper_2003_11076_gb300 import lf
+    from test_gpu_parity import check_parity, params_pair
+    O.build()
+    frames = [scenes.random_frame(i) for i in ORACLE_FRAMES]
+    assert {s.K for s in frames} == {3, 5, 7, 9} and max(s.D for s in frames) == 128
+    gp, op = params_pair()
+    b = lf.Batch(gp, autotune=True)
+    b, got = _run_batch(lf, torch, frames, batch=b)
+    for i, s, g in zip(ORACLE_FRAMES, frames, got):
+        g = dict(g)
+        g["labels"] = g["labels"].view(np.uint16)
+        o = O.run_scene(s, params=op)
+        frac, exc = check_parity(g, o, what=f"random_frame({i}) {s.W}x{s.H} K={s.K} D={s.D}")
+        print(f"random_frame({i}) {s.W}x{s.H} K={s.K} D={s.D}: agreement {frac:.6f}, excused {exc:.5f}")
+    b.close()
