@@ -318,8 +318,13 @@ __device__ __forceinline__ void load_weights(const float2* s_wq, int KP, int j, 
 // sums are
 //   sum_k e_k g_k,   sum_k e_k |g_k|^2,   n = sum_k e_k,
 //   seg = sum_k [e_k ls_k + (1 - e_k) ld_k] = sum_k ld_k - sum_k e_k T_k,
-// formed without selects.
-template <int K, typename TS>
+// formed without selects.  The loop body is straight-line code for the
+// current candidate; the taps the next candidate needs are reloaded at its
+// end (its change mask is read early, so the branch does not wait for it).
+// REF >= 0: camera REF is the reference (known at compile time).  Its ray
+// samples the pixel itself at every candidate (weight 0, shifted descriptor
+// exactly 0), so only its label test and log prior are accumulated.
+template <int K, typename TS, int REF>
 __device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>& st, const float2* s_wq,
                                            const int* s_o, const unsigned* s_chg, const float* s_d,
                                            const float* s_rcp, float cy, float cx, float cz, float mu,
@@ -330,16 +335,26 @@ __device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>&
   // label-test map
   float2 p1[K], d1[K], p2[K], d2[K];
   float t0[K], dt[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    p1[k] = d1[k] = p2[k] = d2[k] = make_float2(0.f, 0.f);
-    t0[k] = dt[k] = 0.f;
-  }
   const int SWp = st.SWp;
   const float2 ref1 = make_float2(-cy, -cx), ref2 = make_float2(-cz, 0.f);
   // outside the triangulation mu is NaN and the prior is uniform: the prior
   // is then evaluated at a finite centre and weighted by pin = 0
   const float lin = a.mseg ? 1.f : 0.f, pin = inside ? 1.f : 0.f, mu_in = inside ? mu : 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int c = st.cbase + s_o[k];
+    const uint8_t* R = st.row(k);
+    float2 yx0, zd0, yx1, zd1;
+    Tx::quad(R, SWp, c, yx0, zd0);
+    Tx::quad(R, SWp, c + 1, yx1, zd1);
+    const float T0 = Tx::t(R, SWp, c), T1 = Tx::t(R, SWp, c + 1);
+    p1[k] = fadd2(yx0, ref1);
+    d1[k] = fsub2(yx1, yx0);
+    p2[k] = fadd2(zd0, ref2);
+    d2[k] = fsub2(zd1, zd0);
+    t0[k] = T0;
+    dt[k] = T1 - T0;
+  }
   float best = -INFINITY, nsum = 0.f;  // nsum: static rays over the candidates (an exact integer)
   int jb = 0;
   auto prior_at = [&](int j) {
@@ -348,34 +363,23 @@ __device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>&
   };
   float pr_next = prior_at(0);
   for (int j = 0; j < a.D; ++j) {
-    const float pr = pr_next;
-    pr_next = prior_at(min(j + 1, a.D - 1));  // the next candidate's prior, off this one's critical path
-    const unsigned ch = s_chg[j];
     float2 w[K];
     load_weights<K>(s_wq, a.KP, j, w);
-    if (ch) {  // same for every pixel: warp-uniform branch
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        if (!(ch & (1u << k))) continue;
-        const int c = st.cbase + s_o[j * a.KP + k];
-        const uint8_t* R = st.row(k);
-        float2 yx0, zd0, yx1, zd1;
-        Tx::quad(R, SWp, c, yx0, zd0);
-        Tx::quad(R, SWp, c + 1, yx1, zd1);
-        const float T0 = Tx::t(R, SWp, c), T1 = Tx::t(R, SWp, c + 1);
-        p1[k] = fadd2(yx0, ref1);
-        d1[k] = fsub2(yx1, yx0);
-        p2[k] = fadd2(zd0, ref2);
-        d2[k] = fsub2(zd1, zd0);
-        t0[k] = T0;
-        dt[k] = T1 - T0;
-      }
-    }
+    const int jn = min(j + 1, a.D - 1);
+    const unsigned chn = j + 1 < a.D ? s_chg[jn] : 0u;  // taps the next candidate reloads
+    const float pr = pr_next;
+    pr_next = prior_at(jn);  // the next candidate's prior, off this one's critical path
     float2 syx = make_float2(0.f, 0.f), szl = make_float2(0.f, 0.f), qq = make_float2(0.f, 0.f);
     float2 nt = make_float2(0.f, 0.f);  // (n, sum of e_k T_k)
     float qz = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
+      if (k == REF) {
+        const float e = t0[k] < a.log_thr ? 1.f : 0.f;
+        szl.y += p2[k].y;
+        nt = ffma2(make_float2(e, e), make_float2(1.f, t0[k]), nt);
+        continue;
+      }
       const float2 ww = make_float2(w[k].x, w[k].x);
       const float2 g1 = ffma2(ww, d1[k], p1[k]);  // (gy, gx)
       const float2 g2 = ffma2(ww, d2[k], p2[k]);  // (gz, ld)
@@ -398,9 +402,53 @@ __device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>&
     const float var = fmaf(-ss, rn, q) * rn;
     const float J = fmaf(-a.beta, var, fmaf(pin, pr, lin * (szl.y - nt.y)));
     if (J > best) { best = J; jb = j; }
+    if (chn) {  // same for every pixel: warp-uniform branch
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (!(chn & (1u << k))) continue;
+        const int c = st.cbase + s_o[jn * a.KP + k];
+        const uint8_t* R = st.row(k);
+        float2 yx0, zd0, yx1, zd1;
+        Tx::quad(R, SWp, c, yx0, zd0);
+        Tx::quad(R, SWp, c + 1, yx1, zd1);
+        const float T0 = Tx::t(R, SWp, c), T1 = Tx::t(R, SWp, c + 1);
+        p1[k] = fadd2(yx0, ref1);
+        d1[k] = fsub2(yx1, yx0);
+        p2[k] = fadd2(zd0, ref2);
+        d2[k] = fsub2(zd1, zd0);
+        t0[k] = T0;
+        dt[k] = T1 - T0;
+      }
+    }
   }
   *n_static = static_cast<unsigned>(nsum);
   return jb;
+}
+
+// Camera k's fixed-label terms from its taps at staged column c (the M-step
+// with fixed labels S below): b1 = (m_Y, m_X), b2 = (m_Zs, m_L) with L the
+// log prior of the ray's label; s1, s2 the slopes to the next tap; ac =
+// (2 m.s, |s|^2) and q0 = |m|^2 over the descriptor (Y, X, Zs).
+template <typename TS>
+__device__ __forceinline__ void fixed_taps(const uint8_t* R, int SWp, int c, bool stat, float lin, float2 ref1,
+                                           float2 ref2, float2& b1, float2& b2, float2& s1, float2& s2, float2& ac,
+                                           float& q0) {
+  using Tx = Texels<TS>;
+  float2 yx0, zd0, yx1, zd1;
+  Tx::quad(R, SWp, c, yx0, zd0);
+  Tx::quad(R, SWp, c + 1, yx1, zd1);
+  const float ls0 = Tx::ls(R, SWp, c), ls1 = Tx::ls(R, SWp, c + 1);
+  zd0.y = stat ? ls0 : zd0.y;  // (Zs, log prior of the label)
+  zd1.y = stat ? ls1 : zd1.y;
+  const float sk = stat ? 1.f : 0.f;
+  const float2 mk = make_float2(sk, sk), ml = make_float2(sk, lin);
+  b1 = fmul2(fadd2(yx0, ref1), mk);
+  s1 = fmul2(fsub2(yx1, yx0), mk);
+  b2 = fmul2(fadd2(zd0, ref2), ml);
+  s2 = fmul2(fsub2(zd1, zd0), ml);
+  const float2 bs = fmul2(b1, s1), sq = fmul2(s1, s1), bb = fmul2(b1, b1);
+  ac = make_float2(2.f * fmaf(b2.x, s2.x, bs.x + bs.y), fmaf(s2.x, s2.x, sq.x + sq.y));
+  q0 = fmaf(b2.x, b2.x, bb.x + bb.y);
 }
 
 // M-step with fixed labels S: every iteration after the first, and the first
@@ -414,83 +462,58 @@ __device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>&
 // three packed fused multiply-adds per ray.  The base sums over k change only
 // at candidates where some camera's tap moves; they are then summed afresh
 // (no drift).  Candidates j0 <= j < j1 (lowest j wins ties; *best_out = the
-// maximum).  RESTART: every camera's taps are loaded at j0, so a range that
-// starts mid-sweep computes each candidate's objective exactly as the whole
-// sweep does (a tap that has not moved since its last load holds the same
-// texels).
-template <int K, typename TS, bool RESTART>
+// maximum).  Every camera's taps are loaded at j0, so a range that starts
+// mid-sweep computes each candidate's objective exactly as the whole sweep
+// does (a tap that has not moved since its last load holds the same texels).
+// As in the first M-step, the loop body is straight-line code for the
+// current candidate and the next candidate's reloads come at its end, and
+// a reference camera known at compile time (REF >= 0) adds nothing per
+// candidate (its slopes are multiplied by weight 0; its log prior is in the
+// base sums).
+template <int K, typename TS, int REF>
 __device__ __forceinline__ int m_step_fixed_range(const SweepArgs& a, const Staged<TS>& st, const float2* s_wq,
                                                   const int* s_o, const unsigned* s_chg, const float* s_d,
                                                   const float* s_rcp, float cy, float cx, float cz, float mu,
                                                   bool inside, unsigned S, int j0, int j1, float* best_out) {
-  using Tx = Texels<TS>;
-  // per camera: b1 = (m_Y, m_X), b2 = (m_Zs, m_L) with L the log prior of the
-  // ray's label; s1, s2 the slopes; ac = (2 m.s, |s|^2) and q0 = |m|^2 over
-  // the descriptor (Y, X, Zs)
   float2 b1[K], b2[K], s1[K], s2[K], ac[K];
   float q0[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    b1[k] = b2[k] = s1[k] = s2[k] = ac[k] = make_float2(0.f, 0.f);
-    q0[k] = 0.f;
-  }
-  float2 B1 = make_float2(0.f, 0.f), B2 = make_float2(0.f, 0.f);
-  float BQ = 0.f;
   const int SWp = st.SWp;
   const float rn = s_rcp[__popc(S)];
   const float2 ref1 = make_float2(-cy, -cx), ref2 = make_float2(-cz, 0.f);
   // outside the triangulation mu is NaN and the prior is uniform: the prior
   // is then evaluated at a finite centre and weighted by pin = 0
   const float lin = a.mseg ? 1.f : 0.f, pin = inside ? 1.f : 0.f, mu_in = inside ? mu : 0.f;
+  const int js = j0 < j1 ? j0 : 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    fixed_taps<TS>(st.row(k), SWp, st.cbase + s_o[js * a.KP + k], (S >> k) & 1u, lin, ref1, ref2, b1[k], b2[k],
+                   s1[k], s2[k], ac[k], q0[k]);
+  float2 B1 = b1[0], B2 = b2[0];
+  float BQ = q0[0];
+#pragma unroll
+  for (int k = 1; k < K; ++k) {
+    B1 = fadd2(B1, b1[k]);
+    B2 = fadd2(B2, b2[k]);
+    BQ += q0[k];
+  }
   float best = -INFINITY;
   int jb = j0;
   auto prior_at = [&](int j) {
     const float t = s_d[j] - mu_in;
     return __logf(a.gamma + __expf(-(t * t) * a.inv2s2));
   };
-  float pr_next = j0 < j1 ? prior_at(j0) : 0.f;
+  float pr_next = prior_at(js);
   for (int j = j0; j < j1; ++j) {
-    const float pr = pr_next;
-    pr_next = prior_at(min(j + 1, j1 - 1));  // the next candidate's prior, off this one's critical path
-    const unsigned ch = RESTART && j == j0 ? (1u << K) - 1u : s_chg[j];
     float2 w[K];
     load_weights<K>(s_wq, a.KP, j, w);
-    if (ch) {  // same for every pixel: warp-uniform branch
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        if (!(ch & (1u << k))) continue;
-        const int c = st.cbase + s_o[j * a.KP + k];
-        const uint8_t* R = st.row(k);
-        const bool stat = (S >> k) & 1u;
-        float2 yx0, zd0, yx1, zd1;
-        Tx::quad(R, SWp, c, yx0, zd0);
-        Tx::quad(R, SWp, c + 1, yx1, zd1);
-        const float ls0 = Tx::ls(R, SWp, c), ls1 = Tx::ls(R, SWp, c + 1);
-        zd0.y = stat ? ls0 : zd0.y;  // (Zs, log prior of the label)
-        zd1.y = stat ? ls1 : zd1.y;
-        const float sk = stat ? 1.f : 0.f;
-        const float2 mk = make_float2(sk, sk), ml = make_float2(sk, lin);
-        b1[k] = fmul2(fadd2(yx0, ref1), mk);
-        s1[k] = fmul2(fsub2(yx1, yx0), mk);
-        b2[k] = fmul2(fadd2(zd0, ref2), ml);
-        s2[k] = fmul2(fsub2(zd1, zd0), ml);
-        const float2 bs = fmul2(b1[k], s1[k]), sq = fmul2(s1[k], s1[k]), bb = fmul2(b1[k], b1[k]);
-        ac[k] = make_float2(2.f * fmaf(b2[k].x, s2[k].x, bs.x + bs.y), fmaf(s2[k].x, s2[k].x, sq.x + sq.y));
-        q0[k] = fmaf(b2[k].x, b2[k].x, bb.x + bb.y);
-      }
-      B1 = b1[0];
-      B2 = b2[0];
-      BQ = q0[0];
-#pragma unroll
-      for (int k = 1; k < K; ++k) {
-        B1 = fadd2(B1, b1[k]);
-        B2 = fadd2(B2, b2[k]);
-        BQ += q0[k];
-      }
-    }
+    const int jn = min(j + 1, j1 - 1);
+    const unsigned chn = j + 1 < j1 ? s_chg[jn] : 0u;  // taps the next candidate reloads
+    const float pr = pr_next;
+    pr_next = prior_at(jn);  // the next candidate's prior, off this one's critical path
     float2 A1 = B1, A2 = B2, QQ = make_float2(BQ, 0.f);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
+      if (k == REF) continue;
       const float2 ww = make_float2(w[k].x, w[k].x);
       A1 = ffma2(ww, s1[k], A1);
       A2 = ffma2(ww, s2[k], A2);
@@ -502,18 +525,35 @@ __device__ __forceinline__ int m_step_fixed_range(const SweepArgs& a, const Stag
     const float var = fmaf(-ss, rn, q) * rn;
     const float J = fmaf(-a.beta, var, fmaf(pin, pr, A2.y));
     if (J > best) { best = J; jb = j; }
+    if (chn) {  // same for every pixel: warp-uniform branch
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (!(chn & (1u << k))) continue;
+        fixed_taps<TS>(st.row(k), SWp, st.cbase + s_o[jn * a.KP + k], (S >> k) & 1u, lin, ref1, ref2, b1[k],
+                       b2[k], s1[k], s2[k], ac[k], q0[k]);
+      }
+      B1 = b1[0];
+      B2 = b2[0];
+      BQ = q0[0];
+#pragma unroll
+      for (int k = 1; k < K; ++k) {
+        B1 = fadd2(B1, b1[k]);
+        B2 = fadd2(B2, b2[k]);
+        BQ += q0[k];
+      }
+    }
   }
   if (best_out) *best_out = best;
   return jb;
 }
 
-template <int K, typename TS>
+template <int K, typename TS, int REF>
 __device__ __forceinline__ int m_step_fixed(const SweepArgs& a, const Staged<TS>& st, const float2* s_wq,
                                             const int* s_o, const unsigned* s_chg, const float* s_d,
                                             const float* s_rcp, float cy, float cx, float cz, float mu,
                                             bool inside, unsigned S) {
-  return m_step_fixed_range<K, TS, false>(a, st, s_wq, s_o, s_chg, s_d, s_rcp, cy, cx, cz, mu, inside, S, 0, a.D,
-                                          nullptr);
+  return m_step_fixed_range<K, TS, REF>(a, st, s_wq, s_o, s_chg, s_d, s_rcp, cy, cx, cz, mu, inside, S, 0, a.D,
+                                   nullptr);
 }
 
 // First-iteration labels of one pixel when they are the same for every
@@ -896,6 +936,87 @@ constexpr int persistent_min_blocks() {
   return K <= 8 ? 2 : 1;
 }
 
+// Luminance of an 8-bit RGB pixel on [0, 1] (BT.601 weights).
+__device__ __forceinline__ float luma_u8(unsigned R, unsigned G, unsigned B) {
+  return fmaf(0.114f, static_cast<float>(B), fmaf(0.587f, static_cast<float>(G), 0.299f * static_cast<float>(R))) *
+         (1.f / 255.f);
+}
+
+// Fused prior of one tile (Sec. III-C "Disparity Prior"), one thread per
+// tile pixel: the triangles of the 16 x 16 bins the tile covers are copied
+// into shared memory first (three rounds of dependent global loads for the
+// whole CTA instead of a chain per pixel), in bin order, so every pixel scans
+// exactly the list it would scan in global memory.  scratch: shared memory
+// that is free until the staging copies land.  A tile whose bins or
+// triangles do not fit scans global memory instead (same result).  Writes
+// mu_out and s_mu (NaN outside the triangulation); contains two
+// __syncthreads.
+constexpr int kTilePriorBins = 32;
+__device__ __forceinline__ void tile_prior(const SweepArgs& a, int u0, int v0, uint8_t* scratch,
+                                           size_t scratch_bytes, float* s_mu) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int bx0 = u0 / kBinSize, bx1 = min(u0 + a.TW - 1, a.W - 1) / kBinSize;
+  const int by0 = v0 / kBinSize, by1 = min(v0 + a.TR - 1, a.H - 1) / kBinSize;
+  const int nbx = bx1 - bx0 + 1, nb = nbx * (by1 - by0 + 1);
+  int* s_off = reinterpret_cast<int*>(scratch);            // [kTilePriorBins + 1] first slot of each bin
+  int* s_beg = s_off + kTilePriorBins + 1;                 // [kTilePriorBins] its first item in bin_items
+  int* s_ok = s_beg + kTilePriorBins;                      // the staged lists are usable
+  const size_t head = align_up((2 * kTilePriorBins + 2) * sizeof(int), 16);
+  PriorTri* s_tri = reinterpret_cast<PriorTri*>(scratch + head);
+  const int cap = scratch_bytes > head ? static_cast<int>((scratch_bytes - head) / sizeof(PriorTri)) : 0;
+  if (tid < 32) {
+    int cnt = 0, beg = 0;
+    if (tid < nb && nb <= kTilePriorBins) {
+      const int bin = (by0 + tid / nbx) * a.pnbx + bx0 + tid % nbx;
+      beg = a.pbin_start[bin];
+      cnt = a.pbin_start[bin + 1] - beg;
+    }
+    int incl = cnt;  // inclusive prefix over the bins
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (tid >= o) incl += y;
+    }
+    if (tid < nb && nb <= kTilePriorBins) {
+      s_off[tid] = incl - cnt;
+      s_beg[tid] = beg;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (tid == 0) {
+      s_off[min(nb, kTilePriorBins)] = total;
+      *s_ok = nb <= kTilePriorBins && total <= cap;
+    }
+  }
+  __syncthreads();
+  const bool ok = *s_ok != 0;
+  if (ok) {
+    const int total = s_off[nb];
+    for (int i = tid; i < total; i += nthr) {
+      int b = 0;
+      while (b + 1 < nb && s_off[b + 1] <= i) ++b;
+      const float4* src = reinterpret_cast<const float4*>(a.ptris + a.pbin_items[s_beg[b] + i - s_off[b]]);
+      float4* dst = reinterpret_cast<float4*>(s_tri + i);
+      static_assert(sizeof(PriorTri) == 48, "a triangle is three 16-byte words");
+      dst[0] = src[0];
+      dst[1] = src[1];
+      dst[2] = src[2];
+    }
+  }
+  __syncthreads();
+  const int u = u0 + tid % a.TW, v = v0 + tid / a.TW;
+  float m = __int_as_float(0x7fc00000);
+  if (u < a.W && v < a.H) {
+    if (ok) {
+      const int b = (v / kBinSize - by0) * nbx + (u / kBinSize - bx0);
+      m = prior::prior_pixel_list(s_tri + s_off[b], s_off[b + 1] - s_off[b], u, v);
+    } else {
+      m = prior::prior_pixel(a.ptris, a.pbin_start, a.pbin_items, a.pnbx, u, v);
+    }
+    a.mu_out[static_cast<size_t>(v) * a.W + u] = m;
+  }
+  s_mu[tid] = m;
+}
+
 // Phases 1-2 for tile (tile_x, tile_y) of one frame: raw rows by TMA, then
 // descriptors and log priors in shared memory.  The CTA's mbarrier
 // (initialised by the caller) completes phase `phase` for this tile's copies.
@@ -946,15 +1067,8 @@ __device__ __forceinline__ bool stage_tile(const SweepArgs& a, const CUtensorMap
     }
     if (tid < 16) s_rcp[tid] = tid >= 2 ? 1.f / static_cast<float>(tid) : 0.f;
   }
-  if (a.ptris) {  // fused prior, computed while the copies are in flight (one thread per tile pixel)
-    const int u = u0 + tid % a.TW, v = v0 + tid / a.TW;
-    float m = __int_as_float(0x7fc00000);
-    if (u < W && v < H) {
-      m = prior::prior_pixel(a.ptris, a.pbin_start, a.pbin_items, a.pnbx, u, v);
-      a.mu_out[static_cast<size_t>(v) * W + u] = m;
-    }
-    reinterpret_cast<float*>(smem + Ly.mu)[tid] = m;
-  }
+  if (a.ptris)  // fused prior, computed while the copies are in flight
+    tile_prior(a, u0, v0, smem + Ly.luma, Ly.feat - Ly.luma, reinterpret_cast<float*>(smem + Ly.mu));
   const bool ok = mbar_wait_bounded(bar, phase, a.timeout_ns);
   if (__syncthreads_or(!ok)) {
     if (!ok) {
@@ -966,50 +1080,101 @@ __device__ __forceinline__ bool stage_tile(const SweepArgs& a, const CUtensorMap
   }
 
   // ---- 2. descriptors and log priors (border replicated)
-  for (int i = tid; i < K * LR * RW; i += nthr) {
-    const uint8_t* px = s_img + static_cast<size_t>(i) * a.bpp;
-    float y;
-    if (a.dtype == 0) {
-      y = a.C == 1 ? static_cast<float>(px[0])
-                   : fmaf(0.114f, static_cast<float>(px[2]),
-                          fmaf(0.587f, static_cast<float>(px[1]), 0.299f * static_cast<float>(px[0])));
-      y *= (1.f / 255.f);
-    } else if (a.dtype == 1) {
-      const float* f = reinterpret_cast<const float*>(px);
-      y = a.C == 1 ? f[0] : fmaf(0.114f, f[2], fmaf(0.587f, f[1], 0.299f * f[0]));
-    } else {
-      float f[3];
-      for (int ch = 0; ch < a.C; ++ch)
-        f[ch] = a.dtype == 2 ? __half2float(reinterpret_cast<const __half*>(px)[ch])
-                             : __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(px)[ch]);
-      y = a.C == 1 ? f[0] : fmaf(0.114f, f[2], fmaf(0.587f, f[1], 0.299f * f[0]));
+  // luminance of every staged raw pixel; four consecutive pixels per thread
+  // for the common input types (same arithmetic per pixel as the general form)
+  const int npx = K * LR * RW;  // a multiple of 16 (RW is)
+  if (a.dtype == 0 && a.C == 3) {
+    for (int q = tid; q < npx / 4; q += nthr) {
+      const uint32_t* w = reinterpret_cast<const uint32_t*>(s_img + static_cast<size_t>(q) * 12);
+      const uint32_t w0 = w[0], w1 = w[1], w2 = w[2];  // R0 G0 B0 R1 | G1 B1 R2 G2 | B2 R3 G3 B3
+      reinterpret_cast<float4*>(s_luma)[q] =
+          make_float4(luma_u8(w0 & 0xffu, (w0 >> 8) & 0xffu, (w0 >> 16) & 0xffu),
+                      luma_u8(w0 >> 24, w1 & 0xffu, (w1 >> 8) & 0xffu),
+                      luma_u8((w1 >> 16) & 0xffu, w1 >> 24, w2 & 0xffu),
+                      luma_u8((w2 >> 8) & 0xffu, (w2 >> 16) & 0xffu, w2 >> 24));
     }
-    s_luma[i] = y;
+  } else if (a.dtype == 0 && a.C == 1) {
+    for (int q = tid; q < npx / 4; q += nthr) {
+      const uint32_t w = reinterpret_cast<const uint32_t*>(s_img)[q];
+      const float sc = 1.f / 255.f;
+      reinterpret_cast<float4*>(s_luma)[q] =
+          make_float4(static_cast<float>(w & 0xffu) * sc, static_cast<float>((w >> 8) & 0xffu) * sc,
+                      static_cast<float>((w >> 16) & 0xffu) * sc, static_cast<float>(w >> 24) * sc);
+    }
+  } else if (a.dtype == 1 && a.C == 1) {
+    for (int q = tid; q < npx / 4; q += nthr)
+      reinterpret_cast<float4*>(s_luma)[q] = reinterpret_cast<const float4*>(s_img)[q];
+  } else {
+    for (int i = tid; i < npx; i += nthr) {
+      const uint8_t* px = s_img + static_cast<size_t>(i) * a.bpp;
+      float y;
+      if (a.dtype == 0) {
+        y = a.C == 1 ? static_cast<float>(px[0]) * (1.f / 255.f) : luma_u8(px[0], px[1], px[2]);
+      } else if (a.dtype == 1) {
+        const float* f = reinterpret_cast<const float*>(px);
+        y = a.C == 1 ? f[0] : fmaf(0.114f, f[2], fmaf(0.587f, f[1], 0.299f * f[0]));
+      } else {
+        float f[3];
+        for (int ch = 0; ch < a.C; ++ch)
+          f[ch] = a.dtype == 2 ? __half2float(reinterpret_cast<const __half*>(px)[ch])
+                               : __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(px)[ch]);
+        y = a.C == 1 ? f[0] : fmaf(0.114f, f[2], fmaf(0.587f, f[1], 0.299f * f[0]));
+      }
+      s_luma[i] = y;
+    }
   }
   __syncthreads();
   const int cam_stride = a.TR * a.SWp * texel_bytes(a.prec);
-  // element (k, r, c) of the K x TR x SW staged maps, walked with a
-  // mixed-radix counter (one step = nthr elements; no division in the loop)
-  int c = tid % a.SW, r = (tid / a.SW) % a.TR, k = tid / (a.SW * a.TR);
-  const int dc = nthr % a.SW, dr = (nthr / a.SW) % a.TR, dk = nthr / (a.SW * a.TR);
-  for (; k < K; c += dc, r += dr, k += dk) {
-    if (c >= a.SW) { c -= a.SW; ++r; }
-    if (r >= a.TR) { r -= a.TR; ++k; }
-    if (k >= K) break;
-    const int Xc = min(max(u0 - a.L + c, 0), W - 1);
-    const int V = min(v0 + r, H - 1);
-    const int rm = max(V - 1, 0) - (v0 - 1), r0 = V - (v0 - 1), rp = min(V + 1, H - 1) - (v0 - 1);
-    const int cm = max(Xc - 1, 0) - cs, c0 = Xc - cs, cp = min(Xc + 1, W - 1) - cs;
-    const float* Lk = s_luma + static_cast<size_t>(k) * LR * RW;
-    const float a00 = Lk[rm * RW + cm], a01 = Lk[rm * RW + c0], a02 = Lk[rm * RW + cp];
-    const float a10 = Lk[r0 * RW + cm], a11 = Lk[r0 * RW + c0], a12 = Lk[r0 * RW + cp];
-    const float a20 = Lk[rp * RW + cm], a21 = Lk[rp * RW + c0], a22 = Lk[rp * RW + cp];
-    const float gx = ((a02 + 2.f * a12) + a22) - ((a00 + 2.f * a10) + a20);
-    const float gy = ((a20 + 2.f * a21) + a22) - ((a00 + 2.f * a01) + a02);
-    const float P = s_p[(static_cast<size_t>(k) * a.TR + (V - v0)) * RW + c0];
-    uint8_t* F = s_feat + static_cast<size_t>(k) * cam_stride + static_cast<size_t>(r) * a.SWp * texel_bytes(a.prec);
-    const float ls = __logf(fmaxf(1.f - P, a.eps)), ld = __logf(fmaxf(P, a.eps));
-    Texels<TS>::store(F, a.SWp, c, a11, gx * 0.125f, gy * 0.125f, ls, ld);
+  const int row_bytes = a.SWp * texel_bytes(a.prec);
+  if (v0 >= 1 && v0 + a.TR <= H - 1) {
+    // no row of the tile touches the top or bottom border: one thread per
+    // staged column (k, c) walks its TR rows with a 3-row window of the
+    // luminance (3 new values per output); same expressions as below
+    for (int item = tid; item < K * a.SW; item += nthr) {
+      const int k = item / a.SW, c = item - k * a.SW;
+      const int Xc = min(max(u0 - a.L + c, 0), W - 1);
+      const int cm = max(Xc - 1, 0) - cs, c0 = Xc - cs, cp = min(Xc + 1, W - 1) - cs;
+      const float* Lk = s_luma + static_cast<size_t>(k) * LR * RW;
+      const float* Pk = s_p + static_cast<size_t>(k) * a.TR * RW + c0;
+      uint8_t* Fk = s_feat + static_cast<size_t>(k) * cam_stride;
+      float m0 = Lk[cm], z0 = Lk[c0], p0 = Lk[cp];                 // staged row r (image row v0 + r - 1)
+      float m1 = Lk[RW + cm], z1 = Lk[RW + c0], p1 = Lk[RW + cp];  // staged row r + 1
+      for (int r = 0; r < a.TR; ++r) {
+        const float* L2 = Lk + static_cast<size_t>(r + 2) * RW;
+        const float m2 = L2[cm], z2 = L2[c0], p2 = L2[cp];
+        const float gx = ((p0 + 2.f * p1) + p2) - ((m0 + 2.f * m1) + m2);
+        const float gy = ((m2 + 2.f * z2) + p2) - ((m0 + 2.f * z0) + p0);
+        const float P = Pk[static_cast<size_t>(r) * RW];
+        const float ls = __logf(fmaxf(1.f - P, a.eps)), ld = __logf(fmaxf(P, a.eps));
+        Texels<TS>::store(Fk + static_cast<size_t>(r) * row_bytes, a.SWp, c, z1, gx * 0.125f, gy * 0.125f, ls, ld);
+        m0 = m1; z0 = z1; p0 = p1;
+        m1 = m2; z1 = z2; p1 = p2;
+      }
+    }
+  } else {
+    // element (k, r, c) of the K x TR x SW staged maps, walked with a
+    // mixed-radix counter (one step = nthr elements; no division in the loop)
+    int c = tid % a.SW, r = (tid / a.SW) % a.TR, k = tid / (a.SW * a.TR);
+    const int dc = nthr % a.SW, dr = (nthr / a.SW) % a.TR, dk = nthr / (a.SW * a.TR);
+    for (; k < K; c += dc, r += dr, k += dk) {
+      if (c >= a.SW) { c -= a.SW; ++r; }
+      if (r >= a.TR) { r -= a.TR; ++k; }
+      if (k >= K) break;
+      const int Xc = min(max(u0 - a.L + c, 0), W - 1);
+      const int V = min(v0 + r, H - 1);
+      const int rm = max(V - 1, 0) - (v0 - 1), r0 = V - (v0 - 1), rp = min(V + 1, H - 1) - (v0 - 1);
+      const int cm = max(Xc - 1, 0) - cs, c0 = Xc - cs, cp = min(Xc + 1, W - 1) - cs;
+      const float* Lk = s_luma + static_cast<size_t>(k) * LR * RW;
+      const float a00 = Lk[rm * RW + cm], a01 = Lk[rm * RW + c0], a02 = Lk[rm * RW + cp];
+      const float a10 = Lk[r0 * RW + cm], a11 = Lk[r0 * RW + c0], a12 = Lk[r0 * RW + cp];
+      const float a20 = Lk[rp * RW + cm], a21 = Lk[rp * RW + c0], a22 = Lk[rp * RW + cp];
+      const float gx = ((a02 + 2.f * a12) + a22) - ((a00 + 2.f * a10) + a20);
+      const float gy = ((a20 + 2.f * a21) + a22) - ((a00 + 2.f * a01) + a02);
+      const float P = s_p[(static_cast<size_t>(k) * a.TR + (V - v0)) * RW + c0];
+      uint8_t* F = s_feat + static_cast<size_t>(k) * cam_stride + static_cast<size_t>(r) * row_bytes;
+      const float ls = __logf(fmaxf(1.f - P, a.eps)), ld = __logf(fmaxf(P, a.eps));
+      Texels<TS>::store(F, a.SWp, c, a11, gx * 0.125f, gy * 0.125f, ls, ld);
+    }
   }
   __syncthreads();
   return true;
@@ -1018,8 +1183,9 @@ __device__ __forceinline__ bool stage_tile(const SweepArgs& a, const CUtensorMap
 // One tile (tile_x, tile_y) of one frame: stage, run the EM, write the
 // outputs.  Staging as in stage_tile.  Ends with a __syncthreads so that the
 // next tile may reuse the shared memory.  Returns false (same in every
-// thread) when the staging wait timed out.
-template <int K, typename TS>
+// thread) when the staging wait timed out.  REF: the reference camera's
+// index when the caller guarantees it (a.ref == REF), else -1.
+template <int K, typename TS, int REF>
 __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap* img_map,
                                            const CUtensorMap* p_map, int tile_x, int tile_y, uint8_t* smem,
                                            unsigned phase, bool load_tables, bool maps_in_global) {
@@ -1096,8 +1262,8 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     const unsigned S0 = ps.S0[p];
     const bool fast = __all_sync(0xffffffffu, f0);
     unsigned ns = __popc(S0) * static_cast<unsigned>(a.D);
-    const int jb = fast ? m_step_fixed<K, TS>(a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, S0)
-                        : m_step_init<K, TS>(a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, &ns);
+    const int jb = fast ? m_step_fixed<K, TS, REF>(a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, S0)
+                        : m_step_init<K, TS, REF>(a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, &ns);
     if (active) my_static += ns;
     Rays rays;
     sample_rays<K, TS>(a, c.st, s_wq, s_o, jb, c.cy, c.cx, c.cz, rays);
@@ -1134,7 +1300,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
         const unsigned Sp = ps.S[p];
         const int per = (a.D + G - 1) / G, j0 = min(gl * per, a.D), j1 = min(j0 + per, a.D);
         float jbest;
-        unsigned jb = static_cast<unsigned>(m_step_fixed_range<K, TS, true>(
+        unsigned jb = static_cast<unsigned>(m_step_fixed_range<K, TS, REF>(
             a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, Sp, j0, j1, &jbest));
         if (act) my_static += __popc(Sp) * static_cast<unsigned>(j1 - j0);
         group_argmax(jbest, jb, G);
@@ -1155,7 +1321,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
       const int p = ps.list[active ? tid : n - 1];
       const PixelCtx<TS> c = load_pixel<TS>(a, s_feat, u0, v0, cam_stride, p, s_mu);
       const unsigned Sp = ps.S[p];
-      const int jb = m_step_fixed<K, TS>(a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, Sp);
+      const int jb = m_step_fixed<K, TS, REF>(a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, Sp);
       if (active) my_static += __popc(Sp) * static_cast<unsigned>(a.D);
       Rays rays;
       sample_rays<K, TS>(a, c.st, s_wq, s_o, jb, c.cy, c.cx, c.cz, rays);
@@ -1236,8 +1402,8 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
   return true;
 }
 
-// One CTA per tile of one frame.
-template <int K, typename TS>
+// One CTA per tile of one frame.  REF: see sweep_tile.
+template <int K, typename TS, int REF>
 __global__ void __launch_bounds__(sweep_max_threads(K), sweep_min_blocks<K>()) em_sweep_kernel(const __grid_constant__ CUtensorMap img_map,
                                                        const __grid_constant__ CUtensorMap p_map,
                                                        const SweepArgs a) {
@@ -1259,7 +1425,7 @@ __global__ void __launch_bounds__(sweep_max_threads(K), sweep_min_blocks<K>()) e
     tx = id % tiles_x;
     ty = id / tiles_x;
   }
-  sweep_tile<K, TS>(a, &img_map, &p_map, tx, ty, smem, 0u, true, false);
+  sweep_tile<K, TS, REF>(a, &img_map, &p_map, tx, ty, smem, 0u, true, false);
 }
 
 // Persistent form for uneven batches: every CTA takes items from one queue
@@ -1303,20 +1469,22 @@ __global__ void __launch_bounds__(256, persistent_min_blocks<K>()) em_sweep_pers
       cur = item.frame;
       __syncthreads();
     }
-    if (!sweep_tile<K, TS>(*s_args, &frames[item.frame].img_map, &frames[item.frame].p_map, item.x, item.y,
+    if (!sweep_tile<K, TS, -1>(*s_args, &frames[item.frame].img_map, &frames[item.frame].p_map, item.x, item.y,
                            smem, phase, fresh, true))
       break;  // a bounded wait expired: stop taking work (the status word says why)
     phase ^= 1u;
   }
 }
 
-template <int K, typename TS>
-cudaError_t launch_em_sweep_k(const CUtensorMap& img_map, const CUtensorMap& p_map, const SweepArgs& a,
-                              cudaStream_t s) {
+// The reference camera sits in the middle of the array in every workload
+// (centred baselines); that case runs the instantiation that knows it.
+template <int K, typename TS, int REF>
+cudaError_t launch_em_sweep_ref(const CUtensorMap& img_map, const CUtensorMap& p_map, const SweepArgs& a,
+                                cudaStream_t s) {
   const size_t smem = sweep_layout(K, a).total;
   static int configured = -1;  // largest dynamic shared size set so far (per process)
   if (static_cast<int>(smem) > configured) {
-    cudaError_t e = cudaFuncSetAttribute(em_sweep_kernel<K, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(em_sweep_kernel<K, TS, REF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     configured = static_cast<int>(smem);
@@ -1324,8 +1492,15 @@ cudaError_t launch_em_sweep_k(const CUtensorMap& img_map, const CUtensorMap& p_m
   if (a.TR * a.TW > sweep_max_threads(K)) return cudaErrorInvalidConfiguration;
   dim3 grid((a.W + a.TW - 1) / a.TW, (a.H + a.TR - 1) / a.TR);
   if (a.tile_list) grid = dim3(grid.x * grid.y, 1);  // one CTA per listed tile (at most all)
-  em_sweep_kernel<K, TS><<<grid, a.TR * a.TW, smem, s>>>(img_map, p_map, a);
+  em_sweep_kernel<K, TS, REF><<<grid, a.TR * a.TW, smem, s>>>(img_map, p_map, a);
   return cudaGetLastError();
+}
+
+template <int K, typename TS>
+cudaError_t launch_em_sweep_k(const CUtensorMap& img_map, const CUtensorMap& p_map, const SweepArgs& a,
+                              cudaStream_t s) {
+  return a.ref == K / 2 ? launch_em_sweep_ref<K, TS, K / 2>(img_map, p_map, a, s)
+                        : launch_em_sweep_ref<K, TS, -1>(img_map, p_map, a, s);
 }
 
 template <int K, typename TS>

@@ -277,9 +277,9 @@ __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorM
     if (run) {
       unsigned S0 = 0, ns = 0;
       const bool f0 = constant_initial_labels<K, float>(a, me.st, &S0);
-      const int jb = f0 ? m_step_fixed<K, float>(a, me.st, s_wq, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu,
+      const int jb = f0 ? m_step_fixed<K, float, -1>(a, me.st, s_wq, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu,
                                                  me.inside, S0)
-                        : m_step_init<K, float>(a, me.st, s_wq, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu,
+                        : m_step_init<K, float, -1>(a, me.st, s_wq, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu,
                                                  me.inside, &ns);
       e_step(me, tid, jb);
     }

@@ -30,6 +30,21 @@ __device__ __forceinline__ int orient_sign(float ax, float ay, float bx, float b
   return (D > 0.0) - (D < 0.0);
 }
 
+// The same test over a contiguous list of n triangles (the pixel's bin, in
+// bin order, staged in shared memory).
+__device__ __forceinline__ float prior_pixel_list(const PriorTri* t, int n, int u, int v) {
+  const float pu = static_cast<float>(u), pv = static_cast<float>(v);
+  for (int i = 0; i < n; ++i, ++t) {
+    if (orient_sign(t->ua, t->va, t->ub, t->vb, pu, pv) < 0) continue;
+    if (orient_sign(t->ub, t->vb, t->uc, t->vc, pu, pv) < 0) continue;
+    if (orient_sign(t->uc, t->vc, t->ua, t->va, pu, pv) < 0) continue;
+    const double m = t->da + t->gu * (static_cast<double>(u) - static_cast<double>(t->ua)) +
+                     t->gv * (static_cast<double>(v) - static_cast<double>(t->va));
+    return static_cast<float>(m);
+  }
+  return __int_as_float(0x7fc00000);  // quiet NaN: outside
+}
+
 __device__ __forceinline__ float prior_pixel(const PriorTri* tris, const int* bin_start, const int* bin_items,
                                              int nbx, int u, int v) {
   const int bin = (v / kBinSize) * nbx + (u / kBinSize);
