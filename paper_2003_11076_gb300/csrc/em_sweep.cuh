@@ -128,6 +128,19 @@ __host__ __device__ constexpr int texel_bytes(int prec) {
 // few units of float32 rounding, far below this margin).
 constexpr float kThresholdMargin = 1e-4f;
 
+// The hardware's base-2 exponential and logarithm (special-function unit,
+// about 2^-22 relative error).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 fsub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 __device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -357,9 +370,12 @@ __device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>&
   }
   float best = -INFINITY, nsum = 0.f;  // nsum: static rays over the candidates (an exact integer)
   int jb = 0;
+  // log prior in base-2 units (the objective takes it times ln 2 * pin):
+  // log2(gamma + 2^(k2 t^2)) with k2 = -log2(e) / (2 sigma^2)
+  const float k2 = -a.inv2s2 * 1.4426950408889634f, pin_ln2 = pin * 0.6931471805599453f;
   auto prior_at = [&](int j) {
     const float t = s_d[j] - mu_in;
-    return __logf(a.gamma + __expf(-(t * t) * a.inv2s2));
+    return lg2_approx(a.gamma + ex2_approx(t * t * k2));
   };
   float pr_next = prior_at(0);
   for (int j = 0; j < a.D; ++j) {
@@ -400,7 +416,7 @@ __device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>&
     const float2 sq = fmul2(syx, syx);
     const float ss = fmaf(szl.x, szl.x, sq.x + sq.y);
     const float var = fmaf(-ss, rn, q) * rn;
-    const float J = fmaf(-a.beta, var, fmaf(pin, pr, lin * (szl.y - nt.y)));
+    const float J = fmaf(-a.beta, var, fmaf(pin_ln2, pr, lin * (szl.y - nt.y)));
     if (J > best) { best = J; jb = j; }
     if (chn) {  // same for every pixel: warp-uniform branch
 #pragma unroll
@@ -498,9 +514,12 @@ __device__ __forceinline__ int m_step_fixed_range(const SweepArgs& a, const Stag
   }
   float best = -INFINITY;
   int jb = j0;
+  // log prior in base-2 units (the objective takes it times ln 2 * pin):
+  // log2(gamma + 2^(k2 t^2)) with k2 = -log2(e) / (2 sigma^2)
+  const float k2 = -a.inv2s2 * 1.4426950408889634f, pin_ln2 = pin * 0.6931471805599453f;
   auto prior_at = [&](int j) {
     const float t = s_d[j] - mu_in;
-    return __logf(a.gamma + __expf(-(t * t) * a.inv2s2));
+    return lg2_approx(a.gamma + ex2_approx(t * t * k2));
   };
   float pr_next = prior_at(js);
   for (int j = j0; j < j1; ++j) {
@@ -523,7 +542,7 @@ __device__ __forceinline__ int m_step_fixed_range(const SweepArgs& a, const Stag
     const float2 sq = fmul2(A1, A1);
     const float ss = fmaf(A2.x, A2.x, sq.x + sq.y);
     const float var = fmaf(-ss, rn, q) * rn;
-    const float J = fmaf(-a.beta, var, fmaf(pin, pr, A2.y));
+    const float J = fmaf(-a.beta, var, fmaf(pin_ln2, pr, A2.y));
     if (J > best) { best = J; jb = j; }
     if (chn) {  // same for every pixel: warp-uniform branch
 #pragma unroll

@@ -256,9 +256,9 @@ void prepare_frame(Frame& f, const lf_params& p, int smem_optin) {
     const double du2 = static_cast<double>(T.uc) - T.ua, dv2 = static_cast<double>(T.vc) - T.va;
     const double det = du1 * dv2 - du2 * dv1;
     if (det == 0.0) continue;
-    T.da = da;
-    T.gu = ((db - da) * dv2 - (dc - da) * dv1) / det;
-    T.gv = (du1 * (dc - da) - du2 * (db - da)) / det;
+    split_double(da, T.da_hi, T.da_lo);
+    split_double(((db - da) * dv2 - (dc - da) * dv1) / det, T.gu_hi, T.gu_lo);
+    split_double((du1 * (dc - da) - du2 * (db - da)) / det, T.gv_hi, T.gv_lo);
     f.tris.push_back(T);
   }
   f.nbx = (f.W + kBinSize - 1) / kBinSize;

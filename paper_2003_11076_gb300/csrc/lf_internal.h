@@ -20,11 +20,20 @@ constexpr unsigned kStatusSmemMisaligned = 2u;
 
 // One support-point triangle of the piecewise-planar prior: vertices (float
 // input coordinates, counter-clockwise) and the plane through them,
-// mu(u, v) = d_a + gu * (u - u_a) + gv * (v - v_a), coefficients in double.
+// mu(u, v) = d_a + gu * (u - u_a) + gv * (v - v_a), with each coefficient
+// (computed in double on the host) stored as an unevaluated float sum
+// hi + lo, hi = float(x), lo = float(x - hi): about 48 significant bits,
+// evaluated on the device in float32 double-float arithmetic (this GPU's
+// float64 rate is a small fraction of its float32 rate).
 struct PriorTri {
   float ua, va, ub, vb, uc, vc;
-  double da, gu, gv;
+  float da_hi, da_lo, gu_hi, gu_lo, gv_hi, gv_lo;
 };
+// Split of a double into float hi + lo (host side).
+inline void split_double(double x, float& hi, float& lo) {
+  hi = static_cast<float>(x);
+  lo = static_cast<float>(x - static_cast<double>(hi));
+}
 
 constexpr int kBinSize = 16;       // prior raster: triangles binned per 16x16 pixels
 

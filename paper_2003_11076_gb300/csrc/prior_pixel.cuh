@@ -7,8 +7,9 @@
 // float32 evaluation is accepted when it clears the rounding-error bound of
 // its own arithmetic, otherwise the determinant is re-evaluated in float64
 // (correctly rounded operations, no contraction).  Points on an edge count
-// as inside.  The disparity is evaluated on the triangle's plane in float64
-// and stored as float32.
+// as inside.  The disparity is evaluated on the triangle's plane in
+// double-float arithmetic (error-free sums and products of float32 numbers,
+// about 44 significant bits) and rounded once to float32.
 #pragma once
 
 #include "lf_internal.h"
@@ -30,6 +31,33 @@ __device__ __forceinline__ int orient_sign(float ax, float ay, float bx, float b
   return (D > 0.0) - (D < 0.0);
 }
 
+// a + b = s + e exactly (Knuth's TwoSum), every operation rounded to nearest.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// mu at the integer pixel (u, v) on triangle t's plane:
+// d_a + gu (u - u_a) + gv (v - v_a) with the coefficients as hi + lo pairs,
+// the differences u - u_a, v - v_a exact as hi + lo pairs, the products with
+// their exact rounding errors (fma), and all parts summed with TwoSum; the
+// result is the one float rounding of the hi + lo total.
+__device__ __forceinline__ float plane_at(const PriorTri& t, float pu, float pv) {
+  float dh, dl, eh, el;
+  two_sum(pu, -t.ua, dh, dl);
+  two_sum(pv, -t.va, eh, el);
+  const float ph = __fmul_rn(t.gu_hi, dh);
+  const float pl = __fadd_rn(__fmaf_rn(t.gu_hi, dh, -ph), __fmaf_rn(t.gu_hi, dl, __fmul_rn(t.gu_lo, dh)));
+  const float qh = __fmul_rn(t.gv_hi, eh);
+  const float ql = __fadd_rn(__fmaf_rn(t.gv_hi, eh, -qh), __fmaf_rn(t.gv_hi, el, __fmul_rn(t.gv_lo, eh)));
+  float s1, e1, s2, e2;
+  two_sum(t.da_hi, ph, s1, e1);
+  two_sum(s1, qh, s2, e2);
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(t.da_lo, pl), __fadd_rn(ql, e1)), e2);
+  return __fadd_rn(s2, lo);
+}
+
 // The same test over a contiguous list of n triangles (the pixel's bin, in
 // bin order, staged in shared memory).
 __device__ __forceinline__ float prior_pixel_list(const PriorTri* t, int n, int u, int v) {
@@ -38,9 +66,7 @@ __device__ __forceinline__ float prior_pixel_list(const PriorTri* t, int n, int 
     if (orient_sign(t->ua, t->va, t->ub, t->vb, pu, pv) < 0) continue;
     if (orient_sign(t->ub, t->vb, t->uc, t->vc, pu, pv) < 0) continue;
     if (orient_sign(t->uc, t->vc, t->ua, t->va, pu, pv) < 0) continue;
-    const double m = t->da + t->gu * (static_cast<double>(u) - static_cast<double>(t->ua)) +
-                     t->gv * (static_cast<double>(v) - static_cast<double>(t->va));
-    return static_cast<float>(m);
+    return plane_at(*t, pu, pv);
   }
   return __int_as_float(0x7fc00000);  // quiet NaN: outside
 }
@@ -54,9 +80,7 @@ __device__ __forceinline__ float prior_pixel(const PriorTri* tris, const int* bi
     if (orient_sign(t.ua, t.va, t.ub, t.vb, pu, pv) < 0) continue;
     if (orient_sign(t.ub, t.vb, t.uc, t.vc, pu, pv) < 0) continue;
     if (orient_sign(t.uc, t.vc, t.ua, t.va, pu, pv) < 0) continue;
-    const double m = t.da + t.gu * (static_cast<double>(u) - static_cast<double>(t.ua)) +
-                     t.gv * (static_cast<double>(v) - static_cast<double>(t.va));
-    return static_cast<float>(m);
+    return plane_at(t, pu, pv);
   }
   return __int_as_float(0x7fc00000);  // quiet NaN: outside
 }
