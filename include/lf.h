@@ -35,6 +35,7 @@
 #ifndef LF_H
 #define LF_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -205,16 +206,26 @@ lf_status lf_set_stream(lf_ctx *ctx, void *stream);
  *                only.
  *   on_device    1: images and seg_prior are device pointers (borrowed until
  *                the stream passes the next lf_run_em); 0: host pointers
- *                (copied now, synchronously with respect to the caller).
+ *                (copied now, synchronously with respect to the caller);
+ *                LF_HOST_ASYNC: host pointers copied to the device on the
+ *                context's stream without waiting -- the caller keeps them
+ *                unchanged until lf_synchronize (page-locked memory, e.g.
+ *                from lf_host_alloc, makes the copy asynchronous; pageable
+ *                memory works but the driver then stages it on the host).
  * Errors: LF_EINVAL (NULL pointer, C not 1 or 3, bad dtype, M < 0 other than
- * LF_DETECT_SUPPORT, non-finite point, detection on a calibrated array),
- * LF_ENOMEM, LF_ECUDA.
+ * LF_DETECT_SUPPORT, non-finite point, detection on a calibrated array,
+ * on_device not 0, 1 or LF_HOST_ASYNC), LF_ENOMEM, LF_ECUDA.
  */
 lf_status lf_set_inputs(lf_ctx *ctx, const void *images, int C, int dtype,
                         const float *seg_prior, const float *sparse_points, int M,
                         int on_device);
 
 #define LF_DETECT_SUPPORT (-1)
+
+/* Transfer mode for lf_set_inputs (on_device) and lf_run_em
+ * (outputs_on_device): host buffers moved by asynchronous copies on the
+ * context's stream; completion through lf_synchronize. */
+#define LF_HOST_ASYNC 2
 
 /*
  * Support-point detection (Sec. III-C "Disparity Prior": points matched along
@@ -294,9 +305,14 @@ lf_status lf_get_support_points(const lf_ctx *ctx, float *points, int max_points
  * other modes run prior, sweep and refocus kernels in order.
  * outputs_on_device: 1 = device pointers (the call returns once the work is
  * enqueued; lf_synchronize waits and reports device errors); 0 = host pointers
- * (the call waits for the results).
+ * (the call waits for the results); LF_HOST_ASYNC = host pointers written by
+ * asynchronous copies on the context's stream (the call returns once the
+ * work and the copies are enqueued; the results are there after
+ * lf_synchronize).  With LF_HOST_ASYNC for inputs and outputs, two contexts
+ * on two streams overlap one frame's copies with the other's kernels.
  * Errors: LF_ESTATE before lf_set_inputs, LF_EINVAL (iters < 1 or > 255, NULL
- * disparity_idx), LF_ETIMEOUT (a bounded device wait expired), LF_ECUDA.
+ * disparity_idx, outputs_on_device not 0, 1 or LF_HOST_ASYNC), LF_ETIMEOUT (a
+ * bounded device wait expired), LF_ECUDA.
  */
 lf_status lf_run_em(lf_ctx *ctx, int iters, int32_t *disparity_idx, float *disparity,
                     float *posteriors, uint16_t *labels, float *refocused,
@@ -305,6 +321,13 @@ lf_status lf_run_em(lf_ctx *ctx, int iters, int32_t *disparity_idx, float *dispa
 /* Wait for the context's stream and report device-side errors of the last
  * run (LF_ETIMEOUT if a bounded wait expired). */
 lf_status lf_synchronize(lf_ctx *ctx);
+
+/* Page-locked host memory for the LF_HOST_ASYNC transfer mode, so that a C
+ * caller needs no CUDA call of its own: *out receives `bytes` bytes (freed
+ * with lf_host_free).  Errors: LF_EINVAL (NULL out, bytes == 0), LF_ENOMEM,
+ * LF_ECUDA. */
+lf_status lf_host_alloc(void **out, size_t bytes);
+void lf_host_free(void *p);
 
 /* Copy the rasterised prior of the last run (Sec. III-C "Disparity Prior"):
  * mu [H][W] float32, the interpolated disparity, NaN outside the

@@ -825,6 +825,7 @@ namespace {
 lf_status set_inputs_impl(lf_ctx* c, const void* images, int C, int dtype, const float* seg_prior,
                           const float* sparse_points, int M, int on_device) {
   if (!images || !seg_prior) return fail(LF_EINVAL, "images and seg_prior must not be NULL");
+  if (on_device < 0 || on_device > LF_HOST_ASYNC) return fail(LF_EINVAL, "on_device must be 0, 1 or LF_HOST_ASYNC");
   if (C != 1 && C != 3) return fail(LF_EINVAL, "C must be 1 or 3");
   if (dtype != LF_U8 && dtype != LF_F32 && dtype != LF_F16 && dtype != LF_BF16)
     return fail(LF_EINVAL, "dtype must be LF_U8, LF_F32, LF_F16 or LF_BF16");
@@ -838,13 +839,13 @@ lf_status set_inputs_impl(lf_ctx* c, const void* images, int C, int dtype, const
   c->C = C;
   c->dtype = dtype;
   c->bpp = C * (dtype == LF_U8 ? 1 : dtype == LF_F32 ? 4 : 2);
-  lf_status s = copy_plane(c, images, static_cast<size_t>(c->W) * c->bpp, on_device != 0, &c->own_img,
+  lf_status s = copy_plane(c, images, static_cast<size_t>(c->W) * c->bpp, on_device == 1, &c->own_img,
                            &c->own_img_cap, &c->img, &c->img_pitch);
   if (s != LF_OK) return s;
   {
     const uint8_t* pp = nullptr;
     uint8_t* ownP = reinterpret_cast<uint8_t*>(c->own_P);
-    s = copy_plane(c, seg_prior, static_cast<size_t>(c->W) * 4, on_device != 0, &ownP, &c->own_P_cap, &pp,
+    s = copy_plane(c, seg_prior, static_cast<size_t>(c->W) * 4, on_device == 1, &ownP, &c->own_P_cap, &pp,
                    &c->p_pitch);
     c->own_P = reinterpret_cast<float*>(ownP);
     if (s != LF_OK) return s;
@@ -868,7 +869,7 @@ lf_status set_inputs_impl(lf_ctx* c, const void* images, int C, int dtype, const
                           c->stream),
           "prior upload");
   if ((s = encode_maps(c)) != LF_OK) return s;
-  if (!on_device) LF_CUDA(cudaStreamSynchronize(c->stream), "input copy");
+  if (on_device == 0) LF_CUDA(cudaStreamSynchronize(c->stream), "input copy");
   c->have_inputs = true;
   return LF_OK;
 }
@@ -877,7 +878,7 @@ lf_status set_inputs_impl(lf_ctx* c, const void* images, int C, int dtype, const
 namespace {
 // Statistics of a run and, for host outputs, the copies back (the call then
 // waits for them).
-lf_status finish_run(lf_ctx* c, int iters, int launched, bool dev, size_t HW, int32_t* disparity_idx,
+lf_status finish_run(lf_ctx* c, int iters, int launched, bool dev, bool async_host, size_t HW, int32_t* disparity_idx,
                      float* disparity, uint16_t* labels, float* posteriors, float* refocused, const int32_t* didx,
                      const float* dout, const uint16_t* lab, const float* post, const float* refo) {
   ++c->runs;
@@ -890,13 +891,14 @@ lf_status finish_run(lf_ctx* c, int iters, int launched, bool dev, size_t HW, in
   c->stats.tile_cols = c->calibrated ? 16 : c->TW;
   c->stats.kernels_launched = launched;
   if (dev) return LF_OK;
+  const cudaMemcpyKind d2h = cudaMemcpyDeviceToHost;
   LF_CUDA(cudaMemcpyAsync(disparity_idx, didx, HW * 4, cudaMemcpyDeviceToHost, c->stream), "output copy");
   if (disparity) LF_CUDA(cudaMemcpyAsync(disparity, dout, HW * 4, cudaMemcpyDeviceToHost, c->stream), "output copy");
   if (labels) LF_CUDA(cudaMemcpyAsync(labels, lab, HW * 2, cudaMemcpyDeviceToHost, c->stream), "output copy");
   if (posteriors)
     LF_CUDA(cudaMemcpyAsync(posteriors, post, HW * 4 * c->K, cudaMemcpyDeviceToHost, c->stream), "output copy");
-  if (refocused)
-    LF_CUDA(cudaMemcpyAsync(refocused, refo, HW * 4 * c->C, cudaMemcpyDeviceToHost, c->stream), "output copy");
+  if (refocused) LF_CUDA(cudaMemcpyAsync(refocused, refo, HW * 4 * c->C, d2h, c->stream), "output copy");
+  if (async_host) return LF_OK;  // LF_HOST_ASYNC: lf_synchronize waits for the copies
   return lf_synchronize(c);
 }
 }  // namespace
@@ -911,7 +913,9 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
   if (iters < 1 || iters > 255) return fail(LF_EINVAL, "iters must be in [1, 255]");
   if (!disparity_idx) return fail(LF_EINVAL, "disparity_idx must not be NULL");
   const size_t HW = static_cast<size_t>(c->H) * c->W;
-  const bool dev = outputs_on_device != 0;
+  if (outputs_on_device < 0 || outputs_on_device > LF_HOST_ASYNC)
+    return fail(LF_EINVAL, "outputs_on_device must be 0, 1 or LF_HOST_ASYNC");
+  const bool dev = outputs_on_device == 1, async_host = outputs_on_device == LF_HOST_ASYNC;
   int32_t* didx = disparity_idx;
   float* dout = disparity;
   uint16_t* lab = labels;
@@ -1005,7 +1009,7 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
         LF_CUDA(mark(4), "event");
       }
     }
-    return finish_run(c, iters, launched, dev, HW, disparity_idx, disparity, labels, posteriors, refocused,
+    return finish_run(c, iters, launched, dev, async_host, HW, disparity_idx, disparity, labels, posteriors, refocused,
                       didx, dout, lab, post, refo);
   }
   SweepArgs a{};
@@ -1088,8 +1092,26 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
       LF_CUDA(mark(4), "event");
     }
   }
-  return finish_run(c, iters, launched, dev, HW, disparity_idx, disparity, labels, posteriors, refocused, didx, dout,
+  return finish_run(c, iters, launched, dev, async_host, HW, disparity_idx, disparity, labels, posteriors, refocused, didx, dout,
                     lab, post, refo);
+}
+
+lf_status lf_host_alloc(void** out, size_t bytes) {
+  g_err.clear();
+  if (!out) return fail(LF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (bytes == 0) return fail(LF_EINVAL, "bytes must be > 0");
+  cudaError_t e = cudaMallocHost(out, bytes);
+  if (e != cudaSuccess) {
+    *out = nullptr;
+    return e == cudaErrorMemoryAllocation ? fail(LF_ENOMEM, "page-locked host allocation failed")
+                                          : cuda_fail(e, "cudaMallocHost");
+  }
+  return LF_OK;
+}
+
+void lf_host_free(void* p) {
+  if (p) cudaFreeHost(p);
 }
 
 lf_status lf_synchronize(lf_ctx* c) {

@@ -26,8 +26,10 @@ EXPORTS = ("lf_default_params", "lf_create", "lf_set_stream", "lf_set_inputs", "
            "lf_triangulate", "lf_set_timing", "lf_run_em_static", "lf_batch_create", "lf_batch_set_stream",
            "lf_batch_add", "lf_batch_run", "lf_batch_synchronize", "lf_batch_clear", "lf_batch_get_stats",
            "lf_batch_destroy", "lf_set_tile", "lf_create_calibrated", "lf_default_support_params",
-           "lf_set_support_params", "lf_get_support_points", "lf_selftest_bounded_wait")
+           "lf_set_support_params", "lf_get_support_points", "lf_selftest_bounded_wait", "lf_host_alloc",
+           "lf_host_free")
 LF_DETECT_SUPPORT = -1
+LF_HOST_ASYNC = 2
 
 
 class LfError(RuntimeError):
@@ -117,6 +119,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         getattr(lib, name).restype = I
     lib.lf_triangulate.argtypes = [P, I, P, I]
     lib.lf_triangulate.restype = I
+    lib.lf_host_alloc.argtypes = [ctypes.POINTER(P), ctypes.c_size_t]
+    lib.lf_host_alloc.restype = I
+    lib.lf_host_free.argtypes = [P]
+    lib.lf_host_free.restype = None
     lib.lf_selftest_bounded_wait.argtypes = [ctypes.c_ulonglong]
     lib.lf_selftest_bounded_wait.restype = I
     for name in ("lf_create", "lf_create_calibrated", "lf_set_stream", "lf_set_inputs", "lf_run_em", "lf_synchronize",
@@ -190,6 +196,38 @@ def run_em_static(baselines, d_min: float, d_max: float, D: int, iters: int, ima
     return out
 
 
+class HostArray(np.ndarray):
+    """A numpy array over page-locked memory from lf_host_alloc (freed with
+    the array), for the LF_HOST_ASYNC transfer mode."""
+
+    def __array_finalize__(self, obj):
+        if obj is not None and getattr(self, "_lf_block", None) is None:
+            self._lf_block = getattr(obj, "_lf_block", None)
+
+
+class _HostBlock:
+    def __init__(self, nbytes: int):
+        ptr = ctypes.c_void_p()
+        _check(load().lf_host_alloc(ctypes.byref(ptr), max(int(nbytes), 1)))
+        self.ptr = ptr.value
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            load().lf_host_free(ctypes.c_void_p(self.ptr))
+            self.ptr = None
+
+
+def host_array(shape, dtype) -> np.ndarray:
+    """Page-locked host array allocated by the library (lf_host_alloc)."""
+    dt = np.dtype(dtype)
+    n = int(np.prod(shape)) * dt.itemsize
+    blk = _HostBlock(n)
+    buf = (ctypes.c_uint8 * max(n, 1)).from_address(blk.ptr)
+    a = np.frombuffer(buf, dtype=dt, count=int(np.prod(shape))).reshape(shape).view(HostArray)
+    a._lf_block = blk
+    return a
+
+
 def _is_torch(x) -> bool:
     return type(x).__module__.startswith("torch")
 
@@ -244,12 +282,14 @@ class Context:
         self.close()
 
     # -- the path
-    def set_inputs(self, images, seg_prior, points):
+    def set_inputs(self, images, seg_prior, points, host_async: bool = False):
         """images [K,H,W] / [K,H,W,3] uint8, float32, float16 or bfloat16
         (the library reads each type as it is); seg_prior [K,H,W] float32
         P(dynamic); points [M,3] float32 (host), or None to detect the
         support points on the device (LF_DETECT_SUPPORT).  numpy arrays and
-        CPU torch tensors are host inputs, torch CUDA tensors device inputs."""
+        CPU torch tensors are host inputs, torch CUDA tensors device inputs.
+        host_async: host inputs copied asynchronously on the context's stream
+        (LF_HOST_ASYNC); keep them unchanged until synchronize()."""
         detect = points is None
         pts = np.zeros((0, 3), np.float32) if detect else np.ascontiguousarray(points, np.float32).reshape(-1, 3)
         pptr = None if detect else pts.ctypes.data
@@ -276,14 +316,20 @@ class Context:
             C = 1 if imgs.ndim == 3 else int(imgs.shape[3])
             dt = dts[imgs.dtype]
             seg = np.ascontiguousarray(seg_prior, np.float32)
-            _check(load().lf_set_inputs(self._h, imgs.ctypes.data, C, dt, seg.ctypes.data, pptr, M, 0))
+            if host_async:
+                self._keep = (imgs, seg)
+            _check(load().lf_set_inputs(self._h, imgs.ctypes.data, C, dt, seg.ctypes.data, pptr, M,
+                                        LF_HOST_ASYNC if host_async else 0))
         self.C = C
 
     def run(self, iters: int, *, posteriors: bool = True, refocus: bool = True, disparity: bool = True,
-            labels: bool = True, out: Optional[dict] = None, device: bool = False) -> dict:
+            labels: bool = True, out: Optional[dict] = None, device: bool = False,
+            host_async: bool = False) -> dict:
         """Run the hot path.  device=False: numpy outputs (the call waits).
         device=True: torch CUDA outputs written on the context's stream (pass
-        preallocated tensors in ``out`` to avoid allocation)."""
+        preallocated tensors in ``out`` to avoid allocation).  host_async:
+        numpy outputs in ``out`` (page-locked, e.g. host_array) written by
+        asynchronous copies (LF_HOST_ASYNC); valid after synchronize()."""
         lib = load()
         K, H, W, C = self.K, self.H, self.W, self.C
         if C is None:
@@ -319,7 +365,7 @@ class Context:
                 res["refocus"] = np.zeros((H, W, C) if C > 1 else (H, W), np.float32)
         ptr = lambda k: res[k].ctypes.data if k in res else None
         _check(lib.lf_run_em(self._h, int(iters), ptr("d_idx"), ptr("d"), ptr("post"), ptr("labels"),
-                             ptr("refocus"), 0))
+                             ptr("refocus"), LF_HOST_ASYNC if host_async else 0))
         return res
 
     def set_support_params(self, params: Optional[SupportParams] = None):

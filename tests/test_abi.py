@@ -269,3 +269,11 @@ def test_static_entry_rejects_dynamic_only(lib):
     s = lib.lf_run_em_static(3, b.ctypes.data, 16, 16, 0.0, 7.0, 8, ctypes.byref(p), 3, img.ctypes.data, 1,
                              lf.LF_F32, img.ctypes.data, mu.ctypes.data, didx.ctypes.data, None, None, None, None)
     assert s == lf.LF_EINVAL and "dynamic_only" in lib.lf_last_error(None).decode()
+
+
+def test_host_alloc_rejects_bad_arguments(lib):
+    from paper_2003_11076_gb300 import lf
+    p = ctypes.c_void_p()
+    assert lib.lf_host_alloc(ctypes.byref(p), 0) == lf.LF_EINVAL and not p.value
+    assert lib.lf_host_alloc(None, 64) == lf.LF_EINVAL
+    lib.lf_host_free(None)  # a no-op

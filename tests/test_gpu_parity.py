@@ -397,3 +397,49 @@ def test_bounded_wait_expiry_is_reported_and_the_device_stays_usable():
     s = scenes.small_gray(0)
     g, o = run_both(s)
     check_parity(g, o, what="after the bounded-wait self-test")
+
+
+def test_async_host_transfers_pipelined_over_two_contexts():
+    """LF_HOST_ASYNC: page-locked host inputs and outputs (lf_host_alloc)
+    moved by asynchronous copies; two contexts on two streams take frames in
+    turn (one frame's copies overlap the other's kernels).  Every frame's
+    outputs equal the blocking host-pointer path's bit for bit."""
+    import torch
+    lf = _lf()
+    frames = [scenes.street_rgb(i, H=96, W=160, D=32, iters=6, M=40) for i in range(6)]
+    s0 = frames[0]
+    K, H, W, C = s0.K, s0.H, s0.W, s0.C
+    ref = [lf.run_scene(s) for s in frames]
+    ctxs, ins, outs = [], [], []
+    for i in range(2):
+        c = lf.Context(s0.baselines, H, W, s0.d_min, s0.d_max, s0.D)
+        c.set_stream(torch.cuda.Stream())
+        ctxs.append(c)
+        ins.append((lf.host_array(s0.images.shape, np.uint8), lf.host_array(s0.seg_prior.shape, np.float32)))
+        outs.append({"d_idx": lf.host_array((H, W), np.int32), "d": lf.host_array((H, W), np.float32),
+                     "post": lf.host_array((K, H, W), np.float32), "labels": lf.host_array((H, W), np.uint16),
+                     "refocus": lf.host_array((H, W, C), np.float32)})
+    got = [None] * len(frames)
+    for f, s in enumerate(frames):
+        i = f % 2
+        if f >= 2:  # this context's previous frame: wait, then keep its results
+            ctxs[i].synchronize()
+            got[f - 2] = {k: v.copy() for k, v in outs[i].items()}
+        ins[i][0][...] = s.images
+        ins[i][1][...] = s.seg_prior
+        ctxs[i].set_inputs(ins[i][0], ins[i][1], s.points, host_async=True)
+        ctxs[i].run(s.iters, out=outs[i], host_async=True)
+    for f in (len(frames) - 2, len(frames) - 1):
+        ctxs[f % 2].synchronize()
+        got[f] = {k: v.copy() for k, v in outs[f % 2].items()}
+    for g, r in zip(got, ref):
+        for k in ("d_idx", "d", "post", "labels", "refocus"):
+            assert np.array_equal(g[k], r[k]), k
+    for c in ctxs:
+        c.close()
+    with lf.Context(s0.baselines, H, W, s0.d_min, s0.d_max, s0.D) as c:
+        c.set_inputs(s0.images, s0.seg_prior, s0.points)
+        with pytest.raises(lf.LfError) as e:
+            didx = np.zeros((H, W), np.int32)
+            lf._check(lf.load().lf_run_em(c._h, 3, didx.ctypes.data, None, None, None, None, 3))
+        assert e.value.status == lf.LF_EINVAL

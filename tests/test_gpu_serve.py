@@ -75,3 +75,47 @@ def test_reduced_precision_served_equals_alone(pool):
         alone = lf.run_scene(pool[r.rid % len(pool)], params=lf.default_params(precision=1))
         assert np.array_equal(r.result["d_idx"], alone["d_idx"])
     srv.close()
+
+
+def test_request_larger_than_the_budget_is_rejected_not_left_waiting(pool):
+    """A frame whose buffers exceed the server's whole device block can never
+    be admitted: submit rejects it at once (status and message), and the
+    other requests are served normally."""
+    from paper_2003_11076_gb300 import lf, serve
+    small = [serve.Request.from_scene(i, pool[i]) for i in range(3)]
+    big = serve.Request.from_scene(99, scenes.street_rgb(0, H=400, W=640, D=32, iters=3, M=40))
+    budget = max(r.device_bytes() for r in small) * 2
+    assert big.device_bytes() > budget
+    srv = serve.Server(max_batch=4, inflight=2, hbm_budget=budget)
+    assert not srv.submit(big)
+    assert big.status == "rejected" and "device bytes" in big.error
+    for r in small:
+        assert srv.submit(r)
+    srv.drain(timeout_s=60)
+    assert [r.status for r in small] == ["done"] * 3 and srv.rejected == [big]
+    assert srv.admitted_bytes == 0
+    _check_equal_alone(lf, small, pool)
+    srv.close()
+
+
+def test_cancelled_requests_return_their_bytes(pool):
+    """Cancelling a request that waits for admission, or one admitted but not
+    launched, returns its device and host bytes; a launched one cannot be
+    cancelled; the rest complete with their results."""
+    from paper_2003_11076_gb300 import lf, serve
+    reqs = [serve.Request.from_scene(i, pool[i]) for i in range(4)]
+    srv = serve.Server(max_batch=4, inflight=1, hbm_budget=sum(r.device_bytes() for r in reqs))
+    for r in reqs:
+        srv.submit(r)
+    assert srv.cancel(reqs[3]) and reqs[3].status == "cancelled"   # still pending
+    srv._admit()                                                     # admitted, not launched
+    used = srv.admitted_bytes
+    assert reqs[2].status == "admitted" and srv.cancel(reqs[2])
+    assert srv.admitted_bytes < used and reqs[2].status == "cancelled"
+    srv._launch()
+    assert not srv.cancel(reqs[0])                                   # on the GPU
+    srv.drain(timeout_s=60)
+    assert [r.status for r in reqs] == ["done", "done", "cancelled", "cancelled"]
+    assert srv.admitted_bytes == 0 and srv.dev_arena.free_list == [(0, srv.dev_arena.capacity)]
+    _check_equal_alone(lf, reqs[:2], pool)
+    srv.close()

@@ -27,3 +27,45 @@ def test_request_device_bytes_cover_inputs_and_outputs():
     HW = s.H * s.W
     assert need >= s.images.nbytes + s.seg_prior.nbytes + HW * (4 + 4 + 2) + s.K * HW * 4 + HW * 4
     assert (r.K, r.H, r.W, r.C) == (s.K, s.H, s.W, 1) and r.arrival == 0.25
+
+
+def test_arena_first_fit_merges_and_never_overlaps():
+    """The server's block allocator: aligned first-fit, freed neighbours
+    merge back into one range, live ranges never overlap, and a request
+    larger than the block never fits."""
+    a = serve.Arena(4096, align=256)
+    offs = [a.alloc(300), a.alloc(256), a.alloc(1000)]
+    assert offs == [0, 512, 768] and a.bytes_used == 512 + 256 + 1024
+    assert a.alloc(4096) is None and not a.fits_ever(4097) and a.fits_ever(4096)
+    a.free(512)
+    assert a.alloc(200) == 512            # first fit reuses the hole
+    a.free(0)
+    a.free(512)
+    a.free(768)
+    assert a.free_list == [(0, 4096)] and a.bytes_used == 0
+    rng = np.random.default_rng(0)
+    live = {}
+    for _ in range(2000):
+        if live and rng.random() < 0.45:
+            off = list(live)[rng.integers(len(live))]
+            a.free(off)
+            del live[off]
+        else:
+            n = int(rng.integers(1, 900))
+            off = a.alloc(n)
+            if off is not None:
+                live[off] = a.size_of(n)
+        spans = sorted(live.items())
+        assert all(o1 + s1 <= o2 for (o1, s1), (o2, _) in zip(spans, spans[1:]))
+        assert all(o % 256 == 0 and o + s <= 4096 for o, s in spans)
+        assert a.bytes_used == sum(live.values())
+        assert sum(s for _, s in a.free_list) == 4096 - a.bytes_used
+
+
+def test_request_output_layout_and_bytes():
+    s = scenes.street_rgb(0, H=40, W=50, D=16, iters=3, M=10)
+    r = serve.Request.from_scene(1, s)
+    names = [n for n, _, _ in r.output_layout()]
+    assert names == ["d_idx", "d", "post", "labels", "refocus"]
+    assert dict((n, sh) for n, sh, _ in r.output_layout())["refocus"] == (40, 50, 3)
+    assert r.output_bytes() % 256 == 0 and r.device_bytes() > r.output_bytes()
