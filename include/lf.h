@@ -322,6 +322,13 @@ lf_status lf_run_em(lf_ctx *ctx, int iters, int32_t *disparity_idx, float *dispa
  * run (LF_ETIMEOUT if a bounded wait expired). */
 lf_status lf_synchronize(lf_ctx *ctx);
 
+/* Fault injection for tests, on the host only: after `after` further
+ * successful device allocations by the library (contexts and batches), the
+ * next one reports LF_ENOMEM without being attempted, once; after < 0
+ * switches the injection off.  Process-wide.  A call that fails this way
+ * leaves its context usable: the next call allocates again. */
+void lf_inject_alloc_failure(int after);
+
 /* Page-locked host memory for the LF_HOST_ASYNC transfer mode, so that a C
  * caller needs no CUDA call of its own: *out receives `bytes` bytes (freed
  * with lf_host_free).  Errors: LF_EINVAL (NULL out, bytes == 0), LF_ENOMEM,

@@ -1,4 +1,6 @@
-"""Build the in-tree CUDA library ``_lib/liblf.so`` for sm_103a.
+"""Build the in-tree CUDA library ``_lib/liblf.so`` for sm_103a (and, on
+request, the debug variant ``_lib/liblf_debug.so``, compiled with -DLF_DEBUG:
+every index into the sweep's shared-memory carve-up is checked).
 
 Every translation unit is compiled in parallel with nvcc (``-gencode
 arch=compute_103a,code=sm_103a``) or g++ (host Delaunay), then linked with the
@@ -19,6 +21,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "_lib", "liblf.so")
+DEBUG_BUILD = os.path.join(HERE, "_build_debug")
+DEBUG_LIB = os.path.join(HERE, "_lib", "liblf_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -38,23 +42,26 @@ def _deps():
         [os.path.join(INCLUDE, "lf.h"), os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_nvcc=()) -> str:
-    if not force and up_to_date():
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra_nvcc=(), debug: bool = False) -> str:
+    lib, bdir = (DEBUG_LIB, DEBUG_BUILD) if debug else (LIB, BUILD)
+    if debug:
+        extra_nvcc = tuple(extra_nvcc) + ("-DLF_DEBUG",)
+    if not force and up_to_date(lib):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
-    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    os.makedirs(bdir, exist_ok=True)
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
     inc = ["-I", INCLUDE, "-I", CSRC]
     jobs = []
     for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
         if src.endswith(".cu"):
             cmd = [nvcc] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
                                    "-c", src, "-o", obj] + inc + list(extra_nvcc)
@@ -74,13 +81,13 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc=()) -> str:
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=max(2, os.cpu_count() or 2)) as ex:
         objs = list(ex.map(run, jobs))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -141,6 +141,25 @@ __device__ __forceinline__ float lg2_approx(float x) {
   return y;
 }
 
+// Debug builds (LF_DEBUG) check the indices into the shared-memory carve-up
+// against their regions: an index outside [lo, hi] sets
+// kStatusBoundsViolation in the run's status word (the call then reports
+// LF_ECUDA) and is clamped into the region, so the access stays inside
+// shared memory.  Release builds compile the check away.
+__device__ __forceinline__ int chk(int i, int lo, int hi, unsigned* status) {
+#ifdef LF_DEBUG
+  if (i < lo || i > hi) {
+    atomicOr(status, kStatusBoundsViolation);
+    return i < lo ? lo : hi;
+  }
+#else
+  (void)lo;
+  (void)hi;
+  (void)status;
+#endif
+  return i;
+}
+
 __device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 fsub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 __device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -355,7 +374,7 @@ __device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>&
   const float lin = a.mseg ? 1.f : 0.f, pin = inside ? 1.f : 0.f, mu_in = inside ? mu : 0.f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const int c = st.cbase + s_o[k];
+    const int c = chk(st.cbase + s_o[k], 0, a.SW - 2, a.status);
     const uint8_t* R = st.row(k);
     float2 yx0, zd0, yx1, zd1;
     Tx::quad(R, SWp, c, yx0, zd0);
@@ -422,7 +441,7 @@ __device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>&
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         if (!(chn & (1u << k))) continue;
-        const int c = st.cbase + s_o[jn * a.KP + k];
+        const int c = chk(st.cbase + s_o[chk(jn * a.KP + k, 0, a.D * a.KP - 1, a.status)], 0, a.SW - 2, a.status);
         const uint8_t* R = st.row(k);
         float2 yx0, zd0, yx1, zd1;
         Tx::quad(R, SWp, c, yx0, zd0);
@@ -502,7 +521,8 @@ __device__ __forceinline__ int m_step_fixed_range(const SweepArgs& a, const Stag
   const int js = j0 < j1 ? j0 : 0;
 #pragma unroll
   for (int k = 0; k < K; ++k)
-    fixed_taps<TS>(st.row(k), SWp, st.cbase + s_o[js * a.KP + k], (S >> k) & 1u, lin, ref1, ref2, b1[k], b2[k],
+    fixed_taps<TS>(st.row(k), SWp, chk(st.cbase + s_o[js * a.KP + k], 0, a.SW - 2, a.status), (S >> k) & 1u, lin,
+                   ref1, ref2, b1[k], b2[k],
                    s1[k], s2[k], ac[k], q0[k]);
   float2 B1 = b1[0], B2 = b2[0];
   float BQ = q0[0];
@@ -548,7 +568,9 @@ __device__ __forceinline__ int m_step_fixed_range(const SweepArgs& a, const Stag
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         if (!(chn & (1u << k))) continue;
-        fixed_taps<TS>(st.row(k), SWp, st.cbase + s_o[jn * a.KP + k], (S >> k) & 1u, lin, ref1, ref2, b1[k],
+        fixed_taps<TS>(st.row(k), SWp,
+                       chk(st.cbase + s_o[chk(jn * a.KP + k, 0, a.D * a.KP - 1, a.status)], 0, a.SW - 2, a.status),
+                       (S >> k) & 1u, lin, ref1, ref2, b1[k],
                        b2[k], s1[k], s2[k], ac[k], q0[k]);
       }
       B1 = b1[0];
@@ -587,7 +609,9 @@ __device__ __forceinline__ bool constant_initial_labels(const SweepArgs& a, cons
   for (int k = 0; k < K; ++k) {
     const uint8_t* R = st.row(k);
     float lo = INFINITY, hi = -INFINITY;
-    for (int c = st.cbase + a.omin[k]; c <= st.cbase + a.omax[k] + 1; ++c) {
+    const int c_lo = chk(st.cbase + a.omin[k], 0, a.SW - 1, a.status);
+    const int c_hi = chk(st.cbase + a.omax[k] + 1, 0, a.SW - 1, a.status);
+    for (int c = c_lo; c <= c_hi; ++c) {
       const float z = Texels<TS>::t(R, st.SWp, c);
       lo = fminf(lo, z);
       hi = fmaxf(hi, z);
@@ -616,8 +640,9 @@ __device__ __forceinline__ void sample_rays(const SweepArgs& a, const Staged<TS>
   r.base = 0.f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const float w = s_wq[jt * a.KP + k].x;
-    const int c = st.cbase + s_o[jt * a.KP + k];
+    const int jk = chk(jt * a.KP + k, 0, a.D * a.KP - 1, a.status);
+    const float w = s_wq[jk].x;
+    const int c = chk(st.cbase + s_o[jk], 0, a.SW - 2, a.status);
     const uint8_t* R = st.row(k);
     float2 yx0, zd0, yx1, zd1;
     Tx::quad(R, SWp, c, yx0, zd0);
@@ -899,6 +924,7 @@ template <typename TS>
 __device__ __forceinline__ PixelCtx<TS> load_pixel(const SweepArgs& a, const uint8_t* s_feat, int u0, int v0,
                                                    int cam_stride, int p, const float* s_mu = nullptr) {
   PixelCtx<TS> c;
+  p = chk(p, 0, a.TR * a.TW - 1, a.status);
   const int r = p / a.TW, tx = p - r * a.TW;
   c.u = u0 + tx;
   c.v = v0 + r;
@@ -1026,7 +1052,7 @@ __device__ __forceinline__ void tile_prior(const SweepArgs& a, int u0, int v0, u
   float m = __int_as_float(0x7fc00000);
   if (u < a.W && v < a.H) {
     if (ok) {
-      const int b = (v / kBinSize - by0) * nbx + (u / kBinSize - bx0);
+      const int b = chk((v / kBinSize - by0) * nbx + (u / kBinSize - bx0), 0, nb - 1, a.status);
       m = prior::prior_pixel_list(s_tri + s_off[b], s_off[b + 1] - s_off[b], u, v);
     } else {
       m = prior::prior_pixel(a.ptris, a.pbin_start, a.pbin_items, a.pnbx, u, v);
@@ -1152,7 +1178,8 @@ __device__ __forceinline__ bool stage_tile(const SweepArgs& a, const CUtensorMap
     for (int item = tid; item < K * a.SW; item += nthr) {
       const int k = item / a.SW, c = item - k * a.SW;
       const int Xc = min(max(u0 - a.L + c, 0), W - 1);
-      const int cm = max(Xc - 1, 0) - cs, c0 = Xc - cs, cp = min(Xc + 1, W - 1) - cs;
+      const int cm = chk(max(Xc - 1, 0) - cs, 0, RW - 1, a.status), c0 = chk(Xc - cs, 0, RW - 1, a.status),
+                cp = chk(min(Xc + 1, W - 1) - cs, 0, RW - 1, a.status);
       const float* Lk = s_luma + static_cast<size_t>(k) * LR * RW;
       const float* Pk = s_p + static_cast<size_t>(k) * a.TR * RW + c0;
       uint8_t* Fk = s_feat + static_cast<size_t>(k) * cam_stride;
@@ -1181,8 +1208,10 @@ __device__ __forceinline__ bool stage_tile(const SweepArgs& a, const CUtensorMap
       if (k >= K) break;
       const int Xc = min(max(u0 - a.L + c, 0), W - 1);
       const int V = min(v0 + r, H - 1);
-      const int rm = max(V - 1, 0) - (v0 - 1), r0 = V - (v0 - 1), rp = min(V + 1, H - 1) - (v0 - 1);
-      const int cm = max(Xc - 1, 0) - cs, c0 = Xc - cs, cp = min(Xc + 1, W - 1) - cs;
+      const int rm = chk(max(V - 1, 0) - (v0 - 1), 0, LR - 1, a.status), r0 = chk(V - (v0 - 1), 0, LR - 1, a.status),
+                rp = chk(min(V + 1, H - 1) - (v0 - 1), 0, LR - 1, a.status);
+      const int cm = chk(max(Xc - 1, 0) - cs, 0, RW - 1, a.status), c0 = chk(Xc - cs, 0, RW - 1, a.status),
+                cp = chk(min(Xc + 1, W - 1) - cs, 0, RW - 1, a.status);
       const float* Lk = s_luma + static_cast<size_t>(k) * LR * RW;
       const float a00 = Lk[rm * RW + cm], a01 = Lk[rm * RW + c0], a02 = Lk[rm * RW + cp];
       const float a10 = Lk[r0 * RW + cm], a11 = Lk[r0 * RW + c0], a12 = Lk[r0 * RW + cp];
@@ -1384,7 +1413,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
       const float scale = a.dtype == 0 ? (1.f / 255.f) : 1.f;
       float* out = a.refocus_out + pix * a.C;
       auto px = [&](int k, int x, int c) {
-        return pixel_element(s_img + ((k * LR + row) * RW + (x - cs)) * a.bpp, c, a.dtype);
+        return pixel_element(s_img + ((k * LR + row) * RW + chk(x - cs, 0, RW - 1, a.status)) * a.bpp, c, a.dtype);
       };
       if (S == 0u) {
         for (int c = 0; c < a.C; ++c) out[c] = px(a.ref, me.u, c) * scale;
@@ -1431,6 +1460,16 @@ __global__ void __launch_bounds__(sweep_max_threads(K), sweep_min_blocks<K>()) e
     if (threadIdx.x == 0) atomicOr(a.status, kStatusSmemMisaligned);
     return;
   }
+#ifdef LF_DEBUG
+  {  // the carve-up must fit the dynamic shared memory of the launch
+    unsigned dyn;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    if (sweep_layout(K, a).total > dyn) {
+      if (threadIdx.x == 0) atomicOr(a.status, kStatusBoundsViolation);
+      return;
+    }
+  }
+#endif
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kSmemBar);
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);

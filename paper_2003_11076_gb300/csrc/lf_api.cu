@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -166,6 +167,7 @@ lf_status grow(T** ptr, size_t* cap, size_t need, const char* what) {
   *ptr = nullptr;
   *cap = 0;
   size_t n = std::max<size_t>(need, 1);
+  if (injected_alloc_failure()) return fail(LF_ENOMEM, std::string(what) + ": out of device memory (injected)");
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), n * sizeof(T));
   if (e != cudaSuccess) {
     *ptr = nullptr;
@@ -181,6 +183,18 @@ constexpr unsigned long long kTimeoutNs = 2000000000ull;  // 2 s bounded device 
 }  // namespace
 
 void lf::set_error_message(const std::string& msg) { g_err = msg; }
+
+namespace {
+std::atomic<long long> g_fail_after{-1};  // successful allocations left before the injected failure; < 0: off
+}  // namespace
+
+bool lf::injected_alloc_failure() {
+  long long v = g_fail_after.load();
+  while (v >= 0) {
+    if (g_fail_after.compare_exchange_weak(v, v - 1)) return v == 0;  // the (after + 1)-th allocation fails
+  }
+  return false;
+}
 
 bool lf::check_params(const lf_params& p, std::string* why) {
   const char* msg = nullptr;
@@ -1096,6 +1110,8 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
                     lab, post, refo);
 }
 
+void lf_inject_alloc_failure(int after) { g_fail_after.store(after < 0 ? -1 : after); }
+
 lf_status lf_host_alloc(void** out, size_t bytes) {
   g_err.clear();
   if (!out) return fail(LF_EINVAL, "out is NULL");
@@ -1123,6 +1139,8 @@ lf_status lf_synchronize(lf_ctx* c) {
   if (st) LF_CUDA(cudaMemset(c->d_status, 0, sizeof(st)), "status reset");
   if (st & kStatusTmaTimeout) return fail(LF_ETIMEOUT, "a bounded TMA wait in the sweep kernel expired");
   if (st & kStatusSmemMisaligned) return fail(LF_ECUDA, "sweep kernel: dynamic shared memory not 128-byte aligned");
+  if (st & kStatusBoundsViolation)
+    return fail(LF_ECUDA, "sweep kernel (debug build): a shared-memory index left its region");
   return LF_OK;
 }
 

@@ -191,6 +191,7 @@ lf_status dev_grow(void** p, size_t* cap, size_t need, bool* moved = nullptr) {
   *p = nullptr;
   *cap = 0;
   const size_t n = std::max<size_t>(need + need / 4, 256);
+  if (injected_alloc_failure()) return fail(LF_ENOMEM, "batch: out of device memory (injected)");
   cudaError_t e = cudaMalloc(p, n);
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -786,6 +787,8 @@ lf_status lf_batch_synchronize(lf_batch* b) {
   if (st) LF_CUDA(cudaMemset(b->d_status, 0, sizeof(st)), "status reset");
   if (st & kStatusTmaTimeout) return fail(LF_ETIMEOUT, "a bounded TMA wait in the sweep kernel expired");
   if (st & kStatusSmemMisaligned) return fail(LF_ECUDA, "sweep kernel: dynamic shared memory not 128-byte aligned");
+  if (st & kStatusBoundsViolation)
+    return fail(LF_ECUDA, "sweep kernel (debug build): a shared-memory index left its region");
   return LF_OK;
 }
 

@@ -17,6 +17,7 @@ constexpr int kPrecF32 = 0, kPrecF16 = 1, kPrecBF16 = 2;
 // Device status word bits (written by kernels, read by the host after a sync).
 constexpr unsigned kStatusTmaTimeout = 1u;
 constexpr unsigned kStatusSmemMisaligned = 2u;
+constexpr unsigned kStatusBoundsViolation = 4u;  // debug builds: a shared-memory index left its region
 
 // One support-point triangle of the piecewise-planar prior: vertices (float
 // input coordinates, counter-clockwise) and the plane through them,
@@ -236,6 +237,11 @@ int em_sweep_persistent_occupancy(int K, int prec, size_t smem, int threads);
 // 0 < seg_threshold < 1; precision and em_mode among their enumerators; the
 // two EM variants on float32 maps only.  False with *why set otherwise.
 bool check_params(const lf_params& p, std::string* why);
+
+// Host-side allocation-failure injection (lf_inject_alloc_failure): true
+// when the library's allocation wrappers must report LF_ENOMEM for the
+// allocation they are about to make (no allocation is attempted).
+bool injected_alloc_failure();
 
 // Sets the calling thread's message returned by lf_last_error.
 void set_error_message(const std::string& msg);

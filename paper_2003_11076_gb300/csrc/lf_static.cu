@@ -237,5 +237,7 @@ extern "C" lf_status lf_run_em_static(int n_cams, const float* baselines, int H,
   if (e != cudaSuccess) return fail(LF_ECUDA, std::string("status read: ") + cudaGetErrorString(e));
   if (st & kStatusTmaTimeout) return fail(LF_ETIMEOUT, "a bounded TMA wait in the sweep kernel expired");
   if (st & kStatusSmemMisaligned) return fail(LF_ECUDA, "sweep kernel: dynamic shared memory not 128-byte aligned");
+  if (st & kStatusBoundsViolation)
+    return fail(LF_ECUDA, "sweep kernel (debug build): a shared-memory index left its region");
   return LF_OK;
 }

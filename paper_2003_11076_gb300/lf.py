@@ -27,7 +27,7 @@ EXPORTS = ("lf_default_params", "lf_create", "lf_set_stream", "lf_set_inputs", "
            "lf_batch_add", "lf_batch_run", "lf_batch_synchronize", "lf_batch_clear", "lf_batch_get_stats",
            "lf_batch_destroy", "lf_set_tile", "lf_create_calibrated", "lf_default_support_params",
            "lf_set_support_params", "lf_get_support_points", "lf_selftest_bounded_wait", "lf_host_alloc",
-           "lf_host_free")
+           "lf_host_free", "lf_inject_alloc_failure")
 LF_DETECT_SUPPORT = -1
 LF_HOST_ASYNC = 2
 
@@ -123,6 +123,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lf_host_alloc.restype = I
     lib.lf_host_free.argtypes = [P]
     lib.lf_host_free.restype = None
+    lib.lf_inject_alloc_failure.argtypes = [I]
+    lib.lf_inject_alloc_failure.restype = None
     lib.lf_selftest_bounded_wait.argtypes = [ctypes.c_ulonglong]
     lib.lf_selftest_bounded_wait.restype = I
     for name in ("lf_create", "lf_create_calibrated", "lf_set_stream", "lf_set_inputs", "lf_run_em", "lf_synchronize",
