@@ -268,6 +268,10 @@ constexpr size_t kSmemArgs = 16;
 constexpr size_t kSmemItem = kSmemArgs + ((sizeof(SweepArgs) + 15) / 16) * 16;
 constexpr size_t kSmemHead = ((kSmemItem + 16 + 127) / 128) * 128;
 
+// float32 gray inputs: the staged raw rows already hold the luminance in the
+// layout the descriptor maps read, so they are used in place.
+__host__ __device__ inline bool luma_is_raw(const SweepArgs& a) { return a.dtype == 1 && a.C == 1; }
+
 // The sampling tables in shared memory: per (candidate, camera) the
 // interpolation weight and its square, (w, w^2) (float2), and the tap
 // offset floor(-d_j b_k) (int).
@@ -278,8 +282,8 @@ __host__ __device__ inline SmemLayout sweep_layout(int K, const SweepArgs& a) {
   o = align_up(o + static_cast<size_t>(K) * (a.TR + 2) * a.RW * a.bpp, 128);
   L.raw_p = o;
   o = align_up(o + static_cast<size_t>(K) * a.TR * a.RW * 4, 128);
-  L.luma = o;
-  o = align_up(o + static_cast<size_t>(K) * (a.TR + 2) * a.RW * 4, 16);
+  L.luma = o;  // float32 gray inputs: the staged rows are the luminance (no region of its own)
+  o = align_up(o + (luma_is_raw(a) ? 0 : static_cast<size_t>(K) * (a.TR + 2) * a.RW * 4), 16);
   L.feat = o;
   o = align_up(o + static_cast<size_t>(K) * a.TR * a.SWp * texel_bytes(a.prec), 16);
   L.wtab = o;
@@ -691,7 +695,7 @@ __device__ __forceinline__ void enum_low(const Rays& r, const Acc& acc, const fl
     if constexpr (MODE == 0) {
       if (E > s.best) { s.best = E; s.bmask = high | MASK; }
     } else {
-      const float e = expf(E - s.emax);
+      const float e = ex2_approx((E - s.emax) * 1.4426950408889634f);  // exp(E - Emax) <= 1
       s.Z += e;
 #pragma unroll
       for (int i = 0; i < L; ++i)
@@ -992,7 +996,8 @@ __device__ __forceinline__ float luma_u8(unsigned R, unsigned G, unsigned B) {
 // into shared memory first (three rounds of dependent global loads for the
 // whole CTA instead of a chain per pixel), in bin order, so every pixel scans
 // exactly the list it would scan in global memory.  scratch: shared memory
-// that is free until the staging copies land.  A tile whose bins or
+// that nothing uses until the staged maps are written (the map region).  A
+// tile whose bins or
 // triangles do not fit scans global memory instead (same result).  Writes
 // mu_out and s_mu (NaN outside the triangulation); contains two
 // __syncthreads.
@@ -1075,7 +1080,7 @@ __device__ __forceinline__ bool stage_tile(const SweepArgs& a, const CUtensorMap
   const SmemLayout Ly = sweep_layout(K, a);
   uint8_t* s_img = smem + Ly.raw_img;
   const float* s_p = reinterpret_cast<const float*>(smem + Ly.raw_p);
-  float* s_luma = reinterpret_cast<float*>(smem + Ly.luma);
+  float* s_luma = luma_is_raw(a) ? reinterpret_cast<float*>(s_img) : reinterpret_cast<float*>(smem + Ly.luma);
   uint8_t* s_feat = smem + Ly.feat;
   float2* s_wq = reinterpret_cast<float2*>(smem + Ly.wtab);
   int* s_o = reinterpret_cast<int*>(smem + Ly.otab);
@@ -1113,7 +1118,7 @@ __device__ __forceinline__ bool stage_tile(const SweepArgs& a, const CUtensorMap
     if (tid < 16) s_rcp[tid] = tid >= 2 ? 1.f / static_cast<float>(tid) : 0.f;
   }
   if (a.ptris)  // fused prior, computed while the copies are in flight
-    tile_prior(a, u0, v0, smem + Ly.luma, Ly.feat - Ly.luma, reinterpret_cast<float*>(smem + Ly.mu));
+    tile_prior(a, u0, v0, smem + Ly.feat, Ly.wtab - Ly.feat, reinterpret_cast<float*>(smem + Ly.mu));
   const bool ok = mbar_wait_bounded(bar, phase, a.timeout_ns);
   if (__syncthreads_or(!ok)) {
     if (!ok) {
@@ -1146,9 +1151,8 @@ __device__ __forceinline__ bool stage_tile(const SweepArgs& a, const CUtensorMap
           make_float4(static_cast<float>(w & 0xffu) * sc, static_cast<float>((w >> 8) & 0xffu) * sc,
                       static_cast<float>((w >> 16) & 0xffu) * sc, static_cast<float>(w >> 24) * sc);
     }
-  } else if (a.dtype == 1 && a.C == 1) {
-    for (int q = tid; q < npx / 4; q += nthr)
-      reinterpret_cast<float4*>(s_luma)[q] = reinterpret_cast<const float4*>(s_img)[q];
+  } else if (luma_is_raw(a)) {
+    // nothing to do: s_luma is s_img
   } else {
     for (int i = tid; i < npx; i += nthr) {
       const uint8_t* px = s_img + static_cast<size_t>(i) * a.bpp;
@@ -1490,7 +1494,7 @@ __global__ void __launch_bounds__(sweep_max_threads(K), sweep_min_blocks<K>()) e
 // (head counter in global memory) until it is empty; items of one frame are
 // adjacent, so a CTA restages the frame's tables only when the frame changes.
 // frames[] holds per-frame arguments and TMA descriptors in global memory.
-template <int K, typename TS>
+template <int K, typename TS, int REF>
 __global__ void __launch_bounds__(256, persistent_min_blocks<K>()) em_sweep_persistent(const FrameDesc* frames,
                                                                                 const TileItem* items,
                                                                                 const int* first_item,
@@ -1527,7 +1531,7 @@ __global__ void __launch_bounds__(256, persistent_min_blocks<K>()) em_sweep_pers
       cur = item.frame;
       __syncthreads();
     }
-    if (!sweep_tile<K, TS, -1>(*s_args, &frames[item.frame].img_map, &frames[item.frame].p_map, item.x, item.y,
+    if (!sweep_tile<K, TS, REF>(*s_args, &frames[item.frame].img_map, &frames[item.frame].p_map, item.x, item.y,
                            smem, phase, fresh, true))
       break;  // a bounded wait expired: stop taking work (the status word says why)
     phase ^= 1u;
@@ -1561,28 +1565,48 @@ cudaError_t launch_em_sweep_k(const CUtensorMap& img_map, const CUtensorMap& p_m
                         : launch_em_sweep_ref<K, TS, -1>(img_map, p_map, a, s);
 }
 
-template <int K, typename TS>
-int em_sweep_persistent_occupancy_k(size_t smem, int threads) {
-  cudaFuncSetAttribute(em_sweep_persistent<K, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+template <int K, typename TS, int REF>
+int em_sweep_persistent_occupancy_ref(size_t smem, int threads) {
+  cudaFuncSetAttribute(em_sweep_persistent<K, TS, REF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(smem));
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, em_sweep_persistent<K, TS>, threads, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, em_sweep_persistent<K, TS, REF>, threads, smem) !=
+      cudaSuccess)
     return 0;
   return blocks;
+}
+
+// centred: every frame of the launch has its reference camera in the middle
+// of the array (index K / 2), which the instantiation that knows it uses.
+template <int K, typename TS>
+int em_sweep_persistent_occupancy_k(size_t smem, int threads, int centred) {
+  return centred ? em_sweep_persistent_occupancy_ref<K, TS, K / 2>(smem, threads)
+                 : em_sweep_persistent_occupancy_ref<K, TS, -1>(smem, threads);
+}
+
+template <int K, typename TS, int REF>
+cudaError_t launch_em_sweep_persistent_ref(const FrameDesc* frames, const TileItem* items, const int* first_item,
+                                           const int* n_items, unsigned* head, size_t smem, int grid, int threads,
+                                           cudaStream_t s) {
+  static int configured = -1;
+  if (static_cast<int>(smem) > configured) {
+    cudaError_t e = cudaFuncSetAttribute(em_sweep_persistent<K, TS, REF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    configured = static_cast<int>(smem);
+  }
+  em_sweep_persistent<K, TS, REF><<<grid, threads, smem, s>>>(frames, items, first_item, n_items, head);
+  return cudaGetLastError();
 }
 
 template <int K, typename TS>
 cudaError_t launch_em_sweep_persistent_k(const FrameDesc* frames, const TileItem* items, const int* first_item,
                                          const int* n_items, unsigned* head, size_t smem, int grid, int threads,
-                                         cudaStream_t s) {
-  static int configured = -1;
-  if (static_cast<int>(smem) > configured) {
-    cudaError_t e = cudaFuncSetAttribute(em_sweep_persistent<K, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    configured = static_cast<int>(smem);
-  }
-  em_sweep_persistent<K, TS><<<grid, threads, smem, s>>>(frames, items, first_item, n_items, head);
-  return cudaGetLastError();
+                                         int centred, cudaStream_t s) {
+  return centred ? launch_em_sweep_persistent_ref<K, TS, K / 2>(frames, items, first_item, n_items, head, smem,
+                                                                 grid, threads, s)
+                 : launch_em_sweep_persistent_ref<K, TS, -1>(frames, items, first_item, n_items, head, smem, grid,
+                                                              threads, s);
 }
 
 }  // namespace dev

@@ -23,8 +23,8 @@ namespace lf {
 #define LF_DECL_SWEEP(t, k)                                                                                   \
   cudaError_t launch_em_sweep_##t##_k##k(const CUtensorMap&, const CUtensorMap&, const SweepArgs&, cudaStream_t); \
   cudaError_t launch_em_sweep_persistent_##t##_k##k(const FrameDesc*, const TileItem*, const int*, const int*, \
-                                                    unsigned*, size_t, int, int, cudaStream_t);                 \
-  int em_sweep_persistent_occupancy_##t##_k##k(size_t, int);
+                                                    unsigned*, size_t, int, int, int, cudaStream_t);            \
+  int em_sweep_persistent_occupancy_##t##_k##k(size_t, int, int);
 #define LF_DECL_SWEEPS(t)                                                                                     \
   LF_DECL_SWEEP(t, 1) LF_DECL_SWEEP(t, 2) LF_DECL_SWEEP(t, 3) LF_DECL_SWEEP(t, 4) LF_DECL_SWEEP(t, 5)           \
   LF_DECL_SWEEP(t, 6) LF_DECL_SWEEP(t, 7) LF_DECL_SWEEP(t, 8) LF_DECL_SWEEP(t, 9) LF_DECL_SWEEP(t, 10)          \
@@ -76,12 +76,12 @@ cudaError_t launch_em_sweep(int K, const CUtensorMap& i, const CUtensorMap& p, c
 }
 
 typedef cudaError_t (*PersistentLaunch)(const FrameDesc*, const TileItem*, const int*, const int*, unsigned*,
-                                        size_t, int, int, cudaStream_t);
-typedef int (*PersistentOcc)(size_t, int);
+                                        size_t, int, int, int, cudaStream_t);
+typedef int (*PersistentOcc)(size_t, int, int);
 
 cudaError_t launch_em_sweep_persistent(int K, int prec, const FrameDesc* frames, const TileItem* items,
                                        const int* first_item, const int* n_items, unsigned* head, size_t smem,
-                                       int grid, int threads, cudaStream_t s) {
+                                       int grid, int threads, int centred, cudaStream_t s) {
 #define LF_ROW(t)                                                                                   \
   {launch_em_sweep_persistent_##t##_k1, launch_em_sweep_persistent_##t##_k2,                         \
    launch_em_sweep_persistent_##t##_k3, launch_em_sweep_persistent_##t##_k4,                         \
@@ -92,7 +92,7 @@ cudaError_t launch_em_sweep_persistent(int K, int prec, const FrameDesc* frames,
   static const PersistentLaunch table[3][kMaxCams] = {LF_ROW(f32), LF_ROW(f16), LF_ROW(bf16)};
 #undef LF_ROW
   if (K < 1 || K > kMaxCams || prec < 0 || prec > 2) return cudaErrorInvalidValue;
-  return table[prec][K - 1](frames, items, first_item, n_items, head, smem, grid, threads, s);
+  return table[prec][K - 1](frames, items, first_item, n_items, head, smem, grid, threads, centred, s);
 }
 
 cudaError_t launch_tile_classify(int K, const SweepArgs& a, const float* seg_prior, size_t p_pitch,
@@ -106,7 +106,7 @@ cudaError_t launch_tile_classify(int K, const SweepArgs& a, const float* seg_pri
   return table[K - 1](a, seg_prior, p_pitch, tile_list, n_tiles, s);
 }
 
-int em_sweep_persistent_occupancy(int K, int prec, size_t smem, int threads) {
+int em_sweep_persistent_occupancy(int K, int prec, size_t smem, int threads, int centred) {
 #define LF_ROW(t)                                                                                       \
   {em_sweep_persistent_occupancy_##t##_k1, em_sweep_persistent_occupancy_##t##_k2,                       \
    em_sweep_persistent_occupancy_##t##_k3, em_sweep_persistent_occupancy_##t##_k4,                       \
@@ -117,7 +117,7 @@ int em_sweep_persistent_occupancy(int K, int prec, size_t smem, int threads) {
   static const PersistentOcc table[3][kMaxCams] = {LF_ROW(f32), LF_ROW(f16), LF_ROW(bf16)};
 #undef LF_ROW
   if (K < 1 || K > kMaxCams || prec < 0 || prec > 2) return 0;
-  return table[prec][K - 1](smem, threads);
+  return table[prec][K - 1](smem, threads, centred);
 }
 }  // namespace lf
 

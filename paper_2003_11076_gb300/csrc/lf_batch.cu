@@ -181,6 +181,7 @@ struct lf_batch {
   int graph_captures = 0;
   int tuned = 0;
   size_t grp_smem[kGroups] = {0};  // shared memory of every group launched so far (only grows)
+  bool grp_generic[kGroups] = {};  // a group has held a frame whose reference is not camera K / 2
 };
 
 namespace {
@@ -710,11 +711,12 @@ lf_status lf_batch_run(lf_batch* b) {
   for (const Frame& f : b->frames) {
     const int g = group_of(f.K, f.tile);
     b->grp_smem[g] = std::max(b->grp_smem[g], f.smem);
+    if (f.ref != f.K / 2) b->grp_generic[g] = true;  // sticky, like the sizes
   }
   const size_t* smem = b->grp_smem;
   std::vector<long long> key = {b->p.precision, b->p.median, reinterpret_cast<long long>(b->d_frames),
                                 reinterpret_cast<long long>(b->d_items), reinterpret_cast<long long>(b->d_rows)};
-  for (int g = 0; g < kGroups; ++g) key.push_back(static_cast<long long>(smem[g]));
+  for (int g = 0; g < kGroups; ++g) key.push_back(static_cast<long long>(smem[g]) * 2 + (b->grp_generic[g] ? 1 : 0));
   if (!b->exec || key != b->key) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
@@ -723,7 +725,8 @@ lf_status lf_batch_run(lf_batch* b) {
     for (int g = 0; g < kGroups; ++g)
       if (smem[g])
         grid[g] = b->num_sms * std::max(1, em_sweep_persistent_occupancy(g / kThreadClasses + 1, b->p.precision,
-                                                                         smem[g], kThreadsOf[g % kThreadClasses]));
+                                                                         smem[g], kThreadsOf[g % kThreadClasses],
+                                                                         b->grp_generic[g] ? 0 : 1));
     cudaStream_t c = b->capture;
     LF_CUDA(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal), "graph capture");
     cudaError_t e = cudaSuccess;
@@ -747,7 +750,8 @@ lf_status lf_batch_run(lf_batch* b) {
       }
       chk(launch_em_sweep_persistent(g / kThreadClasses + 1, b->p.precision, b->d_frames, b->d_items,
                                      b->d_counts + kGroups + 1 + g, b->d_counts + g, b->d_heads + g, smem[g],
-                                     grid[g], kThreadsOf[g % kThreadClasses], b->branch[br]));
+                                     grid[g], kThreadsOf[g % kThreadClasses], b->grp_generic[g] ? 0 : 1,
+                                     b->branch[br]));
     }
     for (int br = 0; br < lf_batch::kBranches; ++br) {
       if (!used[br]) continue;

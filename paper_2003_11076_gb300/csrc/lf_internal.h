@@ -225,12 +225,13 @@ cudaError_t launch_refocus_batched(const RefocusArgs* frames, const RowItem* ite
                                    cudaStream_t s);
 cudaError_t launch_median3_batched(const MedianArgs* frames, const RowItem* items, const int* n_items, int grid,
                                    cudaStream_t s);
-// Persistent sweep over the items of one camera count.
+// Persistent sweep over the items of one camera count; centred: every frame
+// of the launch has its reference camera at index K / 2.
 cudaError_t launch_em_sweep_persistent(int K, int prec, const FrameDesc* frames, const TileItem* items,
                                        const int* first_item, const int* n_items, unsigned* head, size_t smem,
-                                       int grid, int threads, cudaStream_t s);
+                                       int grid, int threads, int centred, cudaStream_t s);
 // Resident CTAs per SM of the persistent sweep for this shared-memory size.
-int em_sweep_persistent_occupancy(int K, int prec, size_t smem, int threads);
+int em_sweep_persistent_occupancy(int K, int prec, size_t smem, int threads, int centred);
 
 // Validity of the model and run parameters every entry point shares: finite
 // constants with sigma > 0, gamma >= 0, eps > 0, beta >= 0 and
