@@ -175,9 +175,10 @@ lf_status lf_create(lf_ctx **out, int n_cams, const float *baselines, int H, int
  * Supports the hard EM on float32 maps only (em_mode = LF_EM_HARD,
  * precision = LF_PREC_F32), dynamic_only and median included.
  * Errors: as lf_create, and LF_EINVAL if cameras is NULL or non-finite, no
- * matrix is [I | 0], another em_mode or precision is asked for, or some ray
+ * matrix is [I | 0], another em_mode or precision is asked for, some ray
  * of the frame at a candidate disparity projects behind its camera (Z <= 0
- * at a corner of [0, W-1] x [0, H-1] x [d_min, d_max]).
+ * at a corner of [0, W-1] x [0, H-1] x [d_min, d_max]), or
+ * n_cams * H * W + W + 1 exceeds 2^31 - 1 (the maps are indexed in 32 bits).
  */
 lf_status lf_create_calibrated(lf_ctx **out, int n_cams, const float *cameras, int H, int W,
                                float d_min, float d_max, int D, const lf_params *p);

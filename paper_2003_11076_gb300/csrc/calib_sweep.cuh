@@ -24,33 +24,62 @@ namespace lf {
 namespace dev {
 
 struct CalibRay {
-  float gy, gx, gz, ls, ld;
+  float2 g;  // (Y, Sobel-x / 8) of the ray minus the reference ray's
+  float gz, ls, ld;
 };
+
+// One axis of a ray's bilinear footprint: the texel index i0 of the lower
+// tap and the weight w of the upper one (i0 + 1), for the position
+// p + off clamped to [0, n - 1].  Outside [0, n - 1) the clamped position is
+// a border texel: w = 0, so the upper tap (still read, and finite: the maps
+// carry one zero-filled row past their end) contributes 0 * finite = 0.
+__device__ __forceinline__ int calib_lower_tap(float off, int p, int n, float& w) {
+  const float f = floorf(off);
+  const int fi = max(min(__float2int_rd(off), n), -n - 1);  // saturated far outside; p + fi cannot overflow
+  const int c = p + fi;
+  const bool in = static_cast<unsigned>(c) < static_cast<unsigned>(n - 1);
+  w = in ? off - f : 0.f;
+  return min(max(c, 0), n - 1);
+}
 
 // Bilinear sample of camera k's maps at the ray of pixel (u, v) at disparity
 // d, both coordinates clamped to the image, with the descriptors shifted by
-// the reference ray's.
+// the reference ray's.  The taps are (i0, j0), (i0 + 1, j0), (i0, j0 + 1),
+// (i0 + 1, j0 + 1); the (Y, Sobel-x) and (Sobel-y, log(1 - P)) pairs are
+// interpolated as float32x2 pairs (the same IEEE operations per lane as the
+// scalar form).
 __device__ __forceinline__ CalibRay calib_sample(const CalibArgs& a, int k, const CalibPix& cp, int u, int v,
-                                                 float d, float cy, float cx, float cz) {
-  const CalibTaps t = calib_taps(a.cam[k], cp, u, v, d, a.W, a.H);
-  const int i0 = t.i0, i1 = t.i1, j0 = t.j0, j1 = t.j1;
-  const float wx = t.wx, wy = t.wy;
-  const size_t plane = static_cast<size_t>(k) * a.H * a.W;
-  const size_t r0 = plane + static_cast<size_t>(j0) * a.W, r1 = plane + static_cast<size_t>(j1) * a.W;
-  const float4 p00 = __ldg(a.fa + r0 + i0), p01 = __ldg(a.fa + r0 + i1);
-  const float4 p10 = __ldg(a.fa + r1 + i0), p11 = __ldg(a.fa + r1 + i1);
-  const float q00 = __ldg(a.fb + r0 + i0), q01 = __ldg(a.fb + r0 + i1);
-  const float q10 = __ldg(a.fb + r1 + i0), q11 = __ldg(a.fb + r1 + i1);
-  auto bl = [&](float v00, float v01, float v10, float v11) {
-    const float top = fmaf(wx, v01 - v00, v00), bot = fmaf(wx, v11 - v10, v10);
-    return fmaf(wy, bot - top, top);
+                                                 float d, float2 cyx, float cz) {
+  const float* M = a.cam[k];
+  const float Z = fmaf(d, M[11], cp.az);
+  const float X = fmaf(d, fmaf(-static_cast<float>(u), M[11], M[3]), cp.ax);
+  const float Y = fmaf(d, fmaf(-static_cast<float>(v), M[11], M[7]), cp.ay);
+  const float iz = 1.f / Z;
+  float wx, wy;
+  const int i0 = calib_lower_tap(X * iz, u, a.W, wx);
+  const int j0 = calib_lower_tap(Y * iz, v, a.H, wy);
+  const int o = (k * a.H + j0) * a.W + i0;  // < K H W: checked when the context is created
+  const float4* f0 = a.fa + o;
+  const float4* f1 = f0 + a.W;
+  const float* b0 = a.fb + o;
+  const float* b1 = b0 + a.W;
+  const float4 p00 = __ldg(f0), p01 = __ldg(f0 + 1), p10 = __ldg(f1), p11 = __ldg(f1 + 1);
+  const float q00 = __ldg(b0), q01 = __ldg(b0 + 1), q10 = __ldg(b1), q11 = __ldg(b1 + 1);
+  const float2 wx2 = make_float2(wx, wx), wy2 = make_float2(wy, wy);
+  auto bl2 = [&](float2 v00, float2 v01, float2 v10, float2 v11) {
+    const float2 top = ffma2(wx2, fsub2(v01, v00), v00), bot = ffma2(wx2, fsub2(v11, v10), v10);
+    return ffma2(wy2, fsub2(bot, top), top);
   };
+  const float2 lo = bl2(make_float2(p00.x, p00.y), make_float2(p01.x, p01.y), make_float2(p10.x, p10.y),
+                        make_float2(p11.x, p11.y));
+  const float2 hi = bl2(make_float2(p00.z, p00.w), make_float2(p01.z, p01.w), make_float2(p10.z, p10.w),
+                        make_float2(p11.z, p11.w));
+  const float top = fmaf(wx, q01 - q00, q00), bot = fmaf(wx, q11 - q10, q10);
   CalibRay r;
-  r.gy = bl(p00.x, p01.x, p10.x, p11.x) - cy;
-  r.gx = bl(p00.y, p01.y, p10.y, p11.y) - cx;
-  r.gz = bl(p00.z, p01.z, p10.z, p11.z) - cz;
-  r.ls = bl(p00.w, p01.w, p10.w, p11.w);
-  r.ld = bl(q00, q01, q10, q11);
+  r.g = fsub2(lo, cyx);
+  r.gz = hi.x - cz;
+  r.ls = hi.y;
+  r.ld = fmaf(wy, bot - top, top);
   return r;
 }
 
@@ -60,7 +89,7 @@ __device__ __forceinline__ CalibRay calib_sample(const CalibArgs& a, int k, cons
 // candidate is evaluated from scratch, so a range computes the same
 // objectives as the whole sweep.
 template <int K, bool INIT>
-__device__ __forceinline__ int calib_m_step(const CalibArgs& a, const CalibPix (&A)[K], int u, int v, float cy, float cx,
+__device__ __forceinline__ int calib_m_step(const CalibArgs& a, const CalibPix (&A)[K], int u, int v, float2 cyx,
                                             float cz, float mu, bool inside, unsigned S, int j0, int j1,
                                             float* best_out) {
   float best = -INFINITY;
@@ -74,22 +103,24 @@ __device__ __forceinline__ int calib_m_step(const CalibArgs& a, const CalibPix (
     const float pr = pr_next;
     pr_next = prior_at(min(j + 1, j1 - 1));  // the next candidate's prior, off this one's critical path
     const float d = __ldg(a.dval + j);
-    float sy = 0.f, sx = 0.f, sz = 0.f, q = 0.f, seg = 0.f;
+    float2 syx = make_float2(0.f, 0.f);
+    float sz = 0.f, q = 0.f, seg = 0.f;
     int n = 0;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if (!INIT && !(S >> k & 1u)) {  // a dynamic ray contributes its log p(dynamic) only
         if (a.mseg) {
-          const CalibRay r = calib_sample(a, k, A[k], u, v, d, cy, cx, cz);
+          const CalibRay r = calib_sample(a, k, A[k], u, v, d, cyx, cz);
           seg += r.ld;
         }
         continue;
       }
-      const CalibRay r = calib_sample(a, k, A[k], u, v, d, cy, cx, cz);
+      const CalibRay r = calib_sample(a, k, A[k], u, v, d, cyx, cz);
       const bool stat = INIT ? (r.ld - r.ls < a.log_thr) : true;
       if (stat) {
-        sy += r.gy; sx += r.gx; sz += r.gz;
-        q = fmaf(r.gy, r.gy, q); q = fmaf(r.gx, r.gx, q); q = fmaf(r.gz, r.gz, q);
+        syx = fadd2(syx, r.g);
+        sz += r.gz;
+        q = fmaf(r.g.x, r.g.x, q); q = fmaf(r.g.y, r.g.y, q); q = fmaf(r.gz, r.gz, q);
         seg += r.ls;
         ++n;
       } else {
@@ -97,7 +128,7 @@ __device__ __forceinline__ int calib_m_step(const CalibArgs& a, const CalibPix (
       }
     }
     const float rn = n >= 2 ? 1.f / static_cast<float>(n) : 0.f;
-    const float ss = fmaf(sz, sz, fmaf(sx, sx, sy * sy));
+    const float ss = fmaf(sz, sz, fmaf(syx.y, syx.y, syx.x * syx.x));
     const float var = fmaf(-ss, rn, q) * rn;
     float J = a.mseg ? seg : 0.f;
     if (inside) J += pr;
@@ -109,15 +140,15 @@ __device__ __forceinline__ int calib_m_step(const CalibArgs& a, const CalibPix (
 }
 
 template <int K>
-__device__ __forceinline__ void calib_rays(const CalibArgs& a, const CalibPix (&A)[K], int u, int v, int j, float cy, float cx,
-                                           float cz, Rays& r) {
+__device__ __forceinline__ void calib_rays(const CalibArgs& a, const CalibPix (&A)[K], int u, int v, int j,
+                                           float2 cyx, float cz, Rays& r) {
   const float d = __ldg(a.dval + j);
   r.base = 0.f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const CalibRay s = calib_sample(a, k, A[k], u, v, d, cy, cx, cz);
-    r.gy[k] = s.gy; r.gx[k] = s.gx; r.gz[k] = s.gz;
-    r.qk[k] = fmaf(s.gz, s.gz, fmaf(s.gx, s.gx, s.gy * s.gy));
+    const CalibRay s = calib_sample(a, k, A[k], u, v, d, cyx, cz);
+    r.gy[k] = s.g.x; r.gx[k] = s.g.y; r.gz[k] = s.gz;
+    r.qk[k] = fmaf(s.gz, s.gz, fmaf(s.g.y, s.g.y, s.g.x * s.g.x));
     r.ak[k] = s.ls - s.ld;
     r.base += s.ld;
   }
@@ -130,7 +161,7 @@ __device__ __forceinline__ void calib_rays(const CalibArgs& a, const CalibPix (&
 // CTA has threads (lanes split the candidates, then the label vectors; same
 // tie rules, same bits).
 template <int K>
-__global__ void __launch_bounds__(256) calib_sweep_kernel(const __grid_constant__ CalibArgs a) {
+__global__ void __launch_bounds__(256, K <= 5 ? 3 : 2) calib_sweep_kernel(const __grid_constant__ CalibArgs a) {
   __shared__ float s_rcp[16];  // 1/n for the E-step's subset sizes (0 for n < 2: Var = 0)
   __shared__ float s_emax[256];
   __shared__ int16_t s_jb[256], s_list[256];
@@ -171,7 +202,8 @@ __global__ void __launch_bounds__(256) calib_sweep_kernel(const __grid_constant_
   struct Px {
     CalibPix A[K];
     int u, v;
-    float mu, cy, cx, cz;
+    float2 cyx;
+    float mu, cz;
     bool inside;
   };
   auto load = [&](int p) {
@@ -185,7 +217,8 @@ __global__ void __launch_bounds__(256) calib_sweep_kernel(const __grid_constant_
     x.mu = a.mu[pix];
     x.inside = !isnan(x.mu);
     const float4 fr = a.fa[static_cast<size_t>(a.ref) * a.H * a.W + pix];
-    x.cy = fr.x; x.cx = fr.y; x.cz = fr.z;
+    x.cyx = make_float2(fr.x, fr.y);
+    x.cz = fr.z;
     return x;
   };
   unsigned long long executed = 0;
@@ -196,9 +229,9 @@ __global__ void __launch_bounds__(256) calib_sweep_kernel(const __grid_constant_
     if (tid < n) {
       const int p = s_list[tid];
       const Px x = load(p);
-      const int jb = calib_m_step<K, true>(a, x.A, x.u, x.v, x.cy, x.cx, x.cz, x.mu, x.inside, 0u, 0, a.D, nullptr);
+      const int jb = calib_m_step<K, true>(a, x.A, x.u, x.v, x.cyx, x.cz, x.mu, x.inside, 0u, 0, a.D, nullptr);
       Rays rays;
-      calib_rays<K>(a, x.A, x.u, x.v, jb, x.cy, x.cx, x.cz, rays);
+      calib_rays<K>(a, x.A, x.u, x.v, jb, x.cyx, x.cz, rays);
       unsigned S = 0;
       float emax = 0.f;
       enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
@@ -228,10 +261,10 @@ __global__ void __launch_bounds__(256) calib_sweep_kernel(const __grid_constant_
         const int per = (a.D + G - 1) / G, j0 = min(gl * per, a.D), j1 = min(j0 + per, a.D);
         float jbest;
         unsigned jb = static_cast<unsigned>(
-            calib_m_step<K, false>(a, x.A, x.u, x.v, x.cy, x.cx, x.cz, x.mu, x.inside, Sp, j0, j1, &jbest));
+            calib_m_step<K, false>(a, x.A, x.u, x.v, x.cyx, x.cz, x.mu, x.inside, Sp, j0, j1, &jbest));
         group_argmax(jbest, jb, G);
         Rays rays;
-        calib_rays<K>(a, x.A, x.u, x.v, static_cast<int>(jb), x.cy, x.cx, x.cz, rays);
+        calib_rays<K>(a, x.A, x.u, x.v, static_cast<int>(jb), x.cyx, x.cz, rays);
         unsigned S = 0;
         float emax = 0.f;
         enumerate_group<K>(rays, s_rcp, a.beta, gl, G, S, emax);
@@ -246,9 +279,9 @@ __global__ void __launch_bounds__(256) calib_sweep_kernel(const __grid_constant_
       const int p = s_list[tid];
       const Px x = load(p);
       const unsigned Sp = s_S[p];
-      const int jb = calib_m_step<K, false>(a, x.A, x.u, x.v, x.cy, x.cx, x.cz, x.mu, x.inside, Sp, 0, a.D, nullptr);
+      const int jb = calib_m_step<K, false>(a, x.A, x.u, x.v, x.cyx, x.cz, x.mu, x.inside, Sp, 0, a.D, nullptr);
       Rays rays;
-      calib_rays<K>(a, x.A, x.u, x.v, jb, x.cy, x.cx, x.cz, rays);
+      calib_rays<K>(a, x.A, x.u, x.v, jb, x.cyx, x.cz, rays);
       unsigned S = 0;
       float emax = 0.f;
       enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
@@ -270,7 +303,7 @@ __global__ void __launch_bounds__(256) calib_sweep_kernel(const __grid_constant_
     if (a.post) {
       const Px x = load(tid);
       Rays rays;
-      calib_rays<K>(a, x.A, x.u, x.v, jb, x.cy, x.cx, x.cz, rays);
+      calib_rays<K>(a, x.A, x.u, x.v, jb, x.cyx, x.cz, rays);
       float post[K];
       unsigned dummy;
       float dummyf;

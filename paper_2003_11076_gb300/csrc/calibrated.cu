@@ -53,6 +53,15 @@ __device__ __forceinline__ float luma(const CalibArgs& a, int k, int v, int u) {
 __global__ void calib_features_kernel(const CalibArgs a) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= a.W) return;
+  if (blockIdx.y == 0) {  // the zero row past the end that the sweep's upper taps may read at the border
+    const size_t end = static_cast<size_t>(a.K) * a.H * a.W;
+    a.fa[end + u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    a.fb[end + u] = 0.f;
+    if (u == 0) {
+      a.fa[end + a.W] = make_float4(0.f, 0.f, 0.f, 0.f);
+      a.fb[end + a.W] = 0.f;
+    }
+  }
   for (int row = blockIdx.y; row < a.K * a.H; row += gridDim.y) {  // row = k * H + v
     const int k = row / a.H, v = row - k * a.H;
     const int vm = max(v - 1, 0), vp = min(v + 1, a.H - 1), um = max(u - 1, 0), up = min(u + 1, a.W - 1);

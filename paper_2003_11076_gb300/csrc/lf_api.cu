@@ -560,6 +560,8 @@ lf_status create_ctx(lf_ctx** out, int n_cams, const float* baselines, const flo
       }
     }
     if (ref < 0) return fail(LF_EINVAL, "no camera matrix equals [I | 0] (reference camera)");
+    if (static_cast<int64_t>(n_cams) * H * W + W + 1 > INT32_MAX)
+      return fail(LF_EINVAL, "calibrated arrays: n_cams * H * W must stay below 2^31");
     zero_b.assign(n_cams, 0.f);
     baselines = zero_b.data();
   } else {
@@ -992,7 +994,7 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
   }
   LF_CUDA(mark(1), "event");
   if (c->calibrated) {  // Eq. 1 with per-camera homographies: maps in HBM, gathered by the sweep
-    const size_t KHW = HW * c->K;
+    const size_t KHW = HW * c->K + c->W + 1;  // + one zero row (and texel) past the end
     if ((s = grow(&c->d_fa, &c->fa_cap, KHW, "descriptor maps")) != LF_OK) return s;
     if ((s = grow(&c->d_fb, &c->fb_cap, KHW, "descriptor maps")) != LF_OK) return s;
     CalibArgs g{};

@@ -130,7 +130,7 @@ def _rect_cams(b):
 
 @pytest.mark.parametrize("case,expect", [
     ("no_reference", "[I | 0]"), ("nan", "non-finite"), ("behind", "behind the camera"),
-    ("soft", "hard EM"), ("f16", "hard EM"),
+    ("soft", "hard EM"), ("f16", "hard EM"), ("huge", "2^31"),
 ])
 def test_create_calibrated_rejects_invalid_arguments(lib, case, expect):
     """Argument checks of lf_create_calibrated run before any device work."""
@@ -147,8 +147,11 @@ def test_create_calibrated_rejects_invalid_arguments(lib, case, expect):
         p = lf.default_params(em_mode=lf.LF_EM_SOFT)
     elif case == "f16":
         p = lf.default_params(precision=lf.LF_PREC_F16)
+    H = W = 16
+    if case == "huge":  # 3 x 27000 x 27000 texels: past 32-bit map indices
+        H = W = 27000
     h = ctypes.c_void_p()
-    s = lib.lf_create_calibrated(ctypes.byref(h), 3, np.ascontiguousarray(cams).ctypes.data, 16, 16, 0.0, 7.0, 8,
+    s = lib.lf_create_calibrated(ctypes.byref(h), 3, np.ascontiguousarray(cams).ctypes.data, H, W, 0.0, 7.0, 8,
                                  ctypes.byref(p))
     assert s == lf.LF_EINVAL
     assert not h.value
