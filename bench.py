@@ -44,23 +44,30 @@ SWEEP_SRC = os.path.join(ROOT, "paper_2003_11076_gb300", "csrc", "em_sweep.cuh")
 
 def sweep_ops_per_pixel_iter(K: int, D: int) -> int:
     """Algorithmic FP32 lane-operations of one pixel-iteration of the fused
-    sweep: per (candidate, camera) 4 interpolations + 3 sums + 3 squares + 1
-    segmentation add = 11; per candidate 12 (|sum|^2, variance, prior
-    exp/log, objective, compare); E-step 13 per label vector (5 subset sums,
-    variance, objective, compare)."""
+    sweep without candidate pruning: per (candidate, camera) 4 interpolations
+    + 3 sums + 3 squares + 1 segmentation add = 11; per candidate 12 (|sum|^2,
+    variance, prior exp/log, objective, compare); E-step 13 per label vector
+    (5 subset sums, variance, objective, compare)."""
     return D * (11 * K + 12) + (1 << K) * 13
 
 
-def scope_ops(pix_iters: float, static_samples: float, K: int, D: int) -> float:
+def tight_ops(pairs: float, pix_iters: float, K: int) -> float:
+    """The same op model over the (pixel, candidate) objectives the M-steps
+    evaluated and the E-steps run."""
+    return pairs * (11 * K + 12) + pix_iters * (1 << K) * 13
+
+
+def scope_ops(samples: float, static_samples: float, pairs: float, pix_iters: float, K: int) -> float:
     """Algorithmic FP32/INT lane-operations of the hard EM by the op model of
     the hot-path scope table: a static ray sample costs 29 (8 interpolations
     of 2, 9 for the shifted sums and squares, 1 segmentation add, 3 for the
     address and weight), a dynamic one 4, each (pixel, candidate) 12 more
     (variance, prior, objective, compare) and each E-step label vector 20.
-    pix_iters: executed pixel-iterations; static_samples: the executed ray
-    samples whose ray was static in its M-step (counted by the kernel)."""
-    samples = pix_iters * K * D
-    return 29.0 * static_samples + 4.0 * (samples - static_samples) + 12.0 * D * pix_iters + \
+    samples: ray samples the M-steps evaluated (K per (pixel, candidate));
+    static_samples: those whose ray was static in its M-step; pairs: the
+    (pixel, candidate) objectives; pix_iters: the E-steps (all counted by the
+    kernel)."""
+    return 29.0 * static_samples + 4.0 * (samples - static_samples) + 12.0 * pairs + \
         20.0 * (1 << K) * pix_iters
 
 
@@ -267,7 +274,7 @@ def run_batch_workload(args, world, rank, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     prec = {"f32": 0, "f16": 1, "bf16": 2}[args.precision]
-    params = lf.default_params(precision=prec)
+    params = lf.default_params(precision=prec, prune=args.prune)
     inputs = [(torch.from_numpy(f.images).to(dev), torch.from_numpy(f.seg_prior).to(dev)) for f in frames]
     outs = [lf.device_outputs(f.K, f.H, f.W, f.C, dev) for f in frames]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -322,6 +329,7 @@ def run_batch_workload(args, world, rank, local):
                 "config": {"workload": f"batch of {n} random frames: 320x240..1280x1024, K in 3/5/7/9, "
                                        "baselines 0.05-0.25 apart, D in 32/64/128, 5 EM iterations",
                            "staged_maps": args.precision, "autotune": bool(args.autotune),
+                           "candidate_pruning": bool(args.prune),
                            "ray_samples_per_s": nominal * steps / t_batch,
                            "per_frame_launch_frames_per_s": n * steps / t_plain,
                            "batched_over_per_frame": t_plain / t_batch,
@@ -433,6 +441,7 @@ def main():
     ap.add_argument("--rates", default="50,100,200,400", help="serve: arrival rates (requests/s)")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals per rate")
     ap.add_argument("--autotune", type=int, default=1, help="batch: tile shapes chosen by timing")
+    ap.add_argument("--prune", type=int, default=1, help="street / batch: exact candidate pruning (0: full sweeps)")
     ap.add_argument("--em-mode", default="hard", choices=["hard", "soft", "joint"],
                     help="street: the paper's hard EM, soft EM or joint MAP over (d, S)")
     ap.add_argument("--dynamic-only", action="store_true",
@@ -463,7 +472,7 @@ def main():
     s = scenes.street_rgb(rank, calibrated=args.calibrated)
     mode = {"hard": 0, "soft": 1, "joint": 2}[args.em_mode]
     params = lf.default_params(precision={"f32": 0, "f16": 1, "bf16": 2}[args.precision], em_mode=mode,
-                               dynamic_only=int(args.dynamic_only))
+                               dynamic_only=int(args.dynamic_only), prune=args.prune)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     img_d = torch.from_numpy(s.images).to(dev)
@@ -606,14 +615,17 @@ def main():
             ops_desc = {"ops_per_pixel_iteration": calib_ops_per_pixel_iter(K, D)}
         elif mode == 0:
             static_mean = st["executed_static_ray_samples"] / st["runs"]
-            ops = scope_ops(pix_iters, static_mean, K, D)
-            tight = pix_iters * sweep_ops_per_pixel_iter(K, D)
-            ops_desc = {"ops_model": "scope-table op model: 29 per static ray sample, 4 per dynamic, 12 per "
-                                     "(pixel, candidate), 20 per E-step label vector",
+            pix_iters = st["executed_pixel_iterations"] / st["runs"]
+            pairs = exec_mean / K
+            ops = scope_ops(exec_mean, static_mean, pairs, pix_iters, K)
+            tight = tight_ops(pairs, pix_iters, K)
+            ops_desc = {"ops_model": "scope-table op model over the evaluated work: 29 per static ray sample, 4 per "
+                                     "dynamic, 12 per (pixel, candidate) objective, 20 per E-step label vector",
                         "ops_per_frame": ops, "static_ray_share": static_mean / exec_mean,
+                        "pixel_iterations_per_frame": pix_iters,
+                        "candidates_per_pixel_iteration": pairs / pix_iters,
                         "frac_tight_model": None, "tight_model": "11 per ray sample, 12 per (pixel, candidate), "
-                                                                 "13 per label vector",
-                        "ops_per_pixel_iteration_tight": sweep_ops_per_pixel_iter(K, D)}
+                                                                 "13 per label vector"}
         elif mode == 1:  # every swept pixel's first iteration is the EM's first M-step
             first = min(pix_iters, H * W * (float(np.mean(s.seg_prior[int(np.argmin(np.abs(s.baselines)))] >= 0.7)) if args.dynamic_only else 1))
             ops = first * sweep_ops_per_pixel_iter(K, D) + (pix_iters - first) * soft_ops_per_pixel_iter(K, D)
@@ -648,6 +660,7 @@ def main():
                        + (", support points detected on the device every step" if args.detect_support else ""),
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "staged_maps": args.precision,
+                       "candidate_pruning": bool(args.prune) and mode == 0 and not args.calibrated,
                        "frames_per_s": args.steps * world / total_s,
                        "executed_ray_samples_per_frame": exec_mean,
                        "executed_ray_samples_per_s": exec_mean * args.steps * world / total_s,

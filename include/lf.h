@@ -98,7 +98,7 @@ typedef enum lf_em_mode {
  * for the threshold (0.7); the defaults of lf_default_params are
  * beta = 200, gamma = 0.1, sigma = 2, seg_threshold = 0.7, eps = 1e-4,
  * mstep_seg_term = 1, median = 0, precision = LF_PREC_F32, early_exit = 1,
- * dynamic_only = 0, em_mode = LF_EM_HARD.
+ * dynamic_only = 0, em_mode = LF_EM_HARD, prune = 1.
  */
 typedef struct lf_params {
     float beta;          /* weight of the static rays' descriptor variance */
@@ -119,6 +119,15 @@ typedef struct lf_params {
                             lf_run_em for what the other pixels receive */
     int em_mode;         /* lf_em_mode: the paper's hard EM, or one of the two
                             variants of its formulation (see lf_em_mode) */
+    int prune;           /* 1: each M-step of the hard EM (Sec. III-C arg-max
+                            over the D candidates) evaluates only the
+                            candidates whose upper bound -- disparity prior
+                            plus the largest segmentation term, the variance
+                            term being <= 0 -- reaches an objective already
+                            computed; the arg-max, and so every output, is
+                            identical to the full sweep's.  0: full sweeps.
+                            Rectified arrays (lf_create, the batch API and
+                            lf_run_em_static); the other modes ignore it. */
 } lf_params;
 
 /* Statistics accumulated over the lf_run_em calls since the previous
@@ -126,7 +135,9 @@ typedef struct lf_params {
 typedef struct lf_stats {
     uint64_t runs;                 /* lf_run_em calls covered */
     uint64_t nominal_ray_samples;  /* H * W * K * D * iters of the last run */
-    uint64_t executed_ray_samples; /* sum over the runs: pixel-sweeps run x K x D */
+    uint64_t executed_ray_samples; /* sum over the runs: ray samples the M-steps
+                                      evaluated, K per (pixel, candidate) objective
+                                      (K x D per pixel-iteration without pruning) */
     int halo_left, halo_right;     /* staged column halo, pixels */
     int tile_rows, tile_cols;      /* sweep tile shape */
     int kernels_launched;          /* kernels one lf_run_em enqueues */
@@ -140,6 +151,10 @@ typedef struct lf_stats {
     uint64_t executed_static_ray_samples; /* of executed_ray_samples, those whose ray was
                                       labelled static in its M-step (hard EM on a
                                       rectified array; 0 for the other modes) */
+    uint64_t executed_pixel_iterations; /* sum over the runs: (pixel, EM iteration)
+                                      pairs run, i.e. E-steps (after the exact
+                                      early exit; hard EM on a rectified array,
+                                      0 for the other modes) */
 } lf_stats;
 
 /* Fill *p with the documented defaults. */

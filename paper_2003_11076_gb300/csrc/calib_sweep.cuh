@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(256, K <= 5 ? 3 : 2) calib_sweep_kernel(const 
       for (int k = 0; k < K; ++k) a.post[k * static_cast<size_t>(a.H) * a.W + pix] = post[k];
     }
   }
-  if (tid == 0 && executed) atomicAdd(a.counter, executed);
+  if (tid == 0 && executed) atomicAdd(a.counter, executed * a.D);  // every candidate of every sweep
 }
 
 template <int K>

@@ -245,20 +245,43 @@ __host__ __device__ inline size_t align_up(size_t x, size_t n) { return (x + n -
 
 // Shared-memory carve-up, identical on host (size) and device (offsets).
 struct SmemLayout {
-  size_t raw_img, raw_p, luma, feat, wtab, otab, chg, dval, rcp, mu, pix, wcnt, bar, total;
+  size_t raw_img, raw_p, luma, feat, wtab, otab, chg, dval, rcp, mu, pix, wcnt, sortc, bar, total;
 };
 
 // Per-pixel EM state of one tile, kept in shared memory between iterations
 // so that the unconverged pixels can be regrouped into dense warps.
 struct PixelState {
   int16_t* list;    // pixel indices (tile order) to process in the current pass
+  int16_t* list2;   // the next pass's (the two alternate)
   uint16_t* S;      // current labels
   uint16_t* S0;     // first-iteration labels when they do not depend on d
   int16_t* jb;      // current arg-max candidate
   float* emax;      // objective of the current labels at jb
+  float* seg_ub;    // upper bound of the segmentation term (candidate pruning)
+  int16_t* lo;      // candidates the next M-step evaluates: lo .. hi
+  int16_t* hi;
   uint8_t* fixed0;  // S0 valid
   uint8_t* conv;    // reached its fixed point
 };
+constexpr int kPixelStateBytes = 24;
+// The per-pixel state of a tile of P pixels at b (kPixelStateBytes * P bytes).
+__device__ __forceinline__ PixelState pixel_state(uint8_t* b, int P) {
+  PixelState ps;
+  ps.emax = reinterpret_cast<float*>(b);
+  ps.seg_ub = ps.emax + P;
+  ps.S = reinterpret_cast<uint16_t*>(ps.seg_ub + P);
+  ps.S0 = ps.S + P;
+  ps.jb = reinterpret_cast<int16_t*>(ps.S0 + P);
+  ps.list = ps.jb + P;
+  ps.list2 = ps.list + P;
+  ps.lo = ps.list2 + P;
+  ps.hi = ps.lo + P;
+  ps.fixed0 = reinterpret_cast<uint8_t*>(ps.hi + P);
+  ps.conv = ps.fixed0 + P;
+  return ps;
+}
+// Counters of the CTA's counting sort (sort_pixels): 128 keys per warp.
+constexpr int kSortKeys = 128;
 
 // Fixed head of the shared memory: the CTA's mbarrier, then (persistent
 // kernel) the current frame's arguments, then the item index.  Everything
@@ -299,9 +322,11 @@ __host__ __device__ inline SmemLayout sweep_layout(int K, const SweepArgs& a) {
   L.mu = o;  // fused prior: the tile's prior centres
   o = align_up(o + static_cast<size_t>(a.TR) * a.TW * 4, 16);
   L.pix = o;
-  o = align_up(o + static_cast<size_t>(a.TR) * a.TW * 14, 16);
-  L.wcnt = o;
-  o = align_up(o + 32 * 4, 16);
+  o = align_up(o + static_cast<size_t>(a.TR) * a.TW * kPixelStateBytes, 16);
+  L.wcnt = o;  // 32 ints of per-warp scratch, then the tile's two statistics counters
+  o = align_up(o + 34 * 4, 16);
+  L.sortc = o;
+  o = align_up(o + static_cast<size_t>(kSortKeys) * ((a.TR * a.TW + 31) / 32) * 2, 16);
   L.bar = kSmemBar;
   L.total = o;
   return L;
@@ -360,11 +385,18 @@ __device__ __forceinline__ void load_weights(const float2* s_wq, int KP, int j, 
 // REF >= 0: camera REF is the reference (known at compile time).  Its ray
 // samples the pixel itself at every candidate (weight 0, shifted descriptor
 // exactly 0), so only its label test and log prior are accumulated.
+// Candidates j0 <= j < j1 (lowest j wins ties; *best_out = the maximum, may
+// be NULL).  Every camera's taps are loaded at j0, so a range that starts
+// mid-sweep computes each candidate's objective exactly as the whole sweep
+// does.  In both M-steps the variance is clamped at 0 (it can come out a few
+// units of rounding below 0 when the static rays agree), so that every
+// objective is at most its prior and segmentation terms: the bound the
+// candidate pruning (prune_range) rests on.
 template <int K, typename TS, int REF>
-__device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>& st, const float2* s_wq,
-                                           const int* s_o, const unsigned* s_chg, const float* s_d,
-                                           const float* s_rcp, float cy, float cx, float cz, float mu,
-                                           bool inside, unsigned* n_static) {
+__device__ __forceinline__ int m_step_init_range(const SweepArgs& a, const Staged<TS>& st, const float2* s_wq,
+                                                 const int* s_o, const unsigned* s_chg, const float* s_d,
+                                                 const float* s_rcp, float cy, float cx, float cz, float mu,
+                                                 bool inside, int j0, int j1, float* best_out, unsigned* n_static) {
   using Tx = Texels<TS>;
   // per camera: p1 = (Y, X) at floor(x) minus the reference's, d1 the slope
   // to the next tap; p2 = (Zs minus the reference's, ld), d2; t0, dt the
@@ -376,9 +408,10 @@ __device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>&
   // outside the triangulation mu is NaN and the prior is uniform: the prior
   // is then evaluated at a finite centre and weighted by pin = 0
   const float lin = a.mseg ? 1.f : 0.f, pin = inside ? 1.f : 0.f, mu_in = inside ? mu : 0.f;
+  const int js = j0 < j1 ? j0 : 0;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const int c = chk(st.cbase + s_o[k], 0, a.SW - 2, a.status);
+    const int c = chk(st.cbase + s_o[chk(js * a.KP + k, 0, a.D * a.KP - 1, a.status)], 0, a.SW - 2, a.status);
     const uint8_t* R = st.row(k);
     float2 yx0, zd0, yx1, zd1;
     Tx::quad(R, SWp, c, yx0, zd0);
@@ -392,7 +425,7 @@ __device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>&
     dt[k] = T1 - T0;
   }
   float best = -INFINITY, nsum = 0.f;  // nsum: static rays over the candidates (an exact integer)
-  int jb = 0;
+  int jb = j0;
   // log prior in base-2 units (the objective takes it times ln 2 * pin):
   // log2(gamma + 2^(k2 t^2)) with k2 = -log2(e) / (2 sigma^2)
   const float k2 = -a.inv2s2 * 1.4426950408889634f, pin_ln2 = pin * 0.6931471805599453f;
@@ -400,12 +433,12 @@ __device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>&
     const float t = s_d[j] - mu_in;
     return lg2_approx(a.gamma + ex2_approx(t * t * k2));
   };
-  float pr_next = prior_at(0);
-  for (int j = 0; j < a.D; ++j) {
+  float pr_next = prior_at(js);
+  for (int j = j0; j < j1; ++j) {
     float2 w[K];
     load_weights<K>(s_wq, a.KP, j, w);
-    const int jn = min(j + 1, a.D - 1);
-    const unsigned chn = j + 1 < a.D ? s_chg[jn] : 0u;  // taps the next candidate reloads
+    const int jn = min(j + 1, j1 - 1);
+    const unsigned chn = j + 1 < j1 ? s_chg[jn] : 0u;  // taps the next candidate reloads
     const float pr = pr_next;
     pr_next = prior_at(jn);  // the next candidate's prior, off this one's critical path
     float2 syx = make_float2(0.f, 0.f), szl = make_float2(0.f, 0.f), qq = make_float2(0.f, 0.f);
@@ -438,7 +471,7 @@ __device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>&
     const float q = qq.x + qq.y + qz;
     const float2 sq = fmul2(syx, syx);
     const float ss = fmaf(szl.x, szl.x, sq.x + sq.y);
-    const float var = fmaf(-ss, rn, q) * rn;
+    const float var = fmaxf(fmaf(-ss, rn, q) * rn, 0.f);
     const float J = fmaf(-a.beta, var, fmaf(pin_ln2, pr, lin * (szl.y - nt.y)));
     if (J > best) { best = J; jb = j; }
     if (chn) {  // same for every pixel: warp-uniform branch
@@ -460,8 +493,18 @@ __device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>&
       }
     }
   }
-  *n_static = static_cast<unsigned>(nsum);
+  if (n_static) *n_static = static_cast<unsigned>(nsum);
+  if (best_out) *best_out = best;
   return jb;
+}
+
+template <int K, typename TS, int REF>
+__device__ __forceinline__ int m_step_init(const SweepArgs& a, const Staged<TS>& st, const float2* s_wq,
+                                           const int* s_o, const unsigned* s_chg, const float* s_d,
+                                           const float* s_rcp, float cy, float cx, float cz, float mu,
+                                           bool inside, unsigned* n_static) {
+  return m_step_init_range<K, TS, REF>(a, st, s_wq, s_o, s_chg, s_d, s_rcp, cy, cx, cz, mu, inside, 0, a.D, nullptr,
+                                       n_static);
 }
 
 // Camera k's fixed-label terms from its taps at staged column c (the M-step
@@ -565,7 +608,7 @@ __device__ __forceinline__ int m_step_fixed_range(const SweepArgs& a, const Stag
     const float q = QQ.x + QQ.y;
     const float2 sq = fmul2(A1, A1);
     const float ss = fmaf(A2.x, A2.x, sq.x + sq.y);
-    const float var = fmaf(-ss, rn, q) * rn;
+    const float var = fmaxf(fmaf(-ss, rn, q) * rn, 0.f);
     const float J = fmaf(-a.beta, var, fmaf(pin_ln2, pr, A2.y));
     if (J > best) { best = J; jb = j; }
     if (chn) {  // same for every pixel: warp-uniform branch
@@ -603,28 +646,150 @@ __device__ __forceinline__ int m_step_fixed(const SweepArgs& a, const Staged<TS>
 
 // First-iteration labels of one pixel when they are the same for every
 // candidate: bit k of *mask is camera k's label (static) and the return value
-// says whether every camera's T texels stay clear of the threshold.
+// says whether every camera's T texels stay clear of the threshold.  The same
+// scan over each camera's sample range gives *seg_max = sum over cameras of
+// the largest max(log p(static), log p(dynamic)) among the texels its rays
+// interpolate, an upper bound (up to rounding) of the segmentation term of
+// any label vector at any candidate; max(ls, ld) is formed as ls + max(T, 0)
+// from the stored T = ld - ls.
 template <int K, typename TS>
 __device__ __forceinline__ bool constant_initial_labels(const SweepArgs& a, const Staged<TS>& st,
-                                                        unsigned* mask) {
+                                                        unsigned* mask, float* seg_max) {
   bool all = true;
   unsigned m = 0;
+  float segsum = 0.f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const uint8_t* R = st.row(k);
-    float lo = INFINITY, hi = -INFINITY;
+    float lo = INFINITY, hi = -INFINITY, smax = -INFINITY;
     const int c_lo = chk(st.cbase + a.omin[k], 0, a.SW - 1, a.status);
     const int c_hi = chk(st.cbase + a.omax[k] + 1, 0, a.SW - 1, a.status);
     for (int c = c_lo; c <= c_hi; ++c) {
       const float z = Texels<TS>::t(R, st.SWp, c);
       lo = fminf(lo, z);
       hi = fmaxf(hi, z);
+      smax = fmaxf(smax, Texels<TS>::ls(R, st.SWp, c) + fmaxf(z, 0.f));
     }
     if (hi < a.log_thr - kThresholdMargin) m |= 1u << k;
     else if (!(lo >= a.log_thr + kThresholdMargin)) all = false;
+    segsum += smax;
   }
   *mask = m;
+  *seg_max = segsum;
   return all;
+}
+
+// ------------------------------------------------------ candidate pruning
+// With the variance clamped at 0 and beta >= 0, the objective of candidate j
+// (either M-step) is at most  pin * prior(j) + seg(j)  (rounding is
+// monotone), prior the log prior (evaluated in base 2 and scaled by ln 2) and
+// seg(j) at most the pixel's seg_max.  Outside the triangulation (pin = 0)
+// nothing is pruned.  Given J* = the objective of one candidate j*, computed by the same
+// code the M-step runs, every candidate whose bound is below J* is beaten by
+// j* and cannot be the arg-max (nor tie with it); the arg-max over the
+// remaining candidates, lowest index on ties, is the arg-max over all D.
+// The prior is unimodal in |d - mu|, so the candidates that remain form one
+// interval around mu: with the prior in natural-log units, log(gamma +
+// exp(-(d_j - mu)^2 / (2 sigma^2))) >= th  <=>  (d_j - mu)^2 <= -2 sigma^2
+// log(e^th - gamma).  Slacks make the interval wider, never narrower, than
+// the exact one: th is lowered by 1e-3 (the hardware exponential and
+// logarithm err by about 1e-6 relative), J* by 2^-18 (1 + |J*|), the radius is
+// widened by 0.1 % + 1e-3, the index range by one candidate on each side, and
+// seg_max carries a margin for the rounding of the segmentation sums
+// (a.seg_margin, set by the host).  j* itself is always kept.
+__device__ __forceinline__ int nearest_candidate(const SweepArgs& a, float mu) {
+  const float f = fminf(fmaxf((mu - a.d0) * a.inv_step, 0.f), static_cast<float>(a.D - 1));
+  return static_cast<int>(rintf(f));
+}
+
+// The interval in natural-log units (the objective's prior term is
+// log(gamma + exp(-(d - mu)^2 / (2 sigma^2)))); d_j = d0 + j / inv_step.
+__device__ __forceinline__ void prune_interval(float mu, float Js, float seg_ub, float gamma, float inv2s2, float d0,
+                                               float inv_step, int D, int js, int& lo, int& hi) {
+  lo = 0;
+  hi = D - 1;
+  if (!(fabsf(Js) <= 3.0e38f)) return;  // no finite objective to bound against
+  const float th = Js - (1.f + fabsf(Js)) * 0x1p-18f - seg_ub - 1e-3f;
+  const float A = expf(th) - gamma;
+  if (!(A > 0.f && A < 1.f)) return;  // every candidate's prior reaches th (A >= 1 cannot happen)
+  const float r = sqrtf(-logf(A) / inv2s2) * 1.001f + 1e-3f;
+  const float flo = fmaxf((mu - r - d0) * inv_step, -2.f);
+  const float fhi = fminf((mu + r - d0) * inv_step, static_cast<float>(D) + 1.f);
+  lo = min(max(static_cast<int>(floorf(flo)) - 1, 0), js);
+  hi = max(min(static_cast<int>(ceilf(fhi)) + 1, D - 1), js);
+}
+
+__device__ __forceinline__ void prune_range(const SweepArgs& a, float mu, float Js, float seg_ub, int js, int& lo,
+                                            int& hi) {
+  prune_interval(mu, Js, seg_ub, a.gamma, a.inv2s2, a.d0, a.inv_step, a.D, js, lo, hi);
+}
+
+// Stable counting sort of the tile pixels (thread tid = tile pixel) whose
+// pred is set, by key in [0, NB): list[0 .. n) = their tile indices in (key,
+// tid) order; returns n (the same in every thread).  s_cnt: NB x warps
+// 16-bit counters, zero on entry and left zero on exit (each thread clears
+// the counters it scanned once the list is written; the next call comes
+// after another __syncthreads); s_tot: one int per warp.  Four
+// __syncthreads.
+__device__ __forceinline__ int sort_pixels(bool pred, int key, int NB, int16_t* list, uint16_t* s_cnt,
+                                           int* s_tot) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int ncnt = NB * nw, per = (ncnt + blockDim.x - 1) / blockDim.x;
+  const unsigned act = __ballot_sync(0xffffffffu, pred);
+  int rank = 0;
+  if (pred) {
+    const unsigned peers = __match_any_sync(act, key);
+    rank = __popc(peers & ((1u << lane) - 1u));
+    if (rank == 0) s_cnt[key * nw + warp] = static_cast<uint16_t>(__popc(peers));
+  }
+  __syncthreads();
+  // exclusive scan over the counters in (key, warp) order; thread tid owns
+  // counters [tid * per, (tid + 1) * per)
+  int loc = 0;
+  for (int q = 0; q < per; ++q) {
+    const int i = tid * per + q;
+    if (i < ncnt) loc += s_cnt[i];
+  }
+  int incl = loc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_tot[warp] = incl;
+  __syncthreads();
+  int run = incl - loc, total = 0;
+  for (int w = 0; w < nw; ++w) {
+    const int t = s_tot[w];
+    run += w < warp ? t : 0;
+    total += t;
+  }
+  for (int q = 0; q < per; ++q) {
+    const int i = tid * per + q;
+    if (i < ncnt) {
+      const int c = s_cnt[i];
+      s_cnt[i] = static_cast<uint16_t>(run);
+      run += c;
+    }
+  }
+  __syncthreads();
+  if (pred) list[s_cnt[key * nw + warp] + rank] = static_cast<int16_t>(tid);
+  __syncthreads();
+  for (int q = 0; q < per; ++q) {
+    const int i = tid * per + q;
+    if (i < ncnt) s_cnt[i] = 0;
+  }
+  return total;
+}
+
+// Sort keys of the bound intervals: pixels whose interval covers more than a
+// quarter of the candidates come after the others, each class in 32 buckets
+// of the interval's first candidate (NB = 64); in the first M-step the
+// pixels whose labels do not depend on the candidate come first (NB = 128).
+constexpr int kLoBuckets = 32;
+__device__ __forceinline__ int interval_key(int lo, int hi, int D) {
+  const int wide = (hi - lo + 1) * 4 > D ? 1 : 0;
+  return wide * kLoBuckets + (lo * kLoBuckets) / D;
 }
 
 // ---------------------------------------------------------------- E-step
@@ -950,7 +1115,7 @@ __device__ __forceinline__ PixelCtx<TS> load_pixel(const SweepArgs& a, const uin
 // Stable CTA-wide compaction: the threads (tile pixel p = threadIdx.x) with
 // pred set write p to list[base + rank]; returns how many did (every thread
 // gets the same count).  Contains two __syncthreads.
-__device__ __forceinline__ int compact(bool pred, int16_t* list, int base, int* s_wcnt) {
+__device__ __forceinline__ int compact_value(bool pred, int value, int16_t* list, int base, int* s_wcnt) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const unsigned b = __ballot_sync(0xffffffffu, pred);
   if (lane == 0) s_wcnt[warp] = __popc(b);
@@ -961,9 +1126,12 @@ __device__ __forceinline__ int compact(bool pred, int16_t* list, int base, int* 
     off += w < warp ? c : 0;
     total += c;
   }
-  if (pred) list[base + off + __popc(b & ((1u << lane) - 1u))] = static_cast<int16_t>(tid);
+  if (pred) list[base + off + __popc(b & ((1u << lane) - 1u))] = static_cast<int16_t>(value);
   __syncthreads();
   return total;
+}
+__device__ __forceinline__ int compact(bool pred, int16_t* list, int base, int* s_wcnt) {
+  return compact_value(pred, static_cast<int>(threadIdx.x), list, base, s_wcnt);
 }
 
 // ---------------------------------------------------------------- kernel
@@ -1228,8 +1396,71 @@ __device__ __forceinline__ bool stage_tile(const SweepArgs& a, const CUtensorMap
       Texels<TS>::store(F, a.SWp, c, a11, gx * 0.125f, gy * 0.125f, ls, ld);
     }
   }
+  {  // the counting sort's counters start at zero (sort_pixels leaves them
+     // so), and so do the tile's statistics counters
+    uint32_t* z = reinterpret_cast<uint32_t*>(smem + Ly.sortc);
+    const int nz = kSortKeys * (nthr >> 5) / 2;
+    for (int i = tid; i < nz; i += nthr) z[i] = 0u;
+    if (tid < 2) reinterpret_cast<unsigned*>(smem + Ly.wcnt)[32 + tid] = 0u;
+  }
   __syncthreads();
   return true;
+}
+
+__device__ __forceinline__ float element_value(uint8_t x) { return static_cast<float>(x); }
+__device__ __forceinline__ float element_value(float x) { return x; }
+__device__ __forceinline__ float element_value(__half x) { return __half2float(x); }
+__device__ __forceinline__ float element_value(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// Eq. 2 for one pixel from the tile's staged raw rows (staged row `row` of
+// every camera, first staged column cs): the mean of the static rays' samples
+// at its final candidate jb (linear interpolation, column clamped), or the
+// reference pixel when no ray is static; elements of type E, C = 1 or 3.
+// Same operations in the same order as the standalone refocus kernel.
+template <int K, typename E>
+__device__ __forceinline__ void refocus_staged(const SweepArgs& a, const uint8_t* s_img, int row, int cs, int u, int jb,
+                                               unsigned S, const int* s_o, const float2* s_wq, float* out) {
+  const E* img = reinterpret_cast<const E*>(s_img);
+  const int C = a.C, RW = a.RW, LR = a.TR + 2;
+  const float scale = a.dtype == 0 ? (1.f / 255.f) : 1.f;
+  if (S == 0u) {
+    const E* px = img + (static_cast<size_t>(a.ref * LR + row) * RW + chk(u - cs, 0, RW - 1, a.status)) * C;
+    out[0] = element_value(px[0]) * scale;
+    if (C > 1) {
+      out[1] = element_value(px[1]) * scale;
+      out[2] = element_value(px[2]) * scale;
+    }
+    return;
+  }
+  float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
+  int n = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (!(S >> k & 1u)) continue;
+    ++n;
+    const int o = s_o[jb * a.KP + k];
+    const float w = s_wq[jb * a.KP + k].x;
+    const int x0 = min(max(u + o, 0), a.W - 1), x1 = min(max(u + o + 1, 0), a.W - 1);
+    const E* r = img + static_cast<size_t>(k * LR + row) * RW * C;
+    const E* p0 = r + chk(x0 - cs, 0, RW - 1, a.status) * C;
+    const E* p1 = r + chk(x1 - cs, 0, RW - 1, a.status) * C;
+    {
+      const float g0 = element_value(p0[0]), g1 = element_value(p1[0]);
+      acc0 += fmaf(w, g1 - g0, g0) * scale;
+    }
+    if (C > 1) {
+      const float g0 = element_value(p0[1]), g1 = element_value(p1[1]);
+      acc1 += fmaf(w, g1 - g0, g0) * scale;
+      const float h0 = element_value(p0[2]), h1 = element_value(p1[2]);
+      acc2 += fmaf(w, h1 - h0, h0) * scale;
+    }
+  }
+  const float inv = 1.f / static_cast<float>(n);
+  out[0] = acc0 * inv;
+  if (C > 1) {
+    out[1] = acc1 * inv;
+    out[2] = acc2 * inv;
+  }
 }
 
 // One tile (tile_x, tile_y) of one frame: stage, run the EM, write the
@@ -1258,24 +1489,19 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
   const int cam_stride = a.TR * a.SWp * texel_bytes(a.prec);
   const float* s_mu = a.ptris ? reinterpret_cast<const float*>(smem + Ly.mu) : nullptr;
 
-  // ---- 3-5. per-pixel EM.  The pixels still iterating are regrouped into
-  // dense warps before every pass (exact per-pixel early exit), and in the
-  // first pass the pixels whose first-iteration labels do not depend on the
-  // candidate come first, so that their warps run the ordinary M-step.
-  PixelState ps;
-  {
-    uint8_t* b = smem + Ly.pix;
-    const int P = a.TR * a.TW;
-    ps.emax = reinterpret_cast<float*>(b);
-    ps.S = reinterpret_cast<uint16_t*>(b + 4 * P);
-    ps.S0 = ps.S + P;
-    ps.jb = reinterpret_cast<int16_t*>(ps.S0 + P);
-    ps.list = ps.jb + P;
-    ps.fixed0 = reinterpret_cast<uint8_t*>(ps.list + P);
-    ps.conv = ps.fixed0 + P;
-  }
+  // ---- 3-5. per-pixel EM.  Before every M-step the pixels still iterating
+  // are sorted into dense warps by the interval of candidates their bound
+  // leaves (exact candidate pruning, see prune_range; exact per-pixel early
+  // exit); a warp sweeps the union of its pixels' intervals.  Each pixel's
+  // first M-step uses the fixed-label form when its first-iteration labels do
+  // not depend on the candidate, else the per-candidate form, whatever its
+  // warp-mates use; those pixels are sorted first, so at most one warp mixes
+  // the two forms.
+  PixelState ps = pixel_state(smem + Ly.pix, a.TR * a.TW);
   int* s_wcnt = reinterpret_cast<int*>(smem + Ly.wcnt);
+  uint16_t* s_sortc = reinterpret_cast<uint16_t*>(smem + Ly.sortc);
   const int warp = tid >> 5;
+  const float lin = a.mseg ? 1.f : 0.f;
 
   bool my_valid = (u0 + tid % a.TW < W) && (v0 + tid / a.TW < H);
   if (a.dyn_only && my_valid) {  // Sec. III-F: only the reference pixels flagged dynamic
@@ -1292,18 +1518,57 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
       my_valid = false;
     }
   }
-  {
+  unsigned my_pairs = 0;   // (pixel, candidate) objectives this thread evaluated for the statistics
+  unsigned my_static = 0;  // static ray samples among them
+  int key = 0;
+  {  // first-iteration labels, the segmentation bound and the first M-step's interval
     const PixelCtx<TS> me = load_pixel<TS>(a, s_feat, u0, v0, cam_stride, tid, s_mu);
     unsigned S0 = 0;
-    const bool f0 = me.valid && constant_initial_labels<K, TS>(a, me.st, &S0);
+    float seg_max = 0.f;
+    const bool f0 = me.valid && constant_initial_labels<K, TS>(a, me.st, &S0, &seg_max);
+    const float seg_ub = fmaf(lin, seg_max, a.seg_margin);
+    int lo = 0, hi = a.D - 1;
+    if (a.prune && my_valid && me.inside) {
+      const int js = nearest_candidate(a, me.mu);
+      float Js;
+      if (f0)
+        m_step_fixed_range<K, TS, REF>(a, me.st, s_wq, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu, true, S0,
+                                       js, js + 1, &Js);
+      else
+        m_step_init_range<K, TS, REF>(a, me.st, s_wq, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu, true, js,
+                                      js + 1, &Js, nullptr);
+      prune_range(a, me.mu, Js, seg_ub, js, lo, hi);
+      ++my_pairs;
+    }
     ps.fixed0[tid] = f0;
     ps.S0[tid] = static_cast<uint16_t>(S0);
     ps.conv[tid] = 0;
+    ps.seg_ub[tid] = seg_ub;
+    ps.lo[tid] = static_cast<int16_t>(lo);
+    ps.hi[tid] = static_cast<int16_t>(hi);
+    key = (f0 ? 0 : 2 * kLoBuckets) + interval_key(lo, hi, a.D);
   }
-  const int nfast = compact(my_valid && ps.fixed0[tid], ps.list, 0, s_wcnt);
-  const int nact = nfast + compact(my_valid && !ps.fixed0[tid], ps.list, nfast, s_wcnt);
+  const int nact = sort_pixels(my_valid, key, kSortKeys, ps.list, s_sortc, s_wcnt);
   unsigned long long executed = static_cast<unsigned long long>(nact);
-  unsigned my_static = 0;  // static ray samples of the M-steps this thread ran (for the statistics)
+
+  // After an E-step of a pixel that goes on: the interval of its next M-step
+  // (fixed labels S), bounded by the objective at the current candidate,
+  // stored for tile pixel p when `write` (the caller has stored its other
+  // results first, so that they are not live across the evaluation).
+  auto bound_next = [&](const PixelCtx<TS>& c, int p, unsigned S, int jb, bool write) {
+    int lo = 0, hi = a.D - 1;
+    if (a.prune && c.inside) {
+      float Js;
+      m_step_fixed_range<K, TS, REF>(a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, true, S, jb,
+                                     jb + 1, &Js);
+      prune_range(a, c.mu, Js, ps.seg_ub[p], jb, lo, hi);
+      if (write) ++my_pairs;
+    }
+    if (write) {
+      ps.lo[p] = static_cast<int16_t>(lo);
+      ps.hi[p] = static_cast<int16_t>(hi);
+    }
+  };
 
   // t = 1
   if (warp * 32 < nact) {
@@ -1312,31 +1577,49 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     const PixelCtx<TS> c = load_pixel<TS>(a, s_feat, u0, v0, cam_stride, p, s_mu);
     const bool f0 = ps.fixed0[p];
     const unsigned S0 = ps.S0[p];
-    const bool fast = __all_sync(0xffffffffu, f0);
-    unsigned ns = __popc(S0) * static_cast<unsigned>(a.D);
-    const int jb = fast ? m_step_fixed<K, TS, REF>(a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, S0)
-                        : m_step_init<K, TS, REF>(a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, &ns);
-    if (active) my_static += ns;
+    const int LO = __reduce_min_sync(0xffffffffu, ps.lo[p]), HI = __reduce_max_sync(0xffffffffu, ps.hi[p]);
+    unsigned ns = __popc(S0) * static_cast<unsigned>(HI - LO + 1);
+    const int jb = f0 ? m_step_fixed_range<K, TS, REF>(a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu,
+                                                       c.inside, S0, LO, HI + 1, nullptr)
+                      : m_step_init_range<K, TS, REF>(a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu,
+                                                      c.inside, LO, HI + 1, nullptr, &ns);
+    if (active) {
+      my_pairs += static_cast<unsigned>(HI - LO + 1);
+      my_static += ns;
+    }
     Rays rays;
     sample_rays<K, TS>(a, c.st, s_wq, s_o, jb, c.cy, c.cx, c.cz, rays);
     unsigned S = 0;
     float emax = 0.f;
     enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
+    // the second M-step would repeat the first one exactly
+    const bool conv = a.early_exit && f0 && S == S0;
     if (active) {
       ps.jb[p] = static_cast<int16_t>(jb);
       ps.S[p] = static_cast<uint16_t>(S);
       ps.emax[p] = emax;
-      // the second M-step would repeat the first one exactly
-      ps.conv[p] = a.early_exit && fast && S == S0;
+      ps.conv[p] = conv;
     }
+    if (!conv && a.iters >= 2) bound_next(c, p, S, jb, active);
   }
   __syncthreads();
   // t >= 2: only the pixels not yet at their fixed point; when fewer than a
   // CTA's threads are left, groups of lanes per pixel
+  // (the pixels still iterating keep the first pass's order: pixels of
+  // similar candidate intervals stay together without sorting again)
   const int nwarps = blockDim.x >> 5, lane = tid & 31;
+  int16_t* list = ps.list;
+  int16_t* list_next = ps.list2;
+  int n_prev = nact;
   for (int t = 2; t <= a.iters; ++t) {
-    const int n = compact(my_valid && !ps.conv[tid], ps.list, 0, s_wcnt);
+    const int p_prev = tid < n_prev ? list[tid] : 0;
+    const bool pend = tid < n_prev && !ps.conv[p_prev];
+    const int n = compact_value(pend, p_prev, list_next, 0, s_wcnt);
     if (n == 0) break;
+    int16_t* tmp = list;
+    list = list_next;
+    list_next = tmp;
+    n_prev = n;
     executed += static_cast<unsigned long long>(n);
     // lanes per pixel: the largest power of two that still fits every
     // remaining pixel into one round of the CTA's warps
@@ -1347,45 +1630,58 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
       const int slot = warp * gpw + lane / G;  // this group's pixel among the n
       if (warp * gpw < n) {
         const bool act = slot < n;
-        const int p = ps.list[act ? slot : n - 1];  // idle groups repeat the last pixel
+        const int p = list[act ? slot : n - 1];  // idle groups repeat the last pixel
         const PixelCtx<TS> c = load_pixel<TS>(a, s_feat, u0, v0, cam_stride, p, s_mu);
         const unsigned Sp = ps.S[p];
-        const int per = (a.D + G - 1) / G, j0 = min(gl * per, a.D), j1 = min(j0 + per, a.D);
+        const int plo = ps.lo[p], phi = ps.hi[p];
+        const int per = (phi - plo + G) / G, j0 = min(plo + gl * per, phi + 1), j1 = min(j0 + per, phi + 1);
         float jbest;
         unsigned jb = static_cast<unsigned>(m_step_fixed_range<K, TS, REF>(
             a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, Sp, j0, j1, &jbest));
-        if (act) my_static += __popc(Sp) * static_cast<unsigned>(j1 - j0);
+        if (act) {
+          my_static += __popc(Sp) * static_cast<unsigned>(j1 - j0);
+          my_pairs += static_cast<unsigned>(j1 - j0);
+        }
         group_argmax(jbest, jb, G);
         Rays rays;
         sample_rays<K, TS>(a, c.st, s_wq, s_o, static_cast<int>(jb), c.cy, c.cx, c.cz, rays);
         unsigned S = 0;
         float emax = 0.f;
         enumerate_group<K>(rays, s_rcp, a.beta, gl, G, S, emax);
+        const bool conv = a.early_exit && S == Sp;
         if (act && gl == 0) {
           ps.jb[p] = static_cast<int16_t>(jb);
           ps.S[p] = static_cast<uint16_t>(S);
           ps.emax[p] = emax;
-          ps.conv[p] = a.early_exit && S == Sp;
+          ps.conv[p] = conv;
         }
+        if (!conv && t < a.iters) bound_next(c, p, S, static_cast<int>(jb), act && gl == 0);
       }
     } else if (warp * 32 < n) {
       const bool active = tid < n;
-      const int p = ps.list[active ? tid : n - 1];
+      const int p = list[active ? tid : n - 1];
       const PixelCtx<TS> c = load_pixel<TS>(a, s_feat, u0, v0, cam_stride, p, s_mu);
       const unsigned Sp = ps.S[p];
-      const int jb = m_step_fixed<K, TS, REF>(a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, Sp);
-      if (active) my_static += __popc(Sp) * static_cast<unsigned>(a.D);
+      const int LO = __reduce_min_sync(0xffffffffu, ps.lo[p]), HI = __reduce_max_sync(0xffffffffu, ps.hi[p]);
+      const int jb = m_step_fixed_range<K, TS, REF>(a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu,
+                                                    c.inside, Sp, LO, HI + 1, nullptr);
+      if (active) {
+        my_pairs += static_cast<unsigned>(HI - LO + 1);
+        my_static += __popc(Sp) * static_cast<unsigned>(HI - LO + 1);
+      }
       Rays rays;
       sample_rays<K, TS>(a, c.st, s_wq, s_o, jb, c.cy, c.cx, c.cz, rays);
       unsigned S = 0;
       float emax = 0.f;
       enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
+      const bool conv = a.early_exit && S == Sp;
       if (active) {
         ps.jb[p] = static_cast<int16_t>(jb);
         ps.S[p] = static_cast<uint16_t>(S);
         ps.emax[p] = emax;
-        ps.conv[p] = a.early_exit && S == Sp;
+        ps.conv[p] = conv;
       }
+      if (!conv && t < a.iters) bound_next(c, p, S, jb, active);
     }
     __syncthreads();
   }
@@ -1411,44 +1707,34 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
       for (int k = 0; k < K; ++k) a.post[k * HW + pix] = post[k];
     }
     if (a.refocus_out) {  // Eq. 2 from the staged raw rows (they hold every tap of every candidate)
-      const uint8_t* s_img = smem + Ly.raw_img;
-      const size_t LR = static_cast<size_t>(a.TR) + 2;
       const int row = me.v - v0 + 1;  // staged rows start one above the tile
-      const float scale = a.dtype == 0 ? (1.f / 255.f) : 1.f;
       float* out = a.refocus_out + pix * a.C;
-      auto px = [&](int k, int x, int c) {
-        return pixel_element(s_img + ((k * LR + row) * RW + chk(x - cs, 0, RW - 1, a.status)) * a.bpp, c, a.dtype);
-      };
-      if (S == 0u) {
-        for (int c = 0; c < a.C; ++c) out[c] = px(a.ref, me.u, c) * scale;
-      } else {
-        float acc[3] = {0.f, 0.f, 0.f};
-        int n = 0;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          if (!(S >> k & 1u)) continue;
-          ++n;
-          const int o = s_o[jb * a.KP + k];
-          const float w = s_wq[jb * a.KP + k].x;
-          const int x0 = min(max(me.u + o, 0), W - 1), x1 = min(max(me.u + o + 1, 0), W - 1);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            if (c >= a.C) break;
-            const float g0 = px(k, x0, c), g1 = px(k, x1, c);
-            acc[c] += fmaf(w, g1 - g0, g0) * scale;
-          }
-        }
-        const float inv = 1.f / static_cast<float>(n);
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          if (c < a.C) out[c] = acc[c] * inv;
-      }
+      const uint8_t* s_img = smem + Ly.raw_img;
+      if (a.dtype == 0)
+        refocus_staged<K, uint8_t>(a, s_img, row, cs, me.u, jb, S, s_o, s_wq, out);
+      else if (a.dtype == 1)
+        refocus_staged<K, float>(a, s_img, row, cs, me.u, jb, S, s_o, s_wq, out);
+      else if (a.dtype == 2)
+        refocus_staged<K, __half>(a, s_img, row, cs, me.u, jb, S, s_o, s_wq, out);
+      else
+        refocus_staged<K, __nv_bfloat16>(a, s_img, row, cs, me.u, jb, S, s_o, s_wq, out);
     }
   }
-  if (tid == 0) atomicAdd(a.counter, executed);
-  if (a.static_counter) {
-    const unsigned wsum = __reduce_add_sync(0xffffffffu, my_static);
-    if (lane == 0 && wsum) atomicAdd(a.static_counter, static_cast<unsigned long long>(wsum));
+  {  // statistics: warp sums into the tile's counters, one global atomic each per tile
+    unsigned* s_stat = reinterpret_cast<unsigned*>(smem + Ly.wcnt) + 32;
+    const unsigned wp = __reduce_add_sync(0xffffffffu, my_pairs);
+    const unsigned ws = __reduce_add_sync(0xffffffffu, my_static);
+    if (lane == 0) {
+      atomicAdd_block(s_stat, wp);
+      atomicAdd_block(s_stat + 1, ws);
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned* s_stat = reinterpret_cast<const unsigned*>(smem + Ly.wcnt) + 32;
+    if (a.sweeps) atomicAdd(a.sweeps, executed);
+    atomicAdd(a.counter, static_cast<unsigned long long>(s_stat[0]));
+    if (a.static_counter) atomicAdd(a.static_counter, static_cast<unsigned long long>(s_stat[1]));
   }
   __syncthreads();
   return true;

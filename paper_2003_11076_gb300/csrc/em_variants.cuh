@@ -236,20 +236,9 @@ __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorM
       }
     }
     const unsigned warp_sum = __reduce_add_sync(0xffffffffu, executed);
-    if (lane == 0 && warp_sum) atomicAdd(a.counter, static_cast<unsigned long long>(warp_sum));
+    if (lane == 0 && warp_sum) atomicAdd(a.counter, static_cast<unsigned long long>(warp_sum) * a.D);
   } else {
-    PixelState ps;
-    {
-      uint8_t* b = smem + Ly.pix;
-      const int P = a.TR * a.TW;
-      ps.emax = reinterpret_cast<float*>(b);
-      ps.S = reinterpret_cast<uint16_t*>(b + 4 * P);
-      ps.S0 = ps.S + P;
-      ps.jb = reinterpret_cast<int16_t*>(ps.S0 + P);
-      ps.list = ps.jb + P;
-      ps.fixed0 = reinterpret_cast<uint8_t*>(ps.list + P);
-      ps.conv = ps.fixed0 + P;
-    }
+    PixelState ps = pixel_state(smem + Ly.pix, a.TR * a.TW);
     int* s_wcnt = reinterpret_cast<int*>(smem + Ly.wcnt);
     float* s_soft = reinterpret_cast<float*>(smem + soft_state_offset(K, a));
     constexpr int NS = kSoftStateFloats<K>;
@@ -276,7 +265,8 @@ __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorM
     // t = 1: the EM's first M-step (labels thresholded per candidate)
     if (run) {
       unsigned S0 = 0, ns = 0;
-      const bool f0 = constant_initial_labels<K, float>(a, me.st, &S0);
+      float seg_max;
+      const bool f0 = constant_initial_labels<K, float>(a, me.st, &S0, &seg_max);
       const int jb = f0 ? m_step_fixed<K, float, -1>(a, me.st, s_wq, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu,
                                                  me.inside, S0)
                         : m_step_init<K, float, -1>(a, me.st, s_wq, s_o, s_chg, s_d, s_rcp, me.cy, me.cx, me.cz, me.mu,
@@ -355,7 +345,7 @@ __device__ __forceinline__ void variant_tile(const SweepArgs& a, const CUtensorM
         for (int k = 0; k < K; ++k) a.post[k * HW + pix] = st[k];
       }
     }
-    if (tid == 0 && executed) atomicAdd(a.counter, executed);
+    if (tid == 0 && executed) atomicAdd(a.counter, executed * a.D);  // every candidate of every sweep
   }
 }
 

@@ -507,6 +507,7 @@ void lf_default_params(lf_params* p) {
   p->early_exit = 1;
   p->dynamic_only = 0;
   p->em_mode = LF_EM_HARD;
+  p->prune = 1;
 }
 
 const char* lf_last_error(const lf_ctx*) { return g_err.c_str(); }
@@ -639,11 +640,11 @@ lf_status create_ctx(lf_ctx** out, int n_cams, const float* baselines, const flo
   cap = 0;
   if ((s = grow(&c->d_mu, &cap, static_cast<size_t>(H) * W, "prior")) != LF_OK) return bail(s);
   cap = 0;
-  if ((s = grow(&c->d_counter, &cap, 2, "counter")) != LF_OK) return bail(s);  // executed sweeps, static samples
+  if ((s = grow(&c->d_counter, &cap, 3, "counter")) != LF_OK) return bail(s);  // objectives, static samples, sweeps
   cap = 0;
   if ((s = grow(&c->d_status, &cap, 1, "status")) != LF_OK) return bail(s);
   cudaError_t e;
-  if ((e = cudaMemset(c->d_counter, 0, 2 * sizeof(unsigned long long))) != cudaSuccess ||
+  if ((e = cudaMemset(c->d_counter, 0, 3 * sizeof(unsigned long long))) != cudaSuccess ||
       (e = cudaMemset(c->d_status, 0, sizeof(unsigned))) != cudaSuccess)
     return bail(cuda_fail(e, "counter init"));
   if ((e = cudaMemcpy(c->d_wtab, c->wtab.data(), c->wtab.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -1057,7 +1058,9 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
     a.omax[k] = hi;
   }
   a.d_idx = didx; a.d_out = dout; a.labels = lab; a.post = post;
-  a.counter = c->d_counter; a.static_counter = c->d_counter + 1; a.status = c->d_status; a.timeout_ns = kTimeoutNs;
+  a.counter = c->d_counter; a.static_counter = c->d_counter + 1; a.sweeps = c->d_counter + 2;
+  a.status = c->d_status; a.timeout_ns = kTimeoutNs;
+  set_pruning(a, c->p.prune, c->K, c->dval.data(), c->D, c->p.eps);
   if (fused) {
     a.refocus_out = refo_stage;
     a.img = c->img;
@@ -1211,12 +1214,13 @@ lf_status lf_get_stats(lf_ctx* c, lf_stats* out) {
   g_err.clear();
   if (!c || !out) return fail(LF_EINVAL, "NULL argument");
   LF_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
-  unsigned long long n[2] = {0, 0};
+  unsigned long long n[3] = {0, 0, 0};
   LF_CUDA(cudaMemcpy(n, c->d_counter, sizeof(n), cudaMemcpyDeviceToHost), "counter read");
   LF_CUDA(cudaMemset(c->d_counter, 0, sizeof(n)), "counter reset");
   c->stats.runs = c->runs;
-  c->stats.executed_ray_samples = static_cast<uint64_t>(n[0]) * c->K * c->D;
+  c->stats.executed_ray_samples = static_cast<uint64_t>(n[0]) * c->K;
   c->stats.executed_static_ray_samples = static_cast<uint64_t>(n[1]);
+  c->stats.executed_pixel_iterations = static_cast<uint64_t>(n[2]);
   float* ms[4] = {&c->stats.ms_prior, &c->stats.ms_sweep, &c->stats.ms_refocus, &c->stats.ms_median};
   for (int i = 0; i < 4; ++i) {
     double acc = 0.0;

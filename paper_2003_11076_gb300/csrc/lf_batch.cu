@@ -161,7 +161,7 @@ struct lf_batch {
   RowItem* d_rows = nullptr;
   size_t rows_cap = 0;
   int* d_counts = nullptr;  // [kGroups] items per launch group, [1] rows, [kGroups] first item
-  unsigned long long* d_fcount = nullptr;  // per frame: pixel-sweeps executed
+  unsigned long long* d_fcount = nullptr;  // per frame: (pixel, candidate) objectives evaluated
   unsigned* d_heads = nullptr;
   unsigned long long* d_counter = nullptr;
   unsigned* d_status = nullptr;
@@ -673,6 +673,7 @@ lf_status lf_batch_run(lf_batch* b) {
     a.labels = lab;
     a.post = f.post;
     a.counter = b->d_fcount + i;
+    set_pruning(a, b->p.prune, f.K, f.dval.data(), f.D, b->p.eps);
     a.status = b->d_status;
     a.timeout_ns = 2000000000ull;
     fd[i].args = a;
@@ -809,7 +810,7 @@ lf_status lf_batch_get_stats(lf_batch* b, lf_stats* out) {
     LF_CUDA(cudaMemcpy(n.data(), b->d_fcount, n.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost),
             "counter read");
     for (size_t i = 0; i < n.size(); ++i)
-      r.executed_ray_samples += n[i] * static_cast<uint64_t>(b->frames[i].K) * b->frames[i].D;
+      r.executed_ray_samples += n[i] * static_cast<uint64_t>(b->frames[i].K);
     float* ms[4] = {&r.ms_prior, &r.ms_sweep, &r.ms_refocus, &r.ms_median};
     for (int i = 0; i < 4; ++i) LF_CUDA(cudaEventElapsedTime(ms[i], b->ev[i], b->ev[i + 1]), "event time");
     r.kernels_launched = 2 + b->p.median;

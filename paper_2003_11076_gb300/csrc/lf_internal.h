@@ -1,6 +1,8 @@
 // Internal declarations shared by the host library and its kernels.
 #pragma once
 
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <string>
 #include <cuda.h>
@@ -86,11 +88,36 @@ struct SweepArgs {
   float* d_out;                    // [H][W] or null
   uint16_t* labels;                // [H][W] or null
   float* post;                     // [K][H][W] or null
-  unsigned long long* counter;     // executed pixel-sweeps
+  unsigned long long* counter;     // (pixel, candidate) objectives the M-steps evaluated
   unsigned long long* static_counter;  // static ray samples the M-steps evaluated (may be null)
+  unsigned long long* sweeps;      // executed pixel-iterations (E-steps; may be null)
   unsigned* status;                // kStatus* bits
   unsigned long long timeout_ns;   // bounded-wait limit
+  // exact candidate pruning (set_pruning): on/off, the rounding margin of
+  // the segmentation bound, and d_j = d0 + j / inv_step
+  int prune;
+  float seg_margin, d0, inv_step;
 };
+
+// Candidate pruning of the sweep: the M-steps skip candidates whose upper
+// bound (prior + largest segmentation term) is below an objective already
+// computed, which leaves every arg-max unchanged.  It is switched off where
+// the candidate spacing is too fine for the float32 index arithmetic of the
+// interval (below 2^-12 of the largest |d|).  seg_margin covers the
+// float32 rounding of the segmentation sums (at most K terms of magnitude
+// <= max(1, |ln eps|) each, summed in at most 2K + 1 operations): 2^-14 (1 +
+// K max(1, |ln eps|)), far above that rounding and far below the spread of the
+// prior (log(1 + 1/gamma)).
+inline void set_pruning(SweepArgs& a, int on, int K, const float* dval, int D, float eps) {
+  const double d0 = dval[0], d1 = dval[D - 1];
+  const double step = D > 1 ? (d1 - d0) / (D - 1) : 0.0;
+  const double scale = std::max(1.0, std::max(std::fabs(d0), std::fabs(d1)));
+  a.prune = on && D > 1 && step >= scale * (1.0 / 4096.0);
+  a.d0 = static_cast<float>(d0);
+  a.inv_step = step > 0.0 ? static_cast<float>(1.0 / step) : 0.f;
+  const double le = std::max(1.0, std::fabs(std::log(static_cast<double>(eps))));
+  a.seg_margin = static_cast<float>((1.0 + K * le) / 16384.0);
+}
 
 // Per-frame arguments of the persistent sweep, in global memory (TMA
 // descriptors must be 64-byte aligned; CUtensorMap's own alignment gives it).

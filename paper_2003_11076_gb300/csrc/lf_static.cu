@@ -226,6 +226,7 @@ extern "C" lf_status lf_run_em_static(int n_cams, const float* baselines, int H,
   a.labels = labels;
   a.post = posteriors;
   a.counter = reinterpret_cast<unsigned long long*>(scratch + kOffCounter);
+  set_pruning(a, prm.prune, n_cams, hd, D, prm.eps);
   a.status = reinterpret_cast<unsigned*>(scratch + kOffStatus);
   a.timeout_ns = 2000000000ull;
   e = launch_em_sweep(n_cams, img_map, p_map, a, s);

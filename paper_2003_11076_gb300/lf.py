@@ -43,7 +43,7 @@ class Params(ctypes.Structure):
                 ("seg_threshold", ctypes.c_float), ("eps", ctypes.c_float),
                 ("mstep_seg_term", ctypes.c_int), ("median", ctypes.c_int), ("precision", ctypes.c_int),
                 ("early_exit", ctypes.c_int), ("dynamic_only", ctypes.c_int),
-                ("em_mode", ctypes.c_int)]
+                ("em_mode", ctypes.c_int), ("prune", ctypes.c_int)]
 
 
 class SupportParams(ctypes.Structure):
@@ -61,7 +61,8 @@ class Stats(ctypes.Structure):
                 ("ms_prior", ctypes.c_float), ("ms_sweep", ctypes.c_float), ("ms_refocus", ctypes.c_float),
                 ("ms_median", ctypes.c_float), ("graph_captures", ctypes.c_int),
                 ("tuned_signatures", ctypes.c_int), ("ms_support", ctypes.c_float),
-                ("ms_set_inputs", ctypes.c_float), ("executed_static_ray_samples", ctypes.c_uint64)]
+                ("ms_set_inputs", ctypes.c_float), ("executed_static_ray_samples", ctypes.c_uint64),
+                ("executed_pixel_iterations", ctypes.c_uint64)]
 
 
 _lib = None

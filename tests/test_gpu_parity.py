@@ -6,6 +6,8 @@ least 99.9 % of the pixels and on every pixel the oracle does not excuse
 refocused intensities within 1e-3 absolute on [0, 1] and posteriors within
 1e-4, on the pixels where disparity and labels agree.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -187,11 +189,12 @@ def test_early_exit_is_exact():
     lf = _lf()
     s = scenes.small_gray(10)
     a = lf.run_scene(s, params=lf.default_params(early_exit=1), iters=8)
-    b = lf.run_scene(s, params=lf.default_params(early_exit=0), iters=8)
+    b = lf.run_scene(s, params=lf.default_params(early_exit=0, prune=0), iters=8)
     for k in ("d_idx", "labels", "post", "refocus"):
         assert np.array_equal(a[k], b[k]), k
     assert a["stats"]["executed_ray_samples"] < b["stats"]["executed_ray_samples"]
     assert b["stats"]["executed_ray_samples"] == b["stats"]["nominal_ray_samples"]
+    assert b["stats"]["executed_pixel_iterations"] == s.H * s.W * 8
 
 
 @pytest.mark.parametrize("make", [
@@ -218,6 +221,53 @@ def test_early_exit_is_exact_across_shapes(make):
     for k in ("d_idx", "d", "labels", "post", "refocus"):
         assert np.array_equal(a[k], b[k]), k
     assert a["stats"]["executed_ray_samples"] < b["stats"]["executed_ray_samples"]
+
+
+PRUNE_CASES = [
+    lambda: (scenes.street_rgb(0), {}),
+    lambda: (scenes.street_rgb(1), {"precision": 1}),
+    lambda: (scenes.small_gray(12, D=7, iters=8), {}),
+    lambda: (scenes.small_gray(13, H=40, W=96, D=1024, iters=6), {}),
+    lambda: (scenes.small_gray(14, baselines=[-0.4, -0.3, -0.2, -0.1, 0.0, 0.1, 0.2, 0.3, 0.4], D=40, iters=8), {}),
+    lambda: (scenes.small_gray(18, H=40, W=200, baselines=[-0.3, -0.2, -0.1, 0.0, 0.1, 0.2, 0.3], D=33, iters=8),
+             {}),
+    lambda: (scenes.random_frame(5, scale=0.3), {}),
+    lambda: (scenes.small_gray(15, H=24, W=48, D=16, iters=6,
+                               baselines=[-0.3, -0.25, -0.2, -0.15, -0.1, -0.05, 0.0, 0.05, 0.1, 0.15, 0.2, 0.25]),
+             {}),
+    # fractional, negative and offset candidates; the prior's floor at 0 (a
+    # log prior unbounded below); the literal M-step energy without the
+    # segmentation term; a steep variance weight; a wide prior; bfloat16 maps
+    lambda: (dataclasses.replace(scenes.small_gray(20), d_min=-3.5, d_max=22.25, D=53), {}),
+    lambda: (scenes.small_gray(21), {"gamma": 0.0}),
+    lambda: (scenes.small_gray(22), {"mstep_seg_term": 0}),
+    lambda: (scenes.small_gray(23), {"beta": 5000.0, "sigma": 0.5}),
+    lambda: (scenes.small_gray(24), {"sigma": 12.0, "gamma": 1e-3}),
+    lambda: (scenes.small_gray(25), {"precision": 2, "eps": 1e-7}),
+    lambda: (scenes.street_rgb(2, H=64, W=320), {"dynamic_only": 1}),
+]
+
+
+@pytest.mark.parametrize("make", PRUNE_CASES)
+def test_pruning_is_exact_across_shapes(make):
+    """Every M-step evaluates only the candidates whose bound (prior plus
+    the largest segmentation term; the variance term is never positive) can
+    still reach an objective already computed, and sweeps of several pixels
+    cover the union of their intervals.  The arg-max, and so every output,
+    is bit-identical to full sweeps, for five to twelve cameras, D from 7 to
+    1024, off-grid candidates and the parameter extremes of the bound."""
+    lf = _lf()
+    s, kw = make()
+    a = lf.run_scene(s, params=lf.default_params(prune=1, **kw))
+    b = lf.run_scene(s, params=lf.default_params(prune=0, **kw))
+    for k in ("d_idx", "d", "labels", "post", "refocus"):
+        assert np.array_equal(a[k], b[k], equal_nan=True), k
+    sa, sb = a["stats"], b["stats"]
+    assert sa["executed_pixel_iterations"] == sb["executed_pixel_iterations"]
+    assert sa["executed_ray_samples"] <= sb["executed_ray_samples"] + s.K * sa["executed_pixel_iterations"]
+    if s.name == "street_rgb" and not kw:
+        # the headline frame: most candidates fall outside the bound
+        assert sa["executed_ray_samples"] < 0.5 * sb["executed_ray_samples"]
 
 
 def test_device_io_equals_host_io():
