@@ -89,15 +89,6 @@ def joint_ops_per_pixel(K: int, D: int) -> int:
     return D * (10 * K + (1 << K) * 13 + 6)
 
 
-def calib_ops_per_pixel_iter(K: int, D: int) -> int:
-    """Calibrated-array sweep: per (candidate, camera) the ray position (3
-    FMA, reciprocal, 2 products, 4 clamps = 10), bilinear weights and indices
-    (8), five bilinear maps (5 x 5), the shift by the reference descriptor (3)
-    and the accumulation (3 sums, 3 squares, 1 segmentation add = 7): 53; per
-    candidate 12; E-step 13 per label vector."""
-    return D * (53 * K + 12) + (1 << K) * 13
-
-
 def sweep_source_hash() -> str:
     return hashlib.sha256(open(SWEEP_SRC, "rb").read()).hexdigest()[:16]
 
@@ -611,8 +602,12 @@ def main():
         exec_mean = st["executed_ray_samples"] / st["runs"]
         pix_iters = exec_mean / (K * D)
         if args.calibrated:
-            ops = pix_iters * calib_ops_per_pixel_iter(K, D)
-            ops_desc = {"ops_per_pixel_iteration": calib_ops_per_pixel_iter(K, D)}
+            pix_iters = st["executed_pixel_iterations"] / st["runs"]
+            pairs = exec_mean / K
+            ops = pairs * (53 * K + 12) + pix_iters * (1 << K) * 13
+            ops_desc = {"ops_model": "53 per (candidate, camera), 12 per (pixel, candidate), 13 per E-step label "
+                                     "vector, over the evaluated work",
+                        "pixel_iterations_per_frame": pix_iters, "candidates_per_pixel_iteration": pairs / pix_iters}
         elif mode == 0:
             static_mean = st["executed_static_ray_samples"] / st["runs"]
             pix_iters = st["executed_pixel_iterations"] / st["runs"]

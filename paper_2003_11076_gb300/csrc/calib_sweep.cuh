@@ -129,7 +129,7 @@ __device__ __forceinline__ int calib_m_step(const CalibArgs& a, const CalibPix (
     }
     const float rn = n >= 2 ? 1.f / static_cast<float>(n) : 0.f;
     const float ss = fmaf(sz, sz, fmaf(syx.y, syx.y, syx.x * syx.x));
-    const float var = fmaf(-ss, rn, q) * rn;
+    const float var = fmaxf(fmaf(-ss, rn, q) * rn, 0.f);  // >= 0: the bound of the candidate pruning
     float J = a.mseg ? seg : 0.f;
     if (inside) J += pr;
     J = fmaf(-a.beta, var, J);
@@ -164,12 +164,16 @@ template <int K>
 __global__ void __launch_bounds__(256, K <= 5 ? 3 : 2) calib_sweep_kernel(const __grid_constant__ CalibArgs a) {
   __shared__ float s_rcp[16];  // 1/n for the E-step's subset sizes (0 for n < 2: Var = 0)
   __shared__ float s_emax[256];
-  __shared__ int16_t s_jb[256], s_list[256];
+  __shared__ int16_t s_jb[256], s_list[256], s_list2[256], s_lo[256], s_hi[256];
   __shared__ uint16_t s_S[256];
   __shared__ uint8_t s_conv[256];
   __shared__ int s_wcnt[8];
+  __shared__ uint16_t s_sortc[2 * kLoBuckets * 8];  // counting sort (sort_pixels), zero between uses
+  __shared__ unsigned s_stat;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   if (tid < 16) s_rcp[tid] = tid >= 2 ? 1.f / static_cast<float>(tid) : 0.f;
+  for (int i = tid; i < 2 * kLoBuckets * 8; i += blockDim.x) s_sortc[i] = 0;
+  if (tid == 0) s_stat = 0u;
   __syncthreads();
   const int bu = blockIdx.x * 16, bv = blockIdx.y * 16;
   const int u = bu + (tid & 15), v = bv + (tid >> 4);
@@ -221,30 +225,83 @@ __global__ void __launch_bounds__(256, K <= 5 ? 3 : 2) calib_sweep_kernel(const 
     x.cz = fr.z;
     return x;
   };
+  // Exact candidate pruning (as in the rectified sweep, prune_interval): the
+  // objective of a candidate is at most its log prior plus the segmentation
+  // term, and every log p(static) / log p(dynamic) is <= 0, so the bound of
+  // the segmentation term is 0 (plus a.seg_margin for rounding).  Before each
+  // M-step a pixel's interval comes from the objective at one candidate (the
+  // one nearest mu, then the last arg-max), evaluated by the same code.
+  const float seg_ub = a.seg_margin;
+  auto interval = [&](const Px& x, float Js, int js, int& lo, int& hi) {
+    prune_interval(x.mu, Js, seg_ub, a.gamma, a.inv2s2, a.d0, a.inv_step, a.D, js, lo, hi);
+  };
+  unsigned my_pairs = 0;  // (pixel, candidate) objectives this thread evaluated
   unsigned long long executed = 0;
-  // t = 1
-  {
-    const int n = compact(run, s_list, 0, s_wcnt);
-    executed += static_cast<unsigned long long>(n);
-    if (tid < n) {
-      const int p = s_list[tid];
-      const Px x = load(p);
-      const int jb = calib_m_step<K, true>(a, x.A, x.u, x.v, x.cyx, x.cz, x.mu, x.inside, 0u, 0, a.D, nullptr);
-      Rays rays;
-      calib_rays<K>(a, x.A, x.u, x.v, jb, x.cyx, x.cz, rays);
-      unsigned S = 0;
-      float emax = 0.f;
-      enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
+  // t = 1: the first M-step's interval, then the pixels sorted by it
+  int key = 0;
+  if (run) {
+    int lo = 0, hi = a.D - 1;
+    if (a.prune) {
+      const Px x = load(tid);
+      if (x.inside) {
+        const int js = min(max(static_cast<int>(rintf((x.mu - a.d0) * a.inv_step)), 0), a.D - 1);
+        float Js;
+        calib_m_step<K, true>(a, x.A, x.u, x.v, x.cyx, x.cz, x.mu, true, 0u, js, js + 1, &Js);
+        interval(x, Js, js, lo, hi);
+        ++my_pairs;
+      }
+    }
+    s_lo[tid] = static_cast<int16_t>(lo);
+    s_hi[tid] = static_cast<int16_t>(hi);
+    key = interval_key(lo, hi, a.D);
+  }
+  const int n1 = sort_pixels(run, key, 2 * kLoBuckets, s_list, s_sortc, s_wcnt);
+  executed += static_cast<unsigned long long>(n1);
+  // a later M-step's interval (labels S of the last E-step), bounded by the
+  // objective at the last arg-max jp, evaluated at the start of the pass by
+  // every lane that takes part in the pixel's M-step
+  auto interval_at = [&](const Px& x, unsigned S, int jp, int& lo, int& hi) {
+    lo = 0;
+    hi = a.D - 1;
+    if (!(a.prune && x.inside)) return false;
+    float Js;
+    calib_m_step<K, false>(a, x.A, x.u, x.v, x.cyx, x.cz, x.mu, true, S, jp, jp + 1, &Js);
+    interval(x, Js, jp, lo, hi);
+    return true;
+  };
+  s_conv[tid] = 0;
+  if (warp * 32 < n1) {
+    const bool active = tid < n1;
+    const int p = s_list[active ? tid : n1 - 1];
+    const Px x = load(p);
+    const int LO = __reduce_min_sync(0xffffffffu, s_lo[p]), HI = __reduce_max_sync(0xffffffffu, s_hi[p]);
+    const int jb = calib_m_step<K, true>(a, x.A, x.u, x.v, x.cyx, x.cz, x.mu, x.inside, 0u, LO, HI + 1, nullptr);
+    if (active) my_pairs += static_cast<unsigned>(HI - LO + 1);
+    Rays rays;
+    calib_rays<K>(a, x.A, x.u, x.v, jb, x.cyx, x.cz, rays);
+    unsigned S = 0;
+    float emax = 0.f;
+    enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
+    if (active) {
       s_jb[p] = static_cast<int16_t>(jb);
       s_S[p] = static_cast<uint16_t>(S);
       s_emax[p] = emax;
     }
-    s_conv[tid] = 0;
-    __syncthreads();
   }
+  __syncthreads();
+  // later passes: the pixels still iterating, in the first pass's order
+  int16_t* list = s_list;
+  int16_t* list_next = s_list2;
+  int n_prev = n1;
   for (int t = 2; t <= a.iters; ++t) {
-    const int n = compact(run && !s_conv[tid], s_list, 0, s_wcnt);
+    const int p_prev = tid < n_prev ? list[tid] : 0;
+    const bool pend = tid < n_prev && !s_conv[p_prev];
+    const int n = compact_value(pend, p_prev, list_next, 0, s_wcnt);
     if (n == 0) break;
+    int16_t* tmp = list;
+    list = list_next;
+    list_next = tmp;
+    n_prev = n;
     executed += static_cast<unsigned long long>(n);
     // lanes per pixel: the largest power of two that still fits every
     // remaining pixel into one round of the CTA's warps
@@ -255,40 +312,52 @@ __global__ void __launch_bounds__(256, K <= 5 ? 3 : 2) calib_sweep_kernel(const 
       const int slot = warp * gpw + lane / G;
       if (warp * gpw < n) {
         const bool act = slot < n;
-        const int p = s_list[act ? slot : n - 1];  // idle groups repeat the last pixel
+        const int p = list[act ? slot : n - 1];  // idle groups repeat the last pixel
         const Px x = load(p);
         const unsigned Sp = s_S[p];
-        const int per = (a.D + G - 1) / G, j0 = min(gl * per, a.D), j1 = min(j0 + per, a.D);
+        int plo, phi;
+        if (interval_at(x, Sp, s_jb[p], plo, phi) && act && gl == 0) ++my_pairs;
+        const int per = (phi - plo + G) / G, j0 = min(plo + gl * per, phi + 1), j1 = min(j0 + per, phi + 1);
         float jbest;
         unsigned jb = static_cast<unsigned>(
             calib_m_step<K, false>(a, x.A, x.u, x.v, x.cyx, x.cz, x.mu, x.inside, Sp, j0, j1, &jbest));
+        if (act) my_pairs += static_cast<unsigned>(j1 - j0);
         group_argmax(jbest, jb, G);
         Rays rays;
         calib_rays<K>(a, x.A, x.u, x.v, static_cast<int>(jb), x.cyx, x.cz, rays);
         unsigned S = 0;
         float emax = 0.f;
         enumerate_group<K>(rays, s_rcp, a.beta, gl, G, S, emax);
+        const bool conv = a.early_exit && S == Sp;  // the next M-step would repeat this one exactly
         if (act && gl == 0) {
           s_jb[p] = static_cast<int16_t>(jb);
           s_S[p] = static_cast<uint16_t>(S);
           s_emax[p] = emax;
-          s_conv[p] = a.early_exit && S == Sp;  // the next M-step would repeat this one exactly
+          s_conv[p] = conv;
         }
       }
-    } else if (tid < n) {
-      const int p = s_list[tid];
+    } else if (warp * 32 < n) {
+      const bool active = tid < n;
+      const int p = list[active ? tid : n - 1];
       const Px x = load(p);
       const unsigned Sp = s_S[p];
-      const int jb = calib_m_step<K, false>(a, x.A, x.u, x.v, x.cyx, x.cz, x.mu, x.inside, Sp, 0, a.D, nullptr);
+      int plo, phi;
+      if (interval_at(x, Sp, s_jb[p], plo, phi) && active) ++my_pairs;
+      const int LO = __reduce_min_sync(0xffffffffu, plo), HI = __reduce_max_sync(0xffffffffu, phi);
+      const int jb = calib_m_step<K, false>(a, x.A, x.u, x.v, x.cyx, x.cz, x.mu, x.inside, Sp, LO, HI + 1, nullptr);
+      if (active) my_pairs += static_cast<unsigned>(HI - LO + 1);
       Rays rays;
       calib_rays<K>(a, x.A, x.u, x.v, jb, x.cyx, x.cz, rays);
       unsigned S = 0;
       float emax = 0.f;
       enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
-      s_jb[p] = static_cast<int16_t>(jb);
-      s_S[p] = static_cast<uint16_t>(S);
-      s_emax[p] = emax;
-      s_conv[p] = a.early_exit && S == Sp;
+      const bool conv = a.early_exit && S == Sp;
+      if (active) {
+        s_jb[p] = static_cast<int16_t>(jb);
+        s_S[p] = static_cast<uint16_t>(S);
+        s_emax[p] = emax;
+        s_conv[p] = conv;
+      }
     }
     __syncthreads();
   }
@@ -312,7 +381,15 @@ __global__ void __launch_bounds__(256, K <= 5 ? 3 : 2) calib_sweep_kernel(const 
       for (int k = 0; k < K; ++k) a.post[k * static_cast<size_t>(a.H) * a.W + pix] = post[k];
     }
   }
-  if (tid == 0 && executed) atomicAdd(a.counter, executed * a.D);  // every candidate of every sweep
+  {  // statistics: one global atomic per block and counter
+    const unsigned wp = __reduce_add_sync(0xffffffffu, my_pairs);
+    if (lane == 0) atomicAdd_block(&s_stat, wp);
+    __syncthreads();
+    if (tid == 0) {
+      atomicAdd(a.counter, static_cast<unsigned long long>(s_stat));
+      if (a.sweeps) atomicAdd(a.sweeps, executed);
+    }
+  }
 }
 
 template <int K>

@@ -1551,23 +1551,18 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
   const int nact = sort_pixels(my_valid, key, kSortKeys, ps.list, s_sortc, s_wcnt);
   unsigned long long executed = static_cast<unsigned long long>(nact);
 
-  // After an E-step of a pixel that goes on: the interval of its next M-step
-  // (fixed labels S), bounded by the objective at the current candidate,
-  // stored for tile pixel p when `write` (the caller has stored its other
-  // results first, so that they are not live across the evaluation).
-  auto bound_next = [&](const PixelCtx<TS>& c, int p, unsigned S, int jb, bool write) {
-    int lo = 0, hi = a.D - 1;
-    if (a.prune && c.inside) {
-      float Js;
-      m_step_fixed_range<K, TS, REF>(a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, true, S, jb,
-                                     jb + 1, &Js);
-      prune_range(a, c.mu, Js, ps.seg_ub[p], jb, lo, hi);
-      if (write) ++my_pairs;
-    }
-    if (write) {
-      ps.lo[p] = static_cast<int16_t>(lo);
-      ps.hi[p] = static_cast<int16_t>(hi);
-    }
+  // A later M-step's interval (fixed labels S of the last E-step), bounded by
+  // the objective at the last arg-max jp; evaluated at the start of the pass
+  // by every lane that takes part in the pixel's M-step.
+  auto interval_at = [&](const PixelCtx<TS>& c, int p, unsigned S, int jp, int& lo, int& hi) {
+    lo = 0;
+    hi = a.D - 1;
+    if (!(a.prune && c.inside)) return false;
+    float Js;
+    m_step_fixed_range<K, TS, REF>(a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, true, S, jp, jp + 1,
+                                   &Js);
+    prune_range(a, c.mu, Js, ps.seg_ub[p], jp, lo, hi);
+    return true;
   };
 
   // t = 1
@@ -1600,7 +1595,6 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
       ps.emax[p] = emax;
       ps.conv[p] = conv;
     }
-    if (!conv && a.iters >= 2) bound_next(c, p, S, jb, active);
   }
   __syncthreads();
   // t >= 2: only the pixels not yet at their fixed point; when fewer than a
@@ -1633,7 +1627,8 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
         const int p = list[act ? slot : n - 1];  // idle groups repeat the last pixel
         const PixelCtx<TS> c = load_pixel<TS>(a, s_feat, u0, v0, cam_stride, p, s_mu);
         const unsigned Sp = ps.S[p];
-        const int plo = ps.lo[p], phi = ps.hi[p];
+        int plo, phi;
+        if (interval_at(c, p, Sp, ps.jb[p], plo, phi) && act && gl == 0) ++my_pairs;
         const int per = (phi - plo + G) / G, j0 = min(plo + gl * per, phi + 1), j1 = min(j0 + per, phi + 1);
         float jbest;
         unsigned jb = static_cast<unsigned>(m_step_fixed_range<K, TS, REF>(
@@ -1655,14 +1650,15 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
           ps.emax[p] = emax;
           ps.conv[p] = conv;
         }
-        if (!conv && t < a.iters) bound_next(c, p, S, static_cast<int>(jb), act && gl == 0);
       }
     } else if (warp * 32 < n) {
       const bool active = tid < n;
       const int p = list[active ? tid : n - 1];
       const PixelCtx<TS> c = load_pixel<TS>(a, s_feat, u0, v0, cam_stride, p, s_mu);
       const unsigned Sp = ps.S[p];
-      const int LO = __reduce_min_sync(0xffffffffu, ps.lo[p]), HI = __reduce_max_sync(0xffffffffu, ps.hi[p]);
+      int plo, phi;
+      if (interval_at(c, p, Sp, ps.jb[p], plo, phi) && active) ++my_pairs;
+      const int LO = __reduce_min_sync(0xffffffffu, plo), HI = __reduce_max_sync(0xffffffffu, phi);
       const int jb = m_step_fixed_range<K, TS, REF>(a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu,
                                                     c.inside, Sp, LO, HI + 1, nullptr);
       if (active) {
@@ -1681,7 +1677,6 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
         ps.emax[p] = emax;
         ps.conv[p] = conv;
       }
-      if (!conv && t < a.iters) bound_next(c, p, S, jb, active);
     }
     __syncthreads();
   }

@@ -1012,6 +1012,8 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
     g.fa = c->d_fa; g.fb = c->d_fb; g.dval = c->d_dval; g.mu = c->d_mu;
     g.d_idx = didx; g.d_out = dout; g.labels = lab; g.post = post; g.refocus = refo_stage;
     g.counter = c->d_counter;
+    g.sweeps = c->d_counter + 2;
+    set_pruning(g, c->p.prune, c->K, c->dval.data(), c->D, c->p.eps);
     LF_CUDA(launch_calib_features(g, c->stream), "calibrated features launch");
     LF_CUDA(launch_calib_sweep(g, c->stream), "calibrated sweep launch");
     launched += 2;

@@ -108,7 +108,9 @@ struct SweepArgs {
 // <= max(1, |ln eps|) each, summed in at most 2K + 1 operations): 2^-14 (1 +
 // K max(1, |ln eps|)), far above that rounding and far below the spread of the
 // prior (log(1 + 1/gamma)).
-inline void set_pruning(SweepArgs& a, int on, int K, const float* dval, int D, float eps) {
+// (SweepArgs and CalibArgs)
+template <typename Args>
+inline void set_pruning(Args& a, int on, int K, const float* dval, int D, float eps) {
   const double d0 = dval[0], d1 = dval[D - 1];
   const double step = D > 1 ? (d1 - d0) / (D - 1) : 0.0;
   const double scale = std::max(1.0, std::max(std::fabs(d0), std::fabs(d1)));
@@ -160,7 +162,10 @@ struct CalibArgs {
   uint16_t* labels;                // [H][W]
   float* post;                     // [K][H][W] or null
   float* refocus;                  // [H][W][C] or null
-  unsigned long long* counter;     // executed pixel-sweeps
+  unsigned long long* counter;     // (pixel, candidate) objectives the M-steps evaluated
+  unsigned long long* sweeps;      // executed pixel-iterations (may be null)
+  int prune;                       // exact candidate pruning (set_pruning; the
+  float seg_margin, d0, inv_step;  // segmentation bound is 0: every log p <= 0)
 };
 
 // Support points of the disparity prior (rectified arrays).

@@ -112,3 +112,30 @@ def test_calibrated_device_io_and_early_exit():
     for k in ("d_idx", "labels", "d", "post", "refocus"):
         assert np.array_equal(slow[k], host[k]), k
     assert host["stats"]["executed_ray_samples"] < slow["stats"]["executed_ray_samples"]
+
+
+PRUNE_FRAMES = FRAMES + [
+    lambda: scenes.street_rgb(0, calibrated=True),
+    lambda: scenes.small_gray(6, calibrated=True, rot_deg=2.0),
+]
+
+
+@pytest.mark.parametrize("i", range(len(PRUNE_FRAMES)))
+def test_calibrated_pruning_is_exact(i):
+    """Candidate pruning of the calibrated sweep (bound: log prior + 0, every
+    log probability being <= 0) gives the full sweeps' bits, one to twelve
+    cameras."""
+    from paper_2003_11076_gb300 import lf
+    s = PRUNE_FRAMES[i]()
+    a = lf.run_scene(s, params=lf.default_params(prune=1))
+    b = lf.run_scene(s, params=lf.default_params(prune=0))
+    for k in ("d_idx", "d", "labels", "post", "refocus"):
+        assert np.array_equal(a[k], b[k], equal_nan=True), k
+    assert a["stats"]["executed_pixel_iterations"] == b["stats"]["executed_pixel_iterations"]
+    assert b["stats"]["executed_ray_samples"] == s.K * s.D * b["stats"]["executed_pixel_iterations"]
+    # each bounded M-step costs one extra objective (the bound's reference
+    # candidate); with more than a few candidates the bound saves far more
+    assert a["stats"]["executed_ray_samples"] <= b["stats"]["executed_ray_samples"] + \
+        s.K * a["stats"]["executed_pixel_iterations"]
+    if s.D >= 16:
+        assert a["stats"]["executed_ray_samples"] < b["stats"]["executed_ray_samples"]
