@@ -873,11 +873,106 @@ __device__ __forceinline__ void enum_low(const Rays& r, const Acc& acc, const fl
   }
 }
 
+// Up to five cameras the subset tree runs on float32x2 pairs: lane .x holds
+// the label vectors without camera 0, lane .y the same vector with camera 0,
+// so each internal node adds camera k to both with one packed add per sum
+// and each pair of leaves (masks m, m | 1) evaluates its two objectives with
+// packed operations (each lane the scalar leaf's IEEE operations).  A
+// vector's sums add camera 0 first, then the others from the highest down;
+// the group form (enumerate_group) forms them in the same order, so both
+// give the same bits.
+constexpr int kPairEnumMaxCams = 5;
+
+struct Acc2 {
+  float2 sy, sx, sz, q, sa;
+};
+
+// the rays of cameras 1..K-1 duplicated into both lanes
+template <int K>
+struct DupRays {
+  float2 gy[K], gx[K], gz[K], qk[K], ak[K];
+};
+
+template <int MODE, int K, int k, int N, unsigned MASK>
+__device__ __forceinline__ void enum_pair(const DupRays<K>& dr, const Acc2& acc, const float2 (&rnp)[K],
+                                          const float2 (&nrnp)[K], float2 nbeta, float2 base2, float2 nemax2,
+                                          EnumState<K>& s) {
+  if constexpr (k < 1) {
+    const float2 ss = ffma2(acc.sz, acc.sz, ffma2(acc.sx, acc.sx, fmul2(acc.sy, acc.sy)));
+    const float2 var = fmul2(ffma2(ss, nrnp[N], acc.q), rnp[N]);
+    const float2 E = ffma2(nbeta, var, fadd2(base2, acc.sa));
+    if constexpr (MODE == 0) {
+      if (E.x > s.best) { s.best = E.x; s.bmask = MASK; }
+      if (E.y > s.best) { s.best = E.y; s.bmask = MASK | 1u; }
+    } else {
+      const float2 t = fmul2(fadd2(E, nemax2), make_float2(1.4426950408889634f, 1.4426950408889634f));
+      const float e0 = ex2_approx(t.x), e1 = ex2_approx(t.y);  // exp(E - Emax) <= 1
+      s.Z += e0;
+#pragma unroll
+      for (int i = 1; i < K; ++i)
+        if (MASK >> i & 1u) s.pl[i] += e0;
+      s.Z += e1;
+      s.pl[0] += e1;
+#pragma unroll
+      for (int i = 1; i < K; ++i)
+        if (MASK >> i & 1u) s.pl[i] += e1;
+    }
+  } else {
+    enum_pair<MODE, K, k - 1, N, MASK>(dr, acc, rnp, nrnp, nbeta, base2, nemax2, s);
+    const Acc2 a2{fadd2(acc.sy, dr.gy[k]), fadd2(acc.sx, dr.gx[k]), fadd2(acc.sz, dr.gz[k]), fadd2(acc.q, dr.qk[k]),
+                  fadd2(acc.sa, dr.ak[k])};
+    enum_pair<MODE, K, k - 1, N + 1, MASK | (1u << k)>(dr, a2, rnp, nrnp, nbeta, base2, nemax2, s);
+  }
+}
+
+template <int MODE, int K>
+__device__ __forceinline__ void enumerate_pairs(const Rays& r, const float* s_rcp, float beta, float emax,
+                                                unsigned& bmask, float& best, float* post) {
+  DupRays<K> dr;
+#pragma unroll
+  for (int k = 1; k < K; ++k) {
+    dr.gy[k] = make_float2(r.gy[k], r.gy[k]);
+    dr.gx[k] = make_float2(r.gx[k], r.gx[k]);
+    dr.gz[k] = make_float2(r.gz[k], r.gz[k]);
+    dr.qk[k] = make_float2(r.qk[k], r.qk[k]);
+    dr.ak[k] = make_float2(r.ak[k], r.ak[k]);
+  }
+  float2 rnp[K], nrnp[K];  // (1/n, 1/(n + 1)) of the leaf pairs with n cameras besides camera 0
+#pragma unroll
+  for (int n = 0; n < K; ++n) {
+    rnp[n] = make_float2(s_rcp[n], s_rcp[n + 1]);
+    nrnp[n] = make_float2(-rnp[n].x, -rnp[n].y);
+  }
+  EnumState<K> s;
+  s.best = -INFINITY;
+  s.bmask = 0;
+  s.emax = emax;
+  s.Z = 0.f;
+#pragma unroll
+  for (int i = 0; i < K; ++i) s.pl[i] = 0.f;
+  const Acc2 root{make_float2(0.f, r.gy[0]), make_float2(0.f, r.gx[0]), make_float2(0.f, r.gz[0]),
+                  make_float2(0.f, r.qk[0]), make_float2(0.f, r.ak[0])};
+  enum_pair<MODE, K, K - 1, 0, 0u>(dr, root, rnp, nrnp, make_float2(-beta, -beta), make_float2(r.base, r.base),
+                                   make_float2(-emax, -emax), s);
+  if constexpr (MODE == 0) {
+    bmask = s.bmask;
+    best = s.best;
+  } else {
+    const float inv = 1.f / s.Z;
+#pragma unroll
+    for (int i = 0; i < K; ++i) post[i] = s.pl[i] * inv;
+  }
+}
+
 // Full enumeration: cameras >= L form a runtime loop over "high" masks (sums
 // built from scratch), cameras < L the unrolled subset tree.
 template <int MODE, int K>
 __device__ __forceinline__ void enumerate(const Rays& r, const float* s_rcp, float beta, float emax,
                                           unsigned& bmask, float& best, float* post) {
+  if constexpr (K <= kPairEnumMaxCams) {
+    enumerate_pairs<MODE, K>(r, s_rcp, beta, emax, bmask, best, post);
+    return;
+  }
   constexpr int L = K < 6 ? K : 6;
   constexpr int NH = K - L;
   float ph[NH > 0 ? NH : 1];
@@ -960,8 +1055,13 @@ __device__ __forceinline__ void enumerate_group(const Rays& r, const float* s_rc
   if constexpr (NH == 0) {
     for (unsigned m = gl; m < (1u << K); m += G) {
       Acc acc{0.f, 0.f, 0.f, 0.f, 0.f};
+      // the order of the one-thread tree: up to five cameras (float32x2
+      // pairs) camera 0 first, then the others from the highest down;
+      // six cameras from the highest down
+      constexpr bool pairs = K <= kPairEnumMaxCams;
+      if (pairs && (m & 1u)) acc = Acc{r.gy[0], r.gx[0], r.gz[0], r.qk[0], r.ak[0]};
 #pragma unroll
-      for (int k = L - 1; k >= 0; --k)
+      for (int k = L - 1; k >= (pairs ? 1 : 0); --k)
         if (m >> k & 1u) {
           acc.sy += r.gy[k]; acc.sx += r.gx[k]; acc.sz += r.gz[k]; acc.q += r.qk[k]; acc.sa += r.ak[k];
         }
