@@ -125,9 +125,14 @@ typedef struct lf_params {
                             plus the largest segmentation term, the variance
                             term being <= 0 -- reaches an objective already
                             computed; the arg-max, and so every output, is
-                            identical to the full sweep's.  0: full sweeps.
-                            Rectified arrays (lf_create, the batch API and
-                            lf_run_em_static); the other modes ignore it. */
+                            identical to the full sweep's; from seven cameras
+                            the E-step likewise skips blocks of label vectors
+                            whose bound (the segmentation terms) is below the
+                            all-static vector's objective.  0: full sweeps and
+                            enumerations.  Hard EM on rectified arrays
+                            (lf_create, the batch API, lf_run_em_static) and
+                            on calibrated arrays; the soft-EM and joint-MAP
+                            modes ignore it. */
 } lf_params;
 
 /* Statistics accumulated over the lf_run_em calls since the previous

@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(256, K <= 5 ? 3 : 2) calib_sweep_kernel(const 
     calib_rays<K>(a, x.A, x.u, x.v, jb, x.cyx, x.cz, rays);
     unsigned S = 0;
     float emax = 0.f;
-    enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
+    enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr, a.prune != 0);
     if (active) {
       s_jb[p] = static_cast<int16_t>(jb);
       s_S[p] = static_cast<uint16_t>(S);
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(256, K <= 5 ? 3 : 2) calib_sweep_kernel(const 
         calib_rays<K>(a, x.A, x.u, x.v, static_cast<int>(jb), x.cyx, x.cz, rays);
         unsigned S = 0;
         float emax = 0.f;
-        enumerate_group<K>(rays, s_rcp, a.beta, gl, G, S, emax);
+        enumerate_group<K>(rays, s_rcp, a.beta, gl, G, S, emax, a.prune != 0);
         const bool conv = a.early_exit && S == Sp;  // the next M-step would repeat this one exactly
         if (act && gl == 0) {
           s_jb[p] = static_cast<int16_t>(jb);
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(256, K <= 5 ? 3 : 2) calib_sweep_kernel(const 
       calib_rays<K>(a, x.A, x.u, x.v, jb, x.cyx, x.cz, rays);
       unsigned S = 0;
       float emax = 0.f;
-      enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
+      enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr, a.prune != 0);
       const bool conv = a.early_exit && S == Sp;
       if (active) {
         s_jb[p] = static_cast<int16_t>(jb);

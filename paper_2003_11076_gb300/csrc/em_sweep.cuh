@@ -833,10 +833,12 @@ struct Acc {
 };
 
 // Leaf evaluation shared by the arg-max and the posterior passes so that both
-// see bit-identical objectives.
+// see bit-identical objectives.  The variance is clamped at 0 (as in the
+// M-steps), so a leaf's objective is at most base + its segmentation sum: the
+// bound of the E-step's block pruning.
 __device__ __forceinline__ float leaf_objective(const Acc& acc, float rn, float base, float beta) {
   const float ss = fmaf(acc.sz, acc.sz, fmaf(acc.sx, acc.sx, acc.sy * acc.sy));
-  const float var = fmaf(-ss, rn, acc.q) * rn;
+  const float var = fmaxf(fmaf(-ss, rn, acc.q) * rn, 0.f);
   return fmaf(-beta, var, base + acc.sa);
 }
 
@@ -899,7 +901,8 @@ __device__ __forceinline__ void enum_pair(const DupRays<K>& dr, const Acc2& acc,
                                           EnumState<K>& s) {
   if constexpr (k < 1) {
     const float2 ss = ffma2(acc.sz, acc.sz, ffma2(acc.sx, acc.sx, fmul2(acc.sy, acc.sy)));
-    const float2 var = fmul2(ffma2(ss, nrnp[N], acc.q), rnp[N]);
+    float2 var = fmul2(ffma2(ss, nrnp[N], acc.q), rnp[N]);
+    var = make_float2(fmaxf(var.x, 0.f), fmaxf(var.y, 0.f));
     const float2 E = ffma2(nbeta, var, fadd2(base2, acc.sa));
     if constexpr (MODE == 0) {
       if (E.x > s.best) { s.best = E.x; s.bmask = MASK; }
@@ -964,11 +967,56 @@ __device__ __forceinline__ void enumerate_pairs(const Rays& r, const float* s_rc
   }
 }
 
+// Block pruning of the E-step arg-max from seven cameras: the label vectors
+// sharing high mask h (cameras >= L) form a block of 2^L leaves whose
+// objectives are at most base + sa_h + sum_{k < L} max(a_k, 0) (the variance
+// term is <= 0; sa_h the block's segmentation sum over its high cameras, a_k
+// = log p(static) - log p(dynamic) of low camera k), plus a margin for the
+// float32 rounding of the sums (at most L + 2 roundings of numbers of
+// magnitude below 1 + |base| + |sa_h| + sum |a_k|; the margin is 2^-20 times
+// that).  A block whose bound is below the objective of one leaf evaluated
+// the same way -- the all-static vector, the usual winner -- holds neither the
+// arg-max nor a tie with it, and is skipped.
+template <int L>
+struct BlockBound {
+  float seed, pos, mag;
+  template <int K>
+  __device__ __forceinline__ void init(const Rays& r, const float* s_rcp, float beta) {
+    constexpr int NH = K - L;
+    // the all-static leaf, summed in the enumeration's order: high cameras
+    // upwards, then the low subset tree from camera L - 1 down
+    Acc acc{0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < NH; ++i) {
+      acc.sy += r.gy[L + i]; acc.sx += r.gx[L + i]; acc.sz += r.gz[L + i];
+      acc.q += r.qk[L + i]; acc.sa += r.ak[L + i];
+    }
+#pragma unroll
+    for (int k = L - 1; k >= 0; --k) {
+      acc.sy += r.gy[k]; acc.sx += r.gx[k]; acc.sz += r.gz[k];
+      acc.q += r.qk[k]; acc.sa += r.ak[k];
+    }
+    seed = leaf_objective(acc, s_rcp[K], r.base, beta);
+    pos = 0.f;
+    mag = 1.f + fabsf(r.base);
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+      pos += fmaxf(r.ak[k], 0.f);
+      mag += fabsf(r.ak[k]);
+    }
+  }
+  __device__ __forceinline__ bool skip(float base, float sa_h) const {
+    const float ub = (base + sa_h + pos) + (mag + fabsf(sa_h)) * 0x1p-20f;
+    return ub < seed;
+  }
+};
+
 // Full enumeration: cameras >= L form a runtime loop over "high" masks (sums
 // built from scratch), cameras < L the unrolled subset tree.
+// prune: skip blocks by BlockBound (arg-max pass, from seven cameras).
 template <int MODE, int K>
 __device__ __forceinline__ void enumerate(const Rays& r, const float* s_rcp, float beta, float emax,
-                                          unsigned& bmask, float& best, float* post) {
+                                          unsigned& bmask, float& best, float* post, bool prune = false) {
   if constexpr (K <= kPairEnumMaxCams) {
     enumerate_pairs<MODE, K>(r, s_rcp, beta, emax, bmask, best, post);
     return;
@@ -985,6 +1033,9 @@ __device__ __forceinline__ void enumerate(const Rays& r, const float* s_rcp, flo
 #pragma unroll
   for (int i = 0; i < (L > 0 ? L : 1); ++i) s.pl[i] = 0.f;
   float Ztot = 0.f;
+  BlockBound<L> bb;
+  if constexpr (MODE == 0 && NH > 0)
+    if (prune) bb.template init<K>(r, s_rcp, beta);
   for (unsigned h = 0; h < (1u << NH); ++h) {
     Acc acc{0.f, 0.f, 0.f, 0.f, 0.f};
     int nh = 0;
@@ -996,6 +1047,8 @@ __device__ __forceinline__ void enumerate(const Rays& r, const float* s_rcp, flo
         ++nh;
       }
     }
+    if constexpr (MODE == 0 && NH > 0)
+      if (prune && bb.skip(r.base, acc.sa)) continue;
     float rnv[L + 1];
 #pragma unroll
     for (int i = 0; i <= L; ++i) rnv[i] = s_rcp[nh + i];
@@ -1047,7 +1100,7 @@ __device__ __forceinline__ void group_argmax(float& best, unsigned& idx, int G) 
 // one-thread enumeration's bit for bit.
 template <int K>
 __device__ __forceinline__ void enumerate_group(const Rays& r, const float* s_rcp, float beta, int gl, int G,
-                                                unsigned& bmask, float& best) {
+                                                unsigned& bmask, float& best, bool prune = false) {
   constexpr int L = K < 6 ? K : 6;
   constexpr int NH = K - L;
   float b = -INFINITY;
@@ -1073,6 +1126,8 @@ __device__ __forceinline__ void enumerate_group(const Rays& r, const float* s_rc
     s.best = -INFINITY;
     s.bmask = bm;
     s.emax = 0.f;
+    BlockBound<L> bb;
+    if (prune) bb.template init<K>(r, s_rcp, beta);
     for (unsigned h = gl; h < (1u << NH); h += G) {
       Acc acc{0.f, 0.f, 0.f, 0.f, 0.f};
       int nh = 0;
@@ -1084,6 +1139,7 @@ __device__ __forceinline__ void enumerate_group(const Rays& r, const float* s_rc
           ++nh;
         }
       }
+      if (prune && bb.skip(r.base, acc.sa)) continue;
       float rnv[L + 1];
 #pragma unroll
       for (int i = 0; i <= L; ++i) rnv[i] = s_rcp[nh + i];
@@ -1686,7 +1742,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     sample_rays<K, TS>(a, c.st, s_wq, s_o, jb, c.cy, c.cx, c.cz, rays);
     unsigned S = 0;
     float emax = 0.f;
-    enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
+    enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr, a.prune != 0);
     // the second M-step would repeat the first one exactly
     const bool conv = a.early_exit && f0 && S == S0;
     if (active) {
@@ -1742,7 +1798,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
         sample_rays<K, TS>(a, c.st, s_wq, s_o, static_cast<int>(jb), c.cy, c.cx, c.cz, rays);
         unsigned S = 0;
         float emax = 0.f;
-        enumerate_group<K>(rays, s_rcp, a.beta, gl, G, S, emax);
+        enumerate_group<K>(rays, s_rcp, a.beta, gl, G, S, emax, a.prune != 0);
         const bool conv = a.early_exit && S == Sp;
         if (act && gl == 0) {
           ps.jb[p] = static_cast<int16_t>(jb);
@@ -1769,7 +1825,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
       sample_rays<K, TS>(a, c.st, s_wq, s_o, jb, c.cy, c.cx, c.cz, rays);
       unsigned S = 0;
       float emax = 0.f;
-      enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr);
+      enumerate<0, K>(rays, s_rcp, a.beta, 0.f, S, emax, nullptr, a.prune != 0);
       const bool conv = a.early_exit && S == Sp;
       if (active) {
         ps.jb[p] = static_cast<int16_t>(jb);
