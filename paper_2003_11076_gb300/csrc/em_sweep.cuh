@@ -280,8 +280,8 @@ __device__ __forceinline__ PixelState pixel_state(uint8_t* b, int P) {
   ps.conv = ps.fixed0 + P;
   return ps;
 }
-// Counters of the CTA's counting sort (sort_pixels): 128 keys per warp.
-constexpr int kSortKeys = 128;
+// Counters of the CTA's counting sort (sort_pixels): up to 64 keys per warp.
+constexpr int kSortKeys = 64;
 
 // Fixed head of the shared memory: the CTA's mbarrier, then (persistent
 // kernel) the current frame's arguments, then the item index.  Everything
@@ -434,10 +434,14 @@ __device__ __forceinline__ int m_step_init_range(const SweepArgs& a, const Stage
     return lg2_approx(a.gamma + ex2_approx(t * t * k2));
   };
   float pr_next = prior_at(js);
+  float2 w_next[K];
+  load_weights<K>(s_wq, a.KP, js, w_next);
   for (int j = j0; j < j1; ++j) {
     float2 w[K];
-    load_weights<K>(s_wq, a.KP, j, w);
+#pragma unroll
+    for (int k = 0; k < K; ++k) w[k] = w_next[k];
     const int jn = min(j + 1, j1 - 1);
+    load_weights<K>(s_wq, a.KP, jn, w_next);  // the next candidate's weights, in flight during this one
     const unsigned chn = j + 1 < j1 ? s_chg[jn] : 0u;  // taps the next candidate reloads
     const float pr = pr_next;
     pr_next = prior_at(jn);  // the next candidate's prior, off this one's critical path
@@ -589,10 +593,14 @@ __device__ __forceinline__ int m_step_fixed_range(const SweepArgs& a, const Stag
     return lg2_approx(a.gamma + ex2_approx(t * t * k2));
   };
   float pr_next = prior_at(js);
+  float2 w_next[K];
+  load_weights<K>(s_wq, a.KP, js, w_next);
   for (int j = j0; j < j1; ++j) {
     float2 w[K];
-    load_weights<K>(s_wq, a.KP, j, w);
+#pragma unroll
+    for (int k = 0; k < K; ++k) w[k] = w_next[k];
     const int jn = min(j + 1, j1 - 1);
+    load_weights<K>(s_wq, a.KP, jn, w_next);  // the next candidate's weights, in flight during this one
     const unsigned chn = j + 1 < j1 ? s_chg[jn] : 0u;  // taps the next candidate reloads
     const float pr = pr_next;
     pr_next = prior_at(jn);  // the next candidate's prior, off this one's critical path
@@ -783,10 +791,11 @@ __device__ __forceinline__ int sort_pixels(bool pred, int key, int NB, int16_t* 
 }
 
 // Sort keys of the bound intervals: pixels whose interval covers more than a
-// quarter of the candidates come after the others, each class in 32 buckets
-// of the interval's first candidate (NB = 64); in the first M-step the
-// pixels whose labels do not depend on the candidate come first (NB = 128).
-constexpr int kLoBuckets = 32;
+// quarter of the candidates come after the others, each class in 16 buckets
+// of the interval's first candidate (NB = 32); in the first M-step the
+// pixels whose labels do not depend on the candidate come first (NB = 64).
+constexpr int kLoBuckets = 16;
+static_assert(4 * kLoBuckets <= kSortKeys, "first-pass sort keys");
 __device__ __forceinline__ int interval_key(int lo, int hi, int D) {
   const int wide = (hi - lo + 1) * 4 > D ? 1 : 0;
   return wide * kLoBuckets + (lo * kLoBuckets) / D;
@@ -1704,7 +1713,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     ps.hi[tid] = static_cast<int16_t>(hi);
     key = (f0 ? 0 : 2 * kLoBuckets) + interval_key(lo, hi, a.D);
   }
-  const int nact = sort_pixels(my_valid, key, kSortKeys, ps.list, s_sortc, s_wcnt);
+  const int nact = sort_pixels(my_valid, key, 4 * kLoBuckets, ps.list, s_sortc, s_wcnt);
   unsigned long long executed = static_cast<unsigned long long>(nact);
 
   // A later M-step's interval (fixed labels S of the last E-step), bounded by
