@@ -17,9 +17,16 @@
 //      every pixel, so the reload branch is warp-uniform).  Each ray sample is
 //      a linear interpolation (Sec. III-F non-integral disparities) and an
 //      accumulation of the shifted sums of the static rays' descriptors.
+//      Each M-step evaluates only the candidates whose upper bound (log prior
+//      plus the largest segmentation term) reaches the objective of one
+//      candidate already evaluated (exact: the arg-max is unchanged), and
+//      the tile's pixels are sorted by that candidate interval so that a
+//      warp's lanes sweep similar ranges.
 //   4. The E-step enumerates all 2^K label vectors in increasing mask order
 //      as a depth-first subset tree (each subset's sums built from its
-//      parent, no subtraction), keeping the first maximum.
+//      parent, no subtraction), keeping the first maximum; from seven
+//      cameras it skips blocks of vectors whose bound is below the
+//      all-static vector's objective.
 //   5. Posteriors: the same enumeration at the final disparity gives the
 //      per-ray marginals of q(S) ~ exp J(d_T, S).
 //
