@@ -1661,10 +1661,11 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
   const int cam_stride = a.TR * a.SWp * texel_bytes(a.prec);
   const float* s_mu = a.ptris ? reinterpret_cast<const float*>(smem + Ly.mu) : nullptr;
 
-  // ---- 3-5. per-pixel EM.  Before every M-step the pixels still iterating
-  // are sorted into dense warps by the interval of candidates their bound
-  // leaves (exact candidate pruning, see prune_range; exact per-pixel early
-  // exit); a warp sweeps the union of its pixels' intervals.  Each pixel's
+  // ---- 3-5. per-pixel EM.  Before the first M-step the tile's pixels are
+  // sorted into warps by the interval of candidates their bound leaves (exact
+  // candidate pruning, see prune_range); the later passes keep that order for
+  // the pixels still iterating (exact per-pixel early exit).  A warp sweeps
+  // the union of its pixels' intervals.  Each pixel's
   // first M-step uses the fixed-label form when its first-iteration labels do
   // not depend on the candidate, else the per-candidate form, whatever its
   // warp-mates use; those pixels are sorted first, so at most one warp mixes
