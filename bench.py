@@ -655,7 +655,7 @@ def main():
                        + (", support points detected on the device every step" if args.detect_support else ""),
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "staged_maps": args.precision,
-                       "candidate_pruning": bool(args.prune) and mode == 0 and not args.calibrated,
+                       "candidate_pruning": bool(args.prune) and mode == 0,
                        "frames_per_s": args.steps * world / total_s,
                        "executed_ray_samples_per_frame": exec_mean,
                        "executed_ray_samples_per_s": exec_mean * args.steps * world / total_s,
