@@ -614,13 +614,22 @@ def main():
             pairs = exec_mean / K
             ops = scope_ops(exec_mean, static_mean, pairs, pix_iters, K)
             tight = tight_ops(pairs, pix_iters, K)
+            # the work the same EM iterations would take without candidate
+            # pruning (every candidate of every executed sweep, the measured
+            # static share): the rate at which the kernel delivers that result
+            full_samples = pix_iters * K * D
+            full_ops = scope_ops(full_samples, full_samples * static_mean / exec_mean, pix_iters * D, pix_iters, K)
             ops_desc = {"ops_model": "scope-table op model over the evaluated work: 29 per static ray sample, 4 per "
                                      "dynamic, 12 per (pixel, candidate) objective, 20 per E-step label vector",
                         "ops_per_frame": ops, "static_ray_share": static_mean / exec_mean,
                         "pixel_iterations_per_frame": pix_iters,
                         "candidates_per_pixel_iteration": pairs / pix_iters,
                         "frac_tight_model": None, "tight_model": "11 per ray sample, 12 per (pixel, candidate), "
-                                                                 "13 per label vector"}
+                                                                 "13 per label vector",
+                        "full_sweep_ops_per_frame": full_ops, "frac_full_sweep_equivalent": None,
+                        "full_sweep_equivalent": "scope-model ops of the same EM iterations without pruning "
+                                                 "(every candidate evaluated) over the measured time: the rate "
+                                                 "the full-sweep result is delivered at, not work executed"}
         elif mode == 1:  # every swept pixel's first iteration is the EM's first M-step
             first = min(pix_iters, H * W * (float(np.mean(s.seg_prior[int(np.argmin(np.abs(s.baselines)))] >= 0.7)) if args.dynamic_only else 1))
             ops = first * sweep_ops_per_pixel_iter(K, D) + (pix_iters - first) * soft_ops_per_pixel_iter(K, D)
@@ -635,6 +644,8 @@ def main():
         peak = n_sm * 128 * f_mhz * 1e6 / 1e9
         if "frac_tight_model" in ops_desc:
             ops_desc["frac_tight_model"] = tight / sweep_s / 1e9 / peak
+        if "frac_full_sweep_equivalent" in ops_desc:
+            ops_desc["frac_full_sweep_equivalent"] = ops_desc["full_sweep_ops_per_frame"] / sweep_s / 1e9 / peak
         traffic = None
         if os.path.exists(TRAFFIC_FILE):
             kv = {}
