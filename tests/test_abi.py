@@ -43,6 +43,25 @@ def test_default_params(lib):
     assert (p.beta, p.gamma, p.sigma, p.eps) == (200.0, pytest.approx(0.1), 2.0, pytest.approx(1e-4))
     assert p.seg_threshold == pytest.approx(0.7) and p.mstep_seg_term == 1 and p.early_exit == 1
     assert p.median == 0 and p.precision == lf.LF_PREC_F32
+    assert p.em_mode == lf.LF_EM_HARD and p.dynamic_only == 0 and p.prune == 1
+
+
+def test_params_and_stats_layouts_match_the_header():
+    """The binding's ctypes structures list the fields of lf_params and
+    lf_stats in the header's order (a field added on one side only would shift
+    every field after it)."""
+    from paper_2003_11076_gb300 import lf
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lf.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", " ", hdr, flags=re.S)  # comments out
+    for struct, cls in (("lf_params", lf.Params), ("lf_stats", lf.Stats)):
+        body = hdr[hdr.index("typedef struct " + struct + " {") + len("typedef struct " + struct + " {"):]
+        body = body[:body.index("} " + struct + ";")]
+        names = []
+        for decl in body.split(";"):
+            words = decl.split()
+            if words:  # "<type> a, b"
+                names += [n for n in " ".join(words[1:]).replace(" ", "").split(",") if n]
+        assert [f for f, _ in cls._fields_] == names, struct
 
 
 @pytest.mark.parametrize("kw,expect", [
