@@ -1770,11 +1770,10 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     }
   }
   __syncthreads();
-  // t >= 2: only the pixels not yet at their fixed point; when fewer than a
-  // CTA's threads are left, groups of lanes per pixel
-  // (the pixels still iterating keep the first pass's order: pixels of
-  // similar candidate intervals stay together without sorting again)
-  const int nwarps = blockDim.x >> 5, lane = tid & 31;
+  // t >= 2: only the pixels not yet at their fixed point, in the first
+  // pass's order (pixels of similar candidate intervals stay together
+  // without sorting again)
+  const int lane = tid & 31;
   int16_t* list = ps.list;
   int16_t* list_next = ps.list2;
   int n_prev = nact;
@@ -1788,43 +1787,11 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, const CUtensorMap
     list_next = tmp;
     n_prev = n;
     executed += static_cast<unsigned long long>(n);
-    // lanes per pixel: the largest power of two that still fits every
-    // remaining pixel into one round of the CTA's warps
-    int G = 1;
-    while (G < 32 && n * (G << 1) <= nwarps * 32) G <<= 1;
-    if (G > 1) {
-      const int gpw = 32 / G, gl = lane & (G - 1);
-      const int slot = warp * gpw + lane / G;  // this group's pixel among the n
-      if (warp * gpw < n) {
-        const bool act = slot < n;
-        const int p = list[act ? slot : n - 1];  // idle groups repeat the last pixel
-        const PixelCtx<TS> c = load_pixel<TS>(a, s_feat, u0, v0, cam_stride, p, s_mu);
-        const unsigned Sp = ps.S[p];
-        int plo, phi;
-        if (interval_at(c, p, Sp, ps.jb[p], plo, phi) && act && gl == 0) ++my_pairs;
-        const int per = (phi - plo + G) / G, j0 = min(plo + gl * per, phi + 1), j1 = min(j0 + per, phi + 1);
-        float jbest;
-        unsigned jb = static_cast<unsigned>(m_step_fixed_range<K, TS, REF>(
-            a, c.st, s_wq, s_o, s_chg, s_d, s_rcp, c.cy, c.cx, c.cz, c.mu, c.inside, Sp, j0, j1, &jbest));
-        if (act) {
-          my_static += __popc(Sp) * static_cast<unsigned>(j1 - j0);
-          my_pairs += static_cast<unsigned>(j1 - j0);
-        }
-        group_argmax(jbest, jb, G);
-        Rays rays;
-        sample_rays<K, TS>(a, c.st, s_wq, s_o, static_cast<int>(jb), c.cy, c.cx, c.cz, rays);
-        unsigned S = 0;
-        float emax = 0.f;
-        enumerate_group<K>(rays, s_rcp, a.beta, gl, G, S, emax, a.prune != 0);
-        const bool conv = a.early_exit && S == Sp;
-        if (act && gl == 0) {
-          ps.jb[p] = static_cast<int16_t>(jb);
-          ps.S[p] = static_cast<uint16_t>(S);
-          ps.emax[p] = emax;
-          ps.conv[p] = conv;
-        }
-      }
-    } else if (warp * 32 < n) {
+    // one lane per pixel, a warp sweeping its lanes' union (splitting the
+    // last pixels over groups of lanes measured slower here: every lane of a
+    // group reloads the taps, and the warps it keeps busy are the issue
+    // slots the SM's other CTA would use)
+    if (warp * 32 < n) {
       const bool active = tid < n;
       const int p = list[active ? tid : n - 1];
       const PixelCtx<TS> c = load_pixel<TS>(a, s_feat, u0, v0, cam_stride, p, s_mu);
