@@ -1089,11 +1089,12 @@ __device__ __forceinline__ void enumerate(const Rays& r, const float* s_rcp, flo
   }
 }
 
-// Cooperative forms for the last pixels of a tile still iterating: a group
-// of G lanes (G a power of two, up to the warp) takes one pixel, splits its
-// candidates and then its label vectors, and reduces with the same tie
-// rules as the one-thread sweep (lowest candidate, smallest mask), so the
-// result is bit-identical.
+// Cooperative forms for the last pixels of a tile still iterating (used by
+// the calibrated sweep and the soft EM; the rectified sweep keeps one lane
+// per pixel): a group of G lanes (G a power of two, up to the warp) takes
+// one pixel, splits its candidates and then its label vectors, and reduces
+// with the same tie rules as the one-thread sweep (lowest candidate,
+// smallest mask), so the result is bit-identical.
 
 // Larger objective, or on a tie the lower index, over the G lanes of each
 // aligned group (every lane of the warp takes part).
