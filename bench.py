@@ -195,6 +195,20 @@ def cpu_oracle_sample(scene, params, seconds: float = 12.0):
     return samples / dt, cores, desc, rows, dt
 
 
+def cpu_oracle_single_thread(scene, params, rows: int = 24):
+    """The same oracle on one host thread over `rows` rows of the frame's
+    middle (a few seconds; the frame's descriptor maps, computed once per
+    call, included).  Returns (ray-samples/s, description)."""
+    from oracle import oracle as O
+    mid = scene.H // 2
+    t0 = time.perf_counter()
+    O.run_scene(scene, params=params, rows=(mid, mid + rows), threads=1)
+    dt = time.perf_counter() - t0
+    samples = rows * scene.W * scene.K * scene.D * (1 if params.em_mode == 2 else scene.iters)
+    desc = f"rows {mid}..{mid + rows - 1} of the 960x600 frame on one host thread ({samples} nominal ray samples)"
+    return samples / dt, desc
+
+
 def oracle_params(lf_params):
     from oracle import oracle as O
     p = lf_params
@@ -707,6 +721,12 @@ def main():
             try:
                 v, cores, desc, _, _ = cpu_oracle_sample(s, oracle_params(params))
                 line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+                try:
+                    v1, desc1 = cpu_oracle_single_thread(s, oracle_params(params))
+                    line["cpu_baseline"]["single_thread"] = {"value": v1, "unit": UNIT, "sample": desc1}
+                except Exception as e:
+                    line["cpu_baseline"]["single_thread"] = {"value": None, "unit": UNIT,
+                                                             "sample": f"unavailable: {e}"}
             except Exception as e:  # the oracle is a reported baseline, not a requirement of the bench
                 line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
                                         "sample": f"unavailable: {e}"}

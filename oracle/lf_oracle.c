@@ -519,8 +519,10 @@ static int run_frame(int K, const float *baselines, const float *cameras, int H,
     if (row_begin < 0) row_begin = 0;
     if (row_end > H) row_end = H;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 1)
+    /* the thread count applies to this region only (rows are independent,
+       so it never changes a result) */
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
 #endif
     for (int v = row_begin; v < row_end; ++v)
         for (int u = 0; u < W; ++u)
