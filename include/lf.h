@@ -458,7 +458,8 @@ void lf_batch_destroy(lf_batch *b);
  *   Every call looks up the array's device address for the current device
  *   (nothing is cached between calls).
  *   The call is synchronous: it waits for `stream` (a cudaStream_t, NULL =
- *   legacy default stream) before returning.
+ *   legacy default stream) before returning, so it cannot be recorded into a
+ *   CUDA graph (a call on a stream being captured fails with LF_ECUDA).
  *   All calls share the one array and leave their contents in it (each call
  *   clears the counter and status it needs); calls whose GPU work overlaps
  *   would race on it, so the call serialises its callers.
