@@ -40,6 +40,25 @@ WORKLOAD = "street_rgb: 5 cameras (0, +-0.1, +-0.2), 960x600 RGB uint8, D=64 (0.
            "one frame per launch"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "em_sweep_street_rgb_traffic.txt")
 SWEEP_SRC = os.path.join(ROOT, "paper_2003_11076_gb300", "csrc", "em_sweep.cuh")
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+HBM_FALLBACK_GBS = 6800.0
+
+
+def hbm_roofline(alg_bytes: float, seconds: float, peaks_path: str = PEAKS_FILE) -> dict:
+    """The kernel's algorithmic HBM bytes (inputs read once, outputs written
+    once) over its measured time, against the measured copy bandwidth of
+    this GPU model (`hbm_gbs` of the peaks file), else the 6.8 TB/s fallback."""
+    peak, basis = HBM_FALLBACK_GBS, "of fallback: 6.8 TB/s (no measured copy bandwidth found)"
+    try:
+        with open(peaks_path) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        if v > 0:
+            peak, basis = v, "of measured: STREAM-style copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError, TypeError):
+        pass
+    achieved = alg_bytes / seconds / 1e9
+    return {"bound": "hbm", "algorithmic_bytes": alg_bytes, "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "peak_basis": basis}
 
 
 def sweep_ops_per_pixel_iter(K: int, D: int) -> int:
@@ -653,6 +672,7 @@ def main():
             ops = pix_iters * joint_ops_per_pixel(K, D)
             ops_desc = {"ops_per_pixel": joint_ops_per_pixel(K, D)}
         sweep_s = st["ms_sweep"] / 1e3
+        fused_frame = mode == 0 and not args.calibrated and not args.dynamic_only
         achieved = ops / sweep_s / 1e9
         f_mhz = clk.get("sm_mhz") or 2070.0
         peak = n_sm * 128 * f_mhz * 1e6 / 1e9
@@ -701,7 +721,13 @@ def main():
                          "traffic_source": "recorded ncu capture of this kernel source (profiles/), not measured "
                                            "in this run" if traffic is not None else None,
                          "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {f_mhz:.0f} MHz (median sampled SM clock "
-                                       f"during the timed region)", **ops_desc},
+                                       f"during the timed region)", **ops_desc,
+                         # the same kernel against HBM (not the binding roof): the frame's inputs read once
+                         # and its outputs written once, where the one kernel is the whole frame
+                         "hbm": hbm_roofline(float(img_d.numel() * img_d.element_size()
+                                                   + seg_d.numel() * seg_d.element_size()
+                                                   + sum(t.numel() * t.element_size() for t in out.values())),
+                                             sweep_s) if fused_frame else None},
             "e2e": {"value": whole_job_value(nominal * e2e_pipe_steps, world, e2e_s), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": 1e3 * e2e_s / e2e_pipe_steps,
