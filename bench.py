@@ -358,6 +358,9 @@ def run_batch_workload(args, world, rank, local):
                            "per_frame_launch_frames_per_s": n * steps / t_plain,
                            "batched_over_per_frame": t_plain / t_batch,
                            "graph_captures": st["graph_captures"], "tuned_signatures": st["tuned_signatures"],
+                           "graph": "one CUDA graph launch per step: a batched prior raster, one persistent "
+                                    "sweep launch per camera count and thread class as parallel branches (the "
+                                    "camera count is a template parameter of the sweep), a batched refocus",
                            "first_run_s_incl_autotune_and_capture": t_tune,
                            "kernel_ms": {"prior_raster": st["ms_prior"], "em_sweeps": st["ms_sweep"],
                                          "refocus": st["ms_refocus"]},
