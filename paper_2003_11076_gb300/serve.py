@@ -477,6 +477,8 @@ class Server:
         out = {"requests": len(self.completed), "rejected": len(self.rejected),
                "frames_per_s": len(self.completed) / span if span > 0 else None,
                "batches": self.batches_run, "peak_admitted": self.peak_admitted,
+               # HBM the admitted requests held at most (device block bytes, since the server started)
+               "peak_device_bytes": self.dev_arena.peak,
                "max_loop_gap_ms": 1e3 * max_gap}
         out.update(percentiles(lat))
         # where the time goes: queueing for admission, admitted to launch,

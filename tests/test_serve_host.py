@@ -69,3 +69,19 @@ def test_request_output_layout_and_bytes():
     assert names == ["d_idx", "d", "post", "labels", "refocus"]
     assert dict((n, sh) for n, sh, _ in r.output_layout())["refocus"] == (40, 50, 3)
     assert r.output_bytes() % 256 == 0 and r.device_bytes() > r.output_bytes()
+
+
+def test_arena_peak_is_the_largest_bytes_in_use():
+    """The server reports the device block's peak use: the largest sum of live
+    (aligned) ranges, which frees do not lower."""
+    a = serve.Arena(8192, align=256)
+    x = a.alloc(1000)            # 1024
+    y = a.alloc(2000)            # 2048
+    assert a.peak == 3072
+    a.free(x)
+    z = a.alloc(100)             # 256, in x's place
+    assert z == 0 and a.bytes_used == 2304 and a.peak == 3072
+    a.alloc(4096)
+    assert a.peak == 2304 + 4096
+    a.free(y)
+    assert a.peak == 2304 + 4096
