@@ -830,6 +830,7 @@ lf_status lf_set_inputs(lf_ctx* c, const void* images, int C, int dtype, const f
                         const float* sparse_points, int M, int on_device) {
   g_err.clear();
   if (!c) return fail(LF_EINVAL, "ctx is NULL");
+  NvtxRange range("lf_set_inputs");
   const auto t0 = std::chrono::steady_clock::now();
   const lf_status st = set_inputs_impl(c, images, C, dtype, seg_prior, sparse_points, M, on_device);
   c->set_inputs_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -869,13 +870,17 @@ lf_status set_inputs_impl(lf_ctx* c, const void* images, int C, int dtype, const
     c->P = reinterpret_cast<const float*>(pp);
   }
   if (detect) {  // Sec. III-C: support points from the inputs themselves (before any 16-bit conversion)
+    NvtxRange range("support points");
     if ((s = detect_support(c)) != LF_OK) return s;
     sparse_points = c->support_pts.data();
     M = static_cast<int>(c->support_pts.size() / 3);
   }
   s = choose_tiles(c);
   if (s != LF_OK) return s;
-  build_prior(c, sparse_points, M);
+  {
+    NvtxRange range("prior: Delaunay and bins");
+    build_prior(c, sparse_points, M);
+  }
   if ((s = grow(&c->d_tris, &c->tris_cap, std::max<size_t>(c->h_tris.size(), 1), "prior")) != LF_OK) return s;
   if ((s = grow(&c->d_bins, &c->bins_cap, c->h_bins.size(), "prior")) != LF_OK) return s;
   if (!c->h_tris.empty())
@@ -926,6 +931,7 @@ lf_status lf_run_em(lf_ctx* c, int iters, int32_t* disparity_idx, float* dispari
                     uint16_t* labels, float* refocused, int outputs_on_device) {
   g_err.clear();
   if (!c) return fail(LF_EINVAL, "ctx is NULL");
+  NvtxRange range("lf_run_em");
   if (!c->have_inputs) return fail(LF_ESTATE, "lf_run_em called before lf_set_inputs");
   if (iters < 1 || iters > 255) return fail(LF_EINVAL, "iters must be in [1, 255]");
   if (!disparity_idx) return fail(LF_EINVAL, "disparity_idx must not be NULL");

@@ -494,8 +494,10 @@ lf_status lf_batch_run(lf_batch* b) {
   if (!b) return fail(LF_EINVAL, "batch is NULL");
   const int nf = static_cast<int>(b->frames.size());
   if (nf == 0) return fail(LF_ESTATE, "lf_batch_run on an empty batch");
+  NvtxRange range("lf_batch_run");
   // 1. host preparation, frames in parallel
   {
+    NvtxRange prep("batch: frame preparation");
     const int nt = std::max(1, std::min<int>(nf, static_cast<int>(std::thread::hardware_concurrency())));
     std::vector<std::thread> pool;
     for (int t = 0; t < nt; ++t)

@@ -7,10 +7,21 @@
 #include <string>
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "lf.h"
 
 namespace lf {
+
+// A named NVTX range over a host scope (the library's entry points and their
+// host phases), so that a profiler's timeline shows where the host time of a
+// call goes; without a profiler attached the push and pop do nothing.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int kMaxCams = 12;       // 2^K label vectors per E-step
 constexpr int kMaxD = 1024;        // candidate disparities per sweep

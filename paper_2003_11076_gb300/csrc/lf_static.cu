@@ -95,6 +95,7 @@ extern "C" lf_status lf_run_em_static(int n_cams, const float* baselines, int H,
                                       int32_t* disparity_idx, float* disparity, float* posteriors,
                                       uint16_t* labels, void* stream) {
   using namespace lf;
+  NvtxRange range("lf_run_em_static");
   set_error_message("");
   if (n_cams < 1 || n_cams > kMaxCams) return fail(LF_EINVAL, "n_cams must be in [1, 12]");
   if (!baselines || !images || !seg_prior || !mu || !disparity_idx)
