@@ -172,8 +172,11 @@ void lf_default_params(lf_params *p);
  * for the defaults; it is copied.  Allocates the context's device buffers on
  * the current CUDA device.
  * Errors: LF_EINVAL if n_cams < 1 or > 12, no baseline is 0, H or W < 3,
- * D < 1 or > 1024, d_max < d_min, a parameter is non-finite, or the
- * disparity halo does not fit the kernel's staging limit; LF_ENOMEM; LF_ECUDA.
+ * D < 1 or > 1024, d_max < d_min, a parameter is non-finite or out of its
+ * range (sigma > 0 with 1 / (2 sigma^2) finite in float32, gamma >= 0,
+ * eps > 0, beta >= 0, 0 < seg_threshold < 1, a known precision and em_mode,
+ * float32 maps for the soft-EM and joint-MAP modes), or the disparity halo
+ * does not fit the kernel's staging limit; LF_ENOMEM; LF_ECUDA.
  * On error *out is NULL.
  */
 lf_status lf_create(lf_ctx **out, int n_cams, const float *baselines, int H, int W,

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -203,6 +204,9 @@ bool lf::check_params(const lf_params& p, std::string* why) {
     msg = "invalid lf_params: non-finite constant";
   else if (p.sigma <= 0.f)
     msg = "invalid lf_params: sigma must be > 0";
+  else if (1.0 / (2.0 * static_cast<double>(p.sigma) * p.sigma) >
+           static_cast<double>(std::numeric_limits<float>::max()))
+    msg = "invalid lf_params: sigma too small (the prior's 1 / (2 sigma^2) must be finite in float32)";
   else if (p.gamma < 0.f)
     msg = "invalid lf_params: gamma must be >= 0";
   else if (p.eps <= 0.f)

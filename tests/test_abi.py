@@ -258,7 +258,8 @@ def test_delaunay_validity_check_catches_a_wrong_flip():
 
 
 @pytest.mark.parametrize("field,value,expect", [
-    ("sigma", 0.0, "sigma"), ("seg_threshold", 1.0, "seg_threshold"), ("seg_threshold", 0.0, "seg_threshold"),
+    ("sigma", 0.0, "sigma"), ("sigma", 1e-20, "sigma too small"),
+    ("seg_threshold", 1.0, "seg_threshold"), ("seg_threshold", 0.0, "seg_threshold"),
     ("eps", 0.0, "eps"), ("gamma", -1.0, "gamma"), ("beta", float("nan"), "non-finite"),
     ("precision", 7, "precision"), ("em_mode", 9, "em_mode"),
 ])
