@@ -197,3 +197,69 @@ def test_label_block_bound_never_skips_the_e_step_argmax(K, beta, seed):
                         skipped += 1
                         assert not (block[0] <= best < block[-1] + 1)
     assert skipped > 0
+
+
+def _interval_f32(mu, Js, seg_ub, gamma, inv2s2, d0, inv_step, D, js):
+    """The candidate interval in float32 with the slacks the sweep applies:
+    J* lowered by 2^-18 (1 + |J*|) and 1e-3 (the hardware exp2 / log2 of the
+    prior), the radius widened by 0.1 % + 1e-3, one more candidate each side,
+    the reference candidate always kept; everything when exp(theta) - gamma
+    is not in (0, 1) or J* is not finite."""
+    f = np.float32
+    if not abs(Js) <= f(3.0e38):
+        return 0, D - 1
+    th = f(f(f(Js - f(f(1) + f(abs(Js))) * f(2.0 ** -18)) - seg_ub) - f(1e-3))
+    A = f(np.exp(th, dtype=np.float32) - gamma)
+    if not (A > 0 and A < 1):
+        return 0, D - 1
+    r = f(f(np.sqrt(f(-np.log(A, dtype=np.float32) / inv2s2), dtype=np.float32)) * f(1.001) + f(1e-3))
+    flo = max(f(f(mu - r - d0) * inv_step), f(-2))
+    fhi = min(f(f(mu + r - d0) * inv_step), f(D) + f(1))
+    return min(max(int(np.floor(flo)) - 1, 0), js), max(min(int(np.ceil(fhi)) + 1, D - 1), js)
+
+
+def test_float32_interval_keeps_every_candidate_that_can_reach_the_reference():
+    """Random candidate grids (|d| up to 1000, the finest spacing pruning is
+    enabled for, 2^-12 max(1, |d|), up to 1024 candidates), sigma from 1e-3
+    to 100, gamma 0 or 1e-6 to 10, prior centres far outside the grid: no
+    candidate whose float32 bound (log prior, raised by 1e-5 for the
+    hardware exp2 / log2, plus seg_max) reaches J* falls outside the
+    interval.  The prior is flushed to -inf where exp(-t^2 / 2 sigma^2)
+    leaves the normal float32 range and gamma = 0, as the sweep's flushing
+    exp2 does: there e^theta is a denormal whose log is not theta, and the
+    candidates it would drop have J = -inf in the sweep."""
+    f = np.float32
+    tiny = np.finfo(np.float32).tiny
+    rng = np.random.default_rng(20)
+    cases = 0
+    pruned = 0.0
+    while cases < 20000:
+        D = int(rng.integers(2, 1025))
+        dmag = 10 ** rng.uniform(-1, 3)
+        d0 = rng.uniform(-dmag, dmag)
+        step = 10 ** rng.uniform(np.log10(max(1.0, abs(d0)) / 4096.0), np.log10(max(1.0, abs(d0)) / 4096.0) + 4)
+        d1 = d0 + step * (D - 1)
+        if step < max(1.0, abs(d0), abs(d1)) / 4096.0:
+            continue
+        dval = (d0 + np.arange(D) * ((d1 - d0) / (D - 1))).astype(np.float32)
+        sigma = 10 ** rng.uniform(-3, 2)
+        inv2s2 = f(1.0 / (2.0 * sigma * sigma))
+        gamma = f(0.0) if rng.random() < 0.2 else f(10 ** rng.uniform(-6, 1))
+        mu = f(rng.uniform(float(dval[0]) - 50 * sigma, float(dval[-1]) + 50 * sigma))
+        seg_ub = f(rng.uniform(-20, 0))
+        t = (dval - mu).astype(np.float32)
+        e = np.exp(-(t * t) * inv2s2, dtype=np.float32)
+        e = np.where(e < tiny, f(0), e)
+        with np.errstate(divide="ignore"):
+            prior = np.log(gamma + e, dtype=np.float32).astype(np.float64)
+        js = int(np.argmin(np.abs(t))) if rng.random() < 0.7 else int(rng.integers(0, D))
+        if not np.isfinite(prior[js]):
+            continue
+        Js = f(prior[js] + float(seg_ub) - rng.exponential(0.5))
+        lo, hi = _interval_f32(mu, Js, seg_ub, gamma, inv2s2, f(dval[0]), f(1.0 / ((d1 - d0) / (D - 1))), D, js)
+        outside = np.ones(D, bool)
+        outside[lo:hi + 1] = False
+        assert not np.any(outside & (prior + 1e-5 + float(seg_ub) >= float(Js))), (D, d0, step, sigma, gamma, mu)
+        pruned += outside.mean()
+        cases += 1
+    assert pruned / cases > 0.1
