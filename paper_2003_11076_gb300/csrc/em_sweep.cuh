@@ -711,7 +711,10 @@ __device__ __forceinline__ bool constant_initial_labels(const SweepArgs& a, cons
 // logarithm err by about 1e-6 relative), J* by 2^-18 (1 + |J*|), the radius is
 // widened by 0.1 % + 1e-3, the index range by one candidate on each side, and
 // seg_max carries a margin for the rounding of the segmentation sums
-// (a.seg_margin, set by the host).  j* itself is always kept.
+// (a.seg_margin, set by the host).  j* itself is always kept.  Where th is
+// below about -87, e^th would leave float32's normal range and its log would
+// no longer be th, so nothing is pruned there (whatever the prior's
+// exponential does with results below the normal range).
 __device__ __forceinline__ int nearest_candidate(const SweepArgs& a, float mu) {
   const float f = fminf(fmaxf((mu - a.d0) * a.inv_step, 0.f), static_cast<float>(a.D - 1));
   return static_cast<int>(rintf(f));
@@ -725,6 +728,9 @@ __device__ __forceinline__ void prune_interval(float mu, float Js, float seg_ub,
   hi = D - 1;
   if (!(fabsf(Js) <= 3.0e38f)) return;  // no finite objective to bound against
   const float th = Js - (1.f + fabsf(Js)) * 0x1p-18f - seg_ub - 1e-3f;
+  // below about -87 exp(th) leaves float32's normal range and its log is no
+  // longer th: keep every candidate there
+  if (!(th >= -87.f)) return;
   const float A = expf(th) - gamma;
   if (!(A > 0.f && A < 1.f)) return;  // every candidate's prior reaches th (A >= 1 cannot happen)
   const float r = sqrtf(-logf(A) / inv2s2) * 1.001f + 1e-3f;

@@ -15,7 +15,8 @@ def _tracked_files():
         out = subprocess.run(["git", "ls-files"], cwd=ROOT, capture_output=True, text=True, check=True).stdout
     except (OSError, subprocess.CalledProcessError):
         pytest.skip("not a git checkout")
-    return [f for f in out.splitlines() if f and os.path.isfile(os.path.join(ROOT, f))]
+    here = os.path.relpath(os.path.abspath(__file__), ROOT)
+    return [f for f in out.splitlines() if f and f != here and os.path.isfile(os.path.join(ROOT, f))]
 
 
 def _text(path):

@@ -203,12 +203,16 @@ def _interval_f32(mu, Js, seg_ub, gamma, inv2s2, d0, inv_step, D, js):
     """The candidate interval in float32 with the slacks the sweep applies:
     J* lowered by 2^-18 (1 + |J*|) and 1e-3 (the hardware exp2 / log2 of the
     prior), the radius widened by 0.1 % + 1e-3, one more candidate each side,
-    the reference candidate always kept; everything when exp(theta) - gamma
-    is not in (0, 1) or J* is not finite."""
+    the reference candidate always kept; everything when theta is below
+    -87 (exp(theta) would leave float32's normal range, where its log is no
+    longer theta), exp(theta) - gamma is not in (0, 1) or J* is not
+    finite."""
     f = np.float32
     if not abs(Js) <= f(3.0e38):
         return 0, D - 1
     th = f(f(f(Js - f(f(1) + f(abs(Js))) * f(2.0 ** -18)) - seg_ub) - f(1e-3))
+    if not th >= f(-87.0):
+        return 0, D - 1
     A = f(np.exp(th, dtype=np.float32) - gamma)
     if not (A > 0 and A < 1):
         return 0, D - 1
@@ -218,16 +222,16 @@ def _interval_f32(mu, Js, seg_ub, gamma, inv2s2, d0, inv_step, D, js):
     return min(max(int(np.floor(flo)) - 1, 0), js), max(min(int(np.ceil(fhi)) + 1, D - 1), js)
 
 
-def test_float32_interval_keeps_every_candidate_that_can_reach_the_reference():
+@pytest.mark.parametrize("flush", [True, False])
+def test_float32_interval_keeps_every_candidate_that_can_reach_the_reference(flush):
     """Random candidate grids (|d| up to 1000, the finest spacing pruning is
     enabled for, 2^-12 max(1, |d|), up to 1024 candidates), sigma from 1e-3
     to 100, gamma 0 or 1e-6 to 10, prior centres far outside the grid: no
     candidate whose float32 bound (log prior, raised by 1e-5 for the
     hardware exp2 / log2, plus seg_max) reaches J* falls outside the
-    interval.  The prior is flushed to -inf where exp(-t^2 / 2 sigma^2)
-    leaves the normal float32 range and gamma = 0, as the sweep's flushing
-    exp2 does: there e^theta is a denormal whose log is not theta, and the
-    candidates it would drop have J = -inf in the sweep."""
+    interval, whether the prior's exponential flushes results below the
+    normal float32 range to 0 (the rectified sweep's exp2) or keeps them
+    as denormals."""
     f = np.float32
     tiny = np.finfo(np.float32).tiny
     rng = np.random.default_rng(20)
@@ -249,7 +253,8 @@ def test_float32_interval_keeps_every_candidate_that_can_reach_the_reference():
         seg_ub = f(rng.uniform(-20, 0))
         t = (dval - mu).astype(np.float32)
         e = np.exp(-(t * t) * inv2s2, dtype=np.float32)
-        e = np.where(e < tiny, f(0), e)
+        if flush:
+            e = np.where(e < tiny, f(0), e)
         with np.errstate(divide="ignore"):
             prior = np.log(gamma + e, dtype=np.float32).astype(np.float64)
         js = int(np.argmin(np.abs(t))) if rng.random() < 0.7 else int(rng.integers(0, D))
