@@ -78,3 +78,45 @@ def test_excusal_follows_its_margins_and_is_rare():
     assert 0 < expect.mean() < 0.02
     # a looser rule excuses a superset, a tighter one a subset
     assert np.all(O.excused(out, tau_rel=1e-3) >= expect) and np.all(O.excused(out, tau_rel=1e-6) <= expect)
+
+
+@pytest.mark.parametrize("seed,K,H,W,D", [(31, 3, 4, 6, 5), (32, 4, 3, 5, 6)])
+def test_calibrated_margins_match_the_brute_force_table(seed, K, H, W, D):
+    """The same for a calibrated (non-rectified) array: the table's rays are
+    sampled by scipy.ndimage.map_coordinates at the cameras' positions."""
+    from scipy import ndimage
+    rng = np.random.default_rng(seed)
+    imgs = rng.random((K, H, W)).astype(np.float32)
+    seg = rng.uniform(0.02, 0.98, size=(K, H, W)).astype(np.float32)
+    b = np.concatenate([[0.0], rng.uniform(-0.6, 0.6, size=K - 1)]).astype(np.float32)
+    cams = scenes.calibrated_cameras(rng, b, H, W, rot_deg=4.0, shift_y=0.3, shift_z=0.1, focal_jitter=0.05)
+    pts = np.stack([rng.uniform(-1, W, 6), rng.uniform(-1, H, 6), rng.uniform(0, 4, 6)], 1).astype(np.float32)
+    p = O.Params(beta=30.0)
+    iters = 3
+    out = O.run(imgs, seg, b, pts, 0.0, 4.0, D, iters, params=p, cameras=cams)
+    feat = BF.descriptors(imgs)
+    P = seg.astype(np.float64)
+    ls = np.log(np.maximum(1.0 - P, p.eps))
+    ld = np.log(np.maximum(P, p.eps))
+    dvals = [j * 4.0 / (D - 1) for j in range(D)]
+    log_thr = np.log(p.seg_threshold / (1.0 - p.seg_threshold))
+    for v in range(H):
+        for u in range(W):
+            J, S_init = BF.em_pixel_table(feat, ls, ld, imgs, b, u, v, dvals, out["mu"][v, u],
+                                          out["inside"][v, u], p, cameras=cams)
+            tol = 1e-9 * (1.0 + np.abs(J).max())
+            S = None
+            for t in range(iters):
+                col = J[np.arange(D), S_init] if t == 0 else J[:, S]
+                j = int(np.argmax(col))
+                assert out["m_margin"][t, v, u] == pytest.approx(_top_two_gap(col), abs=tol)
+                S = int(np.argmax(J[j]))
+                assert out["e_margin"][t, v, u] == pytest.approx(_top_two_gap(J[j]), abs=tol)
+            z = []
+            for d in dvals:
+                for k in range(K):
+                    X = np.asarray(cams[k], np.float64) @ np.array([u, v, 1.0, d])
+                    xy = [[X[1] / X[2]], [X[0] / X[2]]]
+                    z.append(abs(ndimage.map_coordinates(ld[k], xy, order=1, mode="nearest")[0]
+                                 - ndimage.map_coordinates(ls[k], xy, order=1, mode="nearest")[0] - log_thr))
+            assert out["init_margin"][v, u] == pytest.approx(min(z), abs=1e-12)
