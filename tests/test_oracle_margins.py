@@ -120,3 +120,35 @@ def test_calibrated_margins_match_the_brute_force_table(seed, K, H, W, D):
                     z.append(abs(ndimage.map_coordinates(ld[k], xy, order=1, mode="nearest")[0]
                                  - ndimage.map_coordinates(ls[k], xy, order=1, mode="nearest")[0] - log_thr))
             assert out["init_margin"][v, u] == pytest.approx(min(z), abs=1e-12)
+
+
+@pytest.mark.parametrize("seed,K,H,W,D", [(41, 3, 4, 6, 5), (42, 4, 3, 5, 6)])
+def test_soft_em_margins_match_the_brute_force_table(seed, K, H, W, D):
+    """Soft EM (reading R23): after the first iteration the M-step column is
+    Q(d) = sum_S q(S) J(d, S) with q the softmax of the previous E-step's
+    row; the recorded objective is the row's log-sum-exp (the log marginal)."""
+    imgs, seg, b, pts = _tiny_frame(K, H, W, seed)
+    p = O.Params(beta=30.0, em_mode=1)
+    iters = 3
+    out = O.run(imgs, seg, b, pts, 0.0, 4.0, D, iters, params=p)
+    feat = BF.descriptors(imgs)
+    P = seg.astype(np.float64)
+    ls = np.log(np.maximum(1.0 - P, p.eps))
+    ld = np.log(np.maximum(P, p.eps))
+    dvals = [j * 4.0 / (D - 1) for j in range(D)]
+    for v in range(H):
+        for u in range(W):
+            J, S_init = BF.em_pixel_table(feat, ls, ld, imgs, b, u, v, dvals, out["mu"][v, u],
+                                          out["inside"][v, u], p)
+            tol = 1e-9 * (1.0 + np.abs(J).max())
+            q = None
+            for t in range(iters):
+                col = J[np.arange(D), S_init] if t == 0 else J @ q
+                j = int(np.argmax(col))
+                assert out["m_margin"][t, v, u] == pytest.approx(_top_two_gap(col), abs=tol)
+                row = J[j]
+                assert out["e_margin"][t, v, u] == pytest.approx(_top_two_gap(row), abs=tol)
+                m = row.max()
+                q = np.exp(row - m)
+                assert out["J_t"][t, v, u] == pytest.approx(m + np.log(q.sum()), abs=tol)
+                q /= q.sum()
