@@ -152,3 +152,29 @@ def test_soft_em_margins_match_the_brute_force_table(seed, K, H, W, D):
                 q = np.exp(row - m)
                 assert out["J_t"][t, v, u] == pytest.approx(m + np.log(q.sum()), abs=tol)
                 q /= q.sum()
+
+
+@pytest.mark.parametrize("seed,K,H,W,D", [(51, 3, 4, 6, 5), (52, 2, 3, 7, 6)])
+def test_joint_map_margins_match_the_brute_force_table(seed, K, H, W, D):
+    """Joint MAP (reading R24): the M margin is the gap between the two best
+    candidates' row maxima, the E margin the gap inside the winning row, the
+    recorded objective the joint maximum, in every diagnostic slot."""
+    imgs, seg, b, pts = _tiny_frame(K, H, W, seed)
+    p = O.Params(beta=30.0, em_mode=2)
+    iters = 2
+    out = O.run(imgs, seg, b, pts, 0.0, 4.0, D, iters, params=p)
+    feat = BF.descriptors(imgs)
+    P = seg.astype(np.float64)
+    ls = np.log(np.maximum(1.0 - P, p.eps))
+    ld = np.log(np.maximum(P, p.eps))
+    dvals = [j * 4.0 / (D - 1) for j in range(D)]
+    for v in range(H):
+        for u in range(W):
+            J, _ = BF.em_pixel_table(feat, ls, ld, imgs, b, u, v, dvals, out["mu"][v, u], out["inside"][v, u], p)
+            tol = 1e-9 * (1.0 + np.abs(J).max())
+            rowmax = J.max(axis=1)
+            j = int(np.argmax(rowmax))
+            for t in range(iters):
+                assert out["m_margin"][t, v, u] == pytest.approx(_top_two_gap(rowmax), abs=tol)
+                assert out["e_margin"][t, v, u] == pytest.approx(_top_two_gap(J[j]), abs=tol)
+                assert out["J_t"][t, v, u] == pytest.approx(J.max(), abs=tol)
