@@ -300,3 +300,17 @@ def test_host_alloc_rejects_bad_arguments(lib):
     assert lib.lf_host_alloc(ctypes.byref(p), 0) == lf.LF_EINVAL and not p.value
     assert lib.lf_host_alloc(None, 64) == lf.LF_EINVAL
     lib.lf_host_free(None)  # a no-op
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No fallback: with the library absent every entry of the binding raises
+    instead of computing anything on the host."""
+    from paper_2003_11076_gb300 import lf
+    monkeypatch.setattr(lf, "_lib", None)
+    missing = str(tmp_path / "liblf.so")
+    with pytest.raises(ImportError, match="missing"):
+        lf.load(missing)
+    monkeypatch.setattr(lf, "LIB_PATH", missing)
+    monkeypatch.setattr(lf.load, "__defaults__", (missing,))
+    with pytest.raises(ImportError, match="missing"):
+        lf.Context(np.array([-0.1, 0.0, 0.1], np.float32), 16, 16, 0.0, 7.0, 8)
