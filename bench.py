@@ -699,15 +699,19 @@ def main():
         if "frac_full_sweep_equivalent" in ops_desc:
             ops_desc["frac_full_sweep_equivalent"] = ops_desc["full_sweep_ops_per_frame"] / sweep_s / 1e9 / peak
         traffic = None
+        traffic_note = "no recorded ncu capture of this kernel"
         if os.path.exists(TRAFFIC_FILE):
             kv = {}
             for line in open(TRAFFIC_FILE):
                 if "=" in line and not line.lstrip().startswith("#"):
                     k, v = line.split("=", 1)
                     kv[k.strip()] = v.strip()
-            if mode == 0 and not args.dynamic_only and not args.calibrated and \
-                    kv.get("kernel_sha") == sweep_source_hash():
+            if not (mode == 0 and not args.dynamic_only and not args.calibrated):
+                traffic_note = "null: the recorded ncu capture covers the default hard-EM frame only"
+            elif kv.get("kernel_sha") == sweep_source_hash():
                 traffic = float(kv["dram_bytes_per_launch"])
+            else:
+                traffic_note = "null: the recorded ncu capture (profiles/) predates the current kernel source"
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
@@ -737,7 +741,7 @@ def main():
                          ("em_sweep" if mode == 0 else "em_variant"), "achieved": achieved,
                          "peak": peak, "unit": "Gop/s", "frac": achieved / peak, "traffic": traffic,
                          "traffic_source": "recorded ncu capture of this kernel source (profiles/), not measured "
-                                           "in this run" if traffic is not None else None,
+                                           "in this run" if traffic is not None else traffic_note,
                          "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {f_mhz:.0f} MHz (median sampled SM clock "
                                        f"during the timed region)", **ops_desc,
                          # the same kernel against HBM (not the binding roof): the frame's inputs read once
