@@ -31,6 +31,11 @@
  *     passed the work.  Host pointers are copied within the call.
  *   - All compute runs in the library's sm_103a CUDA kernels; there is no CPU
  *     fallback.  Without a usable GPU every compute call returns LF_ECUDA.
+ *   - Entry points that compute part of the method cite the paper passage
+ *     they follow.  The others have no counterpart in the paper, which
+ *     processes one frame at a time on one GPU: streams, synchronisation,
+ *     page-locked buffers, tile and timing controls, statistics, errors, the
+ *     uneven-batch API, the allocation-free entry and the failure hooks.
  */
 #ifndef LF_H
 #define LF_H
@@ -392,8 +397,8 @@ void lf_destroy(lf_ctx *ctx);
 
 /*
  * Uneven batches (workload: many frames of different sizes, camera counts,
- * candidate and iteration counts in one go).  Same method and results per
- * frame as lf_run_em; the batch runs as one CUDA graph: a batched prior
+ * candidate and iteration counts in one go).  Same method (the per-pixel EM
+ * of Sec. III-B to III-E) and results per frame as lf_run_em; the batch runs as one CUDA graph: a batched prior
  * raster, one persistent sweep launch per camera count present (its CTAs take
  * (frame, tile) items from a device-side queue, so small and large frames
  * share the GPU without tail effects) and a batched refocus / median.  The
